@@ -1,0 +1,215 @@
+"""FP64 CPU oracle of the Dufort-Frankel hygrothermal wall update.
+
+TEST INFRASTRUCTURE ONLY: imported by the test suite, by the smoke check and
+by the CPU-baseline leg of the benchmark. The CUDA library never imports it.
+The arithmetic lives in ``hygro_oracle.c`` (plain C, FP64, scalar loops);
+this module only compiles it with gcc and marshals arrays through ctypes.
+
+Parity pins (tests/test_oracle_*.py): the linear DF closed form [eq:dufort],
+the nonlinear DF [eq:DF_NL] and the coupled form [eq:DF_eq2b] one step at a
+time, the ghost-node surface update [eq:ghost_node_v0]/[eq:ghost_node_u0],
+the exact series-resistance and Kirchhoff steady states, the Fourier series
+of linear diffusion with Robin ends, the discrete balance identity, mirror
+symmetry and uniform invariance, and a closed-form room steady state.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import shutil
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hygro_oracle.c")
+_HDR = os.path.join(_HERE, "hygro_oracle.h")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+
+NLAYER_PAR = 9
+NBC_PAR = 12
+NROOM_PAR = 16
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP if available); return the .so path."""
+    os.makedirs(_BUILD, exist_ok=True)
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
+        return _LIB
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        raise RuntimeError("no C compiler found to build the oracle")
+    base = [cc, "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", _LIB + ".tmp", _SRC, "-lm"]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+class _Problem(C.Structure):
+    _fields_ = [
+        ("n_walls", C.c_int32),
+        ("n_nodes", C.c_void_p), ("thickness", C.c_void_p), ("n_layers", C.c_void_p),
+        ("layer_first", C.c_void_p), ("layer_par", C.c_void_p), ("bc_kind", C.c_void_p),
+        ("bc_par", C.c_void_p), ("bc_room", C.c_void_p),
+        ("noise", C.c_void_p * 2), ("noise_len", C.c_int32 * 2),
+        ("dt", C.c_double), ("t0", C.c_double), ("Lv", C.c_double), ("Psat", C.c_double),
+        ("n_rooms", C.c_int32), ("room_par", C.c_void_p), ("wall_area", C.c_void_p),
+    ]
+
+
+class _State(C.Structure):
+    _fields_ = [
+        ("step", C.c_int64),
+        ("T_prev", C.c_void_p), ("T_cur", C.c_void_p), ("P_prev", C.c_void_p), ("P_cur", C.c_void_p),
+        ("cumul", C.c_void_p), ("room", C.c_void_p),
+    ]
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = C.CDLL(build())
+        lib.orc_run.restype = C.c_int
+        lib.orc_run.argtypes = [C.POINTER(_Problem), C.POINTER(_State), C.c_int64, C.c_int32,
+                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32]
+        lib.orc_ambient.restype = None
+        lib.orc_ambient.argtypes = [C.POINTER(_Problem), C.c_int32, C.c_int32, C.c_double,
+                                    C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        lib.orc_coefficients.restype = None
+        lib.orc_coefficients.argtypes = [C.POINTER(_Problem), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
+        _lib = lib
+    return _lib
+
+
+def _ptr(a) -> int | None:
+    return None if a is None else a.ctypes.data
+
+
+def default_threads() -> int:
+    return len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+
+
+class Oracle:
+    """The oracle on one workload: holds the FP64 state between ``run`` calls.
+
+    The state starts at the uniform initial condition [eq:HAM_ic] with level
+    n-1 equal to level 0 (the scheme is stated for n >= 1; the first step
+    uses u^{-1} := u^0), at step 0 (time t0).
+    """
+
+    def __init__(self, wl, n_threads: int | None = None):
+        self.wl = wl
+        self.n_threads = n_threads or default_threads()
+        self._keep = []
+        W = wl.n_walls
+        self.node_off = np.zeros(W + 1, dtype=np.int64)
+        np.cumsum(wl.n_nodes, out=self.node_off[1:])
+        tot = int(self.node_off[-1])
+
+        def keep(a, dt):
+            a = np.ascontiguousarray(a, dtype=dt)
+            self._keep.append(a)
+            return a
+
+        p = _Problem()
+        p.n_walls = W
+        p.n_nodes = _ptr(keep(wl.n_nodes, np.int32))
+        p.thickness = _ptr(keep(wl.thickness, np.float64))
+        p.n_layers = _ptr(keep(wl.n_layers, np.int32))
+        p.layer_first = _ptr(keep(wl.layer_first, np.int32))
+        p.layer_par = _ptr(keep(wl.layer_par.reshape(-1, NLAYER_PAR), np.float64))
+        p.bc_kind = _ptr(keep(wl.bc_kind, np.int32))
+        p.bc_par = _ptr(keep(wl.bc_par.reshape(W, 2, NBC_PAR), np.float64))
+        p.bc_room = _ptr(keep(wl.bc_room, np.int32))
+        for f in range(2):
+            nz = wl.noise[f]
+            if nz is None:
+                p.noise[f] = None
+                p.noise_len[f] = 0
+            else:
+                nz = keep(nz, np.float32)
+                p.noise[f] = nz.ctypes.data
+                p.noise_len[f] = nz.shape[1]
+        p.dt, p.t0, p.Lv, p.Psat = wl.dt, wl.t0, wl.Lv, wl.Psat
+        rooms = wl.rooms
+        if rooms:
+            p.n_rooms = len(rooms["par"])
+            p.room_par = _ptr(keep(rooms["par"], np.float64))
+            p.wall_area = _ptr(keep(rooms["wall_area"], np.float64))
+        else:
+            p.n_rooms = 0
+            p.room_par = None
+            p.wall_area = _ptr(keep(np.zeros(max(W, 1)), np.float64))
+        self._p = p
+
+        self.T_prev = np.repeat(np.asarray(wl.T_init, np.float64), wl.n_nodes)
+        self.T_cur = self.T_prev.copy()
+        self.P_prev = np.repeat(np.asarray(wl.P_init, np.float64), wl.n_nodes)
+        self.P_cur = self.P_prev.copy()
+        assert self.T_cur.shape[0] == tot
+        self.cumul = np.zeros((W, 2, 2), np.float64)
+        R = int(p.n_rooms)
+        self.room = np.zeros((max(R, 1), 4), np.float64)
+        if R:
+            self.room[:, 0:2] = np.asarray(rooms["Ta0"], np.float64)[:, None]
+            self.room[:, 2:4] = np.asarray(rooms["Pa0"], np.float64)[:, None]
+        self.step = 0
+
+    @property
+    def n_rooms(self) -> int:
+        return int(self._p.n_rooms)
+
+    def set_levels(self, T_prev, T_cur, P_prev, P_cur, step: int | None = None):
+        """Overwrite the two stored levels (concatenated walls)."""
+        self.T_prev[:] = T_prev
+        self.T_cur[:] = T_cur
+        self.P_prev[:] = P_prev
+        self.P_cur[:] = P_cur
+        if step is not None:
+            self.step = int(step)
+
+    def run(self, n_steps: int, sample_every: int = 0, want_balance: bool = False):
+        """Advance ``n_steps``; return dict(samples, room_samples, flux, balance)."""
+        W, R = self.wl.n_walls, self.n_rooms
+        ns = n_steps // sample_every if sample_every > 0 else 0
+        samples = np.zeros((ns, W, 2, 2)) if sample_every > 0 else None
+        room_samples = np.zeros((ns, R, 2)) if (sample_every > 0 and R) else None
+        flux = np.zeros((W, 2, 2))
+        bal = np.zeros((W, 2, 4)) if want_balance else None
+        st = _State(self.step, _ptr(self.T_prev), _ptr(self.T_cur), _ptr(self.P_prev), _ptr(self.P_cur),
+                    _ptr(self.cumul), _ptr(self.room))
+        rc = _load().orc_run(C.byref(self._p), C.byref(st), int(n_steps), int(sample_every),
+                             _ptr(samples), _ptr(room_samples), _ptr(flux), _ptr(bal), int(self.n_threads))
+        if rc != 0:
+            raise RuntimeError(f"oracle run failed with code {rc}")
+        self.step = int(st.step)
+        return dict(samples=samples, room_samples=room_samples, flux=flux if n_steps > 0 else None,
+                    balance=bal)
+
+    def wall(self, w: int, field: str = "T", level: int = 0) -> np.ndarray:
+        """Nodes of wall ``w``; level 0 is the newest (n), 1 the previous (n-1)."""
+        arr = {("T", 0): self.T_cur, ("T", 1): self.T_prev, ("P", 0): self.P_cur, ("P", 1): self.P_prev}[(field, level)]
+        return arr[self.node_off[w]: self.node_off[w + 1]]
+
+    def ambient(self, w: int, face: int, t: float) -> tuple[float, float]:
+        T = C.c_double()
+        P = C.c_double()
+        _load().orc_ambient(C.byref(self._p), w, face, float(t), C.byref(T), C.byref(P))
+        return T.value, P.value
+
+    def coefficients(self, w: int, P: np.ndarray):
+        """Node (kM, cM, kTT, cTT, kTM, cTM) and face (kM_f, kTT_f, kTM_f) values."""
+        P = np.ascontiguousarray(P, np.float64)
+        N = P.shape[0]
+        node = np.zeros((N, 6))
+        face = np.zeros((N - 1, 3))
+        _load().orc_coefficients(C.byref(self._p), int(w), _ptr(P), _ptr(node), _ptr(face))
+        return node, face

@@ -1,0 +1,461 @@
+/*
+ * FP64 CPU oracle: plain statement of the Dufort-Frankel hygrothermal wall
+ * update (arXiv:1703.10119). TEST INFRASTRUCTURE ONLY; see hygro_oracle.h
+ * for what each part follows. Scalar loops, no blocking, no reordering.
+ */
+#include "hygro_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+enum { L_KM0, L_A, L_CM0, L_B, L_KTT0, L_AT, L_CTT0, L_BT, L_CHI };
+enum { B_HT, B_HM, B_QINF, B_GINF, B_TMEAN, B_TAMP, B_PMEAN, B_PAMP, B_PERIOD, B_PHT, B_PHP, B_NDT };
+enum { R_VOL, R_ACH, R_QGAIN, R_GVAP, R_TMEAN, R_TAMP, R_PMEAN, R_PAMP, R_PERIOD, R_PHT, R_PHP,
+       R_RHOA, R_CPA, R_CPV, R_PVREF };
+
+static const double TWO_PI = 6.283185307179586476925286766559;
+
+/* Linear interpolation of an evenly spaced (T, Pv) noise table at time t,
+ * held constant beyond its ends. */
+static double noise_at(const float *tab, int32_t len, double noise_dt, double t, int field)
+{
+    if (tab == NULL || len <= 0 || noise_dt <= 0.0) return 0.0;
+    double x = t / noise_dt;
+    if (x <= 0.0) return (double)tab[field];
+    if (x >= (double)(len - 1)) return (double)tab[(size_t)(len - 1) * 2 + field];
+    double i = floor(x);
+    size_t k = (size_t)i;
+    double f = x - i;
+    return (1.0 - f) * (double)tab[k * 2 + field] + f * (double)tab[(k + 1) * 2 + field];
+}
+
+/* Ambient air of an exterior face: daily sinusoid plus interpolated noise
+ * (the T_inf, Pv_inf of [eq:HAM_BC]). */
+void orc_ambient(const orc_problem *p, int32_t w, int32_t face, double t, double *T_inf, double *P_inf)
+{
+    const double *b = p->bc_par + ((size_t)w * 2 + face) * ORC_NBC_PAR;
+    const float *tab = NULL;
+    if (p->noise[face] != NULL && p->noise_len[face] > 0)
+        tab = p->noise[face] + (size_t)w * (size_t)p->noise_len[face] * 2;
+    double T = b[B_TMEAN], P = b[B_PMEAN];
+    if (b[B_PERIOD] > 0.0) {
+        T += b[B_TAMP] * sin(TWO_PI * t / b[B_PERIOD] + b[B_PHT]);
+        P += b[B_PAMP] * sin(TWO_PI * t / b[B_PERIOD] + b[B_PHP]);
+    }
+    T += noise_at(tab, p->noise_len[face], b[B_NDT], t, 0);
+    P += noise_at(tab, p->noise_len[face], b[B_NDT], t, 1);
+    *T_inf = T;
+    *P_inf = P;
+}
+
+typedef struct {
+    int32_t N;
+    double dx;
+    int32_t nl;
+    const int32_t *first;
+    const double *par;
+} wall_view;
+
+static wall_view view_of(const orc_problem *p, const int64_t *layer_off, int32_t w)
+{
+    wall_view v;
+    v.N = p->n_nodes[w];
+    v.dx = p->thickness[w] / (double)(v.N - 1);
+    v.nl = p->n_layers[w];
+    v.first = p->layer_first + layer_off[w];
+    v.par = p->layer_par + (size_t)layer_off[w] * ORC_NLAYER_PAR;
+    return v;
+}
+
+static int32_t layer_of(const wall_view *v, int32_t j)
+{
+    int32_t l = 0;
+    while (l + 1 < v->nl && j >= v->first[l + 1]) ++l;
+    return l;
+}
+
+/* Material coefficients of Sec. 2 evaluated at level n (explicitly, as the
+ * paper prescribes for the DF scheme in Sec. 3.1), then their face values:
+ * arithmetic mean of the two nodes inside a layer (for coefficients affine
+ * in Pv this equals the coefficient at the face-mean Pv, Sec. 3.1) and the
+ * harmonic mean across an interface between two layers. kTM_f = Lv kM_f. */
+static void coefficients(const orc_problem *p, const wall_view *v, const double *P,
+                         double *kM, double *cM, double *kTT, double *cTT, double *kTM, double *cTM,
+                         double *kMf, double *kTTf, double *kTMf)
+{
+    for (int32_t j = 0; j < v->N; ++j) {
+        const double *q = v->par + (size_t)layer_of(v, j) * ORC_NLAYER_PAR;
+        double r = P[j] / p->Psat;
+        kM[j] = q[L_KM0] * (1.0 + q[L_A] * r);
+        cM[j] = q[L_CM0] * (1.0 + q[L_B] * r);
+        kTT[j] = q[L_KTT0] * (1.0 + q[L_AT] * r);
+        cTT[j] = q[L_CTT0] * (1.0 + q[L_BT] * r);
+        kTM[j] = p->Lv * kM[j];
+        cTM[j] = q[L_CHI] * cM[j];
+    }
+    for (int32_t j = 0; j + 1 < v->N; ++j) {
+        if (layer_of(v, j) == layer_of(v, j + 1)) {
+            kMf[j] = 0.5 * (kM[j] + kM[j + 1]);
+            kTTf[j] = 0.5 * (kTT[j] + kTT[j + 1]);
+        } else {
+            kMf[j] = 2.0 * kM[j] * kM[j + 1] / (kM[j] + kM[j + 1]);
+            kTTf[j] = 2.0 * kTT[j] * kTT[j + 1] / (kTT[j] + kTT[j + 1]);
+        }
+        kTMf[j] = p->Lv * kMf[j];
+    }
+}
+
+void orc_coefficients(const orc_problem *p, int32_t w, const double *P, double *node6, double *face3)
+{
+    int64_t *off = (int64_t *)calloc((size_t)p->n_walls + 1, sizeof(int64_t));
+    for (int32_t i = 0; i < p->n_walls; ++i) off[i + 1] = off[i] + p->n_layers[i];
+    wall_view v = view_of(p, off, w);
+    int32_t N = v.N;
+    double *buf = (double *)malloc(sizeof(double) * (size_t)(9 * N));
+    coefficients(p, &v, P, buf, buf + N, buf + 2 * N, buf + 3 * N, buf + 4 * N, buf + 5 * N,
+                 buf + 6 * N, buf + 7 * N, buf + 8 * N);
+    for (int32_t j = 0; j < N; ++j)
+        for (int k = 0; k < 6; ++k) node6[j * 6 + k] = buf[k * N + j];
+    for (int32_t j = 0; j + 1 < N; ++j)
+        for (int k = 0; k < 3; ++k) face3[j * 3 + k] = buf[(6 + k) * N + j];
+    free(buf);
+    free(off);
+}
+
+/* Surface exchange data of one face for this step: the air state and the
+ * coefficients of [eq:HAM_BC]. An adiabatic face exchanges nothing. */
+typedef struct {
+    double hT, hM, q_inf, g_inf, T_inf, P_inf;
+} face_bc;
+
+static face_bc face_of(const orc_problem *p, int32_t w, int32_t f, double t, const double *room_state)
+{
+    face_bc s;
+    memset(&s, 0, sizeof s);
+    const double *b = p->bc_par + ((size_t)w * 2 + f) * ORC_NBC_PAR;
+    int32_t kind = p->bc_kind[w * 2 + f];
+    if (kind == ORC_BC_ADIABATIC) return s;
+    s.hT = b[B_HT];
+    s.hM = b[B_HM];
+    s.q_inf = b[B_QINF];
+    s.g_inf = b[B_GINF];
+    if (kind == ORC_BC_ROOM) {
+        /* explicit coupling [eq:wbse_tn_exp]: the wall sees the room air at level n */
+        int32_t r = p->bc_room[w * 2 + f];
+        s.T_inf = room_state[r * 4 + 1];
+        s.P_inf = room_state[r * 4 + 3];
+    } else {
+        orc_ambient(p, w, f, t, &s.T_inf, &s.P_inf);
+    }
+    return s;
+}
+
+typedef struct {
+    double *kM, *cM, *kTT, *cTT, *kTM, *cTM, *kMf, *kTTf, *kTMf, *Pn, *Tn;
+} scratch;
+
+/* One DF step of one wall. On return Tp / Pp hold level n+1.
+ *
+ * Per node j, with half-cell weight w_j (1/2 at the two surface nodes),
+ * the DF balance of [eq:DF_NL] in conservative form reads
+ *   w_j dx c_j (u_j^{n+1} - u_j^{n-1}) / (2 dt)
+ *      = sum_{faces f of j} k_f (u_nb^n - ubar_j) / dx + surface terms,
+ *   ubar_j = (u_j^{n+1} + u_j^{n-1}) / 2,
+ * which is solved for u_j^{n+1}. Pv is advanced first ([eq:DF_eq1]); the T
+ * equation then carries the kTM cross flux and the cTM storage term with
+ * Pv^{n+1} ([eq:DF_eq2]). At a surface node the Robin exchange enters with
+ * the time-averaged surface value, which is what the ghost node of
+ * [eq:ghost_node_v0] / [eq:ghost_node_u0] substitutes. */
+static void wall_step(const orc_problem *p, const wall_view *v, const face_bc bc[2],
+                      double *Tp, const double *Tc, double *Pp, const double *Pc, scratch *sc,
+                      double flux[2][2], double bal[2][4])
+{
+    const int32_t N = v->N;
+    const double dx = v->dx, dt = p->dt, Lv = p->Lv;
+    coefficients(p, v, Pc, sc->kM, sc->cM, sc->kTT, sc->cTT, sc->kTM, sc->cTM, sc->kMf, sc->kTTf,
+                 sc->kTMf);
+
+    /* vapour pressure first */
+    for (int32_t j = 0; j < N; ++j) {
+        double w = (j == 0 || j == N - 1) ? 0.5 : 1.0;
+        double A = w * dx * sc->cM[j] / (2.0 * dt);
+        double S = 0.0, nb = 0.0, H = 0.0, src = 0.0;
+        if (j > 0) {
+            S += sc->kMf[j - 1] / dx;
+            nb += sc->kMf[j - 1] / dx * Pc[j - 1];
+        }
+        if (j < N - 1) {
+            S += sc->kMf[j] / dx;
+            nb += sc->kMf[j] / dx * Pc[j + 1];
+        }
+        if (j == 0) {
+            H += bc[0].hM;
+            src += bc[0].hM * bc[0].P_inf + bc[0].g_inf;
+        }
+        if (j == N - 1) {
+            H += bc[1].hM;
+            src += bc[1].hM * bc[1].P_inf + bc[1].g_inf;
+        }
+        sc->Pn[j] = ((A - 0.5 * S - 0.5 * H) * Pp[j] + nb + src) / (A + 0.5 * S + 0.5 * H);
+    }
+
+    /* then temperature, using Pv^{n+1} of the same node */
+    for (int32_t j = 0; j < N; ++j) {
+        double w = (j == 0 || j == N - 1) ? 0.5 : 1.0;
+        double B = w * dx * sc->cTT[j] / (2.0 * dt);
+        double C = w * dx * sc->cTM[j] / (2.0 * dt);
+        double Pbar = 0.5 * (sc->Pn[j] + Pp[j]);
+        double S = 0.0, nb = 0.0, cross = 0.0, H = 0.0, src = 0.0;
+        if (j > 0) {
+            S += sc->kTTf[j - 1] / dx;
+            nb += sc->kTTf[j - 1] / dx * Tc[j - 1];
+            cross += sc->kTMf[j - 1] / dx * (Pc[j - 1] - Pbar);
+        }
+        if (j < N - 1) {
+            S += sc->kTTf[j] / dx;
+            nb += sc->kTTf[j] / dx * Tc[j + 1];
+            cross += sc->kTMf[j] / dx * (Pc[j + 1] - Pbar);
+        }
+        for (int f = 0; f < 2; ++f) {
+            if ((f == 0 && j == 0) || (f == 1 && j == N - 1)) {
+                H += bc[f].hT;
+                src += bc[f].hT * bc[f].T_inf + Lv * bc[f].hM * (bc[f].P_inf - Pbar) + bc[f].q_inf;
+            }
+        }
+        sc->Tn[j] = ((B - 0.5 * S - 0.5 * H) * Tp[j] + nb + cross + src - C * (sc->Pn[j] - Pp[j])) /
+                    (B + 0.5 * S + 0.5 * H);
+    }
+
+    /* surface fluxes into the wall, [eq:HAM_BC] with the time-averaged surface values */
+    for (int f = 0; f < 2; ++f) {
+        int32_t j = f == 0 ? 0 : N - 1;
+        double Tbar = 0.5 * (sc->Tn[j] + Tp[j]);
+        double Pbar = 0.5 * (sc->Pn[j] + Pp[j]);
+        double g = bc[f].hM * (bc[f].P_inf - Pbar) + bc[f].g_inf;
+        double q = bc[f].hT * (bc[f].T_inf - Tbar) + Lv * bc[f].hM * (bc[f].P_inf - Pbar) + bc[f].q_inf;
+        flux[f][0] = q;
+        flux[f][1] = g;
+    }
+
+    /* discrete balance of this step: storage S, boundary B, DF defect D */
+    if (bal != NULL) {
+        double S_T = 0, S_P = 0, M_T = 0, M_P = 0, D_T = 0, D_P = 0;
+        for (int32_t j = 0; j < N; ++j) {
+            double w = (j == 0 || j == N - 1) ? 0.5 : 1.0;
+            double sP = w * dx * sc->cM[j] * (sc->Pn[j] - Pp[j]) / (2.0 * dt);
+            double sT = w * dx * (sc->cTT[j] * (sc->Tn[j] - Tp[j]) + sc->cTM[j] * (sc->Pn[j] - Pp[j])) /
+                        (2.0 * dt);
+            S_P += sP;
+            S_T += sT;
+            M_P += fabs(sP);
+            M_T += fabs(sT);
+        }
+        for (int32_t j = 0; j + 1 < N; ++j) {
+            double Pb0 = 0.5 * (sc->Pn[j] + Pp[j]), Pb1 = 0.5 * (sc->Pn[j + 1] + Pp[j + 1]);
+            double Tb0 = 0.5 * (sc->Tn[j] + Tp[j]), Tb1 = 0.5 * (sc->Tn[j + 1] + Tp[j + 1]);
+            double dP = sc->kMf[j] / dx * ((Pc[j + 1] - Pb1) + (Pc[j] - Pb0));
+            double dT = sc->kTTf[j] / dx * ((Tc[j + 1] - Tb1) + (Tc[j] - Tb0)) +
+                        sc->kTMf[j] / dx * ((Pc[j + 1] - Pb1) + (Pc[j] - Pb0));
+            D_P += dP;
+            D_T += dT;
+            M_P += sc->kMf[j] / dx * (fabs(Pc[j + 1] - Pb0) + fabs(Pc[j] - Pb1));
+            M_T += sc->kTTf[j] / dx * (fabs(Tc[j + 1] - Tb0) + fabs(Tc[j] - Tb1)) +
+                   sc->kTMf[j] / dx * (fabs(Pc[j + 1] - Pb0) + fabs(Pc[j] - Pb1));
+        }
+        double B_T = flux[0][0] + flux[1][0], B_P = flux[0][1] + flux[1][1];
+        M_T += fabs(flux[0][0]) + fabs(flux[1][0]);
+        M_P += fabs(flux[0][1]) + fabs(flux[1][1]);
+        bal[0][0] = S_T; bal[0][1] = B_T; bal[0][2] = D_T; bal[0][3] = M_T;
+        bal[1][0] = S_P; bal[1][1] = B_P; bal[1][2] = D_P; bal[1][3] = M_P;
+    }
+
+    for (int32_t j = 0; j < N; ++j) {
+        Tp[j] = sc->Tn[j];
+        Pp[j] = sc->Pn[j];
+    }
+}
+
+/* Room air node of Sec. 5.1 ([eq:LAV_equation] with the sources of the
+ * occupants and of ventilation, the wall exchanges [eq:LAV_couplage]),
+ * humidity ratio w = Pva / Pv_ref. The wall surface values enter at level n
+ * as in [eq:wbse_tn_exp]; the room node itself is advanced with the DF
+ * replacement (Ta^{n+1} + Ta^{n-1}) / 2 of its own value, vapour first. */
+static void room_step(const orc_problem *p, int32_t r, double t, double *rs,
+                      const double *sum_AhT, const double *sum_AhM, const double *sum_AhTTs,
+                      const double *sum_AhMPs)
+{
+    const double *q = p->room_par + (size_t)r * ORC_NROOM_PAR;
+    const double dt = p->dt, Lv = p->Lv;
+    double Ta_p = rs[0], Ta_c = rs[1], Pa_p = rs[2], Pa_c = rs[3];
+    double rhoV = q[R_RHOA] * q[R_VOL];
+    double gv = rhoV * q[R_ACH] / 3600.0;                        /* kg/s of exchanged air */
+    double T_out = q[R_TMEAN], P_out = q[R_PMEAN];
+    if (q[R_PERIOD] > 0.0) {
+        T_out += q[R_TAMP] * sin(TWO_PI * t / q[R_PERIOD] + q[R_PHT]);
+        P_out += q[R_PAMP] * sin(TWO_PI * t / q[R_PERIOD] + q[R_PHP]);
+    }
+    double Pref = q[R_PVREF];
+    double w_out = P_out / Pref;
+    /* vapour: rhoV/Pref dPa/dt = g_vap + gv (w_out - Pa/Pref) + sum A hM (Ps - Pa) */
+    double CP = rhoV / Pref;
+    double a_p = CP / (2.0 * dt);
+    double k_p = gv / Pref + sum_AhM[r];
+    double Pa_n = ((a_p - 0.5 * k_p) * Pa_p + q[R_GVAP] + gv * w_out + sum_AhMPs[r]) / (a_p + 0.5 * k_p);
+    double Pa_bar = 0.5 * (Pa_n + Pa_p);
+    /* heat: rhoV (cpa + cpv w) dTa/dt = Q + Lv g_vap + gv cpa (T_out - Ta) + Lv gv (w_out - w)
+     *       + sum A [hT (Ts - Ta) + Lv hM (Ps - Pa)] */
+    double CT = rhoV * (q[R_CPA] + q[R_CPV] * Pa_c / Pref);
+    double a_t = CT / (2.0 * dt);
+    double k_t = gv * q[R_CPA] + sum_AhT[r];
+    double rhs = q[R_QGAIN] + Lv * q[R_GVAP] + gv * q[R_CPA] * T_out + Lv * gv * (w_out - Pa_bar / Pref) +
+                 sum_AhTTs[r] + Lv * (sum_AhMPs[r] - sum_AhM[r] * Pa_bar);
+    double Ta_n = ((a_t - 0.5 * k_t) * Ta_p + rhs) / (a_t + 0.5 * k_t);
+    rs[0] = Ta_c;
+    rs[1] = Ta_n;
+    rs[2] = Pa_c;
+    rs[3] = Pa_n;
+}
+
+int orc_run(const orc_problem *p, orc_state *s, int64_t n_steps, int32_t sample_every,
+            double *samples, double *room_samples, double *flux_last, double *balance_last,
+            int32_t n_threads)
+{
+    if (p == NULL || s == NULL || n_steps < 0 || p->n_walls < 0) return -1;
+    if ((samples != NULL || room_samples != NULL) && sample_every <= 0) return -1;
+    const int32_t W = p->n_walls;
+    for (int32_t w = 0; w < W; ++w)
+        if (p->n_nodes[w] < 3 || p->n_layers[w] < 1 || !(p->thickness[w] > 0.0)) return -1;
+    if (p->n_rooms > 0 && (s->room == NULL || p->room_par == NULL || p->wall_area == NULL)) return -1;
+
+    int64_t *node_off = (int64_t *)calloc((size_t)W + 1, sizeof(int64_t));
+    int64_t *layer_off = (int64_t *)calloc((size_t)W + 1, sizeof(int64_t));
+    if (!node_off || !layer_off) {
+        free(node_off);
+        free(layer_off);
+        return -2;
+    }
+    int32_t Nmax = 3;
+    for (int32_t w = 0; w < W; ++w) {
+        node_off[w + 1] = node_off[w] + p->n_nodes[w];
+        layer_off[w + 1] = layer_off[w] + p->n_layers[w];
+        if (p->n_nodes[w] > Nmax) Nmax = p->n_nodes[w];
+    }
+    const int32_t R = p->n_rooms;
+    double *surf = (double *)calloc((size_t)W * 4 + 1, sizeof(double)); /* Ts^n, Ps^n of face 0, face 1 */
+    double *rsum = (double *)calloc((size_t)R * 4 + 1, sizeof(double));
+    double *flux = (double *)calloc((size_t)W * 4 + 1, sizeof(double));
+    if (!surf || !rsum || !flux) {
+        free(node_off); free(layer_off); free(surf); free(rsum); free(flux);
+        return -2;
+    }
+    if (n_threads <= 0) n_threads = 1;
+    int rc = 0;
+
+    for (int64_t it = 0; it < n_steps; ++it) {
+        const int64_t n = s->step;
+        const double t = p->t0 + (double)n * p->dt;
+        const int last = (it == n_steps - 1);
+        /* wall surface values at level n, used by the room balance of this step */
+        for (int32_t w = 0; w < W; ++w) {
+            surf[w * 4 + 0] = s->T_cur[node_off[w]];
+            surf[w * 4 + 1] = s->P_cur[node_off[w]];
+            surf[w * 4 + 2] = s->T_cur[node_off[w] + p->n_nodes[w] - 1];
+            surf[w * 4 + 3] = s->P_cur[node_off[w] + p->n_nodes[w] - 1];
+        }
+#ifdef _OPENMP
+#pragma omp parallel num_threads(n_threads)
+#endif
+        {
+            scratch sc;
+            double *buf = (double *)malloc(sizeof(double) * (size_t)Nmax * 11);
+            if (buf == NULL) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+                rc = -2;
+            } else {
+                sc.kM = buf; sc.cM = buf + Nmax; sc.kTT = buf + 2 * Nmax; sc.cTT = buf + 3 * Nmax;
+                sc.kTM = buf + 4 * Nmax; sc.cTM = buf + 5 * Nmax; sc.kMf = buf + 6 * Nmax;
+                sc.kTTf = buf + 7 * Nmax; sc.kTMf = buf + 8 * Nmax; sc.Pn = buf + 9 * Nmax;
+                sc.Tn = buf + 10 * Nmax;
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 4)
+#endif
+                for (int32_t w = 0; w < W; ++w) {
+                    wall_view v = view_of(p, layer_off, w);
+                    face_bc bc[2] = {face_of(p, w, 0, t, s->room), face_of(p, w, 1, t, s->room)};
+                    double fl[2][2], bl[2][4];
+                    int64_t o = node_off[w];
+                    wall_step(p, &v, bc, s->T_prev + o, s->T_cur + o, s->P_prev + o, s->P_cur + o, &sc,
+                              fl, (last && balance_last) ? bl : NULL);
+                    for (int f = 0; f < 2; ++f)
+                        for (int k = 0; k < 2; ++k) {
+                            flux[w * 4 + f * 2 + k] = fl[f][k];
+                            s->cumul[w * 4 + f * 2 + k] += p->dt * fl[f][k];
+                        }
+                    if (last && balance_last)
+                        for (int f = 0; f < 2; ++f)
+                            for (int k = 0; k < 4; ++k) balance_last[(size_t)w * 8 + f * 4 + k] = bl[f][k];
+                    /* rotate: level n becomes n-1, level n+1 (written into *_prev) becomes n */
+                    for (int32_t j = 0; j < v.N; ++j) {
+                        double tt = s->T_prev[o + j];
+                        s->T_prev[o + j] = s->T_cur[o + j];
+                        s->T_cur[o + j] = tt;
+                        double pp = s->P_prev[o + j];
+                        s->P_prev[o + j] = s->P_cur[o + j];
+                        s->P_cur[o + j] = pp;
+                    }
+                }
+                free(buf);
+            }
+        }
+        if (rc != 0) break;
+
+        if (R > 0) {
+            /* per-room sums over the room-side wall faces, surface values at level n */
+            double *AhT = rsum, *AhM = rsum + R, *AhTTs = rsum + 2 * R, *AhMPs = rsum + 3 * R;
+            for (int32_t i = 0; i < 4 * R; ++i) rsum[i] = 0.0;
+            for (int32_t w = 0; w < W; ++w)
+                for (int f = 0; f < 2; ++f) {
+                    if (p->bc_kind[w * 2 + f] != ORC_BC_ROOM) continue;
+                    int32_t r = p->bc_room[w * 2 + f];
+                    const double *b = p->bc_par + ((size_t)w * 2 + f) * ORC_NBC_PAR;
+                    double A = p->wall_area[w];
+                    AhT[r] += A * b[B_HT];
+                    AhM[r] += A * b[B_HM];
+                    AhTTs[r] += A * b[B_HT] * surf[w * 4 + f * 2 + 0];
+                    AhMPs[r] += A * b[B_HM] * surf[w * 4 + f * 2 + 1];
+                }
+            for (int32_t r = 0; r < R; ++r) room_step(p, r, t, s->room + r * 4, AhT, AhM, AhTTs, AhMPs);
+        }
+
+        s->step = n + 1;
+        if (sample_every > 0 && (it + 1) % sample_every == 0) {
+            int64_t k = (it + 1) / sample_every - 1;
+            if (samples != NULL)
+                for (int32_t w = 0; w < W; ++w) {
+                    double *o = samples + ((size_t)k * W + w) * 4;
+                    o[0] = s->T_cur[node_off[w]];
+                    o[1] = s->P_cur[node_off[w]];
+                    o[2] = s->T_cur[node_off[w] + p->n_nodes[w] - 1];
+                    o[3] = s->P_cur[node_off[w] + p->n_nodes[w] - 1];
+                }
+            if (room_samples != NULL)
+                for (int32_t r = 0; r < R; ++r) {
+                    room_samples[((size_t)k * R + r) * 2 + 0] = s->room[r * 4 + 1];
+                    room_samples[((size_t)k * R + r) * 2 + 1] = s->room[r * 4 + 3];
+                }
+        }
+        if (last && flux_last != NULL) memcpy(flux_last, flux, sizeof(double) * (size_t)W * 4);
+    }
+    free(node_off);
+    free(layer_off);
+    free(surf);
+    free(rsum);
+    free(flux);
+    return rc;
+}

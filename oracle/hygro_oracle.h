@@ -1,0 +1,100 @@
+/*
+ * FP64 CPU oracle for the Dufort-Frankel (DF) hygrothermal wall update of
+ * Gasparin, Berger, Dutykh & Mendes, "An improved explicit scheme for
+ * whole-building hygrothermal simulation" (arXiv:1703.10119).
+ *
+ * TEST INFRASTRUCTURE ONLY. This code is the plain, slow, obviously correct
+ * statement of what the CUDA library computes. Only the test suite, the
+ * smoke check and the CPU-baseline leg of the benchmark load it; the CUDA
+ * library neither links nor calls it, and the two share no source.
+ *
+ * What it follows (paper sections / equations, LaTeX labels in brackets):
+ *   - the coupled moisture (Pv) and heat (T) equations [eq:HAM_equation2],
+ *     with coefficients kM, cM, kTT, cTT, kTM, cTM (Sec. 2) taken in the
+ *     affine form kM = kM0 (1 + a Pv/Psat), cM = cM0 (1 + b Pv/Psat),
+ *     kTT = kTT0 (1 + aT Pv/Psat), cTT = cTT0 (1 + bT Pv/Psat),
+ *     kTM = Lv kM, cTM = chi cM;
+ *   - Robin surface exchanges [eq:HAM_BC] (fluxes counted positive INTO the
+ *     wall at both faces), uniform initial state [eq:HAM_ic];
+ *   - the nonlinear DF scheme [eq:DF_NL], [eq:DF_NL_RHS]: coefficients
+ *     evaluated explicitly at level n, face values from the two adjacent
+ *     nodes, u_j^n replaced by (u_j^{n+1} + u_j^{n-1})/2 in the diagonal;
+ *   - the coupled order of Appendix A: Pv first [eq:DF_eq1], then T using
+ *     Pv^{n+1} [eq:DF_eq2], [eq:DF_eq2b];
+ *   - the surface nodes through the ghost-node treatment of Appendix A
+ *     [eq:bc_v], [eq:ghost_node_v0], [eq:ghost_node_u0], written in its
+ *     equivalent half-cell form (identical algebra, no ghost storage);
+ *   - the room air balance of Sec. 5.1 [eq:LAV_equation], [eq:LAV_couplage]
+ *     advanced explicitly with the wall surface values at level n as in
+ *     [eq:wbse_tn_exp], the room node itself taking the DF form.
+ *
+ * Layout: walls are concatenated; the nodes of wall w are
+ * node_offset[w] .. node_offset[w] + n_nodes[w] - 1, node 0 at x = 0 (face 0),
+ * node N-1 at x = L (face 1), dx = L / (N - 1).
+ */
+#ifndef HYGRO_ORACLE_H
+#define HYGRO_ORACLE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_NLAYER_PAR 9   /* kM0, a, cM0, b, kTT0, aT, cTT0, bT, chi */
+#define ORC_NBC_PAR 12     /* hT, hM, q_inf, g_inf, T_mean, T_amp, P_mean, P_amp, period, phase_T, phase_P, noise_dt */
+#define ORC_NROOM_PAR 16   /* volume, ach, Q_gain, g_vap, T_out_mean, T_out_amp, P_out_mean, P_out_amp,
+                              period, phase_T, phase_P, rho_a, cp_a, cp_v, Pv_ref, (unused) */
+
+enum { ORC_BC_AMBIENT = 0, ORC_BC_ADIABATIC = 1, ORC_BC_ROOM = 2 };
+
+typedef struct {
+    int32_t n_walls;
+    const int32_t *n_nodes;      /* [n_walls], each >= 3 */
+    const double *thickness;     /* [n_walls] */
+    const int32_t *n_layers;     /* [n_walls], each >= 1 */
+    const int32_t *layer_first;  /* [sum n_layers]: first local node of each layer (0 for the first) */
+    const double *layer_par;     /* [sum n_layers][ORC_NLAYER_PAR] */
+    const int32_t *bc_kind;      /* [n_walls][2] */
+    const double *bc_par;        /* [n_walls][2][ORC_NBC_PAR] */
+    const int32_t *bc_room;      /* [n_walls][2]: room index of BC_ROOM faces */
+    const float *noise[2];       /* per face: [n_walls][noise_len[f]][2] (T, Pv) or NULL */
+    int32_t noise_len[2];
+    double dt, t0, Lv, Psat;
+    int32_t n_rooms;
+    const double *room_par;      /* [n_rooms][ORC_NROOM_PAR] */
+    const double *wall_area;     /* [n_walls], m^2, used by room faces */
+} orc_problem;
+
+typedef struct {
+    int64_t step;                /* n: T_cur / P_cur hold level n, T_prev / P_prev level n-1 */
+    double *T_prev, *T_cur;      /* [sum n_nodes] */
+    double *P_prev, *P_cur;      /* [sum n_nodes] */
+    double *cumul;               /* [n_walls][2 faces][2] sum over steps of dt * flux (heat, moisture) */
+    double *room;                /* [n_rooms][4]: Ta_prev, Ta_cur, Pa_prev, Pa_cur (may be NULL) */
+} orc_state;
+
+/* Advance n_steps DF steps.
+ *   samples:      [n_steps / sample_every][n_walls][2 faces][2] surface (T, Pv) at level n+1
+ *                 after every sample_every-th step of this call, or NULL
+ *   room_samples: [n_steps / sample_every][n_rooms][2] room (Ta, Pva), or NULL
+ *   flux_last:    [n_walls][2 faces][2] heat (W/m2) and moisture (kg/m2/s) flux of the last step, or NULL
+ *   balance_last: [n_walls][2 fields (T, Pv)][4] storage S, boundary B, DF defect D, scale M of the
+ *                 last step (S = B + D in exact arithmetic; M = sum of the magnitudes of all terms), or NULL
+ * Returns 0 on success, -1 on invalid arguments, -2 on allocation failure. */
+int orc_run(const orc_problem *p, orc_state *s, int64_t n_steps, int32_t sample_every,
+            double *samples, double *room_samples, double *flux_last, double *balance_last,
+            int32_t n_threads);
+
+/* Ambient air state (T_inf, Pv_inf) seen by an ambient face at time t. */
+void orc_ambient(const orc_problem *p, int32_t wall, int32_t face, double t, double *T_inf, double *P_inf);
+
+/* Per-node coefficients (kM, cM, kTT, cTT, kTM, cTM) of wall w at vapour pressures P[0..N-1],
+ * and face values (kM_f, kTT_f, kTM_f) for the N-1 interior faces. */
+void orc_coefficients(const orc_problem *p, int32_t wall, const double *P, double *node6 /* [N][6] */,
+                      double *face3 /* [N-1][3] */);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,292 @@
+"""Seeded synthetic inputs for the hygrothermal wall workloads.
+
+This module only draws numbers: wall geometries, layer splits, material
+parameters, boundary forcing descriptions and noise tables. It contains none
+of the Dufort-Frankel arithmetic, so both the CUDA library binding and the
+FP64 CPU oracle can be fed from it without sharing any of the method.
+
+Random numbers come from SplitMix64 (Steele, Lea & Flood, "Fast splittable
+pseudorandom number generators", OOPSLA 2014) used in counter form: the i-th
+output of the stream with key k is mix(k + (i + 1) * 0x9E3779B97F4A7C15).
+Gaussian noise uses the Box-Muller transform.
+
+Workloads (their shapes follow the paper's wall problems, Sec. 2 and Sec. 4,
+with the ranges of the standard benchmark configurations):
+  * ``config1``: one 10 cm wall, 101 nodes, dt = 60 s, one day.
+  * ``config2``: a batch of ragged multi-layer walls (default 4096 walls of
+    50..400 nodes, dt = 600 s, one year, hourly Gaussian noise on face 0).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+GOLDEN = np.uint64(0x9E3779B97F4A7C15)
+_M1 = np.uint64(0xBF58476D1CE4E5B9)
+_M2 = np.uint64(0x94D049BB133111EB)
+
+# Physical constants used to build the inputs (not the method).
+PSAT_REF = 2337.0        # Pa, saturation pressure at 20 C
+LV = 2.5e6               # J/kg, latent heat of evaporation
+
+# log10 range of the moisture storage coefficient of the batch workloads:
+# cM of the paper's Table 2 walls spans 1.82e-2 .. 1.18e-1 s2/m2.
+CM0_LOG10_RANGE = (math.log10(1.8e-2), math.log10(1.2e-1))
+
+# Boundary kinds (shared numbering with the C ABI and the oracle).
+BC_AMBIENT = 0           # sinusoid + optional hourly noise table
+BC_ADIABATIC = 1         # no exchange through this face
+BC_ROOM = 2              # face exposed to a room air node
+
+# Column order of a boundary parameter row.
+BC_FIELDS = ("hT", "hM", "q_inf", "g_inf", "T_mean", "T_amp", "P_mean",
+             "P_amp", "period", "phase_T", "phase_P", "noise_dt")
+# Column order of a layer parameter row.
+LAYER_FIELDS = ("kM0", "a", "cM0", "b", "kTT0", "aT", "cTT0", "bT", "chi")
+
+
+def _mix(z: np.ndarray) -> np.ndarray:
+    z = np.asarray(z, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * _M1
+        z = (z ^ (z >> np.uint64(27))) * _M2
+    return z ^ (z >> np.uint64(31))
+
+
+def stream_key(seed: int, stream) -> np.ndarray:
+    """Key of an independent stream (vectorised over ``stream``)."""
+    s = np.asarray(stream, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        return _mix(np.uint64(seed & 0xFFFFFFFFFFFFFFFF) ^ _mix(s * GOLDEN + np.uint64(1)))
+
+
+def uniform(key, counter) -> np.ndarray:
+    """Uniform doubles in [0, 1) for (key, counter), broadcast together."""
+    k = np.asarray(key, dtype=np.uint64)
+    c = np.asarray(counter, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        z = _mix(k + (c + np.uint64(1)) * GOLDEN)
+    return (z >> np.uint64(11)).astype(np.float64) * (1.0 / 9007199254740992.0)
+
+
+def normal_pairs(key, counter) -> tuple[np.ndarray, np.ndarray]:
+    """Box-Muller pair from the uniforms at counters 2c and 2c+1."""
+    c = np.asarray(counter, dtype=np.uint64)
+    u1 = 1.0 - uniform(key, c * np.uint64(2))        # (0, 1]
+    u2 = uniform(key, c * np.uint64(2) + np.uint64(1))
+    r = np.sqrt(-2.0 * np.log(u1))
+    return r * np.cos(2.0 * np.pi * u2), r * np.sin(2.0 * np.pi * u2)
+
+
+@dataclasses.dataclass
+class Workload:
+    """A batch of 1D walls, their materials, boundaries and time grid."""
+    name: str
+    n_nodes: np.ndarray          # int32 [n_walls]
+    thickness: np.ndarray        # float64 [n_walls], metres
+    n_layers: np.ndarray         # int32 [n_walls]
+    layer_first: np.ndarray      # int32 [sum n_layers], first local node of each layer
+    layer_par: np.ndarray        # float64 [sum n_layers, 9] (LAYER_FIELDS)
+    T_init: np.ndarray           # float64 [n_walls], K
+    P_init: np.ndarray           # float64 [n_walls], Pa
+    bc_kind: np.ndarray          # int32 [n_walls, 2]
+    bc_par: np.ndarray           # float64 [n_walls, 2, 12] (BC_FIELDS)
+    bc_room: np.ndarray          # int32 [n_walls, 2], room index for BC_ROOM faces, else -1
+    noise: list                  # per face: float32 [n_walls, noise_len, 2] (T, Pv) or None
+    dt: float
+    t0: float
+    n_steps: int
+    Lv: float = LV
+    Psat: float = PSAT_REF
+    rooms: dict | None = None    # room description (whole-building workloads)
+
+    @property
+    def n_walls(self) -> int:
+        return int(self.n_nodes.shape[0])
+
+    @property
+    def total_nodes(self) -> int:
+        return int(self.n_nodes.sum())
+
+    def layer_offset(self) -> np.ndarray:
+        off = np.zeros(self.n_walls + 1, dtype=np.int64)
+        np.cumsum(self.n_layers, out=off[1:])
+        return off
+
+    def subset(self, walls) -> "Workload":
+        """The same problem restricted to the listed walls (no rooms)."""
+        walls = np.asarray(walls, dtype=np.int64)
+        off = self.layer_offset()
+        rows = np.concatenate([np.arange(off[w], off[w + 1]) for w in walls]) if len(walls) else np.zeros(0, np.int64)
+        noise = [None if nz is None else np.ascontiguousarray(nz[walls]) for nz in self.noise]
+        return dataclasses.replace(
+            self, name=f"{self.name}[subset {len(walls)}]",
+            n_nodes=self.n_nodes[walls].copy(), thickness=self.thickness[walls].copy(),
+            n_layers=self.n_layers[walls].copy(), layer_first=self.layer_first[rows].copy(),
+            layer_par=self.layer_par[rows].copy(), T_init=self.T_init[walls].copy(),
+            P_init=self.P_init[walls].copy(), bc_kind=self.bc_kind[walls].copy(),
+            bc_par=self.bc_par[walls].copy(), bc_room=self.bc_room[walls].copy(),
+            noise=noise, rooms=None)
+
+
+def _bc_row(hT, hM, T_mean, T_amp, P_mean, P_amp, period=86400.0, phase_T=0.0,
+            phase_P=0.0, noise_dt=3600.0, q_inf=0.0, g_inf=0.0) -> np.ndarray:
+    return np.array([hT, hM, q_inf, g_inf, T_mean, T_amp, P_mean, P_amp, period,
+                     phase_T, phase_P, noise_dt], dtype=np.float64)
+
+
+def uniform_wall(N: int, L: float, layer: dict, **kw) -> Workload:
+    """A single one-layer wall; ``layer`` maps LAYER_FIELDS names to values."""
+    return layered_wall([N], L, [layer], **kw)
+
+
+def layered_wall(counts, L: float, layers, *, T0=293.0, P0=1000.0,
+                 bc0: dict | None = None, bc1: dict | None = None, dt=60.0,
+                 n_steps=100, t0=0.0, Lv=LV, Psat=PSAT_REF, kinds=(BC_AMBIENT, BC_AMBIENT),
+                 name="wall") -> Workload:
+    """A single wall whose layer l holds ``counts[l]`` consecutive nodes."""
+    N = int(sum(counts))
+    first = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(np.int32)
+    par = np.array([[lay.get(k, 0.0) for k in LAYER_FIELDS] for lay in layers], dtype=np.float64)
+    rows = []
+    for bc in (bc0, bc1):
+        bc = dict(bc or {})
+        rows.append(_bc_row(bc.get("hT", 0.0), bc.get("hM", 0.0), bc.get("T_mean", T0),
+                            bc.get("T_amp", 0.0), bc.get("P_mean", P0), bc.get("P_amp", 0.0),
+                            bc.get("period", 86400.0), bc.get("phase_T", 0.0),
+                            bc.get("phase_P", 0.0), bc.get("noise_dt", 3600.0),
+                            bc.get("q_inf", 0.0), bc.get("g_inf", 0.0)))
+    return Workload(
+        name=name, n_nodes=np.array([N], np.int32), thickness=np.array([L], np.float64),
+        n_layers=np.array([len(counts)], np.int32), layer_first=first, layer_par=par,
+        T_init=np.array([T0]), P_init=np.array([P0]),
+        bc_kind=np.array([list(kinds)], np.int32), bc_par=np.stack(rows)[None],
+        bc_room=np.full((1, 2), -1, np.int32), noise=[None, None], dt=dt, t0=t0,
+        n_steps=n_steps, Lv=Lv, Psat=Psat)
+
+
+def concat(workloads: list[Workload], name="batch") -> Workload:
+    """Stack several single- or multi-wall workloads with the same time grid."""
+    w0 = workloads[0]
+    noise = []
+    for f in range(2):
+        if all(w.noise[f] is None for w in workloads):
+            noise.append(None)
+            continue
+        ln = max(w.noise[f].shape[1] for w in workloads if w.noise[f] is not None)
+        parts = []
+        for w in workloads:
+            z = np.zeros((w.n_walls, ln, 2), np.float32)
+            if w.noise[f] is not None:
+                z[:, : w.noise[f].shape[1]] = w.noise[f]
+            parts.append(z)
+        noise.append(np.concatenate(parts))
+    return dataclasses.replace(
+        w0, name=name,
+        n_nodes=np.concatenate([w.n_nodes for w in workloads]),
+        thickness=np.concatenate([w.thickness for w in workloads]),
+        n_layers=np.concatenate([w.n_layers for w in workloads]),
+        layer_first=np.concatenate([w.layer_first for w in workloads]),
+        layer_par=np.concatenate([w.layer_par for w in workloads]),
+        T_init=np.concatenate([w.T_init for w in workloads]),
+        P_init=np.concatenate([w.P_init for w in workloads]),
+        bc_kind=np.concatenate([w.bc_kind for w in workloads]),
+        bc_par=np.concatenate([w.bc_par for w in workloads]),
+        bc_room=np.concatenate([w.bc_room for w in workloads]),
+        noise=noise, rooms=None)
+
+
+def config1(seed: int = 1) -> Workload:
+    """One 10 cm wall, N = 101, dt = 60 s, 1440 steps (one day), FP64 case.
+
+    kM = kM0 (1 + a Pv/Psat), cM = cM0 (1 + b Pv/Psat) with a, b ~ U[0, 1]
+    and the phase of the vapour-pressure sinusoid ~ U[0, 2 pi). Face 0 sees
+    293 + 10 sin(2 pi t/86400) K and 1200 + 400 sin(2 pi t/86400 + phi) Pa
+    with hT = 25, hM = 2e-8; face 1 stays at 293 K / 1000 Pa with hT = 8,
+    hM = 3e-8. Uniform initial state 293 K, 1000 Pa.
+    """
+    key = stream_key(seed, 0)
+    u = uniform(key, np.arange(3))
+    layer = dict(kM0=2e-11, a=u[0], cM0=1e-4, b=u[1], kTT0=1.5, cTT0=1.2e6)
+    bc0 = dict(hT=25.0, hM=2e-8, T_mean=293.0, T_amp=10.0, P_mean=1200.0, P_amp=400.0,
+               phase_P=2.0 * math.pi * u[2])
+    bc1 = dict(hT=8.0, hM=3e-8, T_mean=293.0, P_mean=1000.0)
+    return uniform_wall(101, 0.1, layer, bc0=bc0, bc1=bc1, dt=60.0, n_steps=1440,
+                        name="config1: 1 wall, N=101, dt=60 s x 1440")
+
+
+def _layer_split(key, N: int, n_layers: int) -> list[int]:
+    """Seeded node counts per layer, each >= 3, summing to N."""
+    if n_layers == 1:
+        return [N]
+    u = uniform(key, np.arange(100, 102))
+    if n_layers == 2:
+        n0 = 3 + int(u[0] * (N - 5))
+        return [n0, N - n0]
+    n0 = 3 + int(u[0] * (N - 8))
+    n1 = 3 + int(u[1] * (N - n0 - 5))
+    return [n0, n1, N - n0 - n1]
+
+
+def config2(seed: int = 2, n_walls: int = 4096, n_steps: int = 52560, dt: float = 600.0,
+            n_min: int = 50, n_max: int = 400, noise: bool = True,
+            name: str | None = None) -> Workload:
+    """Batch of ragged 1..3-layer walls, per-wall seeded forcing.
+
+    Per wall: N ~ U{n_min..n_max}, thickness ~ U[0.05, 0.4] m, layers ~ U{1,2,3}.
+    Per layer: kM0 log-uniform in [1e-12, 1e-10] s, kTT ~ U[0.04, 2] W/m/K,
+    cTT ~ U[1e5, 2e6] J/m3/K, a, b ~ U[0, 2], and cM0 log-uniform over the
+    range of the paper's Table 2 (cM of the one-zone walls, 1.8e-2 ..
+    1.2e-1 s2/m2). With cM0 = 1e-4 the nonlinear DF moisture update at these
+    dt / dx (lambda up to 1e5, surface exchange far above the half-cell
+    capacity) amplifies its own odd-even mode and diverges within a few
+    hundred steps, so the storage coefficient is taken from the paper.
+    Face 0: hT = 25, hM = 2e-8; 293 + 10 sin(2 pi t/86400 + phi_T) K and
+    1200 + 400 sin(2 pi t/86400 + phi_P) Pa plus hourly Gaussian noise
+    (sigma 1 K and 50 Pa, linearly interpolated). Face 1: hT = 8, hM = 3e-8,
+    constant 293 K / 1000 Pa. Uniform initial state 293 K, 1000 Pa.
+    """
+    walls = np.arange(n_walls)
+    keys = stream_key(seed, walls)
+    u = uniform(keys[:, None], np.arange(8)[None, :])
+    N = (n_min + np.floor(u[:, 0] * (n_max - n_min + 1))).astype(np.int32)
+    L = 0.05 + 0.35 * u[:, 1]
+    nl = (1 + np.floor(u[:, 2] * 3)).astype(np.int32)
+    phase_T = 2 * np.pi * u[:, 3]
+    phase_P = 2 * np.pi * u[:, 4]
+    firsts, pars = [], []
+    for w in range(n_walls):
+        counts = _layer_split(keys[w], int(N[w]), int(nl[w]))
+        first = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(np.int32)
+        firsts.append(first)
+        v = uniform(keys[w], np.arange(200, 200 + 6 * nl[w])).reshape(nl[w], 6)
+        for l in range(nl[w]):
+            kM0 = 10.0 ** (-12.0 + 2.0 * v[l, 0])
+            kTT = 0.04 + 1.96 * v[l, 1]
+            cTT = 1e5 + 1.9e6 * v[l, 2]
+            a = 2.0 * v[l, 3]
+            b = 2.0 * v[l, 4]
+            cM0 = 10.0 ** (CM0_LOG10_RANGE[0] + (CM0_LOG10_RANGE[1] - CM0_LOG10_RANGE[0]) * v[l, 5])
+            pars.append([kM0, a, cM0, b, kTT, 0.0, cTT, 0.0, 0.0])
+    horizon = n_steps * dt
+    noise_len = int(math.ceil(horizon / 3600.0)) + 2
+    bc_par = np.zeros((n_walls, 2, 12))
+    bc_par[:, 0] = _bc_row(25.0, 2e-8, 293.0, 10.0, 1200.0, 400.0)
+    bc_par[:, 0, 9] = phase_T
+    bc_par[:, 0, 10] = phase_P
+    bc_par[:, 1] = _bc_row(8.0, 3e-8, 293.0, 0.0, 1000.0, 0.0)
+    nz0 = None
+    if noise:
+        nkey = stream_key(seed, walls + (1 << 32))
+        z0, z1 = normal_pairs(nkey[:, None], np.arange(noise_len, dtype=np.uint64)[None, :])
+        nz0 = np.stack([1.0 * z0, 50.0 * z1], axis=-1).astype(np.float32)
+    return Workload(
+        name=name or f"config2: {n_walls} ragged walls N {n_min}-{n_max}, dt={dt:g} s x {n_steps}",
+        n_nodes=N, thickness=L, n_layers=nl, layer_first=np.concatenate(firsts),
+        layer_par=np.array(pars, dtype=np.float64),
+        T_init=np.full(n_walls, 293.0), P_init=np.full(n_walls, 1000.0),
+        bc_kind=np.zeros((n_walls, 2), np.int32), bc_par=bc_par,
+        bc_room=np.full((n_walls, 2), -1, np.int32), noise=[nz0, None],
+        dt=dt, t0=0.0, n_steps=n_steps)
