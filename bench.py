@@ -1,0 +1,383 @@
+#!/usr/bin/env python
+"""Benchmark of the batched Dufort-Frankel wall update on one GB300 (or N).
+
+Workload: 4096 ragged 1D walls (1-3 layers, 50-400 nodes, 0.05-0.4 m), seeded
+synthetic materials and forcing, dt = 600 s, one year (52560 steps) per run.
+One benchmark step = one hygro_run of the whole year on all walls with the
+persistent FP32 kernel (state carried over from step to step), inputs already
+resident in HBM; the L2 cache is flushed (512 MB write) between timed runs.
+Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle
+instead, on a bounded sample of the same workload.
+
+Metric: DF cell-updates/s (one node advanced one step for both T and Pv).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DF cell-updates/s, batched FP32 vs plain FP64 on GB300 at ≤1e-4 rel L∞; % roofline"
+UNIT = "cell-updates/s"
+# FP32 FMA-pipe operations per cell-update of the DF increment form (coefficients 4, faces 2, Pv 9,
+# T 15; each add, multiply or fused multiply-add counts once) plus 2 reciprocals on the MUFU pipe.
+OPS_PER_UPDATE = 30
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+KERNEL_SOURCES = ["paper_1703_10119_gb300/csrc/df1d_persistent.cuh", "paper_1703_10119_gb300/csrc/df1d_common.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "df1d_persistent_f32_traffic.json")
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--walls", type=int, default=4096)
+    p.add_argument("--year-steps", type=int, default=52560)
+    p.add_argument("--cpu-walls", type=int, default=256, help="walls of the CPU-baseline sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-fp64", action="store_true")
+    return p.parse_args()
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            t = json.load(fh)
+        if t.get("kernel_source_sha") == kernel_source_hash():
+            return t.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        rows = [r.split(",") for r in (self.out or "").strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        import torch
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend, init_method="env://")
+        pg = dist
+    return world, rank, local, pg
+
+
+def reduce_max(pg, x: float) -> float:
+    if pg is None:
+        return x
+    import torch
+
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(pg, x: float) -> float:
+    if pg is None:
+        return x
+    import torch
+
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+def cpu_sample(wl, n_walls: int):
+    step = max(1, wl.n_walls // n_walls)
+    pick = np.arange(0, wl.n_walls, step)[:n_walls]
+    return pick, wl.subset(pick)
+
+
+def run_oracle_sample(sub, n_steps: int):
+    import oracle
+
+    o = oracle.Oracle(sub)
+    t = time.perf_counter()
+    o.run(n_steps)
+    el = time.perf_counter() - t
+    return o, el
+
+
+def bench_reference(args):
+    from paper_1703_10119_gb300 import workloads as wk
+    import oracle
+
+    wl = wk.config2(n_walls=args.walls, n_steps=args.year_steps)
+    pick, sub = cpu_sample(wl, max(8, args.cpu_walls // 8))
+    units = sub.total_nodes * args.year_steps
+    for _ in range(args.warmup):
+        run_oracle_sample(sub, args.year_steps // 8)
+    times = []
+    for _ in range(args.steps):
+        _, el = run_oracle_sample(sub, args.year_steps)
+        times.append(el)
+    ms = 1e3 * float(np.mean(times))
+    value = units / (ms / 1e3)
+    cores = oracle.default_threads()
+    sample = (f"{len(pick)} of {wl.n_walls} walls (every {wl.n_walls // len(pick)}th), all {args.year_steps} "
+              f"steps, FP64 oracle, OpenMP over walls")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def bench_ours(args):
+    import torch
+
+    world, rank, local, pg = dist_setup(args)
+    assert torch.cuda.is_available(), "bench.py needs a CUDA device (no CPU fallback)"
+    torch.cuda.set_device(local)
+    from paper_1703_10119_gb300 import hygro as H
+    from paper_1703_10119_gb300 import workloads as wk
+
+    H.lib(build_if_missing=True)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    wl = wk.config2(seed=2 + rank, n_walls=args.walls, n_steps=args.year_steps)
+    units_per_run = wl.total_nodes * args.year_steps
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    g = H.Hygro(wl, precision="fp32", kernel="persistent", device=local, stream=stream.cuda_stream)
+
+    # parity of one full run from the initial state against the oracle on a sample of walls
+    parity = None
+    cpu_baseline = None
+    pick, sub = cpu_sample(wl, args.cpu_walls)
+    with torch.cuda.stream(stream):
+        g.run(args.year_steps)
+    g.sync()
+    T, P = g.fields(0)
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+
+        o, el = run_oracle_sample(sub, args.year_steps)
+        off = np.concatenate([[0], np.cumsum(wl.n_nodes)])
+        Tg = np.concatenate([T[off[w]:off[w + 1]] for w in pick])
+        Pg = np.concatenate([P[off[w]:off[w + 1]] for w in pick])
+        parity = {"walls_checked": int(len(pick)),
+                  "rel_linf_T": float(np.abs(Tg - o.T_cur).max() / np.abs(o.T_cur).max()),
+                  "rel_linf_P": float(np.abs(Pg - o.P_cur).max() / np.abs(o.P_cur).max())}
+        cpu_baseline = {"value": sub.total_nodes * args.year_steps / el, "unit": UNIT,
+                        "cores": oracle.default_threads(), "kind": "oracle",
+                        "sample": f"{len(pick)} of {wl.n_walls} walls (every {wl.n_walls // len(pick)}th), "
+                                  f"all {args.year_steps} steps, {el:.1f} s"}
+
+    for _ in range(max(0, args.warmup - 1)):
+        with torch.cuda.stream(stream):
+            g.run(args.year_steps)
+    torch.cuda.synchronize()
+    if pg is not None:
+        pg.barrier()
+
+    times = []
+    with ClockSampler(local) as cs:
+        torch.cuda.synchronize()
+        if pg is not None:
+            pg.barrier()
+        t_wall = time.perf_counter()
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                g.run(args.year_steps)
+                e1.record(stream)
+            times.append((e0, e1))
+        torch.cuda.synchronize()
+        if pg is not None:
+            pg.barrier()
+        t_wall = time.perf_counter() - t_wall
+    g.sync()
+    ms_list = [a.elapsed_time(b) for a, b in times]
+    ms = float(np.mean(ms_list))
+    ms_max = reduce_max(pg, ms)
+    units_total = reduce_sum(pg, float(units_per_run))
+    value = units_total / (ms_max / 1e3)
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = OPS_PER_UPDATE * units_per_run / (ms / 1e3) / 1e12
+    traffic = measured_traffic()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s", "frac": achieved / peak,
+                "traffic": traffic,
+                "note": (f"FP32 FMA-pipe roof: {sms} SMs x {FP32_LANES_PER_SM} lanes x {SM_MAX_MHZ:.0f} MHz; "
+                         f"{OPS_PER_UPDATE} FP32 ops + 2 reciprocals per cell-update; kernel "
+                         "df1d_persistent_kernel<float>, one launch per run")}
+
+    # plain FP64 comparator (one thread per node, one launch per step)
+    comparators = {}
+    if not args.no_fp64:
+        for kernel in ("plain", "persistent"):
+            h = H.Hygro(wl, precision="fp64", kernel=kernel, device=local, stream=stream.cuda_stream)
+            n = args.year_steps if kernel == "persistent" else args.year_steps // 4
+            with torch.cuda.stream(stream):
+                h.run(min(n, 2000))
+            torch.cuda.synchronize()
+            with torch.cuda.stream(stream):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                h.run(n)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            el = e0.elapsed_time(e1) / 1e3
+            comparators[f"fp64_{kernel}"] = {"value": wl.total_nodes * n / el, "unit": UNIT,
+                                             "steps_timed": n, "seconds": el}
+            h.close()
+        comparators["fp32_persistent_over_fp64_plain"] = value / world / comparators["fp64_plain"]["value"]
+
+    # end to end through the C ABI with host buffers: inputs H2D, run, samples and fluxes D2H
+    e2e = None
+    if not args.no_e2e:
+        import ctypes as C
+
+        lay = (H.hygro_layer * len(wl.layer_par))(*[H.hygro_layer(*map(float, r)) for r in wl.layer_par])
+        bcs = []
+        noise = [None if z is None else np.ascontiguousarray(z, np.float32) for z in wl.noise]
+        for f in range(2):
+            arr = (H.hygro_bc * wl.n_walls)()
+            for w in range(wl.n_walls):
+                b = arr[w]
+                b.kind = int(wl.bc_kind[w, f])
+                (b.hT, b.hM, b.q_inf, b.g_inf, b.T_mean, b.T_amp, b.P_mean, b.P_amp, b.period, b.phase_T,
+                 b.phase_P, b.noise_dt) = map(float, wl.bc_par[w, f])
+                if noise[f] is not None:
+                    b.noise = noise[f][w].ctypes.data
+                    b.noise_len = noise[f].shape[1]
+            bcs.append(arr)
+        nl = np.ascontiguousarray(wl.n_layers, np.int32)
+        lf = np.ascontiguousarray(wl.layer_first, np.int32)
+        Ti = np.ascontiguousarray(wl.T_init, np.float64)
+        Pi = np.ascontiguousarray(wl.P_init, np.float64)
+        se = 1440
+        samples = np.zeros((args.year_steps // se, wl.n_walls, 2, 2), np.float32)
+        flux = np.zeros((wl.n_walls, 2, 2))
+        cum = np.zeros((wl.n_walls, 2, 2))
+        h2d = (nl.nbytes + lf.nbytes + C.sizeof(lay) + Ti.nbytes + Pi.nbytes + sum(C.sizeof(a) for a in bcs)
+               + sum(z.nbytes for z in noise if z is not None))
+        d2h = samples.nbytes + flux.nbytes + cum.nbytes
+        k = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(k):
+            H.hygro_set_materials(g.ctx, nl, lf, lay, Ti, Pi)
+            H.hygro_set_bc(g.ctx, 0, bcs[0])
+            H.hygro_set_bc(g.ctx, 1, bcs[1])
+            H.hygro_run(g.ctx, args.year_steps, se, samples)
+            H.hygro_fluxes(g.ctx, flux, cum)
+        el = (time.perf_counter() - t) / k
+        el = reduce_max(pg, el)
+        e2e = {"value": units_total / el, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "seconds_per_step": el}
+    g.close()
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": (f"{wl.n_walls} ragged 1D walls per GPU (1-3 layers, 50-400 nodes), "
+                                        f"dt=600 s x {args.year_steps} steps (one year), FP32 persistent kernel"),
+                           "nodes_per_gpu": int(wl.total_nodes), "cell_updates_per_step": int(units_total),
+                           "l2": "flushed between timed runs (512 MB write)", "parallelism": f"replicas x{world}"},
+                "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,
+                "gpu_launches": args.steps, "clocks": cs.summary(), "parity_vs_oracle": parity,
+                "comparators": comparators, "wall_seconds_timed": t_wall}
+        print(json.dumps(line))
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * hygro: GB300 (sm_103a) library for the Dufort-Frankel (DF) explicit update
+ * of coupled heat and moisture transfer in porous building walls, after
+ * Gasparin, Berger, Dutykh & Mendes, "An improved explicit scheme for
+ * whole-building hygrothermal simulation" (arXiv:1703.10119).
+ *
+ * Problem (paper Sec. 2, [eq:HAM_equation2]): on each wall x in [0, L],
+ *     cM  dPv/dt            = d/dx( kM  dPv/dx )
+ *     cTT dT/dt + cTM dPv/dt = d/dx( kTT dT/dx + kTM dPv/dx )
+ * with coefficients re-evaluated at every step from the vapour pressure
+ * (affine form per layer, Psat = desc.Psat):
+ *     kM = kM0 (1 + a Pv/Psat), cM = cM0 (1 + b Pv/Psat),
+ *     kTT = kTT0 (1 + aT Pv/Psat), cTT = cTT0 (1 + bT Pv/Psat),
+ *     kTM = Lv kM, cTM = chi cM,
+ * Robin exchanges at both faces ([eq:HAM_BC]; fluxes positive INTO the wall)
+ *     g = hM (Pv_inf - Pv_s) + g_inf
+ *     q = hT (T_inf - T_s) + Lv hM (Pv_inf - Pv_s) + q_inf
+ * and a uniform initial state ([eq:HAM_ic]).
+ *
+ * Discretisation (Sec. 3.1 [eq:DF_NL], Appendix A [eq:DF_eq1], [eq:DF_eq2],
+ * [eq:ghost_node_v0], [eq:ghost_node_u0]): N uniform nodes per wall
+ * (node 0 at x = 0 = face 0, node N-1 at x = L = face 1, dx = L/(N-1)),
+ * three time levels; level n+1 follows from levels n and n-1 with the
+ * coefficients taken at level n, face values = arithmetic mean of the two
+ * nodes inside a layer and harmonic mean across a layer interface, the
+ * diagonal u_j^n replaced by (u_j^{n+1} + u_j^{n-1})/2, Pv advanced before
+ * T, surface nodes as half cells (the ghost-node form of Appendix A). The
+ * first step uses level -1 := level 0.
+ *
+ * Conventions of every call:
+ *   - returns a hygro_status and never throws across the ABI;
+ *   - validates its arguments before changing any state: a call that fails
+ *     with HYGRO_E_INVALID leaves the context as it was;
+ *   - inputs are copied (the caller keeps ownership of its arrays);
+ *   - output pointers may be host or device memory (device memory is
+ *     recognised with cudaPointerGetAttributes); with device outputs the
+ *     call is stream-ordered on the context's stream and returns after
+ *     enqueueing, with host outputs it returns when the data are there;
+ *   - calls on one context are not thread-safe; separate contexts are;
+ *   - hygro_last_error gives a readable message for the last failure.
+ * Walls are concatenated: the nodes of wall w occupy
+ * [node_offset(w), node_offset(w) + n_nodes[w]) in field arrays, with
+ * node_offset(w) = n_nodes[0] + ... + n_nodes[w-1].
+ */
+#ifndef HYGRO_H
+#define HYGRO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define HYGRO_API __attribute__((visibility("default")))
+#else
+#define HYGRO_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hygro_ctx hygro_ctx;   /* opaque, owned by the library */
+
+typedef enum {
+    HYGRO_OK = 0,
+    HYGRO_E_INVALID = -1,      /* bad argument; nothing changed */
+    HYGRO_E_NOMEM = -2,        /* host or device allocation failed */
+    HYGRO_E_CUDA = -3,         /* a CUDA call failed (message in hygro_last_error) */
+    HYGRO_E_STATE = -4,        /* call out of order (e.g. run before set_materials / set_bc) */
+    HYGRO_E_NONFINITE = -5,    /* a wall produced a NaN or infinity */
+    HYGRO_E_TIMEOUT = -6,      /* a bounded device wait gave up */
+    HYGRO_E_UNSUPPORTED = -7   /* valid request this build does not handle (e.g. N too large) */
+} hygro_status;
+
+enum { HYGRO_FP32 = 0, HYGRO_FP64 = 1 };
+
+/* How hygro_run advances the walls.
+ * PERSISTENT: one launch per hygro_run; each wall is owned by one warp that
+ *   keeps its two time levels in registers for the whole time loop (walls of
+ *   3..512 nodes).
+ * PLAIN: one thread per node, one launch per step, levels in global memory
+ *   (any N >= 3); the straightforward GPU form of the scheme. */
+enum { HYGRO_KERNEL_PERSISTENT = 0, HYGRO_KERNEL_PLAIN = 1 };
+
+enum { HYGRO_BC_AMBIENT = 0, HYGRO_BC_ADIABATIC = 1, HYGRO_BC_ROOM = 2 };
+
+/* Largest wall the persistent kernel accepts (32 lanes x 16 nodes). */
+#define HYGRO_PERSISTENT_MAX_NODES 512
+/* Largest number of layers in one wall. */
+#define HYGRO_MAX_LAYERS 8
+
+typedef struct {
+    int32_t n_walls;           /* >= 1 */
+    const int32_t *n_nodes;    /* [n_walls], each >= 3 (copied) */
+    const double *thickness;   /* [n_walls] metres, > 0 (copied) */
+    double dt;                 /* time step, seconds, > 0 */
+    double t0;                 /* time of level 0, seconds */
+    double Lv;                 /* latent heat of evaporation, J/kg */
+    double Psat;               /* saturation pressure of the coefficient laws, Pa, > 0 */
+    int32_t precision;         /* HYGRO_FP32 or HYGRO_FP64 */
+    int32_t kernel;            /* HYGRO_KERNEL_PERSISTENT or HYGRO_KERNEL_PLAIN */
+    int32_t device;            /* CUDA device ordinal */
+    void *stream;              /* cudaStream_t to run on, or NULL for the default stream */
+} hygro_desc;
+
+/* One material layer (paper Sec. 2 coefficient definitions, affine in Pv). */
+typedef struct {
+    double kM0, a;             /* moisture permeability kM0 (s) and its Pv slope */
+    double cM0, b;             /* moisture storage cM0 (s^2/m^2) and its Pv slope */
+    double kTT0, aT;           /* thermal conductivity (W/m/K) and its Pv slope */
+    double cTT0, bT;           /* volumetric heat capacity (J/m^3/K) and its Pv slope */
+    double chi;                /* cTM = chi * cM (J/kg/K) */
+} hygro_layer;
+
+/* One face of one wall ([eq:HAM_BC]). For HYGRO_BC_AMBIENT the air state is
+ *   T_inf(t)  = T_mean + T_amp sin(2 pi t/period + phase_T) + noise_T(t)
+ *   Pv_inf(t) = P_mean + P_amp sin(2 pi t/period + phase_P) + noise_P(t)
+ * (the sinusoid is dropped when period <= 0), noise(t) being the linear
+ * interpolation at t/noise_dt of the table noise[k][2] = (T, Pv), k = 0 ..
+ * noise_len-1, held at its end values outside it. HYGRO_BC_ROOM faces see
+ * the air of room `room` at level n (paper Sec. 5.2 [eq:wbse_tn_exp]).
+ * HYGRO_BC_ADIABATIC faces exchange nothing. */
+typedef struct {
+    int32_t kind;
+    int32_t room;
+    double hT, hM;             /* W/m^2/K, s/m */
+    double q_inf, g_inf;       /* extra heat (W/m^2) and moisture (kg/m^2/s) fluxes into the wall */
+    double T_mean, T_amp, P_mean, P_amp, period, phase_T, phase_P;
+    const float *noise;        /* host memory, [noise_len][2], or NULL (copied) */
+    int32_t noise_len;
+    double noise_dt;
+} hygro_bc;
+
+/* Create a context on desc->device. *out receives the context. */
+HYGRO_API hygro_status hygro_create(const hygro_desc *desc, hygro_ctx **out);
+
+/* Layer map, materials and uniform initial state ([eq:HAM_ic]).
+ *   n_layers[w] in 1..HYGRO_MAX_LAYERS; the layers of wall w are the next
+ *   n_layers[w] entries of layer_first / layers; layer_first holds the first
+ *   node of each layer (0 for the first layer, strictly increasing, < N).
+ * Resets both stored levels to (T_init[w], P_init[w]) and the step to 0.
+ * All arrays are host memory. */
+HYGRO_API hygro_status hygro_set_materials(hygro_ctx *ctx, const int32_t *n_layers, const int32_t *layer_first,
+                                 const hygro_layer *layers, const double *T_init, const double *P_init);
+
+/* Boundary description of one face (0: x = 0, 1: x = L) for every wall;
+ * bc[w] for w in 0..n_walls-1, host memory. */
+HYGRO_API hygro_status hygro_set_bc(hygro_ctx *ctx, int32_t face, const hygro_bc *bc);
+
+/* Advance n_steps DF steps (n_steps >= 0).
+ * samples: NULL, or [n_steps / sample_every][n_walls][2 faces][2] of float
+ *   (FP32 contexts) or double (FP64 contexts) receiving the surface (T, Pv)
+ *   at level n+1 after every sample_every-th step of this call;
+ *   samples_bytes must cover it. */
+HYGRO_API hygro_status hygro_run(hygro_ctx *ctx, int64_t n_steps, int32_t sample_every, void *samples,
+                       size_t samples_bytes);
+
+/* Wait for the context's stream; HYGRO_E_NONFINITE if any wall went
+ * non-finite in the runs since the last check. */
+HYGRO_API hygro_status hygro_sync(hygro_ctx *ctx);
+
+/* Surface fluxes into the wall of the last step, [n_walls][2 faces][2]
+ * (heat W/m^2, moisture kg/m^2/s), and their running sums over all steps
+ * of dt * flux (J/m^2, kg/m^2), accumulated in FP64. Either may be NULL. */
+HYGRO_API hygro_status hygro_fluxes(hygro_ctx *ctx, double *flux, double *cumulative);
+
+/* Stored levels as absolute values in FP64: level 0 is the newest (n),
+ * level 1 the previous (n-1). T and P hold sum(n_nodes) values each. */
+HYGRO_API hygro_status hygro_get_fields(hygro_ctx *ctx, int32_t level, double *T, double *P);
+
+/* Overwrite one stored level (absolute values, host or device memory). */
+HYGRO_API hygro_status hygro_set_fields(hygro_ctx *ctx, int32_t level, const double *T, const double *P);
+
+/* Index n of the newest stored level. */
+HYGRO_API hygro_status hygro_get_step(const hygro_ctx *ctx, int64_t *step);
+
+/* Checkpoint of the whole evolving state (levels, step, flux sums, room
+ * air). With buf == NULL, *bytes receives the size; otherwise *bytes must
+ * be at least that size. Restoring with hygro_set_state into a context
+ * created with the same description, materials and boundaries continues
+ * the run bit for bit. Host memory. */
+HYGRO_API hygro_status hygro_get_state(hygro_ctx *ctx, void *buf, size_t *bytes);
+HYGRO_API hygro_status hygro_set_state(hygro_ctx *ctx, const void *buf, size_t bytes);
+
+/* Message of the last failed call on ctx (or of the last failed
+ * hygro_create when ctx is NULL). Never NULL. */
+HYGRO_API const char *hygro_last_error(const hygro_ctx *ctx);
+
+/* Release everything the context owns. NULL is accepted. */
+HYGRO_API void hygro_destroy(hygro_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HYGRO_H */

@@ -1,0 +1,733 @@
+// C-ABI of the hygro library: argument validation, device layout of a batch
+// of walls, and the launches of the DF kernels (see include/hygro.h).
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hygro_internal.cuh"
+
+using namespace hygro;
+
+namespace {
+
+thread_local std::string g_create_error = "no error";
+
+struct RawBc {
+    hygro_bc bc;                 // noise pointer not kept
+    std::vector<float> noise;    // copied table [noise_len][2]
+};
+
+template <typename T>
+cudaError_t dalloc(T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc((void **)p, count * sizeof(T));
+}
+
+bool is_device_ptr(const void *p)
+{
+    if (p == nullptr) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+bool finite_nonneg(double x) { return std::isfinite(x) && x >= 0.0; }
+
+uint64_t turns_fixed(double x)
+{
+    // fraction of x in [0, 1) scaled by 2^64
+    double f = x - std::floor(x);
+    double s = std::ldexp(f, 64);
+    if (!(s < 18446744073709551616.0)) return 0;
+    if (s < 0) return 0;
+    return (uint64_t)s;
+}
+
+}  // namespace
+
+struct hygro_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int precision = HYGRO_FP32;
+    int kernel = HYGRO_KERNEL_PERSISTENT;
+    int W = 0;
+    int64_t total_nodes = 0;
+    double dt = 0, t0 = 0, Lv = 0, Psat = 0;
+    std::vector<int32_t> N;
+    std::vector<double> L;
+    std::vector<WallInfo> walls;
+    std::vector<double> Tref, Pref;
+    std::vector<int32_t> n_layers, layer_first;
+    std::vector<hygro_layer> layers;
+    std::vector<RawBc> bc[2];
+    bool have_materials = false, have_bc[2] = {false, false};
+    int64_t step = 0;
+    int cur = 0;
+    int grid_persistent = 1;
+    size_t real_size = 4;
+    std::string err = "no error";
+
+    // device
+    void *dT[2] = {nullptr, nullptr}, *dP[2] = {nullptr, nullptr};
+    WallInfo *d_walls = nullptr;
+    FaceInfo *d_faces = nullptr;
+    void *d_layer_tab = nullptr;
+    int32_t *d_layer_first = nullptr;
+    float2 *d_noise = nullptr;
+    size_t noise_cap = 0;
+    void *d_Tref = nullptr, *d_Pref = nullptr;
+    double *d_cumul = nullptr, *d_flast = nullptr;
+    int32_t *d_nonfinite = nullptr;
+    int32_t *d_order = nullptr;
+    int32_t *d_counter = nullptr;
+    int32_t *d_node_wall = nullptr;
+    int8_t *d_node_layer = nullptr;
+    void *d_samples = nullptr;
+    size_t samples_cap = 0;
+};
+
+namespace {
+
+hygro_status fail(hygro_ctx *c, hygro_status st, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c)
+        c->err = buf;
+    else
+        g_create_error = buf;
+    return st;
+}
+
+#define CUDA_TRY(ctx, call)                                                                              \
+    do {                                                                                                 \
+        cudaError_t e_ = (call);                                                                         \
+        if (e_ != cudaSuccess) return fail(ctx, HYGRO_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+void free_all(hygro_ctx *c)
+{
+    void *ptrs[] = {c->dT[0], c->dT[1], c->dP[0], c->dP[1], c->d_walls, c->d_faces, c->d_layer_tab,
+                    c->d_layer_first, c->d_noise, c->d_Tref, c->d_Pref, c->d_cumul, c->d_flast,
+                    c->d_nonfinite, c->d_order, c->d_counter, c->d_node_wall, c->d_node_layer, c->d_samples};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+template <typename real>
+DevCtx<real> make_dev(const hygro_ctx *c)
+{
+    DevCtx<real> d;
+    d.walls = c->d_walls;
+    d.faces = c->d_faces;
+    d.layer_tab = (const real *)c->d_layer_tab;
+    d.layer_first = c->d_layer_first;
+    d.noise = c->d_noise;
+    d.T[0] = (real *)c->dT[0];
+    d.T[1] = (real *)c->dT[1];
+    d.P[0] = (real *)c->dP[0];
+    d.P[1] = (real *)c->dP[1];
+    d.cur = c->cur;
+    d.W = c->W;
+    d.Tref = (const real *)c->d_Tref;
+    d.Pref = (const real *)c->d_Pref;
+    d.cumul = c->d_cumul;
+    d.flast = c->d_flast;
+    d.nonfinite = c->d_nonfinite;
+    d.order = c->d_order;
+    d.node_wall = c->d_node_wall;
+    d.node_layer = c->d_node_layer;
+    d.total_nodes = (int32_t)c->total_nodes;
+    d.dt = c->dt;
+    d.t0 = c->t0;
+    d.Lv = c->Lv;
+    return d;
+}
+
+// Device copy of one real-typed host vector of doubles.
+hygro_status upload_reals(hygro_ctx *c, void *dst, const std::vector<double> &src)
+{
+    if (c->precision == HYGRO_FP64) {
+        CUDA_TRY(c, cudaMemcpy(dst, src.data(), src.size() * sizeof(double), cudaMemcpyHostToDevice));
+    } else {
+        std::vector<float> f(src.size());
+        for (size_t i = 0; i < src.size(); ++i) f[i] = (float)src[i];
+        CUDA_TRY(c, cudaMemcpy(dst, f.data(), f.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    return HYGRO_OK;
+}
+
+hygro_status download_reals(hygro_ctx *c, const void *src, std::vector<double> &dst)
+{
+    if (c->precision == HYGRO_FP64) {
+        CUDA_TRY(c, cudaMemcpy(dst.data(), src, dst.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    } else {
+        std::vector<float> f(dst.size());
+        CUDA_TRY(c, cudaMemcpy(f.data(), src, f.size() * sizeof(float), cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < f.size(); ++i) dst[i] = (double)f[i];
+    }
+    return HYGRO_OK;
+}
+
+// Face descriptors in the deviation variables of each wall; needs the
+// materials (for T_ref, P_ref) and both faces.
+hygro_status upload_faces(hygro_ctx *c)
+{
+    if (!(c->have_materials && c->have_bc[0] && c->have_bc[1])) return HYGRO_OK;
+    const int W = c->W;
+    std::vector<FaceInfo> fi((size_t)W * 2);
+    size_t total_noise = 0;
+    for (int f = 0; f < 2; ++f)
+        for (int w = 0; w < W; ++w) total_noise += c->bc[f][w].noise.size() / 2;
+    std::vector<float2> noise(total_noise > 0 ? total_noise : 1);
+    size_t off = 0;
+    for (int w = 0; w < W; ++w)
+        for (int f = 0; f < 2; ++f) {
+            const RawBc &r = c->bc[f][w];
+            const hygro_bc &b = r.bc;
+            FaceInfo &o = fi[(size_t)w * 2 + f];
+            memset(&o, 0, sizeof o);
+            o.kind = b.kind;
+            o.room = b.room;
+            if (b.kind == HYGRO_BC_ADIABATIC) continue;
+            o.hT = b.hT;
+            o.hM = b.hM;
+            o.q_inf = b.q_inf;
+            o.g_inf = b.g_inf;
+            o.T_mean_dev = b.T_mean - c->Tref[w];
+            o.T_amp = b.T_amp;
+            o.P_mean_dev = b.P_mean - c->Pref[w];
+            o.P_amp = b.P_amp;
+            o.period = b.period;
+            o.phase_T = b.phase_T;
+            o.phase_P = b.phase_P;
+            o.noise_dt = b.noise_dt;
+            const double two_pi = 6.283185307179586476925286766559;
+            if (b.period > 0) {
+                o.phT0 = turns_fixed(c->t0 / b.period + b.phase_T / two_pi);
+                o.phP0 = turns_fixed(c->t0 / b.period + b.phase_P / two_pi);
+                o.pstep = turns_fixed(c->dt / b.period);
+            }
+            const int64_t nl = (int64_t)r.noise.size() / 2;
+            if (nl > 0) {
+                o.noise_len = (int32_t)nl;
+                o.noise_off = (int64_t)off;
+                for (int64_t k = 0; k < nl; ++k) noise[off + k] = make_float2(r.noise[2 * k], r.noise[2 * k + 1]);
+                off += (size_t)nl;
+                o.npos0 = (int64_t)std::llround(std::ldexp(c->t0 / b.noise_dt, 40));
+                o.nstep = (int64_t)std::llround(std::ldexp(c->dt / b.noise_dt, 40));
+            }
+        }
+    if (noise.size() > c->noise_cap) {
+        if (c->d_noise) cudaFree(c->d_noise);
+        c->d_noise = nullptr;
+        c->noise_cap = 0;
+        CUDA_TRY(c, dalloc(&c->d_noise, noise.size()));
+        c->noise_cap = noise.size();
+    }
+    CUDA_TRY(c, cudaMemcpy(c->d_noise, noise.data(), noise.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(c->d_faces, fi.data(), fi.size() * sizeof(FaceInfo), cudaMemcpyHostToDevice));
+    return HYGRO_OK;
+}
+
+hygro_status check_nonfinite(hygro_ctx *c)
+{
+    int32_t flag = 0;
+    CUDA_TRY(c, cudaMemcpyAsync(&flag, c->d_nonfinite, sizeof flag, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (flag) {
+        CUDA_TRY(c, cudaMemsetAsync(c->d_nonfinite, 0, sizeof(int32_t), c->stream));
+        return fail(c, HYGRO_E_NONFINITE, "a wall produced a non-finite value");
+    }
+    return HYGRO_OK;
+}
+
+const uint64_t kStateMagic = 0x6879677273746174ull;  // "hygrstat"
+
+}  // namespace
+
+extern "C" {
+
+hygro_status hygro_create(const hygro_desc *desc, hygro_ctx **out)
+{
+    if (out == nullptr) return fail(nullptr, HYGRO_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (desc == nullptr) return fail(nullptr, HYGRO_E_INVALID, "desc is NULL");
+    if (desc->n_walls < 1) return fail(nullptr, HYGRO_E_INVALID, "n_walls must be >= 1");
+    if (desc->n_nodes == nullptr || desc->thickness == nullptr)
+        return fail(nullptr, HYGRO_E_INVALID, "n_nodes and thickness are required");
+    if (!(std::isfinite(desc->dt) && desc->dt > 0)) return fail(nullptr, HYGRO_E_INVALID, "dt must be > 0");
+    if (!std::isfinite(desc->t0)) return fail(nullptr, HYGRO_E_INVALID, "t0 must be finite");
+    if (!(std::isfinite(desc->Psat) && desc->Psat > 0)) return fail(nullptr, HYGRO_E_INVALID, "Psat must be > 0");
+    if (!std::isfinite(desc->Lv)) return fail(nullptr, HYGRO_E_INVALID, "Lv must be finite");
+    if (desc->precision != HYGRO_FP32 && desc->precision != HYGRO_FP64)
+        return fail(nullptr, HYGRO_E_INVALID, "precision must be HYGRO_FP32 or HYGRO_FP64");
+    if (desc->kernel != HYGRO_KERNEL_PERSISTENT && desc->kernel != HYGRO_KERNEL_PLAIN)
+        return fail(nullptr, HYGRO_E_INVALID, "unknown kernel %d", desc->kernel);
+    int64_t total = 0;
+    for (int w = 0; w < desc->n_walls; ++w) {
+        if (desc->n_nodes[w] < 3) return fail(nullptr, HYGRO_E_INVALID, "wall %d: n_nodes must be >= 3", w);
+        if (!(std::isfinite(desc->thickness[w]) && desc->thickness[w] > 0))
+            return fail(nullptr, HYGRO_E_INVALID, "wall %d: thickness must be > 0", w);
+        if (desc->kernel == HYGRO_KERNEL_PERSISTENT && desc->n_nodes[w] > HYGRO_PERSISTENT_MAX_NODES)
+            return fail(nullptr, HYGRO_E_UNSUPPORTED, "wall %d: %d nodes exceed the persistent kernel's %d", w,
+                        desc->n_nodes[w], HYGRO_PERSISTENT_MAX_NODES);
+        total += desc->n_nodes[w];
+    }
+    if (total > (int64_t)INT32_MAX / 2) return fail(nullptr, HYGRO_E_UNSUPPORTED, "too many nodes in total");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return fail(nullptr, HYGRO_E_CUDA, "no CUDA device available");
+    }
+    if (desc->device < 0 || desc->device >= ndev) return fail(nullptr, HYGRO_E_INVALID, "bad device %d", desc->device);
+
+    hygro_ctx *c = new (std::nothrow) hygro_ctx();
+    if (c == nullptr) return fail(nullptr, HYGRO_E_NOMEM, "host allocation failed");
+    c->device = desc->device;
+    c->stream = (cudaStream_t)desc->stream;
+    c->precision = desc->precision;
+    c->kernel = desc->kernel;
+    c->W = desc->n_walls;
+    c->dt = desc->dt;
+    c->t0 = desc->t0;
+    c->Lv = desc->Lv;
+    c->Psat = desc->Psat;
+    c->real_size = desc->precision == HYGRO_FP64 ? 8 : 4;
+    c->N.assign(desc->n_nodes, desc->n_nodes + desc->n_walls);
+    c->L.assign(desc->thickness, desc->thickness + desc->n_walls);
+    c->total_nodes = total;
+    c->walls.resize(c->W);
+    int64_t off = 0;
+    for (int w = 0; w < c->W; ++w) {
+        WallInfo &wi = c->walls[w];
+        memset(&wi, 0, sizeof wi);
+        wi.N = c->N[w];
+        wi.K = (wi.N + 31) / 32;
+        wi.Wl = (wi.N + wi.K - 1) / wi.K;
+        wi.m = wi.Wl * wi.K - wi.N;
+        wi.node_off = (int32_t)off;
+        off += wi.N;
+    }
+    hygro_status st = HYGRO_OK;
+    auto bail = [&](hygro_status s) {
+        g_create_error = c->err;
+        free_all(c);
+        delete c;
+        return s;
+    };
+#define CREATE_TRY(call)                                                                          \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess) {                                                                  \
+            fail(c, e_ == cudaErrorMemoryAllocation ? HYGRO_E_NOMEM : HYGRO_E_CUDA, "%s: %s", #call, \
+                 cudaGetErrorString(e_));                                                         \
+            return bail(e_ == cudaErrorMemoryAllocation ? HYGRO_E_NOMEM : HYGRO_E_CUDA);          \
+        }                                                                                         \
+    } while (0)
+    CREATE_TRY(cudaSetDevice(c->device));
+    const size_t rs = c->real_size;
+    for (int i = 0; i < 2; ++i) {
+        CREATE_TRY(cudaMalloc(&c->dT[i], (size_t)total * rs));
+        CREATE_TRY(cudaMalloc(&c->dP[i], (size_t)total * rs));
+        CREATE_TRY(cudaMemset(c->dT[i], 0, (size_t)total * rs));
+        CREATE_TRY(cudaMemset(c->dP[i], 0, (size_t)total * rs));
+    }
+    CREATE_TRY(dalloc(&c->d_walls, c->W));
+    CREATE_TRY(dalloc(&c->d_faces, (size_t)c->W * 2));
+    CREATE_TRY(cudaMalloc(&c->d_Tref, (size_t)c->W * rs));
+    CREATE_TRY(cudaMalloc(&c->d_Pref, (size_t)c->W * rs));
+    CREATE_TRY(dalloc(&c->d_cumul, (size_t)c->W * 4));
+    CREATE_TRY(dalloc(&c->d_flast, (size_t)c->W * 4));
+    CREATE_TRY(cudaMemset(c->d_cumul, 0, (size_t)c->W * 4 * sizeof(double)));
+    CREATE_TRY(cudaMemset(c->d_flast, 0, (size_t)c->W * 4 * sizeof(double)));
+    CREATE_TRY(dalloc(&c->d_nonfinite, 1));
+    CREATE_TRY(cudaMemset(c->d_nonfinite, 0, sizeof(int32_t)));
+    CREATE_TRY(dalloc(&c->d_counter, 1));
+    CREATE_TRY(dalloc(&c->d_order, c->W));
+    CREATE_TRY(dalloc(&c->d_node_wall, (size_t)total));
+    CREATE_TRY(dalloc(&c->d_node_layer, (size_t)total));
+    CREATE_TRY(cudaMemset(c->d_node_layer, 0, (size_t)total));
+    {
+        std::vector<int32_t> nw((size_t)total);
+        for (int w = 0; w < c->W; ++w)
+            for (int j = 0; j < c->N[w]; ++j) nw[(size_t)c->walls[w].node_off + j] = w;
+        CREATE_TRY(cudaMemcpy(c->d_node_wall, nw.data(), nw.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        // persistent work queue: most nodes per lane first, then most nodes
+        std::vector<int32_t> order(c->W);
+        for (int w = 0; w < c->W; ++w) order[w] = w;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            if (c->walls[a].K != c->walls[b].K) return c->walls[a].K > c->walls[b].K;
+            return c->walls[a].N > c->walls[b].N;
+        });
+        CREATE_TRY(cudaMemcpy(c->d_order, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
+    {
+        int sms = 0, per_sm = 0;
+        CREATE_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+        CREATE_TRY(c->precision == HYGRO_FP64 ? occupancy_persistent_f64(&per_sm) : occupancy_persistent_f32(&per_sm));
+        if (per_sm < 1) per_sm = 1;
+        const int need = (c->W + kWarpsPerBlock - 1) / kWarpsPerBlock;
+        c->grid_persistent = std::max(1, std::min(need, sms * per_sm));
+    }
+#undef CREATE_TRY
+    (void)st;
+    *out = c;
+    return HYGRO_OK;
+}
+
+hygro_status hygro_set_materials(hygro_ctx *c, const int32_t *n_layers, const int32_t *layer_first,
+                                 const hygro_layer *layers, const double *T_init, const double *P_init)
+{
+    if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    if (!n_layers || !layer_first || !layers || !T_init || !P_init)
+        return fail(c, HYGRO_E_INVALID, "n_layers, layer_first, layers, T_init and P_init are required");
+    const int W = c->W;
+    size_t total_layers = 0;
+    for (int w = 0; w < W; ++w) {
+        const int nl = n_layers[w];
+        if (nl < 1 || nl > HYGRO_MAX_LAYERS)
+            return fail(c, HYGRO_E_INVALID, "wall %d: n_layers must be in 1..%d", w, HYGRO_MAX_LAYERS);
+        const int32_t *lf = layer_first + total_layers;
+        if (lf[0] != 0) return fail(c, HYGRO_E_INVALID, "wall %d: the first layer must start at node 0", w);
+        for (int l = 1; l < nl; ++l)
+            if (lf[l] <= lf[l - 1] || lf[l] >= c->N[w])
+                return fail(c, HYGRO_E_INVALID, "wall %d: layer_first must increase and stay below N", w);
+        for (int l = 0; l < nl; ++l) {
+            const hygro_layer &y = layers[total_layers + l];
+            if (!(y.kM0 > 0 && y.cM0 > 0 && y.kTT0 > 0 && y.cTT0 > 0) || !std::isfinite(y.kM0) ||
+                !std::isfinite(y.cM0) || !std::isfinite(y.kTT0) || !std::isfinite(y.cTT0) || !std::isfinite(y.a) ||
+                !std::isfinite(y.b) || !std::isfinite(y.aT) || !std::isfinite(y.bT) || !std::isfinite(y.chi))
+                return fail(c, HYGRO_E_INVALID, "wall %d layer %d: coefficients must be finite, kM0, cM0, kTT0, cTT0 > 0",
+                            w, l);
+        }
+        if (!std::isfinite(T_init[w]) || !std::isfinite(P_init[w]))
+            return fail(c, HYGRO_E_INVALID, "wall %d: initial state must be finite", w);
+        total_layers += nl;
+    }
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->n_layers.assign(n_layers, n_layers + W);
+    c->layer_first.assign(layer_first, layer_first + total_layers);
+    c->layers.assign(layers, layers + total_layers);
+    c->Tref.assign(T_init, T_init + W);
+    c->Pref.assign(P_init, P_init + W);
+
+    std::vector<double> tab(total_layers * kLayerStride, 0.0);
+    std::vector<int8_t> node_layer((size_t)c->total_nodes, 0);
+    size_t lo = 0;
+    for (int w = 0; w < W; ++w) {
+        WallInfo &wi = c->walls[w];
+        wi.n_layers = n_layers[w];
+        wi.layer_off = (int32_t)lo;
+        const double dx = c->L[w] / (double)(c->N[w] - 1);
+        const double Ps = c->Psat, Pr = c->Pref[w], dt = c->dt;
+        for (int l = 0; l < wi.n_layers; ++l) {
+            const hygro_layer &y = layers[lo + l];
+            double *t = &tab[(lo + l) * kLayerStride];
+            t[LT_KMA] = y.kM0 * (1.0 + y.a * Pr / Ps) / (2.0 * dx);
+            t[LT_KMB] = y.kM0 * y.a / Ps / (2.0 * dx);
+            t[LT_KTA] = y.kTT0 * (1.0 + y.aT * Pr / Ps) / (2.0 * dx);
+            t[LT_KTB] = y.kTT0 * y.aT / Ps / (2.0 * dx);
+            t[LT_AA] = dx * y.cM0 * (1.0 + y.b * Pr / Ps) / (2.0 * dt);
+            t[LT_AB] = dx * y.cM0 * y.b / Ps / (2.0 * dt);
+            t[LT_BA] = dx * y.cTT0 * (1.0 + y.bT * Pr / Ps) / (2.0 * dt);
+            t[LT_BB] = dx * y.cTT0 * y.bT / Ps / (2.0 * dt);
+            t[LT_CHI] = y.chi;
+            const int j0 = layer_first[lo + l];
+            const int j1 = l + 1 < wi.n_layers ? layer_first[lo + l + 1] : c->N[w];
+            for (int j = j0; j < j1; ++j) node_layer[(size_t)wi.node_off + j] = (int8_t)l;
+        }
+        lo += wi.n_layers;
+    }
+    if (c->d_layer_tab) cudaFree(c->d_layer_tab);
+    if (c->d_layer_first) cudaFree(c->d_layer_first);
+    c->d_layer_tab = nullptr;
+    c->d_layer_first = nullptr;
+    CUDA_TRY(c, cudaMalloc(&c->d_layer_tab, std::max<size_t>(1, tab.size()) * c->real_size));
+    CUDA_TRY(c, dalloc(&c->d_layer_first, total_layers));
+    hygro_status st = upload_reals(c, c->d_layer_tab, tab);
+    if (st != HYGRO_OK) return st;
+    CUDA_TRY(c, cudaMemcpy(c->d_layer_first, layer_first, total_layers * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(c->d_node_layer, node_layer.data(), node_layer.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(c->d_walls, c->walls.data(), c->walls.size() * sizeof(WallInfo), cudaMemcpyHostToDevice));
+    if ((st = upload_reals(c, c->d_Tref, c->Tref)) != HYGRO_OK) return st;
+    if ((st = upload_reals(c, c->d_Pref, c->Pref)) != HYGRO_OK) return st;
+    // uniform initial state: zero deviation at both levels, step 0, no accumulated flux
+    for (int i = 0; i < 2; ++i) {
+        CUDA_TRY(c, cudaMemset(c->dT[i], 0, (size_t)c->total_nodes * c->real_size));
+        CUDA_TRY(c, cudaMemset(c->dP[i], 0, (size_t)c->total_nodes * c->real_size));
+    }
+    CUDA_TRY(c, cudaMemset(c->d_cumul, 0, (size_t)W * 4 * sizeof(double)));
+    CUDA_TRY(c, cudaMemset(c->d_flast, 0, (size_t)W * 4 * sizeof(double)));
+    c->step = 0;
+    c->cur = 0;
+    c->have_materials = true;
+    return upload_faces(c);
+}
+
+hygro_status hygro_set_bc(hygro_ctx *c, int32_t face, const hygro_bc *bc)
+{
+    if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    if (face != 0 && face != 1) return fail(c, HYGRO_E_INVALID, "face must be 0 or 1");
+    if (bc == nullptr) return fail(c, HYGRO_E_INVALID, "bc is NULL");
+    for (int w = 0; w < c->W; ++w) {
+        const hygro_bc &b = bc[w];
+        if (b.kind == HYGRO_BC_ROOM)
+            return fail(c, HYGRO_E_UNSUPPORTED, "wall %d face %d: room faces need hygro_set_rooms", w, face);
+        if (b.kind != HYGRO_BC_AMBIENT && b.kind != HYGRO_BC_ADIABATIC)
+            return fail(c, HYGRO_E_INVALID, "wall %d face %d: unknown kind %d", w, face, b.kind);
+        if (b.kind == HYGRO_BC_ADIABATIC) continue;
+        if (!finite_nonneg(b.hT) || !finite_nonneg(b.hM))
+            return fail(c, HYGRO_E_INVALID, "wall %d face %d: hT and hM must be finite and >= 0", w, face);
+        const double v[] = {b.q_inf, b.g_inf, b.T_mean, b.T_amp, b.P_mean, b.P_amp, b.phase_T, b.phase_P};
+        for (double x : v)
+            if (!std::isfinite(x)) return fail(c, HYGRO_E_INVALID, "wall %d face %d: non-finite value", w, face);
+        if (!finite_nonneg(b.period)) return fail(c, HYGRO_E_INVALID, "wall %d face %d: period must be >= 0", w, face);
+        if (b.noise_len < 0) return fail(c, HYGRO_E_INVALID, "wall %d face %d: noise_len < 0", w, face);
+        if (b.noise_len > 0) {
+            if (b.noise == nullptr) return fail(c, HYGRO_E_INVALID, "wall %d face %d: noise is NULL", w, face);
+            if (!(std::isfinite(b.noise_dt) && b.noise_dt > 0))
+                return fail(c, HYGRO_E_INVALID, "wall %d face %d: noise_dt must be > 0", w, face);
+            if (b.noise_len > (1 << 22) || std::fabs(c->t0 / b.noise_dt) > 4.0e6 || c->dt / b.noise_dt > 4.0e6)
+                return fail(c, HYGRO_E_UNSUPPORTED, "wall %d face %d: noise table too long for its time step", w,
+                            face);
+            for (int64_t k = 0; k < 2 * (int64_t)b.noise_len; ++k)
+                if (!std::isfinite(b.noise[k])) return fail(c, HYGRO_E_INVALID, "wall %d face %d: non-finite noise", w, face);
+        }
+    }
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    std::vector<RawBc> v(c->W);
+    for (int w = 0; w < c->W; ++w) {
+        v[w].bc = bc[w];
+        v[w].bc.noise = nullptr;
+        if (bc[w].kind == HYGRO_BC_AMBIENT && bc[w].noise_len > 0)
+            v[w].noise.assign(bc[w].noise, bc[w].noise + 2 * (size_t)bc[w].noise_len);
+    }
+    c->bc[face].swap(v);
+    c->have_bc[face] = true;
+    return upload_faces(c);
+}
+
+hygro_status hygro_run(hygro_ctx *c, int64_t n_steps, int32_t sample_every, void *samples, size_t samples_bytes)
+{
+    if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    if (n_steps < 0) return fail(c, HYGRO_E_INVALID, "n_steps must be >= 0");
+    if (samples != nullptr && sample_every < 1) return fail(c, HYGRO_E_INVALID, "sample_every must be >= 1");
+    if (!(c->have_materials && c->have_bc[0] && c->have_bc[1]))
+        return fail(c, HYGRO_E_STATE, "hygro_set_materials and hygro_set_bc (both faces) must come first");
+    const int64_t n_samples = samples ? n_steps / sample_every : 0;
+    const size_t need = (size_t)n_samples * c->W * 4 * c->real_size;
+    if (samples != nullptr && samples_bytes < need)
+        return fail(c, HYGRO_E_INVALID, "samples_bytes %zu < %zu needed", samples_bytes, need);
+    if (n_steps == 0) return HYGRO_OK;
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
+
+    const bool host_samples = samples != nullptr && n_samples > 0 && !is_device_ptr(samples);
+    void *dsamp = samples;
+    if (host_samples) {
+        if (need > c->samples_cap) {
+            if (c->d_samples) cudaFree(c->d_samples);
+            c->d_samples = nullptr;
+            c->samples_cap = 0;
+            CUDA_TRY(c, cudaMalloc(&c->d_samples, need));
+            c->samples_cap = need;
+        }
+        dsamp = c->d_samples;
+    }
+    if (n_samples == 0) dsamp = nullptr;
+    const int se = samples ? sample_every : 0;
+
+    if (c->kernel == HYGRO_KERNEL_PERSISTENT) {
+        // chunks of whole sampling periods below 2^30 steps
+        int64_t chunk = int64_t(1) << 30;
+        if (se > 0) chunk -= chunk % se;
+        int64_t done = 0;
+        while (done < n_steps) {
+            const int64_t len = std::min(chunk, n_steps - done);
+            const size_t soff = se > 0 ? (size_t)(done / se) * c->W * 4 : 0;
+            CUDA_TRY(c, cudaMemsetAsync(c->d_counter, 0, sizeof(int32_t), c->stream));
+            if (c->precision == HYGRO_FP64)
+                CUDA_TRY(c, launch_persistent_f64(make_dev<double>(c), c->step + done, (int32_t)len, se,
+                                                  dsamp ? (double *)dsamp + soff : nullptr, c->d_counter,
+                                                  c->grid_persistent, c->stream));
+            else
+                CUDA_TRY(c, launch_persistent_f32(make_dev<float>(c), c->step + done, (int32_t)len, se,
+                                                  dsamp ? (float *)dsamp + soff : nullptr, c->d_counter,
+                                                  c->grid_persistent, c->stream));
+            done += len;
+        }
+    } else {
+        for (int64_t s = 0; s < n_steps; ++s) {
+            const int32_t sidx = (se > 0 && (s + 1) % se == 0) ? (int32_t)((s + 1) / se - 1) : -1;
+            if (c->precision == HYGRO_FP64)
+                CUDA_TRY(c, launch_plain_step_f64(make_dev<double>(c), c->step + s, sidx, (double *)dsamp, c->stream));
+            else
+                CUDA_TRY(c, launch_plain_step_f32(make_dev<float>(c), c->step + s, sidx, (float *)dsamp, c->stream));
+            c->cur = 1 - c->cur;
+        }
+    }
+    c->step += n_steps;
+    if (host_samples) {
+        CUDA_TRY(c, cudaMemcpyAsync(samples, dsamp, need, cudaMemcpyDeviceToHost, c->stream));
+        return check_nonfinite(c);
+    }
+    return HYGRO_OK;
+}
+
+hygro_status hygro_sync(hygro_ctx *c)
+{
+    if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
+    return check_nonfinite(c);
+}
+
+hygro_status hygro_fluxes(hygro_ctx *c, double *flux, double *cumulative)
+{
+    if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
+    const size_t bytes = (size_t)c->W * 4 * sizeof(double);
+    if (flux) CUDA_TRY(c, cudaMemcpyAsync(flux, c->d_flast, bytes, cudaMemcpyDefault, c->stream));
+    if (cumulative) CUDA_TRY(c, cudaMemcpyAsync(cumulative, c->d_cumul, bytes, cudaMemcpyDefault, c->stream));
+    return check_nonfinite(c);
+}
+
+hygro_status hygro_get_fields(hygro_ctx *c, int32_t level, double *T, double *P)
+{
+    if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    if (level != 0 && level != 1) return fail(c, HYGRO_E_INVALID, "level must be 0 (n) or 1 (n-1)");
+    if (!c->have_materials) return fail(c, HYGRO_E_STATE, "hygro_set_materials must come first");
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const int buf = level == 0 ? c->cur : 1 - c->cur;
+    std::vector<double> v((size_t)c->total_nodes);
+    for (int f = 0; f < 2; ++f) {
+        double *dst = f == 0 ? T : P;
+        if (dst == nullptr) continue;
+        hygro_status st = download_reals(c, f == 0 ? c->dT[buf] : c->dP[buf], v);
+        if (st != HYGRO_OK) return st;
+        const std::vector<double> &ref = f == 0 ? c->Tref : c->Pref;
+        for (int w = 0; w < c->W; ++w)
+            for (int j = 0; j < c->N[w]; ++j) v[(size_t)c->walls[w].node_off + j] += ref[w];
+        CUDA_TRY(c, cudaMemcpy(dst, v.data(), v.size() * sizeof(double), cudaMemcpyDefault));
+    }
+    return check_nonfinite(c);
+}
+
+hygro_status hygro_set_fields(hygro_ctx *c, int32_t level, const double *T, const double *P)
+{
+    if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    if (level != 0 && level != 1) return fail(c, HYGRO_E_INVALID, "level must be 0 (n) or 1 (n-1)");
+    if (!c->have_materials) return fail(c, HYGRO_E_STATE, "hygro_set_materials must come first");
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
+    std::vector<double> v[2];
+    for (int f = 0; f < 2; ++f) {
+        const double *src = f == 0 ? T : P;
+        if (src == nullptr) continue;
+        v[f].resize((size_t)c->total_nodes);
+        CUDA_TRY(c, cudaMemcpy(v[f].data(), src, v[f].size() * sizeof(double), cudaMemcpyDefault));
+        for (double x : v[f])
+            if (!std::isfinite(x)) return fail(c, HYGRO_E_INVALID, "non-finite field value");
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const int buf = level == 0 ? c->cur : 1 - c->cur;
+    for (int f = 0; f < 2; ++f) {
+        if (v[f].empty()) continue;
+        const std::vector<double> &ref = f == 0 ? c->Tref : c->Pref;
+        for (int w = 0; w < c->W; ++w)
+            for (int j = 0; j < c->N[w]; ++j) v[f][(size_t)c->walls[w].node_off + j] -= ref[w];
+        hygro_status st = upload_reals(c, f == 0 ? c->dT[buf] : c->dP[buf], v[f]);
+        if (st != HYGRO_OK) return st;
+    }
+    return HYGRO_OK;
+}
+
+hygro_status hygro_get_step(const hygro_ctx *c, int64_t *step)
+{
+    if (c == nullptr || step == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx or step is NULL");
+    *step = c->step;
+    return HYGRO_OK;
+}
+
+// State image: magic, precision, walls, nodes, step | T[n], T[n-1], P[n], P[n-1] (working precision) | cumul,
+// flast (FP64).
+hygro_status hygro_get_state(hygro_ctx *c, void *buf, size_t *bytes)
+{
+    if (c == nullptr || bytes == nullptr) return fail(c, HYGRO_E_INVALID, "ctx or bytes is NULL");
+    const size_t nf = (size_t)c->total_nodes * c->real_size;
+    const size_t need = 5 * sizeof(int64_t) + 4 * nf + 2 * (size_t)c->W * 4 * sizeof(double);
+    if (buf == nullptr) {
+        *bytes = need;
+        return HYGRO_OK;
+    }
+    if (*bytes < need) return fail(c, HYGRO_E_INVALID, "state buffer too small (%zu < %zu)", *bytes, need);
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    char *p = (char *)buf;
+    const int64_t hdr[5] = {(int64_t)kStateMagic, c->precision, c->W, c->total_nodes, c->step};
+    memcpy(p, hdr, sizeof hdr);
+    p += sizeof hdr;
+    void *src[4] = {c->dT[c->cur], c->dT[1 - c->cur], c->dP[c->cur], c->dP[1 - c->cur]};
+    for (void *s : src) {
+        CUDA_TRY(c, cudaMemcpy(p, s, nf, cudaMemcpyDeviceToHost));
+        p += nf;
+    }
+    CUDA_TRY(c, cudaMemcpy(p, c->d_cumul, (size_t)c->W * 4 * sizeof(double), cudaMemcpyDeviceToHost));
+    p += (size_t)c->W * 4 * sizeof(double);
+    CUDA_TRY(c, cudaMemcpy(p, c->d_flast, (size_t)c->W * 4 * sizeof(double), cudaMemcpyDeviceToHost));
+    *bytes = need;
+    return HYGRO_OK;
+}
+
+hygro_status hygro_set_state(hygro_ctx *c, const void *buf, size_t bytes)
+{
+    if (c == nullptr || buf == nullptr) return fail(c, HYGRO_E_INVALID, "ctx or buf is NULL");
+    const size_t nf = (size_t)c->total_nodes * c->real_size;
+    const size_t need = 5 * sizeof(int64_t) + 4 * nf + 2 * (size_t)c->W * 4 * sizeof(double);
+    if (bytes < need) return fail(c, HYGRO_E_INVALID, "state image too small");
+    int64_t hdr[5];
+    memcpy(hdr, buf, sizeof hdr);
+    if (hdr[0] != (int64_t)kStateMagic || hdr[1] != c->precision || hdr[2] != c->W || hdr[3] != c->total_nodes)
+        return fail(c, HYGRO_E_INVALID, "state image does not match this context");
+    if (!c->have_materials) return fail(c, HYGRO_E_STATE, "hygro_set_materials must come first");
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    const char *p = (const char *)buf + sizeof hdr;
+    c->cur = 0;
+    void *dst[4] = {c->dT[0], c->dT[1], c->dP[0], c->dP[1]};
+    for (void *d : dst) {
+        CUDA_TRY(c, cudaMemcpy(d, p, nf, cudaMemcpyHostToDevice));
+        p += nf;
+    }
+    CUDA_TRY(c, cudaMemcpy(c->d_cumul, p, (size_t)c->W * 4 * sizeof(double), cudaMemcpyHostToDevice));
+    p += (size_t)c->W * 4 * sizeof(double);
+    CUDA_TRY(c, cudaMemcpy(c->d_flast, p, (size_t)c->W * 4 * sizeof(double), cudaMemcpyHostToDevice));
+    c->step = hdr[4];
+    return HYGRO_OK;
+}
+
+const char *hygro_last_error(const hygro_ctx *c) { return c ? c->err.c_str() : g_create_error.c_str(); }
+
+void hygro_destroy(hygro_ctx *c)
+{
+    if (c == nullptr) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}
+
+}  // extern "C"

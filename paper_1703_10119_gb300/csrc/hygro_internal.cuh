@@ -1,0 +1,95 @@
+// Internal data layout of the hygro library (device side and launch helpers).
+//
+// A context stores every wall's two time levels (n and n-1) of T and Pv as
+// deviations from a per-wall reference state (the initial state), in the
+// working precision (float or double). Deviations keep the FP32 arithmetic
+// on O(1..100) numbers instead of O(300..1000) ones: the coefficients are
+// affine in Pv, so the reference only shifts their constant parts.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/hygro.h"
+
+namespace hygro {
+
+constexpr int kMaxLayers = HYGRO_MAX_LAYERS;
+constexpr int kLayerStride = 12;   // reals per layer entry of a wall (9 used, padded)
+constexpr int kMaxK = 16;          // nodes per lane of the persistent kernel
+constexpr int kWarpsPerBlock = 4;  // persistent kernel: 128-thread blocks, one wall per warp
+constexpr int kForcingBatch = 16;  // steps of ambient forcing computed per warp-wide batch
+
+// Layer entry of one wall, in the wall's deviation variables (P' = Pv - P_ref):
+//   [0] kMh_a, [1] kMh_b : kM  / (2 dx) = kMh_a + kMh_b P'
+//   [2] kTh_a, [3] kTh_b : kTT / (2 dx)
+//   [4] A_a,   [5] A_b   : dx cM  / (2 dt)
+//   [6] B_a,   [7] B_b   : dx cTT / (2 dt)
+//   [8] chi             : cTM / cM
+enum { LT_KMA = 0, LT_KMB, LT_KTA, LT_KTB, LT_AA, LT_AB, LT_BA, LT_BB, LT_CHI };
+
+struct WallInfo {
+    int32_t N;          // nodes
+    int32_t K;          // persistent kernel: nodes per lane
+    int32_t Wl;         // persistent kernel: lanes holding nodes
+    int32_t m;          // persistent kernel: lanes 0..m-1 hold K-1 nodes, lanes m..Wl-1 hold K
+    int32_t node_off;   // first node in the concatenated field arrays
+    int32_t n_layers;
+    int32_t layer_off;  // first layer entry of this wall
+    int32_t pad;
+};
+
+struct FaceInfo {
+    int32_t kind;       // HYGRO_BC_*
+    int32_t room;
+    int32_t noise_len;
+    int32_t pad;
+    int64_t noise_off;  // first (T, Pv) pair of this face's table in the context's noise array
+    double hT, hM, q_inf, g_inf;     // exchange coefficients (0 for adiabatic faces)
+    double T_mean_dev, T_amp;        // T_mean - T_ref
+    double P_mean_dev, P_amp;        // P_mean - P_ref
+    double period, phase_T, phase_P, noise_dt;
+    // fixed-point forms used by the FP32 kernels:
+    uint64_t phT0, phP0;  // fraction of a period at step 0, scaled by 2^64 (sinusoid phase incl. phase_T/P)
+    uint64_t pstep;       // fraction of a period per step, scaled by 2^64
+    int64_t npos0;        // noise table position at step 0, scaled by 2^40
+    int64_t nstep;        // noise table positions per step, scaled by 2^40
+};
+
+template <typename real>
+struct DevCtx {
+    const WallInfo *walls;       // [W]
+    const FaceInfo *faces;       // [W][2]
+    const real *layer_tab;       // [sum layers][kLayerStride]
+    const int32_t *layer_first;  // [sum layers]
+    const float2 *noise;         // noise tables
+    real *T[2];                  // level buffers: T[cur] level n, T[1-cur] level n-1
+    real *P[2];
+    int32_t cur;
+    int32_t W;
+    const real *Tref;            // [W]
+    const real *Pref;            // [W]
+    double *cumul;               // [W][2][2] running sums of dt * flux, FP64
+    double *flast;               // [W][2][2] flux of the last step
+    int32_t *nonfinite;          // set to 1 when a wall turns non-finite
+    const int32_t *order;        // [W] wall order of the persistent work queue
+    const int32_t *node_wall;    // [total nodes] (plain kernel)
+    const int8_t *node_layer;    // [total nodes] (plain kernel)
+    int32_t total_nodes;
+    double dt, t0, Lv;
+};
+
+// Launchers (defined in the kernel translation units). All are stream-ordered.
+cudaError_t launch_persistent_f32(const DevCtx<float> &d, int64_t n0, int32_t n_steps, int32_t sample_every,
+                                  float *samples, int32_t *queue_counter, int grid, cudaStream_t s);
+cudaError_t launch_persistent_f64(const DevCtx<double> &d, int64_t n0, int32_t n_steps, int32_t sample_every,
+                                  double *samples, int32_t *queue_counter, int grid, cudaStream_t s);
+cudaError_t occupancy_persistent_f32(int *blocks_per_sm);
+cudaError_t occupancy_persistent_f64(int *blocks_per_sm);
+
+cudaError_t launch_plain_step_f32(const DevCtx<float> &d, int64_t n, int32_t sample_idx, float *samples,
+                                  cudaStream_t s);
+cudaError_t launch_plain_step_f64(const DevCtx<double> &d, int64_t n, int32_t sample_idx, double *samples,
+                                  cudaStream_t s);
+
+}  // namespace hygro

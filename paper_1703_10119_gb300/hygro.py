@@ -1,0 +1,300 @@
+"""Python binding of the hygro C ABI (include/hygro.h), argument marshalling only.
+
+Every computation runs in ``libhygro.so`` (CUDA, sm_103a), built in tree by
+``paper_1703_10119_gb300.build``. Loading fails loudly when the library is
+missing: there is no CPU fallback. The functions ``hygro_*`` mirror the C
+entry points one to one; :class:`Hygro` wires a
+:class:`~paper_1703_10119_gb300.workloads.Workload` through them. Device
+buffers may be torch CUDA tensors (PyTorch supplies device memory and
+streams); host buffers are numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+HYGRO_OK = 0
+HYGRO_E_INVALID = -1
+HYGRO_E_NOMEM = -2
+HYGRO_E_CUDA = -3
+HYGRO_E_STATE = -4
+HYGRO_E_NONFINITE = -5
+HYGRO_E_TIMEOUT = -6
+HYGRO_E_UNSUPPORTED = -7
+HYGRO_FP32, HYGRO_FP64 = 0, 1
+HYGRO_KERNEL_PERSISTENT, HYGRO_KERNEL_PLAIN = 0, 1
+HYGRO_BC_AMBIENT, HYGRO_BC_ADIABATIC, HYGRO_BC_ROOM = 0, 1, 2
+STATUS_NAMES = {0: "HYGRO_OK", -1: "HYGRO_E_INVALID", -2: "HYGRO_E_NOMEM", -3: "HYGRO_E_CUDA",
+                -4: "HYGRO_E_STATE", -5: "HYGRO_E_NONFINITE", -6: "HYGRO_E_TIMEOUT", -7: "HYGRO_E_UNSUPPORTED"}
+
+# Exported entry points (names of include/hygro.h).
+ABI_FUNCTIONS = ("hygro_create", "hygro_set_materials", "hygro_set_bc", "hygro_run", "hygro_sync",
+                 "hygro_fluxes", "hygro_get_fields", "hygro_set_fields", "hygro_get_step", "hygro_get_state",
+                 "hygro_set_state", "hygro_last_error", "hygro_destroy")
+
+
+class hygro_desc(C.Structure):
+    _fields_ = [("n_walls", C.c_int32), ("n_nodes", C.c_void_p), ("thickness", C.c_void_p),
+                ("dt", C.c_double), ("t0", C.c_double), ("Lv", C.c_double), ("Psat", C.c_double),
+                ("precision", C.c_int32), ("kernel", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p)]
+
+
+class hygro_layer(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("kM0", "a", "cM0", "b", "kTT0", "aT", "cTT0", "bT", "chi")]
+
+
+class hygro_bc(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("room", C.c_int32), ("hT", C.c_double), ("hM", C.c_double),
+                ("q_inf", C.c_double), ("g_inf", C.c_double), ("T_mean", C.c_double), ("T_amp", C.c_double),
+                ("P_mean", C.c_double), ("P_amp", C.c_double), ("period", C.c_double), ("phase_T", C.c_double),
+                ("phase_P", C.c_double), ("noise", C.c_void_p), ("noise_len", C.c_int32),
+                ("noise_dt", C.c_double)]
+
+
+class HygroError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = False) -> C.CDLL:
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise ImportError(f"hygro CUDA library not built ({path}); run paper_1703_10119_gb300.build.build()")
+    L = C.CDLL(path)
+    P = C.c_void_p
+    sig = {
+        "hygro_create": [C.POINTER(hygro_desc), C.POINTER(P)],
+        "hygro_set_materials": [P, P, P, P, P, P],
+        "hygro_set_bc": [P, C.c_int32, P],
+        "hygro_run": [P, C.c_int64, C.c_int32, P, C.c_size_t],
+        "hygro_sync": [P],
+        "hygro_fluxes": [P, P, P],
+        "hygro_get_fields": [P, C.c_int32, P, P],
+        "hygro_set_fields": [P, C.c_int32, P, P],
+        "hygro_get_step": [P, C.POINTER(C.c_int64)],
+        "hygro_get_state": [P, P, C.POINTER(C.c_size_t)],
+        "hygro_set_state": [P, P, C.c_size_t],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.restype = C.c_int
+        f.argtypes = args
+    L.hygro_last_error.restype = C.c_char_p
+    L.hygro_last_error.argtypes = [P]
+    L.hygro_destroy.restype = None
+    L.hygro_destroy.argtypes = [P]
+    _lib = L
+    return L
+
+
+def _check(status: int, ctx) -> None:
+    if status != HYGRO_OK:
+        raise HygroError(status, lib().hygro_last_error(ctx).decode())
+
+
+def _ptr(a):
+    """Raw pointer of a numpy array or torch tensor (None -> NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _nbytes(a) -> int:
+    if a is None:
+        return 0
+    if hasattr(a, "element_size"):
+        return a.numel() * a.element_size()
+    return a.nbytes
+
+
+# ---- the C entry points, one to one ------------------------------------------
+
+def hygro_create(desc: hygro_desc):
+    out = C.c_void_p()
+    _check(lib().hygro_create(C.byref(desc), C.byref(out)), None)
+    return out
+
+
+def hygro_set_materials(ctx, n_layers, layer_first, layers, T_init, P_init):
+    _check(lib().hygro_set_materials(ctx, _ptr(n_layers), _ptr(layer_first), C.cast(layers, C.c_void_p),
+                                     _ptr(T_init), _ptr(P_init)), ctx)
+
+
+def hygro_set_bc(ctx, face: int, bcs):
+    _check(lib().hygro_set_bc(ctx, int(face), C.cast(bcs, C.c_void_p)), ctx)
+
+
+def hygro_run(ctx, n_steps: int, sample_every: int = 0, samples=None):
+    _check(lib().hygro_run(ctx, int(n_steps), int(sample_every), _ptr(samples), _nbytes(samples)), ctx)
+
+
+def hygro_sync(ctx):
+    _check(lib().hygro_sync(ctx), ctx)
+
+
+def hygro_fluxes(ctx, flux=None, cumulative=None):
+    _check(lib().hygro_fluxes(ctx, _ptr(flux), _ptr(cumulative)), ctx)
+
+
+def hygro_get_fields(ctx, level: int, T=None, P=None):
+    _check(lib().hygro_get_fields(ctx, int(level), _ptr(T), _ptr(P)), ctx)
+
+
+def hygro_set_fields(ctx, level: int, T=None, P=None):
+    _check(lib().hygro_set_fields(ctx, int(level), _ptr(T), _ptr(P)), ctx)
+
+
+def hygro_get_step(ctx) -> int:
+    s = C.c_int64()
+    _check(lib().hygro_get_step(ctx, C.byref(s)), ctx)
+    return s.value
+
+
+def hygro_get_state(ctx) -> bytes:
+    n = C.c_size_t()
+    _check(lib().hygro_get_state(ctx, None, C.byref(n)), ctx)
+    buf = C.create_string_buffer(n.value)
+    _check(lib().hygro_get_state(ctx, buf, C.byref(n)), ctx)
+    return buf.raw
+
+
+def hygro_set_state(ctx, image: bytes):
+    buf = C.create_string_buffer(image, len(image))
+    _check(lib().hygro_set_state(ctx, buf, len(image)), ctx)
+
+
+def hygro_last_error(ctx) -> str:
+    return lib().hygro_last_error(ctx).decode()
+
+
+def hygro_destroy(ctx):
+    lib().hygro_destroy(ctx)
+
+
+# ---- convenience wrapper over a Workload --------------------------------------
+
+class Hygro:
+    """A context holding one workload's walls on the GPU."""
+
+    def __init__(self, wl, precision: str = "fp32", kernel: str = "persistent", device: int = 0, stream=None):
+        self.wl = wl
+        self.precision = {"fp32": HYGRO_FP32, "fp64": HYGRO_FP64}[precision]
+        self.kernel = {"persistent": HYGRO_KERNEL_PERSISTENT, "plain": HYGRO_KERNEL_PLAIN}[kernel]
+        self.dtype = np.float32 if self.precision == HYGRO_FP32 else np.float64
+        self._keep = []
+        n_nodes = np.ascontiguousarray(wl.n_nodes, np.int32)
+        thick = np.ascontiguousarray(wl.thickness, np.float64)
+        d = hygro_desc(n_walls=wl.n_walls, n_nodes=n_nodes.ctypes.data, thickness=thick.ctypes.data,
+                       dt=wl.dt, t0=wl.t0, Lv=wl.Lv, Psat=wl.Psat, precision=self.precision, kernel=self.kernel,
+                       device=device, stream=stream)
+        self.ctx = hygro_create(d)
+        try:
+            self.set_materials()
+            self.set_bc()
+        except Exception:
+            hygro_destroy(self.ctx)
+            self.ctx = None
+            raise
+
+    def set_materials(self):
+        wl = self.wl
+        lay = (hygro_layer * len(wl.layer_par))()
+        for i, row in enumerate(wl.layer_par):
+            lay[i] = hygro_layer(*[float(x) for x in row])
+        hygro_set_materials(self.ctx, np.ascontiguousarray(wl.n_layers, np.int32),
+                            np.ascontiguousarray(wl.layer_first, np.int32), lay,
+                            np.ascontiguousarray(wl.T_init, np.float64), np.ascontiguousarray(wl.P_init, np.float64))
+
+    def set_bc(self):
+        wl = self.wl
+        for f in range(2):
+            arr = (hygro_bc * wl.n_walls)()
+            nz = None if wl.noise[f] is None else np.ascontiguousarray(wl.noise[f], np.float32)
+            for w in range(wl.n_walls):
+                p = wl.bc_par[w, f]
+                b = arr[w]
+                b.kind = int(wl.bc_kind[w, f])
+                b.room = int(wl.bc_room[w, f])
+                (b.hT, b.hM, b.q_inf, b.g_inf, b.T_mean, b.T_amp, b.P_mean, b.P_amp, b.period, b.phase_T,
+                 b.phase_P, b.noise_dt) = [float(x) for x in p]
+                if nz is not None:
+                    b.noise = nz[w].ctypes.data
+                    b.noise_len = nz.shape[1]
+            hygro_set_bc(self.ctx, f, arr)
+
+    def run(self, n_steps: int, sample_every: int = 0, samples=None):
+        """Advance; ``samples`` (numpy or torch, working dtype) receives surface values."""
+        hygro_run(self.ctx, n_steps, sample_every, samples)
+
+    def run_sampled(self, n_steps: int, sample_every: int) -> np.ndarray:
+        ns = n_steps // sample_every
+        out = np.zeros((ns, self.wl.n_walls, 2, 2), self.dtype)
+        hygro_run(self.ctx, n_steps, sample_every, out)
+        return out
+
+    def sync(self):
+        hygro_sync(self.ctx)
+
+    def fields(self, level: int = 0):
+        n = self.wl.total_nodes
+        T = np.zeros(n)
+        P = np.zeros(n)
+        hygro_get_fields(self.ctx, level, T, P)
+        return T, P
+
+    def set_fields(self, level: int, T, P):
+        hygro_set_fields(self.ctx, level, np.ascontiguousarray(T, np.float64), np.ascontiguousarray(P, np.float64))
+
+    def fluxes(self):
+        f = np.zeros((self.wl.n_walls, 2, 2))
+        c = np.zeros((self.wl.n_walls, 2, 2))
+        hygro_fluxes(self.ctx, f, c)
+        return f, c
+
+    @property
+    def step(self) -> int:
+        return hygro_get_step(self.ctx)
+
+    def get_state(self) -> bytes:
+        return hygro_get_state(self.ctx)
+
+    def set_state(self, image: bytes):
+        hygro_set_state(self.ctx, image)
+
+    def close(self):
+        if self.ctx is not None:
+            hygro_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

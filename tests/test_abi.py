@@ -1,0 +1,76 @@
+"""The C-ABI library loads and exports every entry point include/hygro.h declares;
+argument validation that needs no GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+from paper_1703_10119_gb300 import build as hb
+from paper_1703_10119_gb300 import hygro as H
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "hygro.h")).read()
+    return sorted(set(re.findall(r"HYGRO_API\s+[\w\s\*]*?\b(hygro_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    hb.build()
+    return H.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for must in ("hygro_create", "hygro_set_materials", "hygro_set_bc", "hygro_run", "hygro_fluxes"):
+        assert must in names
+    assert set(names) == set(H.ABI_FUNCTIONS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_exports_nothing_else(lib):
+    out = os.popen(f"nm -D --defined-only {hb.LIB}").read()
+    exported = sorted(set(re.findall(r"\bT (hygro_\w+)", out)))
+    assert exported == _declared()
+
+
+def test_struct_sizes_match_header_layout():
+    assert C.sizeof(H.hygro_layer) == 9 * 8
+    assert C.sizeof(H.hygro_desc) == 4 + 4 + 8 + 8 + 8 * 4 + 4 * 3 + 4 + 8
+    assert C.sizeof(H.hygro_bc) == 8 + 8 * 11 + 8 + 8 + 8
+
+
+def test_create_rejects_bad_arguments_before_touching_the_device(lib):
+    with pytest.raises(H.HygroError) as e:
+        H.hygro_create(H.hygro_desc(n_walls=0))
+    assert e.value.status == H.HYGRO_E_INVALID
+    import numpy as np
+    n = np.array([2], np.int32)
+    L = np.array([0.1])
+    d = H.hygro_desc(n_walls=1, n_nodes=n.ctypes.data, thickness=L.ctypes.data, dt=1.0, Psat=2337.0)
+    with pytest.raises(H.HygroError) as e:
+        H.hygro_create(d)
+    assert e.value.status == H.HYGRO_E_INVALID and "n_nodes" in str(e.value)
+    n[0] = 600
+    with pytest.raises(H.HygroError) as e:
+        H.hygro_create(d)
+    assert e.value.status == H.HYGRO_E_UNSUPPORTED
+    n[0] = 10
+    d.dt = -1.0
+    with pytest.raises(H.HygroError) as e:
+        H.hygro_create(d)
+    assert e.value.status == H.HYGRO_E_INVALID
+    assert lib.hygro_create(None, None) == H.HYGRO_E_INVALID
+
+
+def test_null_context_calls_are_rejected(lib):
+    assert lib.hygro_run(None, 1, 0, None, 0) == H.HYGRO_E_INVALID
+    assert lib.hygro_sync(None) == H.HYGRO_E_INVALID
+    lib.hygro_destroy(None)
