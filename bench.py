@@ -29,9 +29,13 @@ if ROOT not in sys.path:
 
 METRIC = "DF cell-updates/s, batched FP32 vs plain FP64 on GB300 at ≤1e-4 rel L∞; % roofline"
 UNIT = "cell-updates/s"
-# FP32 FMA-pipe operations per cell-update of the DF increment form (coefficients 4, faces 2, Pv 9,
-# T 15; each add, multiply or fused multiply-add counts once) plus 2 reciprocals on the MUFU pipe.
-OPS_PER_UPDATE = 30
+# Algorithmic FP32 operations per cell-update of the DF increment form, each add, multiply or fused
+# multiply-add counted once (they all issue to the FMA pipe); reciprocals run on the MUFU pipe apart.
+#   general wall:     coefficients 5, faces 2, Pv 10, T 10 = 27 (+ 2 reciprocals)
+#   simple-heat wall: (kTT, cTT independent of Pv, cTM = 0: constant thermal faces and T denominators)
+#                     coefficients 2, face 1, Pv 10, T 7 = 20 (+ 1 reciprocal)
+OPS_GENERAL = 27
+OPS_SIMPLE_HEAT = 20
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 KERNEL_SOURCES = ["paper_1703_10119_gb300/csrc/df1d_persistent.cuh", "paper_1703_10119_gb300/csrc/df1d_common.cuh"]
@@ -159,6 +163,17 @@ def reduce_sum(pg, x: float) -> float:
     return float(t.item())
 
 
+def algorithmic_ops_per_step(wl) -> float:
+    """FP32 FMA-pipe operations of one DF step over all walls (see OPS_GENERAL / OPS_SIMPLE_HEAT)."""
+    off = wl.layer_offset()
+    ops = 0.0
+    for w in range(wl.n_walls):
+        lp = wl.layer_par[off[w]:off[w + 1]]
+        simple = bool(np.all(lp[:, 5] == 0) and np.all(lp[:, 7] == 0) and np.all(lp[:, 8] == 0))
+        ops += wl.n_nodes[w] * (OPS_SIMPLE_HEAT if simple else OPS_GENERAL)
+    return ops
+
+
 def cpu_sample(wl, n_walls: int):
     step = max(1, wl.n_walls // n_walls)
     pick = np.arange(0, wl.n_walls, step)[:n_walls]
@@ -278,13 +293,15 @@ def bench_ours(args):
 
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = sms * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
-    achieved = OPS_PER_UPDATE * units_per_run / (ms / 1e3) / 1e12
+    ops_per_step = algorithmic_ops_per_step(wl)
+    achieved = ops_per_step * args.year_steps / (ms / 1e3) / 1e12
     traffic = measured_traffic()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s", "frac": achieved / peak,
                 "traffic": traffic,
                 "note": (f"FP32 FMA-pipe roof: {sms} SMs x {FP32_LANES_PER_SM} lanes x {SM_MAX_MHZ:.0f} MHz; "
-                         f"{OPS_PER_UPDATE} FP32 ops + 2 reciprocals per cell-update; kernel "
-                         "df1d_persistent_kernel<float>, one launch per run")}
+                         f"{ops_per_step / wl.total_nodes:.1f} algorithmic FP32 ops per cell-update "
+                         f"({OPS_SIMPLE_HEAT} on simple-heat walls, {OPS_GENERAL} otherwise) plus reciprocals on "
+                         "the MUFU pipe; kernel df1d_persistent_kernel<float>, one launch per run")}
 
     # plain FP64 comparator (one thread per node, one launch per step)
     comparators = {}

@@ -35,7 +35,13 @@ __device__ __forceinline__ LayerC<real> load_layer(const real *tab, int l)
     return c;
 }
 
-__device__ __forceinline__ float fast_div(float a, float b) { return __fdividef(a, b); }
+// FP32: a times the hardware approximate reciprocal of b (one MUFU op); FP64: IEEE division.
+__device__ __forceinline__ float fast_div(float a, float b)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(b));
+    return a * r;
+}
 __device__ __forceinline__ double fast_div(double a, double b) { return a / b; }
 
 // Face conductance / dx from the two half values kh = k / (2 dx) of the

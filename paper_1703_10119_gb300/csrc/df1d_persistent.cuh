@@ -2,12 +2,15 @@
 // advances it through all the steps of a hygro_run call with both time
 // levels held in registers.
 //
-// Lane layout of a wall of N nodes: K = ceil(N / 32) nodes per lane,
-// Wl = ceil(N / K) lanes in use, m = Wl K - N "short" lanes. Lanes 0..m-1
-// hold K-1 consecutive nodes (their slot K-1 is a frozen dummy), lanes
-// m..Wl-1 hold K; so node 0 sits in lane 0 slot 0 and node N-1 always in
-// lane Wl-1 slot K-1, and only those two slots carry surface terms. Lanes
+// Lane layout of a wall of N nodes (chosen on the host, WallInfo): K nodes
+// per lane, Wl lanes in use, each lane holding K or K-1 consecutive nodes
+// (bit i of short_mask: lane i holds K-1, its slot K-1 is a frozen dummy).
+// Node 0 sits in lane 0 slot 0 and node N-1 in lane Wl-1 slot K-1 (the last
+// lane is always full), so only those two slots carry surface terms. Lanes
 // >= Wl hold nothing (all-zero state with zero faces, which stays zero).
+// When every layer interface falls on a lane boundary ("aligned" walls,
+// the common case) a lane holds one layer and its material constants stay
+// in registers; otherwise a variant switches constants inside the lane.
 // Neighbour values across lanes move with warp shuffles (4 values each way
 // per step); there is no shared-memory traffic and no block barrier in the
 // time loop. Per step and node the work is the coefficient evaluation at
@@ -15,7 +18,9 @@
 // means, the Pv update and then the T update using Pv^{n+1} (Appendix A
 // order), written in increment form:
 //   du = [sum_f F_f (u_nb^n - u^{n-1}) + surface terms] / (C + sum_f F_f / 2 + H / 2)
-// which is the DF balance of [eq:DF_NL] solved for u^{n+1} - u^{n-1}.
+// which is the DF balance of [eq:DF_NL] solved for u^{n+1} - u^{n-1}. The
+// latent cross flux of the T equation, sum_f F_f (Pv_nb - Pvbar), reuses the
+// Pv numerator: num_P - (S / 2) dPv.
 // Surface fluxes are summed in the working precision over batches of 16
 // steps and then added to FP64 running sums.
 #pragma once
@@ -27,92 +32,125 @@ namespace hygro {
 template <typename real>
 struct LaneCtx {
     LayerC<real> c0;          // constants of the layer of slot 0
-    real clkMa, clkMb;        // kM half-values constants of the last real slot's layer
-    real clkTa, clkTb;
+    real clkMa, clkMb;        // kM half-value constants of the last real slot's layer
+    real clkTa, clkTb;        // kTT half-value constants of the last real slot's layer
     real w0, w1;              // half-cell weights of slot 0 / slot K-1 (1/2 at a wall surface)
     real hM0, hT0, q0, g0;    // face-0 exchange (lane 0 only, else 0)
     real hM1, hT1, q1, g1;    // face-1 exchange (lane Wl-1 only, else 0)
+    real hMs, hTs, qs, gs;    // this lane's face exchange (sum of the two sets above)
     uint32_t imask;           // bit k: slot k is the first node of a layer >= 1 (its left face is an interface)
-    uint32_t wimask;          // OR of imask over the warp (warp-uniform)
+    uint32_t wimask;          // OR of imask bits 1.. over the warp (warp-uniform)
     int l0;                   // layer of slot 0
     bool short_lane;          // lane holds K-1 nodes
+    bool face1;               // this lane holds the face-1 surface node (slot K-1)
     bool has_left, has_right; // a face exists between this lane and its neighbour lane
     bool iface_left0;         // the lane-boundary face on the left is an interface
     bool iface_right;         // the lane-boundary face on the right is an interface
     bool any_lb_iface;        // some lane-boundary face of the warp is an interface (warp-uniform)
+    // simple-heat walls (kTT, cTT independent of Pv and cTM = 0 in every layer): the thermal faces and the
+    // T denominators do not change in time and are set up once per wall
+    real FTin;                // in-lane thermal face kTT / dx (one layer per lane)
+    real FTl0c, FTbc;         // thermal faces at the left / right lane boundary (0 at wall ends)
+    real rT0, rTm, rTK2, rTK1; // 1 / T denominator of slot 0, interior slots, slot K-2, slot K-1
 };
 
 // One DF step of the lane's K slots: level n+1 is written into Tp / Pp.
 // fT, fP: ambient air of this lane's surface face (if any) at level n.
 // fq, fg: receive this lane's surface heat / moisture flux of the step.
-template <typename real, int K>
+// IFACE: the wall has layer interfaces inside lanes. SIMPLE: simple-heat
+// wall (see LaneCtx; only with one layer per lane).
+// With IFACE && SIMPLE, sft / srt hold this lane's per-slot right thermal face and reciprocal T
+// denominator (stride 32 between slots), set up once per wall.
+template <typename real, int K, bool IFACE, bool SIMPLE>
 __device__ __forceinline__ void df_step(real (&Tp)[K], const real (&Tc)[K], real (&Pp)[K], const real (&Pc)[K],
                                         const LaneCtx<real> &L, const real *tab, const real fT, const real fP,
-                                        const real Lv, real &fq, real &fg)
+                                        const real Lv, real &fq, real &fg, const real *sft, const real *srt)
 {
     constexpr unsigned FULL = 0xffffffffu;
     const real half = real(0.5);
 
-    // values of the lane's first and last real nodes, exchanged with the neighbour lanes
+    // the lane's last real node: its values go to the next lane, with the right boundary face
     const real lastT = (K >= 2 && L.short_lane) ? Tc[K >= 2 ? K - 2 : 0] : Tc[K - 1];
     const real lastP = (K >= 2 && L.short_lane) ? Pc[K >= 2 ? K - 2 : 0] : Pc[K - 1];
     const real khM_first = fma(L.c0.kMb, Pc[0], L.c0.kMa);
-    const real khT_first = fma(L.c0.kTb, Pc[0], L.c0.kTa);
     const real khM_last = fma(L.clkMb, lastP, L.clkMa);
-    const real khT_last = fma(L.clkTb, lastP, L.clkTa);
-
-    const real lT = __shfl_up_sync(FULL, lastT, 1);
-    const real lP = __shfl_up_sync(FULL, lastP, 1);
-    const real lkM = __shfl_up_sync(FULL, khM_last, 1);
-    const real lkT = __shfl_up_sync(FULL, khT_last, 1);
     const real rT = __shfl_down_sync(FULL, Tc[0], 1);
     const real rP = __shfl_down_sync(FULL, Pc[0], 1);
     const real rkM = __shfl_down_sync(FULL, khM_first, 1);
-    const real rkT = __shfl_down_sync(FULL, khT_first, 1);
-
-    // lane-boundary faces (zero at the wall ends and on unused lanes)
-    real FMl0 = lkM + khM_first, FTl0 = lkT + khT_first;
-    real FMb = khM_last + rkM, FTb = khT_last + rkT;
-    if (L.any_lb_iface) {
-        if (L.iface_left0) {
-            FMl0 = face_harmonic(lkM, khM_first);
-            FTl0 = face_harmonic(lkT, khT_first);
-        }
-        if (L.iface_right) {
-            FMb = face_harmonic(khM_last, rkM);
-            FTb = face_harmonic(khT_last, rkT);
-        }
+    real FMb = khM_last + rkM;
+    real FTb;
+    if (SIMPLE) {
+        FTb = L.FTbc;
+    } else {
+        const real khT_first = fma(L.c0.kTb, Pc[0], L.c0.kTa);
+        const real khT_last = fma(L.clkTb, lastP, L.clkTa);
+        const real rkT = __shfl_down_sync(FULL, khT_first, 1);
+        FTb = khT_last + rkT;
+        if (L.any_lb_iface && L.iface_right) FTb = face_harmonic(khT_last, rkT);
     }
-    FMl0 = L.has_left ? FMl0 : real(0);
-    FTl0 = L.has_left ? FTl0 : real(0);
+    if (L.any_lb_iface && L.iface_right) FMb = face_harmonic(khM_last, rkM);
     FMb = L.has_right ? FMb : real(0);
-    FTb = L.has_right ? FTb : real(0);
+    if (!SIMPLE) FTb = L.has_right ? FTb : real(0);
+    // left boundary: the previous lane's last node and its right face
+    const real lT = __shfl_up_sync(FULL, lastT, 1);
+    const real lP = __shfl_up_sync(FULL, lastP, 1);
+    real FMl0 = __shfl_up_sync(FULL, FMb, 1);
+    real FTl0;
+    if (SIMPLE)
+        FTl0 = L.FTl0c;
+    else
+        FTl0 = __shfl_up_sync(FULL, FTb, 1);
+    FMl0 = L.has_left ? FMl0 : real(0);
+    if (!SIMPLE) FTl0 = L.has_left ? FTl0 : real(0);
 
-    LayerC<real> c = L.c0;
+    LayerC<real> c = L.c0;         // constants of the current slot's layer
     int lcur = L.l0;
     real FMl = FMl0, FTl = FTl0;   // left face of the current slot
     real Tl = lT, Pl = lP;         // left neighbour at level n
-    real khM = khM_first, khT = khT_first;
-    fq = real(0);
-    fg = real(0);
+    real khM = khM_first;
+    real khT = SIMPLE ? real(0) : fma(L.c0.kTb, Pc[0], L.c0.kTa);
+    real sPbar = real(0), sTbar = real(0);   // time-averaged surface values of this lane's face
 
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        // constants and half-values of the next slot, and the right face of this one
-        LayerC<real> cn = c;
+        // storage terms of slot k at level n (half-cell weight at the wall surfaces)
+        const real Pk = Pc[k];
+        real A = fma(c.Ab, Pk, c.Aa);
+        real B = SIMPLE ? real(0) : fma(c.Bb, Pk, c.Ba);
+        if (k == 0) {
+            A *= L.w0;
+            if (!SIMPLE) B *= L.w0;
+        }
+        if (k == K - 1) {
+            A *= L.w1;
+            if (!SIMPLE) B *= L.w1;
+        }
+        const real chiA = SIMPLE ? real(0) : c.chi * A;
+
+        // right neighbour and right face
         real FMr, FTr, Tr, Pr, khMn = real(0), khTn = real(0);
         if (k + 1 < K) {
-            if ((L.wimask >> (k + 1)) & 1u) {
-                if ((L.imask >> (k + 1)) & 1u) cn = load_layer(tab, lcur + 1);
-            }
-            khMn = fma(cn.kMb, Pc[k + 1], cn.kMa);
-            khTn = fma(cn.kTb, Pc[k + 1], cn.kTa);
+            khMn = fma(c.kMb, Pc[k + 1], c.kMa);
             FMr = khM + khMn;
-            FTr = khT + khTn;
-            if ((L.wimask >> (k + 1)) & 1u) {
-                if ((L.imask >> (k + 1)) & 1u) {
-                    FMr = face_harmonic(khM, khMn);
-                    FTr = face_harmonic(khT, khTn);
+            if (SIMPLE) {
+                FTr = IFACE ? sft[k * 32] : L.FTin;
+            } else {
+                khTn = fma(c.kTb, Pc[k + 1], c.kTa);
+                FTr = khT + khTn;
+            }
+            if (IFACE) {
+                // the next slot may open a new layer (warp-uniform test first)
+                if ((L.wimask >> (k + 1)) & 1u) {
+                    if ((L.imask >> (k + 1)) & 1u) {
+                        ++lcur;
+                        c = load_layer(tab, lcur);
+                        khMn = fma(c.kMb, Pc[k + 1], c.kMa);
+                        FMr = face_harmonic(khM, khMn);
+                        if (!SIMPLE) {
+                            khTn = fma(c.kTb, Pc[k + 1], c.kTa);
+                            FTr = face_harmonic(khT, khTn);
+                        }
+                    }
                 }
             }
             Tr = Tc[k + 1];
@@ -125,7 +163,7 @@ __device__ __forceinline__ void df_step(real (&Tp)[K], const real (&Tc)[K], real
             }
         } else {
             FMr = FMb;
-            FTr = FTb;
+            FTr = (SIMPLE && IFACE) ? sft[k * 32] : FTb;
             Tr = rT;
             Pr = rP;
             if (K >= 2) {           // short lanes: freeze the dummy slot K-1
@@ -136,66 +174,65 @@ __device__ __forceinline__ void df_step(real (&Tp)[K], const real (&Tc)[K], real
             }
         }
 
-        // node coefficients at level n (storage terms), half-cell weight at surfaces
-        const real Pk = Pc[k];
-        real A = fma(c.Ab, Pk, c.Aa);
-        real B = fma(c.Bb, Pk, c.Ba);
-        if (k == 0) {
-            A *= L.w0;
-            B *= L.w0;
-        }
-        if (k == K - 1) {
-            A *= L.w1;
-            B *= L.w1;
-        }
-
-        // vapour pressure
+        // vapour pressure: num = sum_f F (P_nb - P^{n-1}) [+ hM (Pinf - P^{n-1})], S = sum_f F [+ hM]
         const real pp = Pp[k];
         real numP = fma(FMl, Pl - pp, FMr * (Pr - pp));
-        real denP = fma(half, FMl + FMr, A);
+        real S = FMl + FMr;
+        real gsrc = real(0);
         if (k == 0) {
-            numP = fma(L.hM0, fP - pp, numP + L.g0);
-            denP = fma(half, L.hM0, denP);
+            numP = fma(L.hM0, fP - pp, numP);
+            S += L.hM0;
+            gsrc = L.g0;
         }
         if (k == K - 1) {
-            numP = fma(L.hM1, fP - pp, numP + L.g1);
-            denP = fma(half, L.hM1, denP);
+            numP = fma(L.hM1, fP - pp, numP);
+            S += L.hM1;
+            gsrc += L.g1;
         }
-        const real dP = fast_div(numP, denP);
-        const real Pbar = fma(half, dP, pp);
+        const real dP = fast_div(numP + gsrc, fma(half, S, A));
+        // latent cross flux sum_f F (P_nb - Pbar) [+ hM (Pinf - Pbar)] = num - S dP / 2
+        const real hdP = half * dP;
+        const real X = fma(-S, hdP, numP);
 
-        // temperature, with the kTM cross flux (kTM_f = Lv kM_f) and the cTM storage term
+        // temperature: conduction, Lv x cross flux, cTM storage
         const real tp = Tp[k];
         real numT = fma(FTl, Tl - tp, FTr * (Tr - tp));
-        numT = fma(Lv, fma(FMl, Pl - Pbar, FMr * (Pr - Pbar)), numT);
-        numT = fma(-c.chi * A, dP, numT);
-        real denT = fma(half, FTl + FTr, B);
-        real hm0 = real(0), hm1 = real(0);   // hM (Pv_inf - Pbar) at the surfaces
+        real ST = SIMPLE ? real(0) : FTl + FTr;
         if (k == 0) {
-            hm0 = L.hM0 * (fP - Pbar);
-            numT = fma(L.hT0, fT - tp, fma(Lv, hm0, numT + L.q0));
-            denT = fma(half, L.hT0, denT);
+            numT = fma(L.hT0, fT - tp, numT + L.q0);
+            if (!SIMPLE) ST += L.hT0;
         }
         if (k == K - 1) {
-            hm1 = L.hM1 * (fP - Pbar);
-            numT = fma(L.hT1, fT - tp, fma(Lv, hm1, numT + L.q1));
-            denT = fma(half, L.hT1, denT);
+            numT = fma(L.hT1, fT - tp, numT + L.q1);
+            if (!SIMPLE) ST += L.hT1;
         }
-        const real dT = fast_div(numT, denT);
+        numT = fma(Lv, X, numT);
+        real dT;
+        if (SIMPLE) {
+            real r;
+            if (IFACE) {
+                r = srt[k * 32];
+            } else {
+                r = L.rTm;
+                if (k == K - 2) r = L.rTK2;
+                if (k == K - 1) r = L.rTK1;
+                if (k == 0) r = L.rT0;
+            }
+            dT = numT * r;
+        } else {
+            numT = fma(-chiA, dP, numT);
+            dT = fast_div(numT, fma(half, ST, B));
+        }
         Pp[k] = pp + dP;
         Tp[k] = tp + dT;
 
-        if (k == 0 || k == K - 1) {
-            // surface fluxes into the wall with the time-averaged surface values
-            const real Tbar = fma(half, dT, tp);
-            if (k == 0) {
-                fq += fma(L.hT0, fT - Tbar, fma(Lv, hm0, L.q0));
-                fg += hm0 + L.g0;
-            }
-            if (k == K - 1) {
-                fq += fma(L.hT1, fT - Tbar, fma(Lv, hm1, L.q1));
-                fg += hm1 + L.g1;
-            }
+        if (k == 0) {
+            sPbar = pp + hdP;
+            sTbar = fma(half, dT, tp);
+        }
+        if (k == K - 1) {
+            sPbar = L.face1 ? pp + hdP : sPbar;
+            sTbar = L.face1 ? fma(half, dT, tp) : sTbar;
         }
 
         // advance to the next slot
@@ -205,27 +242,26 @@ __device__ __forceinline__ void df_step(real (&Tp)[K], const real (&Tc)[K], real
         FTl = FTr;
         khM = khMn;
         khT = khTn;
-        if (k + 1 < K) {
-            if ((L.wimask >> (k + 1)) & 1u) {
-                if ((L.imask >> (k + 1)) & 1u) ++lcur;
-            }
-        }
-        c = cn;
     }
+    // surface fluxes into the wall with the time-averaged surface values ([eq:HAM_BC])
+    const real hm = L.hMs * (fP - sPbar);
+    fq = fma(L.hTs, fT - sTbar, fma(Lv, hm, L.qs));
+    fg = hm + L.gs;
 }
 
 // Everything one warp does for one wall over n_steps steps.
-template <typename real, int K>
+template <typename real, int K, bool IFACE, bool SIMPLE>
 __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi, int w, const real *tab, int64_t n0,
-                                      int32_t n_steps, int32_t sample_every, real *samples)
+                                      int32_t n_steps, int32_t sample_every, real *samples, real *sft, real *srt)
 {
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const int Wl = wi.Wl, m = wi.m;
+    const int Wl = wi.Wl;
+    const uint32_t smask = (uint32_t)wi.short_mask;
 
     LaneCtx<real> L;
-    L.short_lane = (K >= 2) && lane < m;
-    const int first = L.short_lane ? lane * (K - 1) : lane * K - m;   // wall-local node of slot 0
+    L.short_lane = (K >= 2) && ((smask >> lane) & 1u);
+    const int first = lane * K - __popc(smask & ((1u << lane) - 1u));   // wall-local node of slot 0
     const int nreal = lane >= Wl ? 0 : (L.short_lane ? K - 1 : K);
     const int32_t *lf = d.layer_first + wi.layer_off;
 
@@ -262,6 +298,7 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
     L.hM0 = L.hT0 = L.q0 = L.g0 = real(0);
     L.hM1 = L.hT1 = L.q1 = L.g1 = real(0);
     const int my_face = lane == 0 ? 0 : (lane == Wl - 1 ? 1 : -1);
+    L.face1 = my_face == 1;
     if (my_face == 0) {
         L.hM0 = (real)fw[0].hM;
         L.hT0 = (real)fw[0].hT;
@@ -273,8 +310,76 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
         L.q1 = (real)fw[1].q_inf;
         L.g1 = (real)fw[1].g_inf;
     }
+    L.hMs = L.hM0 + L.hM1;
+    L.hTs = L.hT0 + L.hT1;
+    L.qs = L.q0 + L.q1;
+    L.gs = L.g0 + L.g1;
     const real Lv = (real)d.Lv;
     const real Tref = d.Tref[w], Pref = d.Pref[w];
+    L.FTin = L.FTl0c = L.FTbc = real(0);
+    L.rT0 = L.rTm = L.rTK2 = L.rTK1 = real(1);
+    if (SIMPLE) {
+        // constant thermal faces and T denominators B w + (F_left + F_right + hT) / 2
+        const real half = real(0.5);
+        const real khf = L.c0.kTa;                        // kTT / (2 dx) of slot 0's layer
+        const real khl = L.clkTa;                         // of the last real slot's layer
+        const real khr = __shfl_down_sync(FULL, khf, 1);  // of the next lane's first slot
+        real Fb = L.iface_right ? face_harmonic(khl, khr) : khl + khr;
+        Fb = L.has_right ? Fb : real(0);
+        real Fl = __shfl_up_sync(FULL, Fb, 1);
+        Fl = L.has_left ? Fl : real(0);
+        L.FTin = real(2) * khf;
+        L.FTl0c = Fl;
+        L.FTbc = Fb;
+        if (!IFACE) {
+            const real Bc = L.c0.Ba;
+            // slot 0: right face FTin, or the boundary face when slot 0 is the last real slot (K = 1, or
+            // K = 2 on a short lane); with K = 1 it is also slot K-1 (both surface sets apply)
+            real d0;
+            if (K == 1)
+                d0 = Bc * L.w0 * L.w1 + half * (Fl + Fb + L.hT0 + L.hT1);
+            else
+                d0 = Bc * L.w0 + half * (Fl + ((K == 2 && L.short_lane) ? Fb : L.FTin) + L.hT0);
+            L.rT0 = real(1) / d0;
+            L.rTm = real(1) / (Bc + L.FTin);
+            L.rTK2 = real(1) / (Bc + half * (L.FTin + (L.short_lane ? Fb : L.FTin)));
+            L.rTK1 = L.short_lane ? real(1) : real(1) / (Bc * L.w1 + half * (L.FTin + Fb + L.hT1));
+        } else {
+            // per-slot table: layer of each slot, right face (harmonic at an interface, the lane
+            // boundary after the last real slot, zero around a short lane's dummy slot) and 1 / denominator
+            int l = l0;
+            real Fleft = Fl;
+            for (int k = 0; k < K; ++k) {
+                if (k > 0 && ((imask >> k) & 1u)) ++l;
+                const real kh = tab[l * kLayerStride + LT_KTA];
+                real Fr;
+                if (k + 1 < nreal) {
+                    const bool nl = (imask >> (k + 1)) & 1u;
+                    const real khn = tab[(l + (nl ? 1 : 0)) * kLayerStride + LT_KTA];
+                    Fr = nl ? face_harmonic(kh, khn) : kh + khn;
+                } else if (k + 1 == nreal) {
+                    Fr = Fb;
+                } else {
+                    Fr = real(0);
+                }
+                const bool dummy = k >= nreal;
+                const real Fl_k = dummy ? real(0) : Fleft;
+                real B = tab[l * kLayerStride + LT_BA];
+                real hT = real(0);
+                if (k == 0) {
+                    B *= L.w0;
+                    hT += L.hT0;
+                }
+                if (k == K - 1) {
+                    B *= L.w1;
+                    hT += L.hT1;
+                }
+                sft[k * 32] = Fr;
+                srt[k * 32] = real(1) / (B + half * (Fl_k + Fr + hT));
+                Fleft = Fr;
+            }
+        }
+    }
 
     // load the two levels
     const int cur = d.cur;
@@ -298,7 +403,7 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
     int scount = sample_every;
     int64_t sidx = 0;
     const int W = d.W;
-    // surface values written by a sample: lane 0 -> face 0 (slot 0), lane Wl-1 -> face 1 (slot K-1)
+    // a sample holds the surface values: lane 0 -> face 0 (slot 0), lane Wl-1 -> face 1 (slot K-1)
     auto sample = [&](const real (&Tn)[K], const real (&Pn)[K]) {
         if (sample_every > 0 && --scount == 0) {
             scount = sample_every;
@@ -329,13 +434,13 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
             real fq, fg;
             real fT = __shfl_sync(FULL, bT, src_base + i);
             real fP = __shfl_sync(FULL, bP, src_base + i);
-            df_step<real, K>(Ta, Tb, Pa, Pb, L, tab, fT, fP, Lv, fq, fg);
+            df_step<real, K, IFACE, SIMPLE>(Ta, Tb, Pa, Pb, L, tab, fT, fP, Lv, fq, fg, sft, srt);
             acc_q += fq;
             acc_g += fg;
             sample(Ta, Pa);
             fT = __shfl_sync(FULL, bT, src_base + i + 1);
             fP = __shfl_sync(FULL, bP, src_base + i + 1);
-            df_step<real, K>(Tb, Ta, Pb, Pa, L, tab, fT, fP, Lv, fq, fg);
+            df_step<real, K, IFACE, SIMPLE>(Tb, Ta, Pb, Pa, L, tab, fT, fP, Lv, fq, fg, sft, srt);
             acc_q += fq;
             acc_g += fg;
             sample(Tb, Pb);
@@ -346,7 +451,7 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
             real fq, fg;
             const real fT = __shfl_sync(FULL, bT, src_base + i);
             const real fP = __shfl_sync(FULL, bP, src_base + i);
-            df_step<real, K>(Ta, Tb, Pa, Pb, L, tab, fT, fP, Lv, fq, fg);
+            df_step<real, K, IFACE, SIMPLE>(Ta, Tb, Pa, Pb, L, tab, fT, fP, Lv, fq, fg, sft, srt);
             acc_q += fq;
             acc_g += fg;
             sample(Ta, Pa);
@@ -382,28 +487,59 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
     }
 }
 
+// The simple-heat specialisation is built for FP32 only; FP64 runs those walls through the general code.
 template <typename real>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32)
-    df1d_persistent_kernel(const DevCtx<real> d, int64_t n0, int32_t n_steps, int32_t sample_every, real *samples,
-                           int32_t *queue_counter)
+constexpr bool kSimpleVariant = sizeof(real) == 4;
+
+template <typename real>
+__global__ void __launch_bounds__(PersistCfg<real>::warps * 32, 1)
+    df1d_persistent_kernel(const DevCtx<real> d, int64_t n0, int32_t n_steps, int32_t sample_every, real *samples)
 {
-    __shared__ real s_tab[kWarpsPerBlock][kMaxLayers * kLayerStride];
+    // Each block owns a sequence of rounds of walls (balanced across blocks on the host by estimated
+    // cost; a round holds walls of one code variant); warp i takes entry i of each round in turn,
+    // without block-wide synchronisation.
+    // dynamic shared memory per warp: layer table of the current wall, then (simple-heat walls with
+    // interfaces inside lanes) the per-slot thermal face and reciprocal T denominator tables
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    real *s_all = reinterpret_cast<real *>(s_raw);
     const int lane = threadIdx.x & 31;
     const int wib = threadIdx.x >> 5;
-    for (;;) {
-        int idx = 0;
-        if (lane == 0) idx = atomicAdd(queue_counter, 1);
-        idx = __shfl_sync(0xffffffffu, idx, 0);
-        if (idx >= d.W) break;
+    const int R = d.round_size;
+    if (wib >= R) return;
+    const int end = d.block_off[blockIdx.x + 1];
+    for (int idx = d.block_off[blockIdx.x] + wib; idx < end; idx += R) {
         const int w = d.order[idx];
+        if (w < 0) continue;
         const WallInfo wi = d.walls[w];
+        real *tabw = s_all + (size_t)wib * kSmemRealsPerWarp;
         for (int i = lane; i < wi.n_layers * kLayerStride; i += 32)
-            s_tab[wib][i] = d.layer_tab[(size_t)wi.layer_off * kLayerStride + i];
+            tabw[i] = d.layer_tab[(size_t)wi.layer_off * kLayerStride + i];
         __syncwarp();
-        const real *tab = s_tab[wib];
-        switch (wi.K) {
-#define HYGRO_CASE(KK) \
-    case KK: run_wall<real, KK>(d, wi, w, tab, n0, n_steps, sample_every, samples); break;
+        const real *tab = tabw;
+        real *sft = tabw + kMaxLayers * kLayerStride + lane;
+        real *srt = sft + kMaxK * 32;
+        // variant: 0 = one layer per lane, simple heat; 1 = one layer per lane; 2 = interfaces in lanes;
+        // 3 = interfaces in lanes, simple heat
+        const bool simple = wi.simple && kSimpleVariant<real>;
+        const int kind = wi.aligned ? (simple ? 0 : 1) : (simple ? 3 : 2);
+        unsigned long long t_start = 0;
+        if (d.trace != nullptr) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
+        switch (wi.K * 4 + kind) {
+#define HYGRO_CASE(KK)                                                                                        \
+    case 4 * KK:                                                                                              \
+        run_wall<real, KK, false, kSimpleVariant<real>>(d, wi, w, tab, n0, n_steps, sample_every, samples, sft,   \
+                                                        srt);                                                 \
+        break;                                                                                                \
+    case 4 * KK + 1:                                                                                          \
+        run_wall<real, KK, false, false>(d, wi, w, tab, n0, n_steps, sample_every, samples, sft, srt);         \
+        break;                                                                                                \
+    case 4 * KK + 2:                                                                                          \
+        run_wall<real, KK, true, false>(d, wi, w, tab, n0, n_steps, sample_every, samples, sft, srt);          \
+        break;                                                                                                \
+    case 4 * KK + 3:                                                                                          \
+        run_wall<real, KK, true, kSimpleVariant<real>>(d, wi, w, tab, n0, n_steps, sample_every, samples, sft,    \
+                                                       srt);                                                  \
+        break;
             HYGRO_CASE(1) HYGRO_CASE(2) HYGRO_CASE(3) HYGRO_CASE(4) HYGRO_CASE(5) HYGRO_CASE(6)
             HYGRO_CASE(7) HYGRO_CASE(8) HYGRO_CASE(9) HYGRO_CASE(10) HYGRO_CASE(11) HYGRO_CASE(12)
             HYGRO_CASE(13) HYGRO_CASE(14) HYGRO_CASE(15) HYGRO_CASE(16)
@@ -411,6 +547,17 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
             default: break;
         }
         __syncwarp();
+        if (d.trace != nullptr && lane == 0) {
+            unsigned long long t_end;
+            unsigned int smid;
+            asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
+            asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+            unsigned long long *t = d.trace + (size_t)w * 4;
+            t[0] = ((unsigned long long)smid << 32) | ((unsigned long long)blockIdx.x << 8) | (unsigned long long)wib;
+            t[1] = t_start;
+            t[2] = t_end;
+            t[3] = (unsigned long long)n_steps;
+        }
     }
 }
 

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -73,6 +74,7 @@ struct hygro_ctx {
     int64_t step = 0;
     int cur = 0;
     int grid_persistent = 1;
+    int round_size = 1;
     size_t real_size = 4;
     std::string err = "no error";
 
@@ -88,7 +90,9 @@ struct hygro_ctx {
     double *d_cumul = nullptr, *d_flast = nullptr;
     int32_t *d_nonfinite = nullptr;
     int32_t *d_order = nullptr;
-    int32_t *d_counter = nullptr;
+    int32_t *d_block_off = nullptr;
+    unsigned long long *d_trace = nullptr;   // wall trace of the persistent kernel (HYGRO_TRACE)
+    std::string trace_path;
     int32_t *d_node_wall = nullptr;
     int8_t *d_node_layer = nullptr;
     void *d_samples = nullptr;
@@ -121,7 +125,7 @@ void free_all(hygro_ctx *c)
 {
     void *ptrs[] = {c->dT[0], c->dT[1], c->dP[0], c->dP[1], c->d_walls, c->d_faces, c->d_layer_tab,
                     c->d_layer_first, c->d_noise, c->d_Tref, c->d_Pref, c->d_cumul, c->d_flast,
-                    c->d_nonfinite, c->d_order, c->d_counter, c->d_node_wall, c->d_node_layer, c->d_samples};
+                    c->d_nonfinite, c->d_order, c->d_block_off, c->d_trace, c->d_node_wall, c->d_node_layer, c->d_samples};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -147,6 +151,9 @@ DevCtx<real> make_dev(const hygro_ctx *c)
     d.flast = c->d_flast;
     d.nonfinite = c->d_nonfinite;
     d.order = c->d_order;
+    d.block_off = c->d_block_off;
+    d.round_size = c->round_size;
+    d.trace = c->d_trace;
     d.node_wall = c->d_node_wall;
     d.node_layer = c->d_node_layer;
     d.total_nodes = (int32_t)c->total_nodes;
@@ -256,6 +263,56 @@ hygro_status check_nonfinite(hygro_ctx *c)
 
 const uint64_t kStateMagic = 0x6879677273746174ull;  // "hygrstat"
 
+// Lane layout of one wall for the persistent kernel: K nodes per lane, Wl lanes, lanes of K or K-1
+// nodes (short_mask), the last lane full. Preferred: every layer interface on a lane boundary
+// (each layer split into lanes of K or K-1 nodes, its short lanes first), trying K from
+// ceil(N/32) up while the lanes fit in a warp. Otherwise the plain split (short lanes first).
+void wall_layout(int N, const int32_t *first, int nl, WallInfo &wi)
+{
+    const int K0 = (N + 31) / 32;
+    for (int K = K0; K <= kMaxK; ++K) {
+        int lanes = 0;
+        uint32_t mask = 0;
+        bool ok = true;
+        for (int l = 0; l < nl && ok; ++l) {
+            const int Nl = (l + 1 < nl ? first[l + 1] : N) - first[l];
+            const int c = (Nl + K - 1) / K;
+            const int sh = c * K - Nl;
+            const bool last = l + 1 == nl;
+            if (sh > c - (last ? 1 : 0) || lanes + c > 32) {
+                ok = false;
+                break;
+            }
+            for (int i = 0; i < sh; ++i) mask |= 1u << (lanes + i);
+            lanes += c;
+        }
+        if (ok) {
+            wi.K = K;
+            wi.Wl = lanes;
+            wi.short_mask = mask;
+            wi.aligned = 1;
+            return;
+        }
+    }
+    wi.K = K0;
+    wi.Wl = (N + K0 - 1) / K0;
+    const int m = wi.Wl * K0 - N;
+    wi.short_mask = m > 0 ? ((1u << m) - 1u) : 0u;
+    // aligned by chance when every interface is a lane start
+    int aligned = 1;
+    for (int l = 1; l < nl; ++l) {
+        int start = 0, lane = 0;
+        bool hit = false;
+        while (lane < wi.Wl && start <= first[l]) {
+            if (start == first[l]) hit = true;
+            start += ((wi.short_mask >> lane) & 1u) ? K0 - 1 : K0;
+            ++lane;
+        }
+        if (!hit) aligned = 0;
+    }
+    wi.aligned = aligned;
+}
+
 }  // namespace
 
 extern "C" {
@@ -315,9 +372,8 @@ hygro_status hygro_create(const hygro_desc *desc, hygro_ctx **out)
         WallInfo &wi = c->walls[w];
         memset(&wi, 0, sizeof wi);
         wi.N = c->N[w];
-        wi.K = (wi.N + 31) / 32;
-        wi.Wl = (wi.N + wi.K - 1) / wi.K;
-        wi.m = wi.Wl * wi.K - wi.N;
+        const int32_t zero = 0;
+        wall_layout(wi.N, &zero, 1, wi);
         wi.node_off = (int32_t)off;
         off += wi.N;
     }
@@ -355,8 +411,7 @@ hygro_status hygro_create(const hygro_desc *desc, hygro_ctx **out)
     CREATE_TRY(cudaMemset(c->d_flast, 0, (size_t)c->W * 4 * sizeof(double)));
     CREATE_TRY(dalloc(&c->d_nonfinite, 1));
     CREATE_TRY(cudaMemset(c->d_nonfinite, 0, sizeof(int32_t)));
-    CREATE_TRY(dalloc(&c->d_counter, 1));
-    CREATE_TRY(dalloc(&c->d_order, c->W));
+    CREATE_TRY(dalloc(&c->d_order, (size_t)c->W + PersistCfg<float>::warps + PersistCfg<double>::warps));
     CREATE_TRY(dalloc(&c->d_node_wall, (size_t)total));
     CREATE_TRY(dalloc(&c->d_node_layer, (size_t)total));
     CREATE_TRY(cudaMemset(c->d_node_layer, 0, (size_t)total));
@@ -365,22 +420,22 @@ hygro_status hygro_create(const hygro_desc *desc, hygro_ctx **out)
         for (int w = 0; w < c->W; ++w)
             for (int j = 0; j < c->N[w]; ++j) nw[(size_t)c->walls[w].node_off + j] = w;
         CREATE_TRY(cudaMemcpy(c->d_node_wall, nw.data(), nw.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-        // persistent work queue: most nodes per lane first, then most nodes
-        std::vector<int32_t> order(c->W);
-        for (int w = 0; w < c->W; ++w) order[w] = w;
-        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-            if (c->walls[a].K != c->walls[b].K) return c->walls[a].K > c->walls[b].K;
-            return c->walls[a].N > c->walls[b].N;
-        });
-        CREATE_TRY(cudaMemcpy(c->d_order, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     }
     {
         int sms = 0, per_sm = 0;
         CREATE_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
         CREATE_TRY(c->precision == HYGRO_FP64 ? occupancy_persistent_f64(&per_sm) : occupancy_persistent_f32(&per_sm));
         if (per_sm < 1) per_sm = 1;
-        const int need = (c->W + kWarpsPerBlock - 1) / kWarpsPerBlock;
-        c->grid_persistent = std::max(1, std::min(need, sms * per_sm));
+        // one persistent block per SM slot, but never more blocks than walls (few walls spread over SMs)
+        c->grid_persistent = std::max(1, std::min(c->W, sms * per_sm));
+        CREATE_TRY(dalloc(&c->d_block_off, (size_t)c->grid_persistent + 1));
+    }
+    if (const char *tp = getenv("HYGRO_TRACE")) {
+        // diagnostic: per-wall SM, block, warp and start / end times of every persistent launch,
+        // appended to the named file after each hygro_run
+        c->trace_path = tp;
+        CREATE_TRY(dalloc(&c->d_trace, (size_t)c->W * 4));
+        CREATE_TRY(cudaMemset(c->d_trace, 0, (size_t)c->W * 4 * sizeof(unsigned long long)));
     }
 #undef CREATE_TRY
     (void)st;
@@ -432,6 +487,12 @@ hygro_status hygro_set_materials(hygro_ctx *c, const int32_t *n_layers, const in
         WallInfo &wi = c->walls[w];
         wi.n_layers = n_layers[w];
         wi.layer_off = (int32_t)lo;
+        wall_layout(wi.N, layer_first + lo, wi.n_layers, wi);
+        wi.simple = 1;
+        for (int l = 0; l < wi.n_layers; ++l) {
+            const hygro_layer &y = layers[lo + l];
+            if (y.aT != 0.0 || y.bT != 0.0 || y.chi != 0.0) wi.simple = 0;
+        }
         const double dx = c->L[w] / (double)(c->N[w] - 1);
         const double Ps = c->Psat, Pr = c->Pref[w], dt = c->dt;
         for (int l = 0; l < wi.n_layers; ++l) {
@@ -463,6 +524,62 @@ hygro_status hygro_set_materials(hygro_ctx *c, const int32_t *n_layers, const in
     CUDA_TRY(c, cudaMemcpy(c->d_layer_first, layer_first, total_layers * sizeof(int32_t), cudaMemcpyHostToDevice));
     CUDA_TRY(c, cudaMemcpy(c->d_node_layer, node_layer.data(), node_layer.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(c, cudaMemcpy(c->d_walls, c->walls.data(), c->walls.size() * sizeof(WallInfo), cudaMemcpyHostToDevice));
+    {
+        // Persistent blocks: walls sorted by nodes per lane and code variant, cut into rounds of
+        // round_size walls (one per warp of a block); rounds dealt to blocks largest estimated cost
+        // first, each to the least loaded block (LPT); a block runs its rounds largest first. Cost
+        // per step ~ K * (cost of a slot) + fixed part.
+        const int G = c->grid_persistent;
+        const int wpb = c->precision == HYGRO_FP64 ? PersistCfg<double>::warps : PersistCfg<float>::warps;
+        const int R = std::max(1, std::min(wpb, W / G));
+        c->round_size = R;
+        // code variant (as in the kernel) and time per step of a wall with K nodes per lane when an SM
+        // is shared by its full warp count, a + b K (nanoseconds, measured on GB300 for variants 0 and 2)
+        auto kind_of = [&](const WallInfo &x) {
+            const bool simple = x.simple && c->precision == HYGRO_FP32;
+            return x.aligned ? (simple ? 0 : 1) : (simple ? 3 : 2);
+        };
+        auto cost = [&](const WallInfo &x) {
+            static const double a[4] = {162.0, 190.0, 127.0, 199.0};
+            static const double b[4] = {41.3, 62.0, 102.0, 61.7};
+            const int k = kind_of(x);
+            return a[k] + b[k] * x.K;
+        };
+        std::vector<int32_t> srt(W);
+        for (int w = 0; w < W; ++w) srt[w] = w;
+        std::stable_sort(srt.begin(), srt.end(), [&](int a, int b) {
+            const WallInfo &x = c->walls[a], &y = c->walls[b];
+            if (x.K != y.K) return x.K > y.K;
+            if (kind_of(x) != kind_of(y)) return kind_of(x) < kind_of(y);
+            return x.N > y.N;
+        });
+        const int n_rounds = (W + R - 1) / R;
+        std::vector<double> rcost(n_rounds, 0.0);
+        for (int i = 0; i < W; ++i) rcost[i / R] = std::max(rcost[i / R], cost(c->walls[srt[i]]));
+        std::vector<int32_t> ridx(n_rounds);
+        for (int r = 0; r < n_rounds; ++r) ridx[r] = r;
+        std::stable_sort(ridx.begin(), ridx.end(), [&](int a, int b) { return rcost[a] > rcost[b]; });
+        std::vector<double> load(G, 0.0);
+        std::vector<std::vector<int32_t>> lists(G);
+        for (int r : ridx) {
+            int best = 0;
+            for (int g = 1; g < G; ++g)
+                if (load[g] < load[best]) best = g;
+            load[best] += rcost[r];
+            lists[best].push_back(r);
+        }
+        std::vector<int32_t> order;
+        std::vector<int32_t> boff(G + 1, 0);
+        order.reserve((size_t)n_rounds * R);
+        for (int g = 0; g < G; ++g) {
+            boff[g] = (int32_t)order.size();
+            for (int r : lists[g])
+                for (int i = 0; i < R; ++i) order.push_back(r * R + i < W ? srt[r * R + i] : -1);
+        }
+        boff[G] = (int32_t)order.size();
+        CUDA_TRY(c, cudaMemcpy(c->d_order, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemcpy(c->d_block_off, boff.data(), boff.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
     if ((st = upload_reals(c, c->d_Tref, c->Tref)) != HYGRO_OK) return st;
     if ((st = upload_reals(c, c->d_Pref, c->Pref)) != HYGRO_OK) return st;
     // uniform initial state: zero deviation at both levels, step 0, no accumulated flux
@@ -559,15 +676,14 @@ hygro_status hygro_run(hygro_ctx *c, int64_t n_steps, int32_t sample_every, void
         while (done < n_steps) {
             const int64_t len = std::min(chunk, n_steps - done);
             const size_t soff = se > 0 ? (size_t)(done / se) * c->W * 4 : 0;
-            CUDA_TRY(c, cudaMemsetAsync(c->d_counter, 0, sizeof(int32_t), c->stream));
             if (c->precision == HYGRO_FP64)
                 CUDA_TRY(c, launch_persistent_f64(make_dev<double>(c), c->step + done, (int32_t)len, se,
-                                                  dsamp ? (double *)dsamp + soff : nullptr, c->d_counter,
-                                                  c->grid_persistent, c->stream));
+                                                  dsamp ? (double *)dsamp + soff : nullptr, c->grid_persistent,
+                                                  c->stream));
             else
                 CUDA_TRY(c, launch_persistent_f32(make_dev<float>(c), c->step + done, (int32_t)len, se,
-                                                  dsamp ? (float *)dsamp + soff : nullptr, c->d_counter,
-                                                  c->grid_persistent, c->stream));
+                                                  dsamp ? (float *)dsamp + soff : nullptr, c->grid_persistent,
+                                                  c->stream));
             done += len;
         }
     } else {
@@ -581,6 +697,21 @@ hygro_status hygro_run(hygro_ctx *c, int64_t n_steps, int32_t sample_every, void
         }
     }
     c->step += n_steps;
+    if (c->d_trace != nullptr && c->kernel == HYGRO_KERNEL_PERSISTENT) {
+        std::vector<unsigned long long> tr((size_t)c->W * 4);
+        CUDA_TRY(c, cudaMemcpyAsync(tr.data(), c->d_trace, tr.size() * sizeof(unsigned long long),
+                                    cudaMemcpyDeviceToHost, c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        if (FILE *f = fopen(c->trace_path.c_str(), "a")) {
+            for (int w = 0; w < c->W; ++w) {
+                const unsigned long long *t = &tr[(size_t)w * 4];
+                fprintf(f, "%d %d %d %d %llu %llu %llu %d %d %d\n", w, (int)(t[0] >> 32), (int)((t[0] >> 8) & 0xFFFFFF),
+                        (int)(t[0] & 0xFF), t[1], t[2], t[3], c->walls[w].K, c->walls[w].N,
+                        c->walls[w].aligned ? (c->walls[w].simple ? 0 : 1) : (c->walls[w].simple ? 3 : 2));
+            }
+            fclose(f);
+        }
+    }
     if (host_samples) {
         CUDA_TRY(c, cudaMemcpyAsync(samples, dsamp, need, cudaMemcpyDeviceToHost, c->stream));
         return check_nonfinite(c);

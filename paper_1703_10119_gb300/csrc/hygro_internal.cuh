@@ -17,7 +17,20 @@ namespace hygro {
 constexpr int kMaxLayers = HYGRO_MAX_LAYERS;
 constexpr int kLayerStride = 12;   // reals per layer entry of a wall (9 used, padded)
 constexpr int kMaxK = 16;          // nodes per lane of the persistent kernel
-constexpr int kWarpsPerBlock = 4;  // persistent kernel: 128-thread blocks, one wall per warp
+// Persistent kernel: one wall per warp; warps per block by precision (register budget:
+// FP32 fits 12 warps per SM without spills, FP64 needs the 255-register budget of 8 warps).
+template <typename real>
+struct PersistCfg {
+    static constexpr int warps = sizeof(real) == 4 ? 12 : 8;
+};
+// Dynamic shared memory of the persistent kernel per warp (in reals): layer table, then two per-slot
+// tables of 32 lanes x kMaxK slots.
+constexpr int kSmemRealsPerWarp = kMaxLayers * kLayerStride + 2 * kMaxK * 32;
+template <typename real>
+constexpr size_t persistent_smem_bytes()
+{
+    return (size_t)PersistCfg<real>::warps * kSmemRealsPerWarp * sizeof(real);
+}
 constexpr int kForcingBatch = 16;  // steps of ambient forcing computed per warp-wide batch
 
 // Layer entry of one wall, in the wall's deviation variables (P' = Pv - P_ref):
@@ -29,14 +42,15 @@ constexpr int kForcingBatch = 16;  // steps of ambient forcing computed per warp
 enum { LT_KMA = 0, LT_KMB, LT_KTA, LT_KTB, LT_AA, LT_AB, LT_BA, LT_BB, LT_CHI };
 
 struct WallInfo {
-    int32_t N;          // nodes
-    int32_t K;          // persistent kernel: nodes per lane
-    int32_t Wl;         // persistent kernel: lanes holding nodes
-    int32_t m;          // persistent kernel: lanes 0..m-1 hold K-1 nodes, lanes m..Wl-1 hold K
-    int32_t node_off;   // first node in the concatenated field arrays
+    int32_t N;            // nodes
+    int32_t K;            // persistent kernel: nodes per lane
+    int32_t Wl;           // persistent kernel: lanes holding nodes (lane Wl-1 always holds K)
+    uint32_t short_mask;  // persistent kernel: bit i set when lane i holds K-1 nodes
+    int32_t node_off;     // first node in the concatenated field arrays
     int32_t n_layers;
-    int32_t layer_off;  // first layer entry of this wall
-    int32_t pad;
+    int32_t layer_off;    // first layer entry of this wall
+    int16_t aligned;      // 1 when every layer interface falls on a lane boundary
+    int16_t simple;       // 1 when kTT, cTT do not depend on Pv and cTM = 0 in every layer
 };
 
 struct FaceInfo {
@@ -72,7 +86,10 @@ struct DevCtx {
     double *cumul;               // [W][2][2] running sums of dt * flux, FP64
     double *flast;               // [W][2][2] flux of the last step
     int32_t *nonfinite;          // set to 1 when a wall turns non-finite
-    const int32_t *order;        // [W] wall order of the persistent work queue
+    const int32_t *order;        // walls of the persistent blocks in rounds of round_size (-1: empty entry)
+    const int32_t *block_off;    // [grid + 1] first entry of each persistent block's rounds in order
+    int32_t round_size;          // walls per round (warp i of a block takes entry i of each of its rounds)
+    unsigned long long *trace;   // optional [W][4]: SM id << 32 | block << 8 | warp, start ns, end ns, steps
     const int32_t *node_wall;    // [total nodes] (plain kernel)
     const int8_t *node_layer;    // [total nodes] (plain kernel)
     int32_t total_nodes;
@@ -81,9 +98,9 @@ struct DevCtx {
 
 // Launchers (defined in the kernel translation units). All are stream-ordered.
 cudaError_t launch_persistent_f32(const DevCtx<float> &d, int64_t n0, int32_t n_steps, int32_t sample_every,
-                                  float *samples, int32_t *queue_counter, int grid, cudaStream_t s);
+                                  float *samples, int grid, cudaStream_t s);
 cudaError_t launch_persistent_f64(const DevCtx<double> &d, int64_t n0, int32_t n_steps, int32_t sample_every,
-                                  double *samples, int32_t *queue_counter, int grid, cudaStream_t s);
+                                  double *samples, int grid, cudaStream_t s);
 cudaError_t occupancy_persistent_f32(int *blocks_per_sm);
 cudaError_t occupancy_persistent_f64(int *blocks_per_sm);
 

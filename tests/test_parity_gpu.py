@@ -35,10 +35,11 @@ def relinf(x, ref):
     return float(np.max(np.abs(np.asarray(x, np.float64) - ref)) / np.max(np.abs(ref)))
 
 
-def ragged_batch(Ns, n_steps, seed=7, dt=600.0):
+def ragged_batch(Ns, n_steps, seed=7, dt=600.0, simple_heat=False):
     """Walls with the given node counts, 1-3 layers (some a single node thick),
     noisy sinusoidal face 0, sinusoidal face 1, a few adiabatic faces, and all
-    coefficient terms switched on (Pv slopes of kTT, cTT, cTM storage, q_inf, g_inf)."""
+    coefficient terms switched on (Pv slopes of kTT, cTT, cTM storage, q_inf, g_inf);
+    with simple_heat, kTT and cTT are constant and cTM = 0 (the benchmark's materials)."""
     rng = np.random.default_rng(seed)
     walls = []
     for i, N in enumerate(Ns):
@@ -51,6 +52,8 @@ def ragged_batch(Ns, n_steps, seed=7, dt=600.0):
                                cM0=10 ** rng.uniform(*wk.CM0_LOG10_RANGE), b=rng.uniform(0, 2),
                                kTT0=rng.uniform(0.04, 2), aT=rng.uniform(0, 0.3), cTT0=rng.uniform(1e5, 2e6),
                                bT=rng.uniform(0, 0.3), chi=8.36e4))
+            if simple_heat:
+                layers[-1].update(aT=0.0, bT=0.0, chi=0.0)
         bc0 = dict(hT=25.0, hM=2e-8, T_mean=293.0, T_amp=10.0, P_mean=1200.0, P_amp=400.0,
                    phase_T=rng.uniform(0, 6.28), phase_P=rng.uniform(0, 6.28), q_inf=rng.uniform(-30, 30),
                    g_inf=rng.uniform(-2e-7, 2e-7))
@@ -105,11 +108,13 @@ def test_config1_single_wall(H, oracle_mod, precision, kernel):
     _compare(H, oracle_mod, wl, precision, kernel, 1440, 60)
 
 
+@pytest.mark.parametrize("simple_heat", [False, True])
 @pytest.mark.parametrize("precision,kernel", COMBOS)
-def test_ragged_batch_all_lane_layouts(H, oracle_mod, precision, kernel):
+def test_ragged_batch_all_lane_layouts(H, oracle_mod, precision, kernel, simple_heat):
     """Walls of 3..512 nodes: every nodes-per-lane count 1..16, short lanes, unused lanes,
-    interfaces inside lanes and on lane boundaries, adiabatic faces; an odd split of the run."""
-    wl = ragged_batch(EDGE_NS, 401)
+    interfaces inside lanes and on lane boundaries, adiabatic faces; an odd split of the run.
+    Both the general and the simple-heat (constant kTT, cTT, no cTM) persistent variants."""
+    wl = ragged_batch(EDGE_NS, 401, simple_heat=simple_heat)
     _compare(H, oracle_mod, wl, precision, kernel, 401, 7, splits=[200, 201])
 
 
