@@ -253,7 +253,7 @@ def config2(seed: int = 2, n_walls: int = 4096, n_steps: int = 52560, dt: float 
     u = uniform(keys[:, None], np.arange(8)[None, :])
     N = (n_min + np.floor(u[:, 0] * (n_max - n_min + 1))).astype(np.int32)
     L = 0.05 + 0.35 * u[:, 1]
-    nl = (1 + np.floor(u[:, 2] * 3)).astype(np.int32)
+    nl = np.minimum((1 + np.floor(u[:, 2] * 3)).astype(np.int32), N // 3)   # every layer >= 3 nodes
     phase_T = 2 * np.pi * u[:, 3]
     phase_P = 2 * np.pi * u[:, 4]
     firsts, pars = [], []
