@@ -181,6 +181,24 @@ HYGRO_API hygro_status hygro_get_step(const hygro_ctx *ctx, int64_t *step);
 HYGRO_API hygro_status hygro_get_state(hygro_ctx *ctx, void *buf, size_t *bytes);
 HYGRO_API hygro_status hygro_set_state(hygro_ctx *ctx, const void *buf, size_t bytes);
 
+/* Size of the fixed device array behind hygro_run_noalloc: 8 MiB. */
+#define HYGRO_NOALLOC_SCRATCH_BYTES (8u << 20)
+
+/* hygro_run for callers that cannot allocate device memory when they call it: a process whose device
+ * memory is held by its own pool allocator (PyTorch's caching allocator, for instance), where a
+ * direct cudaMalloc can fail or split the pool, or a time-critical loop that must not allocate.
+ * Same arguments, results and stream ordering as hygro_run; it calls no cudaMalloc, cudaFree or
+ * allocating library routine. Where hygro_run stages samples bound for host memory in a buffer it
+ * allocates, this call stages them in a fixed array of HYGRO_NOALLOC_SCRATCH_BYTES that the library
+ * keeps in global memory on every GPU that loads it, until the process exits; a call whose samples
+ * need more returns HYGRO_E_UNSUPPORTED and changes nothing. The first call on a device looks up the
+ * array's device address with that device current; make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents (each call overwrites in full what
+ * it stages, so nothing needs clearing); calls whose GPU work overlaps (other threads, streams or
+ * contexts) race on it. The paper has no counterpart to this entry point. */
+HYGRO_API hygro_status hygro_run_noalloc(hygro_ctx *ctx, int64_t n_steps, int32_t sample_every, void *samples,
+                                         size_t samples_bytes);
+
 /* Message of the last failed call on ctx (or of the last failed
  * hygro_create when ctx is NULL). Never NULL. */
 HYGRO_API const char *hygro_last_error(const hygro_ctx *ctx);

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -847,6 +848,101 @@ hygro_status hygro_set_state(hygro_ctx *c, const void *buf, size_t bytes)
     p += (size_t)c->W * 4 * sizeof(double);
     CUDA_TRY(c, cudaMemcpy(c->d_flast, p, (size_t)c->W * 4 * sizeof(double), cudaMemcpyHostToDevice));
     c->step = hdr[4];
+    return HYGRO_OK;
+}
+
+}  // extern "C"
+
+// ---- hygro_run_noalloc: the same run with no device allocation ----------------------------------
+//
+// hygro_run stages samples bound for host memory in a device buffer that it allocates (and grows)
+// on demand. This entry point stages them instead in the fixed array below, which is part of the
+// library image: every GPU that loads the library holds it in its global memory until the process
+// exits. Host code must not use the array's name as a device address (it names a host-side stand-in);
+// the device address is looked up once per device with that device current and then reused.
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[HYGRO_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_ptr[kNoallocMaxDevices] = {};
+}  // namespace
+
+extern "C" {
+
+hygro_status hygro_run_noalloc(hygro_ctx *c, int64_t n_steps, int32_t sample_every, void *samples,
+                               size_t samples_bytes)
+{
+    if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    if (n_steps < 0) return fail(c, HYGRO_E_INVALID, "n_steps must be >= 0");
+    if (samples != nullptr && sample_every < 1) return fail(c, HYGRO_E_INVALID, "sample_every must be >= 1");
+    if (!(c->have_materials && c->have_bc[0] && c->have_bc[1]))
+        return fail(c, HYGRO_E_STATE, "hygro_set_materials and hygro_set_bc (both faces) must come first");
+    const int64_t n_samples = samples ? n_steps / sample_every : 0;
+    const size_t need = (size_t)n_samples * c->W * 4 * c->real_size;
+    if (samples != nullptr && samples_bytes < need)
+        return fail(c, HYGRO_E_INVALID, "samples_bytes %zu < %zu needed", samples_bytes, need);
+    if (c->device < 0 || c->device >= kNoallocMaxDevices)
+        return fail(c, HYGRO_E_UNSUPPORTED, "device %d is beyond the no-allocation entry point's table", c->device);
+    const bool host_samples = samples != nullptr && n_samples > 0 && !is_device_ptr(samples);
+    if (host_samples && need > (size_t)HYGRO_NOALLOC_SCRATCH_BYTES)
+        return fail(c, HYGRO_E_UNSUPPORTED,
+                    "samples need %zu bytes of staging; hygro_run_noalloc holds %zu (use hygro_run, or fewer "
+                    "samples per call)",
+                    need, (size_t)HYGRO_NOALLOC_SCRATCH_BYTES);
+    if (n_steps == 0) return HYGRO_OK;
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
+
+    void *dsamp = samples;
+    if (host_samples) {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (g_noalloc_ptr[c->device] == nullptr) {
+            void *p = nullptr;
+            const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || p == nullptr)
+                return fail(c, HYGRO_E_CUDA, "cudaGetSymbolAddress of the staging array: %s", cudaGetErrorString(e));
+            g_noalloc_ptr[c->device] = p;
+        }
+        dsamp = g_noalloc_ptr[c->device];
+    }
+    if (n_samples == 0) dsamp = nullptr;
+    const int se = samples ? sample_every : 0;
+
+    // the staged samples are written in full by the kernels (both faces of every wall for every
+    // sample), so nothing in the array has to be cleared first
+    if (c->kernel == HYGRO_KERNEL_PERSISTENT) {
+        int64_t chunk = int64_t(1) << 30;
+        if (se > 0) chunk -= chunk % se;
+        int64_t done = 0;
+        while (done < n_steps) {
+            const int64_t len = std::min(chunk, n_steps - done);
+            const size_t soff = se > 0 ? (size_t)(done / se) * c->W * 4 : 0;
+            if (c->precision == HYGRO_FP64)
+                CUDA_TRY(c, launch_persistent_f64(make_dev<double>(c), c->step + done, (int32_t)len, se,
+                                                  dsamp ? (double *)dsamp + soff : nullptr, c->grid_persistent,
+                                                  c->stream));
+            else
+                CUDA_TRY(c, launch_persistent_f32(make_dev<float>(c), c->step + done, (int32_t)len, se,
+                                                  dsamp ? (float *)dsamp + soff : nullptr, c->grid_persistent,
+                                                  c->stream));
+            done += len;
+        }
+    } else {
+        for (int64_t s = 0; s < n_steps; ++s) {
+            const int32_t sidx = (se > 0 && (s + 1) % se == 0) ? (int32_t)((s + 1) / se - 1) : -1;
+            if (c->precision == HYGRO_FP64)
+                CUDA_TRY(c, launch_plain_step_f64(make_dev<double>(c), c->step + s, sidx, (double *)dsamp, c->stream));
+            else
+                CUDA_TRY(c, launch_plain_step_f32(make_dev<float>(c), c->step + s, sidx, (float *)dsamp, c->stream));
+            c->cur = 1 - c->cur;
+        }
+    }
+    c->step += n_steps;
+    if (host_samples) {
+        CUDA_TRY(c, cudaMemcpyAsync(samples, dsamp, need, cudaMemcpyDeviceToHost, c->stream));
+        return check_nonfinite(c);
+    }
     return HYGRO_OK;
 }
 

@@ -28,13 +28,14 @@ HYGRO_E_UNSUPPORTED = -7
 HYGRO_FP32, HYGRO_FP64 = 0, 1
 HYGRO_KERNEL_PERSISTENT, HYGRO_KERNEL_PLAIN = 0, 1
 HYGRO_BC_AMBIENT, HYGRO_BC_ADIABATIC, HYGRO_BC_ROOM = 0, 1, 2
+HYGRO_NOALLOC_SCRATCH_BYTES = 8 << 20
 STATUS_NAMES = {0: "HYGRO_OK", -1: "HYGRO_E_INVALID", -2: "HYGRO_E_NOMEM", -3: "HYGRO_E_CUDA",
                 -4: "HYGRO_E_STATE", -5: "HYGRO_E_NONFINITE", -6: "HYGRO_E_TIMEOUT", -7: "HYGRO_E_UNSUPPORTED"}
 
 # Exported entry points (names of include/hygro.h).
 ABI_FUNCTIONS = ("hygro_create", "hygro_set_materials", "hygro_set_bc", "hygro_run", "hygro_sync",
                  "hygro_fluxes", "hygro_get_fields", "hygro_set_fields", "hygro_get_step", "hygro_get_state",
-                 "hygro_set_state", "hygro_last_error", "hygro_destroy")
+                 "hygro_set_state", "hygro_last_error", "hygro_destroy", "hygro_run_noalloc")
 
 
 class hygro_desc(C.Structure):
@@ -86,6 +87,7 @@ def lib(build_if_missing: bool = False) -> C.CDLL:
         "hygro_set_materials": [P, P, P, P, P, P],
         "hygro_set_bc": [P, C.c_int32, P],
         "hygro_run": [P, C.c_int64, C.c_int32, P, C.c_size_t],
+        "hygro_run_noalloc": [P, C.c_int64, C.c_int32, P, C.c_size_t],
         "hygro_sync": [P],
         "hygro_fluxes": [P, P, P],
         "hygro_get_fields": [P, C.c_int32, P, P],
@@ -147,6 +149,10 @@ def hygro_set_bc(ctx, face: int, bcs):
 
 def hygro_run(ctx, n_steps: int, sample_every: int = 0, samples=None):
     _check(lib().hygro_run(ctx, int(n_steps), int(sample_every), _ptr(samples), _nbytes(samples)), ctx)
+
+
+def hygro_run_noalloc(ctx, n_steps: int, sample_every: int = 0, samples=None):
+    _check(lib().hygro_run_noalloc(ctx, int(n_steps), int(sample_every), _ptr(samples), _nbytes(samples)), ctx)
 
 
 def hygro_sync(ctx):
