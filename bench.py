@@ -325,6 +325,30 @@ def bench_ours(args):
             h.close()
         comparators["fp32_persistent_over_fp64_plain"] = value / world / comparators["fp64_plain"]["value"]
 
+    # whole-building workload (64 rooms x 6 walls, FP64 room nodes, 30 days): walls + rooms per run
+    other = {}
+    if not args.no_fp64:
+        wl3 = wk.config3(seed=3 + rank)
+        h = H.Hygro(wl3, precision="fp32", kernel="persistent", device=local, stream=stream.cuda_stream)
+        with torch.cuda.stream(stream):
+            h.run(wl3.n_steps)
+        torch.cuda.synchronize()
+        tl = []
+        for _ in range(3):
+            with torch.cuda.stream(stream):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                h.run(wl3.n_steps)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            tl.append(e0.elapsed_time(e1))
+        h.close()
+        ms3 = float(np.mean(tl))
+        other["rooms_64x6_30days"] = {"value": wl3.total_nodes * wl3.n_steps / (ms3 / 1e3), "unit": UNIT,
+                                      "ms_per_run": ms3, "walls": wl3.n_walls, "rooms": 64,
+                                      "note": "wall cell-updates/s; one block per room, FP64 room nodes"}
+
     # end to end through the C ABI with host buffers: inputs H2D, run, samples and fluxes D2H
     e2e = None
     if not args.no_e2e:
@@ -380,7 +404,7 @@ def bench_ours(args):
                            "l2": "flushed between timed runs (512 MB write)", "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,
                 "gpu_launches": args.steps, "clocks": cs.summary(), "parity_vs_oracle": parity,
-                "comparators": comparators, "wall_seconds_timed": t_wall}
+                "comparators": comparators, "other_workloads": other, "wall_seconds_timed": t_wall}
         print(json.dumps(line))
     if pg is not None:
         pg.destroy_process_group()

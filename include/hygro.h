@@ -130,6 +130,25 @@ typedef struct {
     double noise_dt;
 } hygro_bc;
 
+/* One room: a perfectly mixed air zone (paper Sec. 5.1, [eq:LAV_equation], [eq:LAV_couplage]).
+ * Air state Ta (K) and Pva (Pa), humidity ratio w = Pva / Pv_ref. Per step, with the wall surface
+ * values Ts, Pvs of the room's walls at level n (explicit coupling, Sec. 5.2 [eq:wbse_tn_exp]):
+ *   rho V / Pv_ref dPva/dt = g_vap + gv (w_out - w) + sum_walls A hM (Pvs - Pva)
+ *   rho V (cp_a + cp_v w) dTa/dt = Q_gain + Lv g_vap + gv cp_a (T_out - Ta) + Lv gv (w_out - w)
+ *                                  + sum_walls A [hT (Ts - Ta) + Lv hM (Pvs - Pva)]
+ * gv = rho V ach / 3600 (kg/s), outdoor air T_out, Pv_out as the ambient sinusoid of hygro_bc
+ * (no noise). Each room equation is advanced as one more DF node (its own value at level n replaced
+ * by the mean of levels n+1 and n-1; the heat capacity at level n), vapour first. */
+typedef struct {
+    double volume, ach, Q_gain, g_vap;   /* m^3, 1/h, W, kg/s */
+    double T_out_mean, T_out_amp, P_out_mean, P_out_amp, period, phase_T, phase_P;
+    double rho_a, cp_a, cp_v, Pv_ref;    /* kg/m^3, J/kg/K, J/kg/K, Pa */
+    double Ta0, Pa0;                     /* initial air state (both stored levels) */
+} hygro_room;
+
+/* Most walls one room may have (each wall has at most one face on a room). */
+#define HYGRO_MAX_ROOM_WALLS 8
+
 /* Create a context on desc->device. *out receives the context. */
 HYGRO_API hygro_status hygro_create(const hygro_desc *desc, hygro_ctx **out);
 
@@ -145,6 +164,15 @@ HYGRO_API hygro_status hygro_set_materials(hygro_ctx *ctx, const int32_t *n_laye
 /* Boundary description of one face (0: x = 0, 1: x = L) for every wall;
  * bc[w] for w in 0..n_walls-1, host memory. */
 HYGRO_API hygro_status hygro_set_bc(hygro_ctx *ctx, int32_t face, const hygro_bc *bc);
+
+/* Rooms of the whole-building model: rooms[r] for r in 0..n_rooms-1, wall_area[w] (m^2) the area
+ * of wall w seen by the room its HYGRO_BC_ROOM face points at (host memory, copied). Resets the room
+ * air to (Ta0, Pa0). Rooms need the persistent kernel. */
+HYGRO_API hygro_status hygro_set_rooms(hygro_ctx *ctx, int32_t n_rooms, const hygro_room *rooms,
+                                       const double *wall_area);
+
+/* Room air state of level 0 (n) or 1 (n-1): Ta[n_rooms], Pa[n_rooms] (host or device memory). */
+HYGRO_API hygro_status hygro_get_rooms(hygro_ctx *ctx, int32_t level, double *Ta, double *Pa);
 
 /* Advance n_steps DF steps (n_steps >= 0).
  * samples: NULL, or [n_steps / sample_every][n_walls][2 faces][2] of float

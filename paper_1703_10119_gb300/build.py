@@ -18,7 +18,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libhygro.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-SOURCES = ["hygro_api.cu", "df1d_plain.cu", "df1d_persistent_f32.cu", "df1d_persistent_f64.cu"]
+SOURCES = ["hygro_api.cu", "df1d_plain.cu", "df1d_persistent_f32.cu", "df1d_persistent_f64.cu", "df1d_rooms_f32.cu",
+           "df1d_rooms_f64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I" + INCLUDE]

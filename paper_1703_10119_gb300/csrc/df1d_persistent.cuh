@@ -249,10 +249,62 @@ __device__ __forceinline__ void df_step(real (&Tp)[K], const real (&Tc)[K], real
     fg = hm + L.gs;
 }
 
-// Everything one warp does for one wall over n_steps steps.
-template <typename real, int K, bool IFACE, bool SIMPLE>
+// Air state of a room and the level-n surface values of its walls, shared by the room's warps.
+struct RoomShared {
+    double Ta_p, Ta_c, Pa_p, Pa_c;        // levels n-1 and n
+    double surfT[HYGRO_MAX_ROOM_WALLS];   // room-side surface T of each wall at level n
+    double surfP[HYGRO_MAX_ROOM_WALLS];
+};
+
+// Room air node of Sec. 5.1 advanced from level n to n+1 in FP64 with the walls' level-n surface
+// values (explicit coupling of [eq:wbse_tn_exp]); the room's own value in its balance is the mean of
+// levels n+1 and n-1 (one more DF node), vapour first, heat capacity at level n.
+static __device__ __noinline__ void room_update(RoomShared &rs, const RoomInfo &ri, const FaceInfo *faces, int64_t n,
+                                         double t0, double dt, double Lv)
+{
+    const double *q = ri.par;
+    double AhT = 0.0, AhM = 0.0, AhTTs = 0.0, AhMPs = 0.0;
+    for (int i = 0; i < ri.n_walls; ++i) {
+        const FaceInfo &fc = faces[(size_t)ri.wall[i] * 2 + ri.face[i]];
+        const double A = ri.area[i];
+        AhT += A * fc.hT;
+        AhM += A * fc.hM;
+        AhTTs += A * fc.hT * rs.surfT[i];
+        AhMPs += A * fc.hM * rs.surfP[i];
+    }
+    const double two_pi = 6.283185307179586476925286766559;
+    const double t = t0 + (double)n * dt;
+    const double rhoV = q[RP_RHOA] * q[RP_VOL];
+    const double gv = rhoV * q[RP_ACH] / 3600.0;
+    double T_out = q[RP_TMEAN], P_out = q[RP_PMEAN];
+    if (q[RP_PERIOD] > 0.0) {
+        T_out += q[RP_TAMP] * sin(two_pi * t / q[RP_PERIOD] + q[RP_PHT]);
+        P_out += q[RP_PAMP] * sin(two_pi * t / q[RP_PERIOD] + q[RP_PHP]);
+    }
+    const double Pref = q[RP_PVREF];
+    const double w_out = P_out / Pref;
+    const double a_p = rhoV / Pref / (2.0 * dt);
+    const double k_p = gv / Pref + AhM;
+    const double Pa_n = ((a_p - 0.5 * k_p) * rs.Pa_p + q[RP_GVAP] + gv * w_out + AhMPs) / (a_p + 0.5 * k_p);
+    const double Pa_bar = 0.5 * (Pa_n + rs.Pa_p);
+    const double a_t = rhoV * (q[RP_CPA] + q[RP_CPV] * rs.Pa_c / Pref) / (2.0 * dt);
+    const double k_t = gv * q[RP_CPA] + AhT;
+    const double rhs = q[RP_QGAIN] + Lv * q[RP_GVAP] + gv * q[RP_CPA] * T_out + Lv * gv * (w_out - Pa_bar / Pref) +
+                       AhTTs + Lv * (AhMPs - AhM * Pa_bar);
+    const double Ta_n = ((a_t - 0.5 * k_t) * rs.Ta_p + rhs) / (a_t + 0.5 * k_t);
+    rs.Ta_p = rs.Ta_c;
+    rs.Ta_c = Ta_n;
+    rs.Pa_p = rs.Pa_c;
+    rs.Pa_c = Pa_n;
+}
+
+// Everything one warp does for one wall over n_steps steps. ROOM: the wall is one of the walls of
+// the block's room (rs, its face room_face on the room); every step then ends with the room update
+// between two block barriers, which all warps of the block pass once per step.
+template <typename real, int K, bool IFACE, bool SIMPLE, bool ROOM = false>
 __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi, int w, const real *tab, int64_t n0,
-                                      int32_t n_steps, int32_t sample_every, real *samples, real *sft, real *srt)
+                                      int32_t n_steps, int32_t sample_every, real *samples, real *sft, real *srt,
+                                      RoomShared *rs = nullptr, int room_face = -1)
 {
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -421,6 +473,48 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
     const FaceInfo &ff = fw[f_face];
     const bool f_ambient = ff.kind == HYGRO_BC_AMBIENT;
 
+    // room coupling: the lane of the room face takes the room air at level n as its ambient air and
+    // publishes its level-n surface values for the room update
+    const int room_lane = room_face == 0 ? 0 : Wl - 1;
+    const double Tref_d = (double)Tref, Pref_d = (double)Pref;
+    const int wib = threadIdx.x >> 5;
+    real acc_q = real(0), acc_g = real(0);
+    int64_t n_cur = n0;
+    auto one_step = [&](auto &Tp_, auto &Tc_, auto &Pp_, auto &Pc_, real bT, real bP, int src) {
+        real fT = __shfl_sync(FULL, bT, src);
+        real fP = __shfl_sync(FULL, bP, src);
+        if (ROOM) {
+            if (lane == room_lane) {
+                fT = (real)(rs->Ta_c - Tref_d);
+                fP = (real)(rs->Pa_c - Pref_d);
+            }
+        }
+        real fq, fg;
+        df_step<real, K, IFACE, SIMPLE>(Tp_, Tc_, Pp_, Pc_, L, tab, fT, fP, Lv, fq, fg, sft, srt);
+        acc_q += fq;
+        acc_g += fg;
+        last_q = fq;
+        last_g = fg;
+        sample(Tp_, Pp_);
+        if (ROOM) {
+            if (lane == room_lane) {
+                const int slot = room_face == 0 ? 0 : K - 1;
+                real ts = Tc_[0], ps = Pc_[0];
+#pragma unroll
+                for (int k = 1; k < K; ++k) {
+                    ts = k == slot ? Tc_[k] : ts;
+                    ps = k == slot ? Pc_[k] : ps;
+                }
+                rs->surfT[wib] = Tref_d + (double)ts;
+                rs->surfP[wib] = Pref_d + (double)ps;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) room_update(*rs, d.rooms[blockIdx.x], d.faces, n_cur, d.t0, d.dt, d.Lv);
+            __syncthreads();
+        }
+        ++n_cur;
+    };
+
     int s = 0;
     bool flipped = false;
     while (s < n_steps) {
@@ -428,35 +522,15 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
         // ambient air for steps n0+s .. n0+s+15: lane i<16 computes face 0 at step i, lane 16+i face 1
         real bT = real(0), bP = real(0);
         if (f_ambient) ambient_at(ff, d.noise, n0 + s + (lane % kForcingBatch), d.t0, d.dt, bT, bP);
-        real acc_q = real(0), acc_g = real(0);
+        acc_q = real(0);
+        acc_g = real(0);
         int i = 0;
         for (; i + 1 < cnt; i += 2) {
-            real fq, fg;
-            real fT = __shfl_sync(FULL, bT, src_base + i);
-            real fP = __shfl_sync(FULL, bP, src_base + i);
-            df_step<real, K, IFACE, SIMPLE>(Ta, Tb, Pa, Pb, L, tab, fT, fP, Lv, fq, fg, sft, srt);
-            acc_q += fq;
-            acc_g += fg;
-            sample(Ta, Pa);
-            fT = __shfl_sync(FULL, bT, src_base + i + 1);
-            fP = __shfl_sync(FULL, bP, src_base + i + 1);
-            df_step<real, K, IFACE, SIMPLE>(Tb, Ta, Pb, Pa, L, tab, fT, fP, Lv, fq, fg, sft, srt);
-            acc_q += fq;
-            acc_g += fg;
-            sample(Tb, Pb);
-            last_q = fq;
-            last_g = fg;
+            one_step(Ta, Tb, Pa, Pb, bT, bP, src_base + i);
+            one_step(Tb, Ta, Pb, Pa, bT, bP, src_base + i + 1);
         }
         if (i < cnt) {   // odd final step: afterwards level n lives in the "a" arrays
-            real fq, fg;
-            const real fT = __shfl_sync(FULL, bT, src_base + i);
-            const real fP = __shfl_sync(FULL, bP, src_base + i);
-            df_step<real, K, IFACE, SIMPLE>(Ta, Tb, Pa, Pb, L, tab, fT, fP, Lv, fq, fg, sft, srt);
-            acc_q += fq;
-            acc_g += fg;
-            sample(Ta, Pa);
-            last_q = fq;
-            last_g = fg;
+            one_step(Ta, Tb, Pa, Pb, bT, bP, src_base + i);
             flipped = true;
         }
         cum_q += (double)acc_q * d.dt;

@@ -93,6 +93,17 @@ struct hygro_ctx {
     int32_t *d_order = nullptr;
     int32_t *d_block_off = nullptr;
     unsigned long long *d_trace = nullptr;   // wall trace of the persistent kernel (HYGRO_TRACE)
+    // rooms (whole-building model)
+    std::vector<hygro_room> rooms;
+    std::vector<double> wall_area;
+    bool have_rooms = false;
+    RoomInfo *d_rooms = nullptr;
+    size_t rooms_cap = 0;
+    double *d_room_state = nullptr;
+    bool any_room_walls = false;   // some wall has a face on a room (those walls run in the room kernel)
+    int room_warps = 1;            // warps of the room kernel's blocks (most walls of one room)
+    int n_free = 0;                // walls of the persistent kernel
+    std::string room_issue;        // room configuration problem reported by hygro_run
     std::string trace_path;
     int32_t *d_node_wall = nullptr;
     int8_t *d_node_layer = nullptr;
@@ -126,7 +137,7 @@ void free_all(hygro_ctx *c)
 {
     void *ptrs[] = {c->dT[0], c->dT[1], c->dP[0], c->dP[1], c->d_walls, c->d_faces, c->d_layer_tab,
                     c->d_layer_first, c->d_noise, c->d_Tref, c->d_Pref, c->d_cumul, c->d_flast,
-                    c->d_nonfinite, c->d_order, c->d_block_off, c->d_trace, c->d_node_wall, c->d_node_layer, c->d_samples};
+                    c->d_nonfinite, c->d_order, c->d_block_off, c->d_trace, c->d_rooms, c->d_room_state, c->d_node_wall, c->d_node_layer, c->d_samples};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -155,6 +166,9 @@ DevCtx<real> make_dev(const hygro_ctx *c)
     d.block_off = c->d_block_off;
     d.round_size = c->round_size;
     d.trace = c->d_trace;
+    d.rooms = c->d_rooms;
+    d.room_state = c->d_room_state;
+    d.n_rooms = (int32_t)c->rooms.size();
     d.node_wall = c->d_node_wall;
     d.node_layer = c->d_node_layer;
     d.total_nodes = (int32_t)c->total_nodes;
@@ -314,6 +328,187 @@ void wall_layout(int N, const int32_t *first, int nl, WallInfo &wi)
     wi.aligned = aligned;
 }
 
+
+// Work partition of hygro_run. Walls with no face on a room go to the persistent kernel: sorted by
+// nodes per lane and code variant, cut into rounds, rounds dealt to blocks by LPT. Walls facing a
+// room are grouped by room for the room kernel. Problems of the room configuration are kept and
+// reported by hygro_run (rooms and boundaries may be set in either order).
+hygro_status build_schedule(hygro_ctx *c)
+{
+    if (!c->have_materials) return HYGRO_OK;
+    const int W = c->W;
+    std::vector<char> in_room(W, 0);
+    c->room_issue.clear();
+    const int NR = (int)c->rooms.size();
+    std::vector<std::vector<std::pair<int, int>>> members(NR);
+    char msg[256];
+    for (int w = 0; w < W; ++w) {
+        int nf = 0;
+        for (int f = 0; f < 2; ++f) {
+            if (!c->have_bc[f] || c->bc[f][w].bc.kind != HYGRO_BC_ROOM) continue;
+            ++nf;
+            const int r = c->bc[f][w].bc.room;
+            if (r < 0 || r >= NR) {
+                if (c->room_issue.empty()) {
+                    snprintf(msg, sizeof msg, "wall %d face %d: room %d is not defined (hygro_set_rooms)", w, f, r);
+                    c->room_issue = msg;
+                }
+                continue;
+            }
+            members[r].push_back({w, f});
+        }
+        if (nf > 0) in_room[w] = 1;
+        if (nf > 1 && c->room_issue.empty()) {
+            snprintf(msg, sizeof msg, "wall %d has both faces on rooms; a wall may face one room", w);
+            c->room_issue = msg;
+        }
+    }
+    c->any_room_walls = false;
+    c->room_warps = 1;
+    for (int w = 0; w < W; ++w)
+        if (in_room[w]) c->any_room_walls = true;
+    if (NR > 0) {
+        std::vector<RoomInfo> ri(NR);
+        for (int r = 0; r < NR; ++r) {
+            RoomInfo &o = ri[r];
+            memset(&o, 0, sizeof o);
+            if ((int)members[r].size() > HYGRO_MAX_ROOM_WALLS) {
+                if (c->room_issue.empty()) {
+                    snprintf(msg, sizeof msg, "room %d has %zu walls; at most %d", r, members[r].size(),
+                             HYGRO_MAX_ROOM_WALLS);
+                    c->room_issue = msg;
+                }
+                continue;
+            }
+            o.n_walls = (int32_t)members[r].size();
+            for (int i = 0; i < o.n_walls; ++i) {
+                o.wall[i] = members[r][i].first;
+                o.face[i] = members[r][i].second;
+                o.area[i] = c->wall_area[members[r][i].first];
+            }
+            const hygro_room &q = c->rooms[r];
+            const double pv[15] = {q.volume, q.ach, q.Q_gain, q.g_vap, q.T_out_mean, q.T_out_amp, q.P_out_mean,
+                                   q.P_out_amp, q.period, q.phase_T, q.phase_P, q.rho_a, q.cp_a, q.cp_v, q.Pv_ref};
+            for (int k = 0; k < 15; ++k) o.par[k] = pv[k];
+            c->room_warps = std::max(c->room_warps, (int)o.n_walls);
+        }
+        CUDA_TRY(c, cudaMemcpy(c->d_rooms, ri.data(), ri.size() * sizeof(RoomInfo), cudaMemcpyHostToDevice));
+    }
+    {
+        // Persistent blocks: walls sorted by nodes per lane and code variant, cut into rounds of
+        // round_size walls (one per warp of a block); rounds dealt to blocks largest estimated cost
+        // first, each to the least loaded block (LPT); a block runs its rounds largest first. Cost
+        // per step ~ K * (cost of a slot) + fixed part.
+        std::vector<int32_t> srt;
+        for (int w = 0; w < W; ++w)
+            if (!in_room[w]) srt.push_back(w);
+        const int Wf = (int)srt.size();
+        c->n_free = Wf;
+        const int G = c->grid_persistent;
+        const int wpb = c->precision == HYGRO_FP64 ? PersistCfg<double>::warps : PersistCfg<float>::warps;
+        const int R = std::max(1, std::min(wpb, Wf / G));
+        c->round_size = R;
+        // code variant (as in the kernel) and time per step of a wall with K nodes per lane when an SM
+        // is shared by its full warp count, a + b K (nanoseconds, measured on GB300 with a wall trace)
+        auto kind_of = [&](const WallInfo &x) {
+            const bool simple = x.simple && c->precision == HYGRO_FP32;
+            return x.aligned ? (simple ? 0 : 1) : (simple ? 3 : 2);
+        };
+        auto cost = [&](const WallInfo &x) {
+            static const double a[4] = {162.0, 190.0, 127.0, 199.0};
+            static const double b[4] = {41.3, 62.0, 102.0, 61.7};
+            const int k = kind_of(x);
+            return a[k] + b[k] * x.K;
+        };
+        std::stable_sort(srt.begin(), srt.end(), [&](int a, int b) {
+            const WallInfo &x = c->walls[a], &y = c->walls[b];
+            if (x.K != y.K) return x.K > y.K;
+            if (kind_of(x) != kind_of(y)) return kind_of(x) < kind_of(y);
+            return x.N > y.N;
+        });
+        const int n_rounds = (Wf + R - 1) / R;
+        std::vector<double> rcost(n_rounds, 0.0);
+        for (int i = 0; i < Wf; ++i) rcost[i / R] = std::max(rcost[i / R], cost(c->walls[srt[i]]));
+        std::vector<int32_t> ridx(n_rounds);
+        for (int r = 0; r < n_rounds; ++r) ridx[r] = r;
+        std::stable_sort(ridx.begin(), ridx.end(), [&](int a, int b) { return rcost[a] > rcost[b]; });
+        std::vector<double> load(G, 0.0);
+        std::vector<std::vector<int32_t>> lists(G);
+        for (int r : ridx) {
+            int best = 0;
+            for (int g = 1; g < G; ++g)
+                if (load[g] < load[best]) best = g;
+            load[best] += rcost[r];
+            lists[best].push_back(r);
+        }
+        std::vector<int32_t> order;
+        std::vector<int32_t> boff(G + 1, 0);
+        order.reserve((size_t)n_rounds * R);
+        for (int g = 0; g < G; ++g) {
+            boff[g] = (int32_t)order.size();
+            for (int r : lists[g])
+                for (int i = 0; i < R; ++i) order.push_back(r * R + i < Wf ? srt[r * R + i] : -1);
+        }
+        boff[G] = (int32_t)order.size();
+        if (!order.empty())
+            CUDA_TRY(c, cudaMemcpy(c->d_order, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+        CUDA_TRY(c, cudaMemcpy(c->d_block_off, boff.data(), boff.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    }
+    return HYGRO_OK;
+}
+
+// Checks that the rooms of a context can run (hygro_run, hygro_run_noalloc).
+hygro_status rooms_ready(hygro_ctx *c)
+{
+    if (!c->room_issue.empty()) return fail(c, HYGRO_E_STATE, "%s", c->room_issue.c_str());
+    if (c->any_room_walls && c->kernel != HYGRO_KERNEL_PERSISTENT)
+        return fail(c, HYGRO_E_UNSUPPORTED, "rooms need the persistent kernel");
+    return HYGRO_OK;
+}
+
+// Enqueues n_steps steps of every wall (and room) on the context's stream; samples go to dsamp.
+hygro_status launch_steps(hygro_ctx *c, int64_t n_steps, int se, void *dsamp)
+{
+    if (c->kernel == HYGRO_KERNEL_PERSISTENT) {
+        // chunks of whole sampling periods below 2^30 steps
+        int64_t chunk = int64_t(1) << 30;
+        if (se > 0) chunk -= chunk % se;
+        int64_t done = 0;
+        const int NR = (int)c->rooms.size();
+        while (done < n_steps) {
+            const int64_t len = std::min(chunk, n_steps - done);
+            const size_t soff = se > 0 ? (size_t)(done / se) * c->W * 4 : 0;
+            if (c->precision == HYGRO_FP64) {
+                double *sp = dsamp ? (double *)dsamp + soff : nullptr;
+                if (c->n_free > 0)
+                    CUDA_TRY(c, launch_persistent_f64(make_dev<double>(c), c->step + done, (int32_t)len, se, sp,
+                                                      c->grid_persistent, c->stream));
+                if (c->any_room_walls)
+                    CUDA_TRY(c, launch_rooms_f64(make_dev<double>(c), c->step + done, (int32_t)len, se, sp, NR,
+                                                 c->room_warps, c->stream));
+            } else {
+                float *sp = dsamp ? (float *)dsamp + soff : nullptr;
+                if (c->n_free > 0)
+                    CUDA_TRY(c, launch_persistent_f32(make_dev<float>(c), c->step + done, (int32_t)len, se, sp,
+                                                      c->grid_persistent, c->stream));
+                if (c->any_room_walls)
+                    CUDA_TRY(c, launch_rooms_f32(make_dev<float>(c), c->step + done, (int32_t)len, se, sp, NR,
+                                                 c->room_warps, c->stream));
+            }
+            done += len;
+        }
+    } else {
+        for (int64_t s = 0; s < n_steps; ++s) {
+            const int32_t sidx = (se > 0 && (s + 1) % se == 0) ? (int32_t)((s + 1) / se - 1) : -1;
+            if (c->precision == HYGRO_FP64)
+                CUDA_TRY(c, launch_plain_step_f64(make_dev<double>(c), c->step + s, sidx, (double *)dsamp, c->stream));
+            else
+                CUDA_TRY(c, launch_plain_step_f32(make_dev<float>(c), c->step + s, sidx, (float *)dsamp, c->stream));
+            c->cur = 1 - c->cur;
+        }
+    }
+    return HYGRO_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -525,62 +720,7 @@ hygro_status hygro_set_materials(hygro_ctx *c, const int32_t *n_layers, const in
     CUDA_TRY(c, cudaMemcpy(c->d_layer_first, layer_first, total_layers * sizeof(int32_t), cudaMemcpyHostToDevice));
     CUDA_TRY(c, cudaMemcpy(c->d_node_layer, node_layer.data(), node_layer.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(c, cudaMemcpy(c->d_walls, c->walls.data(), c->walls.size() * sizeof(WallInfo), cudaMemcpyHostToDevice));
-    {
-        // Persistent blocks: walls sorted by nodes per lane and code variant, cut into rounds of
-        // round_size walls (one per warp of a block); rounds dealt to blocks largest estimated cost
-        // first, each to the least loaded block (LPT); a block runs its rounds largest first. Cost
-        // per step ~ K * (cost of a slot) + fixed part.
-        const int G = c->grid_persistent;
-        const int wpb = c->precision == HYGRO_FP64 ? PersistCfg<double>::warps : PersistCfg<float>::warps;
-        const int R = std::max(1, std::min(wpb, W / G));
-        c->round_size = R;
-        // code variant (as in the kernel) and time per step of a wall with K nodes per lane when an SM
-        // is shared by its full warp count, a + b K (nanoseconds, measured on GB300 for variants 0 and 2)
-        auto kind_of = [&](const WallInfo &x) {
-            const bool simple = x.simple && c->precision == HYGRO_FP32;
-            return x.aligned ? (simple ? 0 : 1) : (simple ? 3 : 2);
-        };
-        auto cost = [&](const WallInfo &x) {
-            static const double a[4] = {162.0, 190.0, 127.0, 199.0};
-            static const double b[4] = {41.3, 62.0, 102.0, 61.7};
-            const int k = kind_of(x);
-            return a[k] + b[k] * x.K;
-        };
-        std::vector<int32_t> srt(W);
-        for (int w = 0; w < W; ++w) srt[w] = w;
-        std::stable_sort(srt.begin(), srt.end(), [&](int a, int b) {
-            const WallInfo &x = c->walls[a], &y = c->walls[b];
-            if (x.K != y.K) return x.K > y.K;
-            if (kind_of(x) != kind_of(y)) return kind_of(x) < kind_of(y);
-            return x.N > y.N;
-        });
-        const int n_rounds = (W + R - 1) / R;
-        std::vector<double> rcost(n_rounds, 0.0);
-        for (int i = 0; i < W; ++i) rcost[i / R] = std::max(rcost[i / R], cost(c->walls[srt[i]]));
-        std::vector<int32_t> ridx(n_rounds);
-        for (int r = 0; r < n_rounds; ++r) ridx[r] = r;
-        std::stable_sort(ridx.begin(), ridx.end(), [&](int a, int b) { return rcost[a] > rcost[b]; });
-        std::vector<double> load(G, 0.0);
-        std::vector<std::vector<int32_t>> lists(G);
-        for (int r : ridx) {
-            int best = 0;
-            for (int g = 1; g < G; ++g)
-                if (load[g] < load[best]) best = g;
-            load[best] += rcost[r];
-            lists[best].push_back(r);
-        }
-        std::vector<int32_t> order;
-        std::vector<int32_t> boff(G + 1, 0);
-        order.reserve((size_t)n_rounds * R);
-        for (int g = 0; g < G; ++g) {
-            boff[g] = (int32_t)order.size();
-            for (int r : lists[g])
-                for (int i = 0; i < R; ++i) order.push_back(r * R + i < W ? srt[r * R + i] : -1);
-        }
-        boff[G] = (int32_t)order.size();
-        CUDA_TRY(c, cudaMemcpy(c->d_order, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-        CUDA_TRY(c, cudaMemcpy(c->d_block_off, boff.data(), boff.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
-    }
+
     if ((st = upload_reals(c, c->d_Tref, c->Tref)) != HYGRO_OK) return st;
     if ((st = upload_reals(c, c->d_Pref, c->Pref)) != HYGRO_OK) return st;
     // uniform initial state: zero deviation at both levels, step 0, no accumulated flux
@@ -593,6 +733,8 @@ hygro_status hygro_set_materials(hygro_ctx *c, const int32_t *n_layers, const in
     c->step = 0;
     c->cur = 0;
     c->have_materials = true;
+    hygro_status sst = build_schedule(c);
+    if (sst != HYGRO_OK) return sst;
     return upload_faces(c);
 }
 
@@ -603,9 +745,9 @@ hygro_status hygro_set_bc(hygro_ctx *c, int32_t face, const hygro_bc *bc)
     if (bc == nullptr) return fail(c, HYGRO_E_INVALID, "bc is NULL");
     for (int w = 0; w < c->W; ++w) {
         const hygro_bc &b = bc[w];
-        if (b.kind == HYGRO_BC_ROOM)
-            return fail(c, HYGRO_E_UNSUPPORTED, "wall %d face %d: room faces need hygro_set_rooms", w, face);
-        if (b.kind != HYGRO_BC_AMBIENT && b.kind != HYGRO_BC_ADIABATIC)
+        if (b.kind == HYGRO_BC_ROOM && b.room < 0)
+            return fail(c, HYGRO_E_INVALID, "wall %d face %d: room index must be >= 0", w, face);
+        if (b.kind != HYGRO_BC_AMBIENT && b.kind != HYGRO_BC_ADIABATIC && b.kind != HYGRO_BC_ROOM)
             return fail(c, HYGRO_E_INVALID, "wall %d face %d: unknown kind %d", w, face, b.kind);
         if (b.kind == HYGRO_BC_ADIABATIC) continue;
         if (!finite_nonneg(b.hT) || !finite_nonneg(b.hM))
@@ -637,7 +779,74 @@ hygro_status hygro_set_bc(hygro_ctx *c, int32_t face, const hygro_bc *bc)
     }
     c->bc[face].swap(v);
     c->have_bc[face] = true;
+    hygro_status sst = build_schedule(c);
+    if (sst != HYGRO_OK) return sst;
     return upload_faces(c);
+}
+
+hygro_status hygro_set_rooms(hygro_ctx *c, int32_t n_rooms, const hygro_room *rooms, const double *wall_area)
+{
+    if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    if (n_rooms < 0) return fail(c, HYGRO_E_INVALID, "n_rooms must be >= 0");
+    if (n_rooms > 0 && (rooms == nullptr || wall_area == nullptr))
+        return fail(c, HYGRO_E_INVALID, "rooms and wall_area are required");
+    for (int r = 0; r < n_rooms; ++r) {
+        const hygro_room &q = rooms[r];
+        const double v[] = {q.volume, q.ach, q.Q_gain, q.g_vap, q.T_out_mean, q.T_out_amp, q.P_out_mean, q.P_out_amp,
+                            q.period, q.phase_T, q.phase_P, q.rho_a, q.cp_a, q.cp_v, q.Pv_ref, q.Ta0, q.Pa0};
+        for (double x : v)
+            if (!std::isfinite(x)) return fail(c, HYGRO_E_INVALID, "room %d: non-finite value", r);
+        if (!(q.volume > 0 && q.rho_a > 0 && q.cp_a > 0 && q.Pv_ref > 0 && q.ach >= 0 && q.period >= 0))
+            return fail(c, HYGRO_E_INVALID, "room %d: volume, rho_a, cp_a, Pv_ref must be > 0, ach, period >= 0", r);
+    }
+    if (n_rooms > 0)
+        for (int w = 0; w < c->W; ++w)
+            if (!finite_nonneg(wall_area[w])) return fail(c, HYGRO_E_INVALID, "wall %d: area must be >= 0", w);
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if ((size_t)n_rooms > c->rooms_cap) {
+        if (c->d_rooms) cudaFree(c->d_rooms);
+        if (c->d_room_state) cudaFree(c->d_room_state);
+        c->d_rooms = nullptr;
+        c->d_room_state = nullptr;
+        c->rooms_cap = 0;
+        CUDA_TRY(c, dalloc(&c->d_rooms, (size_t)n_rooms));
+        CUDA_TRY(c, dalloc(&c->d_room_state, (size_t)n_rooms * 4));
+        c->rooms_cap = (size_t)n_rooms;
+    }
+    c->rooms.assign(rooms, rooms + n_rooms);
+    if (n_rooms > 0)
+        c->wall_area.assign(wall_area, wall_area + c->W);
+    else
+        c->wall_area.clear();
+    std::vector<double> st((size_t)n_rooms * 4);
+    for (int r = 0; r < n_rooms; ++r) {
+        st[r * 4 + 0] = st[r * 4 + 1] = rooms[r].Ta0;
+        st[r * 4 + 2] = st[r * 4 + 3] = rooms[r].Pa0;
+    }
+    if (n_rooms > 0)
+        CUDA_TRY(c, cudaMemcpy(c->d_room_state, st.data(), st.size() * sizeof(double), cudaMemcpyHostToDevice));
+    c->have_rooms = true;
+    return build_schedule(c);
+}
+
+hygro_status hygro_get_rooms(hygro_ctx *c, int32_t level, double *Ta, double *Pa)
+{
+    if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    if (level != 0 && level != 1) return fail(c, HYGRO_E_INVALID, "level must be 0 (n) or 1 (n-1)");
+    const int NR = (int)c->rooms.size();
+    if (NR == 0) return HYGRO_OK;
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    std::vector<double> st((size_t)NR * 4), a(NR), b(NR);
+    CUDA_TRY(c, cudaMemcpy(st.data(), c->d_room_state, st.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int r = 0; r < NR; ++r) {
+        a[r] = st[r * 4 + (level == 0 ? 1 : 0)];
+        b[r] = st[r * 4 + (level == 0 ? 3 : 2)];
+    }
+    if (Ta) CUDA_TRY(c, cudaMemcpy(Ta, a.data(), NR * sizeof(double), cudaMemcpyDefault));
+    if (Pa) CUDA_TRY(c, cudaMemcpy(Pa, b.data(), NR * sizeof(double), cudaMemcpyDefault));
+    return HYGRO_OK;
 }
 
 hygro_status hygro_run(hygro_ctx *c, int64_t n_steps, int32_t sample_every, void *samples, size_t samples_bytes)
@@ -647,6 +856,10 @@ hygro_status hygro_run(hygro_ctx *c, int64_t n_steps, int32_t sample_every, void
     if (samples != nullptr && sample_every < 1) return fail(c, HYGRO_E_INVALID, "sample_every must be >= 1");
     if (!(c->have_materials && c->have_bc[0] && c->have_bc[1]))
         return fail(c, HYGRO_E_STATE, "hygro_set_materials and hygro_set_bc (both faces) must come first");
+    {
+        const hygro_status rst = rooms_ready(c);
+        if (rst != HYGRO_OK) return rst;
+    }
     const int64_t n_samples = samples ? n_steps / sample_every : 0;
     const size_t need = (size_t)n_samples * c->W * 4 * c->real_size;
     if (samples != nullptr && samples_bytes < need)
@@ -669,33 +882,9 @@ hygro_status hygro_run(hygro_ctx *c, int64_t n_steps, int32_t sample_every, void
     if (n_samples == 0) dsamp = nullptr;
     const int se = samples ? sample_every : 0;
 
-    if (c->kernel == HYGRO_KERNEL_PERSISTENT) {
-        // chunks of whole sampling periods below 2^30 steps
-        int64_t chunk = int64_t(1) << 30;
-        if (se > 0) chunk -= chunk % se;
-        int64_t done = 0;
-        while (done < n_steps) {
-            const int64_t len = std::min(chunk, n_steps - done);
-            const size_t soff = se > 0 ? (size_t)(done / se) * c->W * 4 : 0;
-            if (c->precision == HYGRO_FP64)
-                CUDA_TRY(c, launch_persistent_f64(make_dev<double>(c), c->step + done, (int32_t)len, se,
-                                                  dsamp ? (double *)dsamp + soff : nullptr, c->grid_persistent,
-                                                  c->stream));
-            else
-                CUDA_TRY(c, launch_persistent_f32(make_dev<float>(c), c->step + done, (int32_t)len, se,
-                                                  dsamp ? (float *)dsamp + soff : nullptr, c->grid_persistent,
-                                                  c->stream));
-            done += len;
-        }
-    } else {
-        for (int64_t s = 0; s < n_steps; ++s) {
-            const int32_t sidx = (se > 0 && (s + 1) % se == 0) ? (int32_t)((s + 1) / se - 1) : -1;
-            if (c->precision == HYGRO_FP64)
-                CUDA_TRY(c, launch_plain_step_f64(make_dev<double>(c), c->step + s, sidx, (double *)dsamp, c->stream));
-            else
-                CUDA_TRY(c, launch_plain_step_f32(make_dev<float>(c), c->step + s, sidx, (float *)dsamp, c->stream));
-            c->cur = 1 - c->cur;
-        }
+    {
+        const hygro_status lst = launch_steps(c, n_steps, se, dsamp);
+        if (lst != HYGRO_OK) return lst;
     }
     c->step += n_steps;
     if (c->d_trace != nullptr && c->kernel == HYGRO_KERNEL_PERSISTENT) {
@@ -800,7 +989,8 @@ hygro_status hygro_get_state(hygro_ctx *c, void *buf, size_t *bytes)
 {
     if (c == nullptr || bytes == nullptr) return fail(c, HYGRO_E_INVALID, "ctx or bytes is NULL");
     const size_t nf = (size_t)c->total_nodes * c->real_size;
-    const size_t need = 5 * sizeof(int64_t) + 4 * nf + 2 * (size_t)c->W * 4 * sizeof(double);
+    const size_t nroom = c->rooms.size() * 4 * sizeof(double);
+    const size_t need = 5 * sizeof(int64_t) + 4 * nf + 2 * (size_t)c->W * 4 * sizeof(double) + nroom;
     if (buf == nullptr) {
         *bytes = need;
         return HYGRO_OK;
@@ -820,6 +1010,8 @@ hygro_status hygro_get_state(hygro_ctx *c, void *buf, size_t *bytes)
     CUDA_TRY(c, cudaMemcpy(p, c->d_cumul, (size_t)c->W * 4 * sizeof(double), cudaMemcpyDeviceToHost));
     p += (size_t)c->W * 4 * sizeof(double);
     CUDA_TRY(c, cudaMemcpy(p, c->d_flast, (size_t)c->W * 4 * sizeof(double), cudaMemcpyDeviceToHost));
+    p += (size_t)c->W * 4 * sizeof(double);
+    if (nroom) CUDA_TRY(c, cudaMemcpy(p, c->d_room_state, nroom, cudaMemcpyDeviceToHost));
     *bytes = need;
     return HYGRO_OK;
 }
@@ -828,7 +1020,8 @@ hygro_status hygro_set_state(hygro_ctx *c, const void *buf, size_t bytes)
 {
     if (c == nullptr || buf == nullptr) return fail(c, HYGRO_E_INVALID, "ctx or buf is NULL");
     const size_t nf = (size_t)c->total_nodes * c->real_size;
-    const size_t need = 5 * sizeof(int64_t) + 4 * nf + 2 * (size_t)c->W * 4 * sizeof(double);
+    const size_t nroom = c->rooms.size() * 4 * sizeof(double);
+    const size_t need = 5 * sizeof(int64_t) + 4 * nf + 2 * (size_t)c->W * 4 * sizeof(double) + nroom;
     if (bytes < need) return fail(c, HYGRO_E_INVALID, "state image too small");
     int64_t hdr[5];
     memcpy(hdr, buf, sizeof hdr);
@@ -847,6 +1040,8 @@ hygro_status hygro_set_state(hygro_ctx *c, const void *buf, size_t bytes)
     CUDA_TRY(c, cudaMemcpy(c->d_cumul, p, (size_t)c->W * 4 * sizeof(double), cudaMemcpyHostToDevice));
     p += (size_t)c->W * 4 * sizeof(double);
     CUDA_TRY(c, cudaMemcpy(c->d_flast, p, (size_t)c->W * 4 * sizeof(double), cudaMemcpyHostToDevice));
+    p += (size_t)c->W * 4 * sizeof(double);
+    if (nroom) CUDA_TRY(c, cudaMemcpy(c->d_room_state, p, nroom, cudaMemcpyHostToDevice));
     c->step = hdr[4];
     return HYGRO_OK;
 }
@@ -879,6 +1074,10 @@ hygro_status hygro_run_noalloc(hygro_ctx *c, int64_t n_steps, int32_t sample_eve
     if (samples != nullptr && sample_every < 1) return fail(c, HYGRO_E_INVALID, "sample_every must be >= 1");
     if (!(c->have_materials && c->have_bc[0] && c->have_bc[1]))
         return fail(c, HYGRO_E_STATE, "hygro_set_materials and hygro_set_bc (both faces) must come first");
+    {
+        const hygro_status rst = rooms_ready(c);
+        if (rst != HYGRO_OK) return rst;
+    }
     const int64_t n_samples = samples ? n_steps / sample_every : 0;
     const size_t need = (size_t)n_samples * c->W * 4 * c->real_size;
     if (samples != nullptr && samples_bytes < need)
@@ -911,32 +1110,9 @@ hygro_status hygro_run_noalloc(hygro_ctx *c, int64_t n_steps, int32_t sample_eve
 
     // the staged samples are written in full by the kernels (both faces of every wall for every
     // sample), so nothing in the array has to be cleared first
-    if (c->kernel == HYGRO_KERNEL_PERSISTENT) {
-        int64_t chunk = int64_t(1) << 30;
-        if (se > 0) chunk -= chunk % se;
-        int64_t done = 0;
-        while (done < n_steps) {
-            const int64_t len = std::min(chunk, n_steps - done);
-            const size_t soff = se > 0 ? (size_t)(done / se) * c->W * 4 : 0;
-            if (c->precision == HYGRO_FP64)
-                CUDA_TRY(c, launch_persistent_f64(make_dev<double>(c), c->step + done, (int32_t)len, se,
-                                                  dsamp ? (double *)dsamp + soff : nullptr, c->grid_persistent,
-                                                  c->stream));
-            else
-                CUDA_TRY(c, launch_persistent_f32(make_dev<float>(c), c->step + done, (int32_t)len, se,
-                                                  dsamp ? (float *)dsamp + soff : nullptr, c->grid_persistent,
-                                                  c->stream));
-            done += len;
-        }
-    } else {
-        for (int64_t s = 0; s < n_steps; ++s) {
-            const int32_t sidx = (se > 0 && (s + 1) % se == 0) ? (int32_t)((s + 1) / se - 1) : -1;
-            if (c->precision == HYGRO_FP64)
-                CUDA_TRY(c, launch_plain_step_f64(make_dev<double>(c), c->step + s, sidx, (double *)dsamp, c->stream));
-            else
-                CUDA_TRY(c, launch_plain_step_f32(make_dev<float>(c), c->step + s, sidx, (float *)dsamp, c->stream));
-            c->cur = 1 - c->cur;
-        }
+    {
+        const hygro_status lst = launch_steps(c, n_steps, se, dsamp);
+        if (lst != HYGRO_OK) return lst;
     }
     c->step += n_steps;
     if (host_samples) {

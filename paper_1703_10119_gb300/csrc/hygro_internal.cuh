@@ -70,6 +70,17 @@ struct FaceInfo {
     int64_t nstep;        // noise table positions per step, scaled by 2^40
 };
 
+// A room and the walls facing it (room kernel: one block per room, one warp per wall).
+struct RoomInfo {
+    int32_t n_walls;
+    int32_t wall[HYGRO_MAX_ROOM_WALLS];   // ascending wall indices
+    int32_t face[HYGRO_MAX_ROOM_WALLS];   // which face of the wall is on the room
+    double area[HYGRO_MAX_ROOM_WALLS];    // m^2
+    double par[16];                       // hygro_room fields volume .. Pv_ref (15 used)
+};
+enum { RP_VOL = 0, RP_ACH, RP_QGAIN, RP_GVAP, RP_TMEAN, RP_TAMP, RP_PMEAN, RP_PAMP, RP_PERIOD, RP_PHT, RP_PHP,
+       RP_RHOA, RP_CPA, RP_CPV, RP_PVREF };
+
 template <typename real>
 struct DevCtx {
     const WallInfo *walls;       // [W]
@@ -90,6 +101,9 @@ struct DevCtx {
     const int32_t *block_off;    // [grid + 1] first entry of each persistent block's rounds in order
     int32_t round_size;          // walls per round (warp i of a block takes entry i of each of its rounds)
     unsigned long long *trace;   // optional [W][4]: SM id << 32 | block << 8 | warp, start ns, end ns, steps
+    const RoomInfo *rooms;       // [n_rooms] (room kernel)
+    double *room_state;          // [n_rooms][4]: Ta(n-1), Ta(n), Pa(n-1), Pa(n)
+    int32_t n_rooms;
     const int32_t *node_wall;    // [total nodes] (plain kernel)
     const int8_t *node_layer;    // [total nodes] (plain kernel)
     int32_t total_nodes;
@@ -103,6 +117,11 @@ cudaError_t launch_persistent_f64(const DevCtx<double> &d, int64_t n0, int32_t n
                                   double *samples, int grid, cudaStream_t s);
 cudaError_t occupancy_persistent_f32(int *blocks_per_sm);
 cudaError_t occupancy_persistent_f64(int *blocks_per_sm);
+
+cudaError_t launch_rooms_f32(const DevCtx<float> &d, int64_t n0, int32_t n_steps, int32_t sample_every,
+                             float *samples, int n_rooms, int warps, cudaStream_t s);
+cudaError_t launch_rooms_f64(const DevCtx<double> &d, int64_t n0, int32_t n_steps, int32_t sample_every,
+                             double *samples, int n_rooms, int warps, cudaStream_t s);
 
 cudaError_t launch_plain_step_f32(const DevCtx<float> &d, int64_t n, int32_t sample_idx, float *samples,
                                   cudaStream_t s);

@@ -35,7 +35,8 @@ STATUS_NAMES = {0: "HYGRO_OK", -1: "HYGRO_E_INVALID", -2: "HYGRO_E_NOMEM", -3: "
 # Exported entry points (names of include/hygro.h).
 ABI_FUNCTIONS = ("hygro_create", "hygro_set_materials", "hygro_set_bc", "hygro_run", "hygro_sync",
                  "hygro_fluxes", "hygro_get_fields", "hygro_set_fields", "hygro_get_step", "hygro_get_state",
-                 "hygro_set_state", "hygro_last_error", "hygro_destroy", "hygro_run_noalloc")
+                 "hygro_set_state", "hygro_last_error", "hygro_destroy", "hygro_run_noalloc", "hygro_set_rooms",
+                 "hygro_get_rooms")
 
 
 class hygro_desc(C.Structure):
@@ -54,6 +55,12 @@ class hygro_bc(C.Structure):
                 ("P_mean", C.c_double), ("P_amp", C.c_double), ("period", C.c_double), ("phase_T", C.c_double),
                 ("phase_P", C.c_double), ("noise", C.c_void_p), ("noise_len", C.c_int32),
                 ("noise_dt", C.c_double)]
+
+
+class hygro_room(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("volume", "ach", "Q_gain", "g_vap", "T_out_mean", "T_out_amp",
+                                          "P_out_mean", "P_out_amp", "period", "phase_T", "phase_P", "rho_a",
+                                          "cp_a", "cp_v", "Pv_ref", "Ta0", "Pa0")]
 
 
 class HygroError(RuntimeError):
@@ -95,6 +102,8 @@ def lib(build_if_missing: bool = False) -> C.CDLL:
         "hygro_get_step": [P, C.POINTER(C.c_int64)],
         "hygro_get_state": [P, P, C.POINTER(C.c_size_t)],
         "hygro_set_state": [P, P, C.c_size_t],
+        "hygro_set_rooms": [P, C.c_int32, P, P],
+        "hygro_get_rooms": [P, C.c_int32, P, P],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -190,6 +199,15 @@ def hygro_set_state(ctx, image: bytes):
     _check(lib().hygro_set_state(ctx, buf, len(image)), ctx)
 
 
+def hygro_set_rooms(ctx, n_rooms: int, rooms, wall_area):
+    _check(lib().hygro_set_rooms(ctx, int(n_rooms), C.cast(rooms, C.c_void_p) if rooms is not None else None,
+                                 _ptr(wall_area)), ctx)
+
+
+def hygro_get_rooms(ctx, level: int, Ta=None, Pa=None):
+    _check(lib().hygro_get_rooms(ctx, int(level), _ptr(Ta), _ptr(Pa)), ctx)
+
+
 def hygro_last_error(ctx) -> str:
     return lib().hygro_last_error(ctx).decode()
 
@@ -218,6 +236,8 @@ class Hygro:
         try:
             self.set_materials()
             self.set_bc()
+            if wl.rooms:
+                self.set_rooms()
         except Exception:
             hygro_destroy(self.ctx)
             self.ctx = None
@@ -248,6 +268,21 @@ class Hygro:
                     b.noise = nz[w].ctypes.data
                     b.noise_len = nz.shape[1]
             hygro_set_bc(self.ctx, f, arr)
+
+    def set_rooms(self):
+        rm = self.wl.rooms
+        par = np.asarray(rm["par"], np.float64)
+        arr = (hygro_room * len(par))()
+        for r in range(len(par)):
+            arr[r] = hygro_room(*[float(x) for x in par[r, :15]], float(rm["Ta0"][r]), float(rm["Pa0"][r]))
+        hygro_set_rooms(self.ctx, len(par), arr, np.ascontiguousarray(rm["wall_area"], np.float64))
+
+    def rooms(self, level: int = 0):
+        n = len(self.wl.rooms["par"]) if self.wl.rooms else 0
+        Ta = np.zeros(n)
+        Pa = np.zeros(n)
+        hygro_get_rooms(self.ctx, level, Ta, Pa)
+        return Ta, Pa
 
     def run(self, n_steps: int, sample_every: int = 0, samples=None):
         """Advance; ``samples`` (numpy or torch, working dtype) receives surface values."""

@@ -290,3 +290,52 @@ def config2(seed: int = 2, n_walls: int = 4096, n_steps: int = 52560, dt: float 
         bc_kind=np.zeros((n_walls, 2), np.int32), bc_par=bc_par,
         bc_room=np.full((n_walls, 2), -1, np.int32), noise=[nz0, None],
         dt=dt, t0=0.0, n_steps=n_steps)
+
+
+# Column order of a room parameter row (whole-building workloads).
+ROOM_FIELDS = ("volume", "ach", "Q_gain", "g_vap", "T_out_mean", "T_out_amp", "P_out_mean", "P_out_amp",
+               "period", "phase_T", "phase_P", "rho_a", "cp_a", "cp_v", "Pv_ref", "unused")
+
+
+def config3(seed: int = 3, n_rooms: int = 64, walls_per_room: int = 6, n_steps: int = 8640,
+            dt: float = 300.0, n_min: int = 80, n_max: int = 300) -> Workload:
+    """Whole building: rooms of six walls each, FP64 room air balances.
+
+    Each room is a cube of volume V ~ U[30, 200] m3 (wall area V^(2/3)) with
+    ventilation ACH ~ U[0.5, 2] 1/h, internal heat gain ~ U[100, 600] W and
+    vapour gain ~ U[0.05, 0.3] g/s. Walls: N ~ U{80..300}, materials as the
+    batch workload; face 0 outdoors (a shared daily sinusoid, 283 +- 8 K and
+    900 +- 300 Pa with seeded phases, plus hourly per-wall noise), face 1 on
+    the room (hT = 8, hM = 3e-8). The room's ventilation sees the same
+    outdoor sinusoid. Air: rho 1.2 kg/m3, cp 1006 / 1860 J/kg/K, Pv_ref
+    1.61e5 Pa (paper Sec. 5.1). Initial state 293 K / 1000 Pa everywhere.
+    dt = 300 s x 8640 (30 days).
+    """
+    n_walls = n_rooms * walls_per_room
+    base = config2(seed=seed, n_walls=n_walls, n_steps=n_steps, dt=dt, n_min=n_min, n_max=n_max,
+                   name=f"config3: {n_rooms} rooms x {walls_per_room} walls, dt={dt:g} s x {n_steps}")
+    key = stream_key(seed, 1 << 40)
+    g = uniform(key, np.arange(2))
+    phase_T, phase_P = 2 * np.pi * g[0], 2 * np.pi * g[1]
+    rooms = np.arange(n_rooms)
+    rk = stream_key(seed, rooms + (1 << 41))
+    u = uniform(rk[:, None], np.arange(4)[None, :])
+    V = 30.0 + 170.0 * u[:, 0]
+    par = np.zeros((n_rooms, 16))
+    par[:, 0] = V
+    par[:, 1] = 0.5 + 1.5 * u[:, 1]
+    par[:, 2] = 100.0 + 500.0 * u[:, 2]
+    par[:, 3] = (0.05 + 0.25 * u[:, 3]) * 1e-3
+    par[:, 4:11] = [283.0, 8.0, 900.0, 300.0, 86400.0, phase_T, phase_P]
+    par[:, 11:15] = [1.2, 1006.0, 1860.0, 1.61e5]
+    bc_par = base.bc_par.copy()
+    bc_par[:, 0, 4:11] = [283.0, 8.0, 900.0, 300.0, 86400.0, phase_T, phase_P]
+    bc_par[:, 1] = _bc_row(8.0, 3e-8, 293.0, 0.0, 1000.0, 0.0)
+    bc_kind = np.zeros((n_walls, 2), np.int32)
+    bc_kind[:, 1] = BC_ROOM
+    bc_room = np.full((n_walls, 2), -1, np.int32)
+    bc_room[:, 1] = np.repeat(rooms, walls_per_room)
+    area = np.repeat(V ** (2.0 / 3.0), walls_per_room)
+    return dataclasses.replace(base, bc_par=bc_par, bc_kind=bc_kind, bc_room=bc_room,
+                               rooms=dict(par=par, wall_area=area, Ta0=np.full(n_rooms, 293.0),
+                                          Pa0=np.full(n_rooms, 1000.0)))

@@ -1,0 +1,106 @@
+"""GPU parity of the whole-building model: walls coupled to FP64 room air nodes (paper Sec. 5).
+
+The room kernel (one block per room, one warp per wall, two block barriers per step) against the
+FP64 oracle's room_step on the same seeded inputs: wall fields, surface samples and room air states.
+Tolerances as the wall parity tests (FP64 1e-12, FP32 1e-4 relative L-infinity).
+"""
+import numpy as np
+import pytest
+
+from paper_1703_10119_gb300 import workloads as wk
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def H():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1703_10119_gb300 import build, hygro
+
+    build.build()
+    return hygro
+
+
+def relinf(x, ref):
+    return float(np.max(np.abs(np.asarray(x, np.float64) - ref)) / np.max(np.abs(ref)))
+
+
+def mixed_building(seed=4, n_steps=600):
+    """8 rooms of 1..8 walls (N 3..300, some multi-layer) plus free walls without rooms."""
+    base = wk.config3(seed=seed, n_rooms=8, walls_per_room=8, n_steps=n_steps, n_min=3, n_max=300)
+    counts = [1, 2, 3, 4, 5, 6, 7, 8]
+    keep = []
+    for r, c in enumerate(counts):
+        keep += list(range(r * 8, r * 8 + c))
+    sub = base.subset(keep)
+    sub.bc_kind = base.bc_kind[keep].copy()
+    sub.bc_room = base.bc_room[keep].copy()
+    # three more walls on room 2 become free walls (ambient on both faces)
+    free = wk.config2(seed=seed + 1, n_walls=5, n_steps=n_steps, n_min=3, n_max=200)
+    wl = wk.concat([sub, free])
+    wl.bc_kind = np.concatenate([sub.bc_kind, free.bc_kind])
+    wl.bc_room = np.concatenate([sub.bc_room, free.bc_room])
+    rooms = dict(base.rooms)
+    rooms["wall_area"] = np.concatenate([base.rooms["wall_area"][keep], np.zeros(free.n_walls)])
+    wl.rooms = rooms
+    return wl
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-4)])
+def test_rooms_mixed_building(H, oracle_mod, precision, tol):
+    wl = mixed_building()
+    g = H.Hygro(wl, precision=precision)
+    s1 = g.run_sampled(301, 7)
+    s2 = g.run_sampled(299, 13)
+    T, P = g.fields(0)
+    Ta, Pa = g.rooms(0)
+    Ta1, Pa1 = g.rooms(1)
+    g.close()
+    o = oracle_mod.Oracle(wl)
+    r1 = o.run(301, 7)
+    r2 = o.run(299, 13)
+    assert relinf(T, o.T_cur) <= tol and relinf(P, o.P_cur) <= tol
+    assert relinf(s1, r1["samples"]) <= tol and relinf(s2, r2["samples"]) <= tol
+    assert relinf(Ta, o.room[:, 1]) <= tol and relinf(Pa, o.room[:, 3]) <= tol
+    assert relinf(Ta1, o.room[:, 0]) <= tol and relinf(Pa1, o.room[:, 2]) <= tol
+
+
+def test_rooms_full_building_fp32(H, oracle_mod):
+    """The whole-building configuration (64 rooms x 6 walls, 30 days at dt = 300 s), FP32."""
+    wl = wk.config3()
+    g = H.Hygro(wl, precision="fp32")
+    s = g.run_sampled(wl.n_steps, 288)
+    T, P = g.fields(0)
+    Ta, Pa = g.rooms(0)
+    g.close()
+    o = oracle_mod.Oracle(wl)
+    r = o.run(wl.n_steps, 288)
+    assert relinf(T, o.T_cur) <= 1e-4 and relinf(P, o.P_cur) <= 1e-4
+    assert relinf(s, r["samples"]) <= 1e-4
+    assert relinf(Ta, o.room[:, 1]) <= 1e-4 and relinf(Pa, o.room[:, 3]) <= 1e-4
+
+
+def test_rooms_checkpoint_and_errors(H):
+    wl = mixed_building(n_steps=200)
+    g = H.Hygro(wl, precision="fp64")
+    g.run(50)
+    img = g.get_state()
+    g.run(31)
+    Ta, Pa = g.rooms(0)
+    T, P = g.fields(0)
+    g.set_state(img)
+    g.run(31)
+    Tb, Pb = g.rooms(0)
+    T2, P2 = g.fields(0)
+    assert np.array_equal(Ta, Tb) and np.array_equal(Pa, Pb)
+    assert np.array_equal(T, T2) and np.array_equal(P, P2)
+    g.close()
+    # rooms need the persistent kernel
+    h = H.Hygro(wl, precision="fp64", kernel="plain")
+    with pytest.raises(H.HygroError) as e:
+        h.run(1)
+    assert e.value.status == H.HYGRO_E_UNSUPPORTED
+    h.close()
