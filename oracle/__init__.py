@@ -23,6 +23,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hygro_oracle.c")
+_SRC2 = os.path.join(_HERE, "hygro_oracle2d.c")
 _HDR = os.path.join(_HERE, "hygro_oracle.h")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
@@ -35,13 +36,13 @@ NROOM_PAR = 16
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (OpenMP if available); return the .so path."""
     os.makedirs(_BUILD, exist_ok=True)
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_HDR))
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC2), os.path.getmtime(_HDR))
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
         return _LIB
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         raise RuntimeError("no C compiler found to build the oracle")
-    base = [cc, "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", _LIB + ".tmp", _SRC, "-lm"]
+    base = [cc, "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", _LIB + ".tmp", _SRC, _SRC2, "-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
     except subprocess.CalledProcessError:
@@ -70,6 +71,21 @@ class _State(C.Structure):
     ]
 
 
+class _Problem2D(C.Structure):
+    _fields_ = [
+        ("n_grids", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("h", C.c_double),
+        ("region", C.c_void_p), ("n_regions", C.c_int32), ("region_par", C.c_void_p),
+        ("bc_kind", C.c_void_p), ("bc_par", C.c_void_p),
+        ("noise", C.c_void_p * 4), ("noise_len", C.c_int32 * 4),
+        ("dt", C.c_double), ("t0", C.c_double), ("Lv", C.c_double), ("Psat", C.c_double),
+    ]
+
+
+class _State2D(C.Structure):
+    _fields_ = [("step", C.c_int64), ("T_prev", C.c_void_p), ("T_cur", C.c_void_p), ("P_prev", C.c_void_p),
+                ("P_cur", C.c_void_p)]
+
+
 _lib = None
 
 
@@ -83,6 +99,8 @@ def _load():
         lib.orc_ambient.restype = None
         lib.orc_ambient.argtypes = [C.POINTER(_Problem), C.c_int32, C.c_int32, C.c_double,
                                     C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        lib.orc2d_run.restype = C.c_int
+        lib.orc2d_run.argtypes = [C.POINTER(_Problem2D), C.POINTER(_State2D), C.c_int64, C.c_int32]
         lib.orc_coefficients.restype = None
         lib.orc_coefficients.argtypes = [C.POINTER(_Problem), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
         _lib = lib
@@ -213,3 +231,58 @@ class Oracle:
         face = np.zeros((N - 1, 3))
         _load().orc_coefficients(C.byref(self._p), int(w), _ptr(P), _ptr(node), _ptr(face))
         return node, face
+
+
+class Oracle2D:
+    """The oracle on a batch of 2D sections (attributes of ``sec``: n_grids, nx, ny, h, region
+    [G, ny, nx] uint8, region_par [G, n_regions, 9], bc_kind [G, 4], bc_par [G, 4, 12], noise (4 faces,
+    each [G, len, 2] float32 or None), dt, t0, Lv, Psat, T_init, P_init [G]). Level -1 := level 0."""
+
+    def __init__(self, sec, n_threads: int | None = None):
+        self.sec = sec
+        self.n_threads = n_threads or default_threads()
+        self._keep = []
+
+        def keep(a, dt):
+            a = np.ascontiguousarray(a, dtype=dt)
+            self._keep.append(a)
+            return a
+
+        G, ny, nx = sec.region.shape
+        p = _Problem2D()
+        p.n_grids, p.nx, p.ny, p.h = G, nx, ny, sec.h
+        p.region = _ptr(keep(sec.region, np.uint8))
+        p.n_regions = sec.region_par.shape[1]
+        p.region_par = _ptr(keep(sec.region_par, np.float64))
+        p.bc_kind = _ptr(keep(sec.bc_kind, np.int32))
+        p.bc_par = _ptr(keep(sec.bc_par, np.float64))
+        for f in range(4):
+            nz = sec.noise[f]
+            if nz is None:
+                p.noise[f] = None
+                p.noise_len[f] = 0
+            else:
+                nz = keep(nz, np.float32)
+                p.noise[f] = nz.ctypes.data
+                p.noise_len[f] = nz.shape[1]
+        p.dt, p.t0, p.Lv, p.Psat = sec.dt, sec.t0, sec.Lv, sec.Psat
+        self._p = p
+        shape = (G, ny, nx)
+        self.T_cur = np.broadcast_to(np.asarray(sec.T_init, np.float64)[:, None, None], shape).copy()
+        self.P_cur = np.broadcast_to(np.asarray(sec.P_init, np.float64)[:, None, None], shape).copy()
+        self.T_prev = self.T_cur.copy()
+        self.P_prev = self.P_cur.copy()
+        self.step = 0
+
+    def set_levels(self, T_prev, T_cur, P_prev, P_cur):
+        self.T_prev[...] = T_prev
+        self.T_cur[...] = T_cur
+        self.P_prev[...] = P_prev
+        self.P_cur[...] = P_cur
+
+    def run(self, n_steps: int):
+        st = _State2D(self.step, _ptr(self.T_prev), _ptr(self.T_cur), _ptr(self.P_prev), _ptr(self.P_cur))
+        rc = _load().orc2d_run(C.byref(self._p), C.byref(st), int(n_steps), int(self.n_threads))
+        if rc != 0:
+            raise RuntimeError(f"2D oracle run failed with code {rc}")
+        self.step = int(st.step)

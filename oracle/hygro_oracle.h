@@ -94,6 +94,28 @@ void orc_ambient(const orc_problem *p, int32_t wall, int32_t face, double t, dou
 void orc_coefficients(const orc_problem *p, int32_t wall, const double *P, double *node6 /* [N][6] */,
                       double *face3 /* [N-1][3] */);
 
+/* 2D wall sections (hygro_oracle2d.c): G grids of nx x ny nodes, spacing h in x and y. */
+typedef struct {
+    int32_t n_grids, nx, ny;
+    double h;                    /* m */
+    const uint8_t *region;       /* [G][ny][nx] material region of every node */
+    int32_t n_regions;           /* rows per grid in region_par */
+    const double *region_par;    /* [G][n_regions][ORC_NLAYER_PAR] */
+    const int32_t *bc_kind;      /* [G][4] faces 0: x = 0, 1: x = Lx, 2: y = 0, 3: y = Ly (ambient or adiabatic) */
+    const double *bc_par;        /* [G][4][ORC_NBC_PAR] */
+    const float *noise[4];       /* per face: [G][noise_len[f]][2] or NULL */
+    int32_t noise_len[4];
+    double dt, t0, Lv, Psat;
+} orc2d_problem;
+
+typedef struct {
+    int64_t step;
+    double *T_prev, *T_cur, *P_prev, *P_cur;   /* [G][ny][nx] */
+} orc2d_state;
+
+/* Advance n_steps DF steps of every grid (OpenMP over grids). 0 on success. */
+int orc2d_run(const orc2d_problem *p, orc2d_state *s, int64_t n_steps, int32_t n_threads);
+
 #ifdef __cplusplus
 }
 #endif

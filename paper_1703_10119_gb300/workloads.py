@@ -339,3 +339,97 @@ def config3(seed: int = 3, n_rooms: int = 64, walls_per_room: int = 6, n_steps: 
     return dataclasses.replace(base, bc_par=bc_par, bc_kind=bc_kind, bc_room=bc_room,
                                rooms=dict(par=par, wall_area=area, Ta0=np.full(n_rooms, 293.0),
                                           Pa0=np.full(n_rooms, 1000.0)))
+
+
+@dataclasses.dataclass
+class Section2D:
+    """A batch of 2D wall sections on uniform grids (dx = dy = h)."""
+    name: str
+    h: float
+    region: np.ndarray           # uint8 [G, ny, nx] material region of every node
+    region_par: np.ndarray       # float64 [G, n_regions, 9] (LAYER_FIELDS)
+    bc_kind: np.ndarray          # int32 [G, 4] faces 0: x = 0, 1: x = Lx, 2: y = 0, 3: y = Ly
+    bc_par: np.ndarray           # float64 [G, 4, 12] (BC_FIELDS)
+    noise: list                  # per face: float32 [G, noise_len, 2] or None
+    T_init: np.ndarray           # float64 [G]
+    P_init: np.ndarray           # float64 [G]
+    dt: float
+    t0: float
+    n_steps: int
+    Lv: float = LV
+    Psat: float = PSAT_REF
+
+    @property
+    def n_grids(self) -> int:
+        return int(self.region.shape[0])
+
+    @property
+    def ny(self) -> int:
+        return int(self.region.shape[1])
+
+    @property
+    def nx(self) -> int:
+        return int(self.region.shape[2])
+
+    @property
+    def total_nodes(self) -> int:
+        return int(self.region.size)
+
+    def subset(self, grids) -> "Section2D":
+        g = np.asarray(grids, dtype=np.int64)
+        return dataclasses.replace(
+            self, name=f"{self.name}[subset {len(g)}]", region=self.region[g].copy(),
+            region_par=self.region_par[g].copy(), bc_kind=self.bc_kind[g].copy(), bc_par=self.bc_par[g].copy(),
+            noise=[None if z is None else np.ascontiguousarray(z[g]) for z in self.noise],
+            T_init=self.T_init[g].copy(), P_init=self.P_init[g].copy())
+
+
+def config4(seed: int = 4, n_grids: int = 64, nx: int = 512, ny: int = 512, h: float = 1e-3, dt: float = 60.0,
+            n_steps: int = 10000) -> Section2D:
+    """Thermal-bridge corners: 2D sections with an L-shaped outer leaf and an optional inner column.
+
+    Per grid: region 0 = base material; region 1 = the L along the two exposed faces,
+    {x < a} u {y < b} with a, b ~ U[0.05, 0.25] of the section; region 2 (every other grid) = a
+    rectangle inside the base. Materials per region with the batch ranges (kM0 log-U[1e-12, 1e-10],
+    kTT U[0.04, 2], cTT U[1e5, 2e6], a, b U[0, 2], cM0 over Table 2's range; kTT, cTT independent of
+    Pv, no cTM). Faces x = 0 and y = 0 exchange with the outdoor air (hT = 25, hM = 2e-8,
+    293 + 10 sin(2 pi t/86400 + phi_T) K, 1200 + 400 sin(2 pi t/86400 + phi_P) Pa, hourly noise
+    sigma 1 K / 50 Pa, the same air on both faces); faces x = L and y = L are adiabatic. Uniform
+    initial state 293 K / 1000 Pa. dx = dy = 1 mm, dt = 60 s.
+    """
+    grids = np.arange(n_grids)
+    keys = stream_key(seed, grids + (1 << 42))
+    u = uniform(keys[:, None], np.arange(12)[None, :])
+    region = np.zeros((n_grids, ny, nx), np.uint8)
+    par = np.zeros((n_grids, 3, 9))
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    for g in range(n_grids):
+        a = int((0.05 + 0.2 * u[g, 0]) * nx)
+        b = int((0.05 + 0.2 * u[g, 1]) * ny)
+        r = region[g]
+        r[(xx < a) | (yy < b)] = 1
+        if g % 2 == 1:
+            x0 = a + int(u[g, 2] * (nx - a) * 0.5)
+            y0 = b + int(u[g, 3] * (ny - b) * 0.5)
+            x1 = min(nx, x0 + 4 + int(u[g, 4] * nx * 0.2))
+            y1 = min(ny, y0 + 4 + int(u[g, 5] * ny * 0.2))
+            r[y0:y1, x0:x1] = 2
+        v = uniform(keys[g], np.arange(100, 118)).reshape(3, 6)
+        for k in range(3):
+            par[g, k] = [10.0 ** (-12.0 + 2.0 * v[k, 0]), 2.0 * v[k, 1],
+                         10.0 ** (CM0_LOG10_RANGE[0] + (CM0_LOG10_RANGE[1] - CM0_LOG10_RANGE[0]) * v[k, 2]),
+                         2.0 * v[k, 3], 0.04 + 1.96 * v[k, 4], 0.0, 1e5 + 1.9e6 * v[k, 5], 0.0, 0.0]
+    bc_kind = np.tile(np.array([BC_AMBIENT, BC_ADIABATIC, BC_AMBIENT, BC_ADIABATIC], np.int32), (n_grids, 1))
+    bc_par = np.zeros((n_grids, 4, 12))
+    for f in (0, 2):
+        bc_par[:, f] = _bc_row(25.0, 2e-8, 293.0, 10.0, 1200.0, 400.0)
+        bc_par[:, f, 9] = 2 * np.pi * u[:, 6]
+        bc_par[:, f, 10] = 2 * np.pi * u[:, 7]
+    noise_len = int(math.ceil(n_steps * dt / 3600.0)) + 2
+    nkey = stream_key(seed, grids + (1 << 43))
+    z0, z1 = normal_pairs(nkey[:, None], np.arange(noise_len, dtype=np.uint64)[None, :])
+    nz = np.stack([1.0 * z0, 50.0 * z1], axis=-1).astype(np.float32)
+    return Section2D(name=f"config4: {n_grids} sections {nx}x{ny}, h={h:g} m, dt={dt:g} s x {n_steps}",
+                     h=h, region=region, region_par=par, bc_kind=bc_kind, bc_par=bc_par, noise=[nz, None, nz, None],
+                     T_init=np.full(n_grids, 293.0), P_init=np.full(n_grids, 1000.0), dt=dt, t0=0.0,
+                     n_steps=n_steps)
