@@ -56,6 +56,100 @@ uint64_t turns_fixed(double x)
 
 }  // namespace
 
+namespace hygro {
+
+hygro_status check_bc(const hygro_bc &b, bool allow_room, double t0, double dt, std::string *why)
+{
+    if (b.kind == HYGRO_BC_ROOM && !allow_room) {
+        *why = "room faces are not accepted here";
+        return HYGRO_E_INVALID;
+    }
+    if (b.kind == HYGRO_BC_ROOM && b.room < 0) {
+        *why = "room index must be >= 0";
+        return HYGRO_E_INVALID;
+    }
+    if (b.kind != HYGRO_BC_AMBIENT && b.kind != HYGRO_BC_ADIABATIC && b.kind != HYGRO_BC_ROOM) {
+        *why = "unknown kind " + std::to_string(b.kind);
+        return HYGRO_E_INVALID;
+    }
+    if (b.kind == HYGRO_BC_ADIABATIC) return HYGRO_OK;
+    if (!finite_nonneg(b.hT) || !finite_nonneg(b.hM)) {
+        *why = "hT and hM must be finite and >= 0";
+        return HYGRO_E_INVALID;
+    }
+    const double v[] = {b.q_inf, b.g_inf, b.T_mean, b.T_amp, b.P_mean, b.P_amp, b.phase_T, b.phase_P};
+    for (double x : v)
+        if (!std::isfinite(x)) {
+            *why = "non-finite value";
+            return HYGRO_E_INVALID;
+        }
+    if (!finite_nonneg(b.period)) {
+        *why = "period must be >= 0";
+        return HYGRO_E_INVALID;
+    }
+    if (b.noise_len < 0) {
+        *why = "noise_len < 0";
+        return HYGRO_E_INVALID;
+    }
+    if (b.noise_len > 0) {
+        if (b.noise == nullptr) {
+            *why = "noise is NULL";
+            return HYGRO_E_INVALID;
+        }
+        if (!(std::isfinite(b.noise_dt) && b.noise_dt > 0)) {
+            *why = "noise_dt must be > 0";
+            return HYGRO_E_INVALID;
+        }
+        if (b.noise_len > (1 << 22) || std::fabs(t0 / b.noise_dt) > 4.0e6 || dt / b.noise_dt > 4.0e6) {
+            *why = "noise table too long for its time step";
+            return HYGRO_E_UNSUPPORTED;
+        }
+        for (int64_t k = 0; k < 2 * (int64_t)b.noise_len; ++k)
+            if (!std::isfinite(b.noise[k])) {
+                *why = "non-finite noise";
+                return HYGRO_E_INVALID;
+            }
+    }
+    return HYGRO_OK;
+}
+
+FaceInfo face_info(const hygro_bc &b, double T_ref, double P_ref, double t0, double dt, int64_t noise_off,
+                   int64_t noise_len)
+{
+    FaceInfo o;
+    memset(&o, 0, sizeof o);
+    o.kind = b.kind;
+    o.room = b.room;
+    if (b.kind == HYGRO_BC_ADIABATIC) return o;
+    o.hT = b.hT;
+    o.hM = b.hM;
+    o.q_inf = b.q_inf;
+    o.g_inf = b.g_inf;
+    o.T_mean_dev = b.T_mean - T_ref;
+    o.T_amp = b.T_amp;
+    o.P_mean_dev = b.P_mean - P_ref;
+    o.P_amp = b.P_amp;
+    o.period = b.period;
+    o.phase_T = b.phase_T;
+    o.phase_P = b.phase_P;
+    o.noise_dt = b.noise_dt;
+    const double two_pi = 6.283185307179586476925286766559;
+    if (b.period > 0) {
+        o.phT0 = turns_fixed(t0 / b.period + b.phase_T / two_pi);
+        o.phP0 = turns_fixed(t0 / b.period + b.phase_P / two_pi);
+        o.pstep = turns_fixed(dt / b.period);
+    }
+    if (noise_len > 0) {
+        o.noise_len = (int32_t)noise_len;
+        o.noise_off = noise_off;
+        o.npos0 = (int64_t)std::llround(std::ldexp(t0 / b.noise_dt, 40));
+        o.nstep = (int64_t)std::llround(std::ldexp(dt / b.noise_dt, 40));
+    }
+    return o;
+}
+
+}  // namespace hygro
+
 struct hygro_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -218,39 +312,11 @@ hygro_status upload_faces(hygro_ctx *c)
     for (int w = 0; w < W; ++w)
         for (int f = 0; f < 2; ++f) {
             const RawBc &r = c->bc[f][w];
-            const hygro_bc &b = r.bc;
-            FaceInfo &o = fi[(size_t)w * 2 + f];
-            memset(&o, 0, sizeof o);
-            o.kind = b.kind;
-            o.room = b.room;
-            if (b.kind == HYGRO_BC_ADIABATIC) continue;
-            o.hT = b.hT;
-            o.hM = b.hM;
-            o.q_inf = b.q_inf;
-            o.g_inf = b.g_inf;
-            o.T_mean_dev = b.T_mean - c->Tref[w];
-            o.T_amp = b.T_amp;
-            o.P_mean_dev = b.P_mean - c->Pref[w];
-            o.P_amp = b.P_amp;
-            o.period = b.period;
-            o.phase_T = b.phase_T;
-            o.phase_P = b.phase_P;
-            o.noise_dt = b.noise_dt;
-            const double two_pi = 6.283185307179586476925286766559;
-            if (b.period > 0) {
-                o.phT0 = turns_fixed(c->t0 / b.period + b.phase_T / two_pi);
-                o.phP0 = turns_fixed(c->t0 / b.period + b.phase_P / two_pi);
-                o.pstep = turns_fixed(c->dt / b.period);
-            }
             const int64_t nl = (int64_t)r.noise.size() / 2;
-            if (nl > 0) {
-                o.noise_len = (int32_t)nl;
-                o.noise_off = (int64_t)off;
-                for (int64_t k = 0; k < nl; ++k) noise[off + k] = make_float2(r.noise[2 * k], r.noise[2 * k + 1]);
-                off += (size_t)nl;
-                o.npos0 = (int64_t)std::llround(std::ldexp(c->t0 / b.noise_dt, 40));
-                o.nstep = (int64_t)std::llround(std::ldexp(c->dt / b.noise_dt, 40));
-            }
+            fi[(size_t)w * 2 + f] = face_info(r.bc, c->Tref[w], c->Pref[w], c->t0, c->dt, (int64_t)off, nl);
+            if (r.bc.kind == HYGRO_BC_ADIABATIC) continue;
+            for (int64_t k = 0; k < nl; ++k) noise[off + k] = make_float2(r.noise[2 * k], r.noise[2 * k + 1]);
+            off += (size_t)nl;
         }
     if (noise.size() > c->noise_cap) {
         if (c->d_noise) cudaFree(c->d_noise);
@@ -744,29 +810,9 @@ hygro_status hygro_set_bc(hygro_ctx *c, int32_t face, const hygro_bc *bc)
     if (face != 0 && face != 1) return fail(c, HYGRO_E_INVALID, "face must be 0 or 1");
     if (bc == nullptr) return fail(c, HYGRO_E_INVALID, "bc is NULL");
     for (int w = 0; w < c->W; ++w) {
-        const hygro_bc &b = bc[w];
-        if (b.kind == HYGRO_BC_ROOM && b.room < 0)
-            return fail(c, HYGRO_E_INVALID, "wall %d face %d: room index must be >= 0", w, face);
-        if (b.kind != HYGRO_BC_AMBIENT && b.kind != HYGRO_BC_ADIABATIC && b.kind != HYGRO_BC_ROOM)
-            return fail(c, HYGRO_E_INVALID, "wall %d face %d: unknown kind %d", w, face, b.kind);
-        if (b.kind == HYGRO_BC_ADIABATIC) continue;
-        if (!finite_nonneg(b.hT) || !finite_nonneg(b.hM))
-            return fail(c, HYGRO_E_INVALID, "wall %d face %d: hT and hM must be finite and >= 0", w, face);
-        const double v[] = {b.q_inf, b.g_inf, b.T_mean, b.T_amp, b.P_mean, b.P_amp, b.phase_T, b.phase_P};
-        for (double x : v)
-            if (!std::isfinite(x)) return fail(c, HYGRO_E_INVALID, "wall %d face %d: non-finite value", w, face);
-        if (!finite_nonneg(b.period)) return fail(c, HYGRO_E_INVALID, "wall %d face %d: period must be >= 0", w, face);
-        if (b.noise_len < 0) return fail(c, HYGRO_E_INVALID, "wall %d face %d: noise_len < 0", w, face);
-        if (b.noise_len > 0) {
-            if (b.noise == nullptr) return fail(c, HYGRO_E_INVALID, "wall %d face %d: noise is NULL", w, face);
-            if (!(std::isfinite(b.noise_dt) && b.noise_dt > 0))
-                return fail(c, HYGRO_E_INVALID, "wall %d face %d: noise_dt must be > 0", w, face);
-            if (b.noise_len > (1 << 22) || std::fabs(c->t0 / b.noise_dt) > 4.0e6 || c->dt / b.noise_dt > 4.0e6)
-                return fail(c, HYGRO_E_UNSUPPORTED, "wall %d face %d: noise table too long for its time step", w,
-                            face);
-            for (int64_t k = 0; k < 2 * (int64_t)b.noise_len; ++k)
-                if (!std::isfinite(b.noise[k])) return fail(c, HYGRO_E_INVALID, "wall %d face %d: non-finite noise", w, face);
-        }
+        std::string why;
+        const hygro_status st = check_bc(bc[w], true, c->t0, c->dt, &why);
+        if (st != HYGRO_OK) return fail(c, st, "wall %d face %d: %s", w, face, why.c_str());
     }
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));

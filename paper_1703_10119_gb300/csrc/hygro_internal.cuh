@@ -10,6 +10,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "../../include/hygro.h"
 
 namespace hygro {
@@ -109,6 +111,15 @@ struct DevCtx {
     int32_t total_nodes;
     double dt, t0, Lv;
 };
+
+// Host helpers shared by the 1D and 2D entry points (hygro_api.cu).
+// Validates one face description (kind, coefficients, noise table against the time step); room faces
+// only where allow_room. Returns HYGRO_OK, or an error status with the reason in *why.
+hygro_status check_bc(const hygro_bc &b, bool allow_room, double t0, double dt, std::string *why);
+// Device form of one face in the deviation variables of its wall or section (reference T_ref, P_ref),
+// with its noise table at noise_off of the context's noise array.
+FaceInfo face_info(const hygro_bc &b, double T_ref, double P_ref, double t0, double dt, int64_t noise_off,
+                   int64_t noise_len);
 
 // Launchers (defined in the kernel translation units). All are stream-ordered.
 cudaError_t launch_persistent_f32(const DevCtx<float> &d, int64_t n0, int32_t n_steps, int32_t sample_every,

@@ -1,4 +1,4 @@
-"""Python binding of the hygro C ABI (include/hygro.h), argument marshalling only.
+"""Python binding of the hygro C ABI (include/hygro.h, include/hygro2d.h), argument marshalling only.
 
 Every computation runs in ``libhygro.so`` (CUDA, sm_103a), built in tree by
 ``paper_1703_10119_gb300.build``. Loading fails loudly when the library is
@@ -37,12 +37,24 @@ ABI_FUNCTIONS = ("hygro_create", "hygro_set_materials", "hygro_set_bc", "hygro_r
                  "hygro_fluxes", "hygro_get_fields", "hygro_set_fields", "hygro_get_step", "hygro_get_state",
                  "hygro_set_state", "hygro_last_error", "hygro_destroy", "hygro_run_noalloc", "hygro_set_rooms",
                  "hygro_get_rooms")
+# Exported entry points of the 2D sections (names of include/hygro2d.h).
+ABI_FUNCTIONS_2D = ("hygro2d_create", "hygro2d_set_materials", "hygro2d_set_bc", "hygro2d_run", "hygro2d_sync",
+                    "hygro2d_get_fields", "hygro2d_set_fields", "hygro2d_get_step", "hygro2d_last_error",
+                    "hygro2d_destroy")
+HYGRO2D_MAX_REGIONS = 8
 
 
 class hygro_desc(C.Structure):
     _fields_ = [("n_walls", C.c_int32), ("n_nodes", C.c_void_p), ("thickness", C.c_void_p),
                 ("dt", C.c_double), ("t0", C.c_double), ("Lv", C.c_double), ("Psat", C.c_double),
                 ("precision", C.c_int32), ("kernel", C.c_int32), ("device", C.c_int32), ("stream", C.c_void_p)]
+
+
+class hygro2d_desc(C.Structure):
+    _fields_ = [("n_grids", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("h", C.c_double),
+                ("dt", C.c_double), ("t0", C.c_double), ("Lv", C.c_double), ("Psat", C.c_double),
+                ("precision", C.c_int32), ("steps_per_launch", C.c_int32), ("device", C.c_int32),
+                ("stream", C.c_void_p)]
 
 
 class hygro_layer(C.Structure):
@@ -104,6 +116,14 @@ def lib(build_if_missing: bool = False) -> C.CDLL:
         "hygro_set_state": [P, P, C.c_size_t],
         "hygro_set_rooms": [P, C.c_int32, P, P],
         "hygro_get_rooms": [P, C.c_int32, P, P],
+        "hygro2d_create": [C.POINTER(hygro2d_desc), C.POINTER(P)],
+        "hygro2d_set_materials": [P, C.c_int32, P, P, P, P],
+        "hygro2d_set_bc": [P, C.c_int32, P],
+        "hygro2d_run": [P, C.c_int64],
+        "hygro2d_sync": [P],
+        "hygro2d_get_fields": [P, C.c_int32, P, P],
+        "hygro2d_set_fields": [P, C.c_int32, P, P],
+        "hygro2d_get_step": [P, C.POINTER(C.c_int64)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -113,6 +133,10 @@ def lib(build_if_missing: bool = False) -> C.CDLL:
     L.hygro_last_error.argtypes = [P]
     L.hygro_destroy.restype = None
     L.hygro_destroy.argtypes = [P]
+    L.hygro2d_last_error.restype = C.c_char_p
+    L.hygro2d_last_error.argtypes = [P]
+    L.hygro2d_destroy.restype = None
+    L.hygro2d_destroy.argtypes = [P]
     _lib = L
     return L
 
@@ -120,6 +144,11 @@ def lib(build_if_missing: bool = False) -> C.CDLL:
 def _check(status: int, ctx) -> None:
     if status != HYGRO_OK:
         raise HygroError(status, lib().hygro_last_error(ctx).decode())
+
+
+def _check2d(status: int, ctx) -> None:
+    if status != HYGRO_OK:
+        raise HygroError(status, lib().hygro2d_last_error(ctx).decode())
 
 
 def _ptr(a):
@@ -216,6 +245,69 @@ def hygro_destroy(ctx):
     lib().hygro_destroy(ctx)
 
 
+# ---- the 2D entry points, one to one ---------------------------------------------
+
+def hygro2d_create(desc: hygro2d_desc):
+    out = C.c_void_p()
+    _check2d(lib().hygro2d_create(C.byref(desc), C.byref(out)), None)
+    return out
+
+
+def hygro2d_set_materials(ctx, n_regions: int, region, layers, T_init, P_init):
+    _check2d(lib().hygro2d_set_materials(ctx, int(n_regions), _ptr(region), C.cast(layers, C.c_void_p),
+                                         _ptr(T_init), _ptr(P_init)), ctx)
+
+
+def hygro2d_set_bc(ctx, face: int, bcs):
+    _check2d(lib().hygro2d_set_bc(ctx, int(face), C.cast(bcs, C.c_void_p)), ctx)
+
+
+def hygro2d_run(ctx, n_steps: int):
+    _check2d(lib().hygro2d_run(ctx, int(n_steps)), ctx)
+
+
+def hygro2d_sync(ctx):
+    _check2d(lib().hygro2d_sync(ctx), ctx)
+
+
+def hygro2d_get_fields(ctx, level: int, T=None, P=None):
+    _check2d(lib().hygro2d_get_fields(ctx, int(level), _ptr(T), _ptr(P)), ctx)
+
+
+def hygro2d_set_fields(ctx, level: int, T=None, P=None):
+    _check2d(lib().hygro2d_set_fields(ctx, int(level), _ptr(T), _ptr(P)), ctx)
+
+
+def hygro2d_get_step(ctx) -> int:
+    s = C.c_int64()
+    _check2d(lib().hygro2d_get_step(ctx, C.byref(s)), ctx)
+    return s.value
+
+
+def hygro2d_last_error(ctx) -> str:
+    return lib().hygro2d_last_error(ctx).decode()
+
+
+def hygro2d_destroy(ctx):
+    lib().hygro2d_destroy(ctx)
+
+
+def _bc_array(n: int, kind, par, noise):
+    """hygro_bc[n] from kinds [n], rows [n, 12] and an optional noise table [n, len, 2] (kept alive by
+    the caller)."""
+    arr = (hygro_bc * n)()
+    for i in range(n):
+        p = par[i]
+        b = arr[i]
+        b.kind = int(kind[i])
+        (b.hT, b.hM, b.q_inf, b.g_inf, b.T_mean, b.T_amp, b.P_mean, b.P_amp, b.period, b.phase_T,
+         b.phase_P, b.noise_dt) = [float(x) for x in p]
+        if noise is not None:
+            b.noise = noise[i].ctypes.data
+            b.noise_len = noise.shape[1]
+    return arr
+
+
 # ---- convenience wrapper over a Workload --------------------------------------
 
 class Hygro:
@@ -255,18 +347,10 @@ class Hygro:
     def set_bc(self):
         wl = self.wl
         for f in range(2):
-            arr = (hygro_bc * wl.n_walls)()
             nz = None if wl.noise[f] is None else np.ascontiguousarray(wl.noise[f], np.float32)
+            arr = _bc_array(wl.n_walls, wl.bc_kind[:, f], wl.bc_par[:, f], nz)
             for w in range(wl.n_walls):
-                p = wl.bc_par[w, f]
-                b = arr[w]
-                b.kind = int(wl.bc_kind[w, f])
-                b.room = int(wl.bc_room[w, f])
-                (b.hT, b.hM, b.q_inf, b.g_inf, b.T_mean, b.T_amp, b.P_mean, b.P_amp, b.period, b.phase_T,
-                 b.phase_P, b.noise_dt) = [float(x) for x in p]
-                if nz is not None:
-                    b.noise = nz[w].ctypes.data
-                    b.noise_len = nz.shape[1]
+                arr[w].room = int(wl.bc_room[w, f])
             hygro_set_bc(self.ctx, f, arr)
 
     def set_rooms(self):
@@ -326,6 +410,78 @@ class Hygro:
     def close(self):
         if self.ctx is not None:
             hygro_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Hygro2D:
+    """A context holding a batch of 2D sections (workloads.Section2D) on the GPU."""
+
+    def __init__(self, sec, precision: str = "fp32", steps_per_launch: int = 0, device: int = 0, stream=None):
+        self.sec = sec
+        self.precision = {"fp32": HYGRO_FP32, "fp64": HYGRO_FP64}[precision]
+        d = hygro2d_desc(n_grids=sec.n_grids, nx=sec.nx, ny=sec.ny, h=sec.h, dt=sec.dt, t0=sec.t0, Lv=sec.Lv,
+                         Psat=sec.Psat, precision=self.precision, steps_per_launch=steps_per_launch, device=device,
+                         stream=stream)
+        self.ctx = hygro2d_create(d)
+        try:
+            self.set_materials()
+            self.set_bc()
+        except Exception:
+            hygro2d_destroy(self.ctx)
+            self.ctx = None
+            raise
+
+    def set_materials(self):
+        sec = self.sec
+        G, R = sec.region_par.shape[:2]
+        lay = (hygro_layer * (G * R))()
+        for i, row in enumerate(sec.region_par.reshape(G * R, -1)):
+            lay[i] = hygro_layer(*[float(x) for x in row])
+        hygro2d_set_materials(self.ctx, R, np.ascontiguousarray(sec.region, np.uint8), lay,
+                              np.ascontiguousarray(sec.T_init, np.float64), np.ascontiguousarray(sec.P_init, np.float64))
+
+    def set_bc(self):
+        sec = self.sec
+        for f in range(4):
+            nz = None if sec.noise[f] is None else np.ascontiguousarray(sec.noise[f], np.float32)
+            hygro2d_set_bc(self.ctx, f, _bc_array(sec.n_grids, sec.bc_kind[:, f], sec.bc_par[:, f], nz))
+
+    def run(self, n_steps: int):
+        hygro2d_run(self.ctx, n_steps)
+
+    def sync(self):
+        hygro2d_sync(self.ctx)
+
+    def fields(self, level: int = 0):
+        shape = (self.sec.n_grids, self.sec.ny, self.sec.nx)
+        T = np.zeros(shape)
+        P = np.zeros(shape)
+        hygro2d_get_fields(self.ctx, level, T, P)
+        return T, P
+
+    def set_fields(self, level: int, T, P):
+        hygro2d_set_fields(self.ctx, level, None if T is None else np.ascontiguousarray(T, np.float64),
+                           None if P is None else np.ascontiguousarray(P, np.float64))
+
+    @property
+    def step(self) -> int:
+        return hygro2d_get_step(self.ctx)
+
+    def close(self):
+        if self.ctx is not None:
+            hygro2d_destroy(self.ctx)
             self.ctx = None
 
     def __del__(self):

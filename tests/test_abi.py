@@ -12,9 +12,12 @@ from paper_1703_10119_gb300 import hygro as H
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared():
-    src = open(os.path.join(ROOT, "include", "hygro.h")).read()
-    return sorted(set(re.findall(r"HYGRO_API\s+[\w\s\*]*?\b(hygro_\w+)\s*\(", src)))
+def _declared(header=None):
+    names = set()
+    for h in ([header] if header else ("hygro.h", "hygro2d.h")):
+        src = open(os.path.join(ROOT, "include", h)).read()
+        names |= set(re.findall(r"HYGRO_API\s+[\w\s\*]*?\b(hygro2?d?_\w+)\s*\(", src))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -24,10 +27,12 @@ def lib():
 
 
 def test_header_declares_the_boundary():
-    names = _declared()
+    names = _declared("hygro.h")
     for must in ("hygro_create", "hygro_set_materials", "hygro_set_bc", "hygro_run", "hygro_fluxes"):
         assert must in names
     assert set(names) == set(H.ABI_FUNCTIONS)
+    names2d = _declared("hygro2d.h")
+    assert set(names2d) == set(H.ABI_FUNCTIONS_2D)
 
 
 def test_library_exports_every_declared_symbol(lib):
@@ -37,7 +42,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_exports_nothing_else(lib):
     out = os.popen(f"nm -D --defined-only {hb.LIB}").read()
-    exported = sorted(set(re.findall(r"\bT (hygro_\w+)", out)))
+    exported = sorted(set(re.findall(r"\bT (hygro2?d?_\w+)", out)))
     assert exported == _declared()
 
 
@@ -74,3 +79,22 @@ def test_null_context_calls_are_rejected(lib):
     assert lib.hygro_run(None, 1, 0, None, 0) == H.HYGRO_E_INVALID
     assert lib.hygro_sync(None) == H.HYGRO_E_INVALID
     lib.hygro_destroy(None)
+
+
+def test_2d_desc_layout_and_rejections_before_touching_the_device(lib):
+    assert C.sizeof(H.hygro2d_desc) == 3 * 4 + 4 + 5 * 8 + 3 * 4 + 4 + 8
+    good = dict(n_grids=1, nx=8, ny=8, h=1e-3, dt=60.0, Psat=2337.0)
+    for bad in (dict(n_grids=0), dict(nx=1), dict(ny=1), dict(h=0.0), dict(dt=-1.0), dict(Psat=0.0),
+                dict(precision=2), dict(steps_per_launch=9), dict(steps_per_launch=-1)):
+        d = H.hygro2d_desc(**{**good, **bad})
+        with pytest.raises(H.HygroError) as e:
+            H.hygro2d_create(d)
+        assert e.value.status == H.HYGRO_E_INVALID, bad
+    d = H.hygro2d_desc(**{**good, "precision": H.HYGRO_FP64, "steps_per_launch": 5})
+    with pytest.raises(H.HygroError) as e:
+        H.hygro2d_create(d)
+    assert e.value.status == H.HYGRO_E_INVALID and "steps_per_launch" in str(e.value)
+    assert lib.hygro2d_create(None, None) == H.HYGRO_E_INVALID
+    assert lib.hygro2d_run(None, 1) == H.HYGRO_E_INVALID
+    assert lib.hygro2d_sync(None) == H.HYGRO_E_INVALID
+    lib.hygro2d_destroy(None)
