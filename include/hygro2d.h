@@ -45,8 +45,7 @@ typedef struct {
     double h;                  /* node spacing in x and y, metres, > 0 */
     double dt, t0, Lv, Psat;   /* as in hygro_desc */
     int32_t precision;         /* HYGRO_FP32 or HYGRO_FP64 */
-    int32_t steps_per_launch;  /* DF steps fused in one launch (temporal blocking depth), 0 = the most the
-                                  kernel's halo allows (8 for FP32, 4 for FP64); any value in 1..that most */
+    int32_t steps_per_launch;  /* DF steps fused in one launch (temporal blocking depth), 1..4, or 0 for 4 */
     int32_t device;            /* CUDA device ordinal */
     void *stream;              /* cudaStream_t to run on, or NULL for the default stream */
 } hygro2d_desc;

@@ -18,13 +18,13 @@ using namespace hygro;
 
 namespace {
 
-// Tile shapes: FP32 64 x 64 cores with an 8-node halo (8 fused steps), 512 threads; FP64 32 x 32
-// cores with a 4-node halo, 256 threads (each fits one CTA's shared memory with both levels of T
-// and Pv, the two half-conductance arrays and the region map of its box).
-using Cfg32 = Tile2D<float, 64, 64, 8, 512>;
-using Cfg64 = Tile2D<double, 32, 32, 4, 256>;
-constexpr int kTX32 = 64, kTY32 = 64, kH32 = 8, kNT32 = 512;
-constexpr int kTX64 = 32, kTY64 = 32, kH64 = 4, kNT64 = 256;
+// Tile shapes (a 4-node halo, so up to 4 fused steps): FP32 64 x 64 cores in 72 x 72 boxes, 4 runs of
+// rows per column, two CTAs per SM; FP64 32 x 32 cores in 40 x 40 boxes, 4 runs, two CTAs per SM.
+// Each CTA holds both levels of its box as (T, Pv) pairs and the node flags in shared memory.
+constexpr int kTX32 = 64, kTY32 = 64, kH32 = 4, kSeg32 = 4, kMinB32 = 2;
+constexpr int kTX64 = 32, kTY64 = 32, kH64 = 4, kSeg64 = 4, kMinB64 = 2;
+using Cfg32 = Tile2D<float, kTX32, kTY32, kH32, kSeg32>;
+using Cfg64 = Tile2D<double, kTX64, kTY64, kH64, kSeg64>;
 
 thread_local std::string g_create_error2d = "no error";
 
@@ -68,10 +68,11 @@ struct hygro2d_ctx {
     int64_t step = 0;
     int set = 0;           // buffer set holding the newest levels
     std::string err = "no error";
-    // device: F[s][0..3] = T level n, T level n-1, P level n, P level n-1 of buffer set s
-    void *F[2][4] = {{nullptr, nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr, nullptr}};
-    CUtensorMap maps[2][4];
-    uint8_t *d_region = nullptr;
+    // device: F[s][0], F[s][1] = (T, Pv) pairs of level n and n-1 of buffer set s
+    void *F[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    CUtensorMap maps[2][2];
+    CUtensorMap flag_map;
+    uint8_t *d_flags8 = nullptr;   // node flags: region | neighbour-in-another-region bits
     void *d_tab = nullptr;
     FaceInfo *d_faces = nullptr;
     float2 *d_noise = nullptr;
@@ -107,9 +108,9 @@ hygro_status fail(hygro2d_ctx *c, hygro_status st, const char *fmt, ...)
 void free_all(hygro2d_ctx *c)
 {
     for (int s = 0; s < 2; ++s)
-        for (int f = 0; f < 4; ++f)
-            if (c->F[s][f]) cudaFree(c->F[s][f]);
-    void *p[] = {c->d_region, c->d_tab, c->d_faces, c->d_noise, c->d_flags};
+        for (int l = 0; l < 2; ++l)
+            if (c->F[s][l]) cudaFree(c->F[s][l]);
+    void *p[] = {c->d_flags8, c->d_tab, c->d_faces, c->d_noise, c->d_flags};
     for (void *q : p)
         if (q) cudaFree(q);
 }
@@ -118,44 +119,57 @@ hygro_status encode_maps(hygro2d_ctx *c)
 {
     PFN_cuTensorMapEncodeTiled_v12000 enc = encode_fn();
     if (enc == nullptr) return fail(c, HYGRO_E_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
-    const int BX = c->precision == HYGRO_FP64 ? Cfg64::BX : Cfg32::BX;
-    const int BY = c->precision == HYGRO_FP64 ? Cfg64::BY : Cfg32::BY;
-    const cuuint64_t dims[3] = {(cuuint64_t)c->nx, (cuuint64_t)c->ny, (cuuint64_t)c->G};
-    const cuuint64_t strides[2] = {(cuuint64_t)c->pitch * c->rs, (cuuint64_t)c->pitch * c->ny * c->rs};
-    const cuuint32_t box[3] = {(cuuint32_t)BX, (cuuint32_t)BY, 1};
-    const cuuint32_t estr[3] = {1, 1, 1};
-    const CUtensorMapDataType dtype =
-        c->precision == HYGRO_FP64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const bool f64 = c->precision == HYGRO_FP64;
+    const cuuint32_t BX = f64 ? Cfg64::BX : Cfg32::BX, BY = f64 ? Cfg64::BY : Cfg32::BY;
+    const cuuint64_t P = (cuuint64_t)c->pitch, NY = (cuuint64_t)c->ny;
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
     for (int s = 0; s < 2; ++s)
-        for (int f = 0; f < 4; ++f) {
-            const CUresult r = enc(&c->maps[s][f], dtype, 3, c->F[s][f], dims, strides, box, estr,
-                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-            if (r != CUDA_SUCCESS) return fail(c, HYGRO_E_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+        for (int l = 0; l < 2; ++l) {
+            CUresult r;
+            if (f64) {
+                // (T, Pv) doubles as a 4D tensor (component, x, y, grid): 16-byte rows of the innermost dimension
+                const cuuint64_t dims[4] = {2, (cuuint64_t)c->nx, NY, (cuuint64_t)c->G};
+                const cuuint64_t strides[3] = {16, P * 16, P * NY * 16};
+                const cuuint32_t box[4] = {2, BX, BY, 1};
+                r = enc(&c->maps[s][l], CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, c->F[s][l], dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            } else {
+                // (T, Pv) floats as one 8-byte element per node
+                const cuuint64_t dims[3] = {(cuuint64_t)c->nx, NY, (cuuint64_t)c->G};
+                const cuuint64_t strides[2] = {P * 8, P * NY * 8};
+                const cuuint32_t box[3] = {BX, BY, 1};
+                r = enc(&c->maps[s][l], CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, c->F[s][l], dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            }
+            if (r != CUDA_SUCCESS) return fail(c, HYGRO_E_CUDA, "cuTensorMapEncodeTiled (levels) failed (%d)", (int)r);
         }
+    const cuuint64_t dims[3] = {(cuuint64_t)c->nx, NY, (cuuint64_t)c->G};
+    const cuuint64_t strides[2] = {P, P * NY};
+    const cuuint32_t box[3] = {(cuuint32_t)(f64 ? Cfg64::FBX : Cfg32::FBX), BY, 1};
+    const CUresult r = enc(&c->flag_map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, c->d_flags8, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(c, HYGRO_E_CUDA, "cuTensorMapEncodeTiled (flags) failed (%d)", (int)r);
     return HYGRO_OK;
 }
 
-template <typename real, int TX, int TY, int H, int NT>
+template <typename real, int TX, int TY, int H, int SEG, int MINB>
 cudaError_t launch2d(const hygro2d_ctx *c, int64_t n0, int n_sub)
 {
-    using L = Tile2D<real, TX, TY, H, NT>;
-    auto kern = df2d_kernel<real, TX, TY, H, NT>;
+    using L = Tile2D<real, TX, TY, H, SEG>;
     Dev2D d;
     d.G = c->G;
     d.nx = c->nx;
     d.ny = c->ny;
     d.pitch = c->pitch;
     d.n_regions = c->n_regions;
-    d.region = c->d_region;
     d.region_tab = c->d_tab;
     d.faces = c->d_faces;
     d.noise = c->d_noise;
-    const int out = 1 - c->set;
-    d.outT[0] = c->F[out][0];
-    d.outT[1] = c->F[out][1];
-    d.outP[0] = c->F[out][2];
-    d.outP[1] = c->F[out][3];
+    d.out_new = c->F[1 - c->set][0];
+    d.out_old = c->F[1 - c->set][1];
     d.err = c->d_flags;
     d.nonfinite = c->d_flags + 1;
     d.dt = c->dt;
@@ -163,7 +177,8 @@ cudaError_t launch2d(const hygro2d_ctx *c, int64_t n0, int n_sub)
     d.Lv = c->Lv;
     const int tiles = ((c->nx + TX - 1) / TX) * ((c->ny + TY - 1) / TY);
     const CUtensorMap *m = c->maps[c->set];
-    kern<<<(unsigned)((int64_t)tiles * c->G), NT, L::BYTES, c->stream>>>(m[0], m[1], m[2], m[3], d, n0, n_sub);
+    df2d_kernel<real, TX, TY, H, SEG, MINB><<<(unsigned)((int64_t)tiles * c->G), L::NT, L::BYTES, c->stream>>>(
+        m[0], m[1], c->flag_map, d, n0, n_sub);
     return cudaGetLastError();
 }
 
@@ -171,9 +186,9 @@ cudaError_t launch2d(const hygro2d_ctx *c, int64_t n0, int n_sub)
 cudaError_t prepare_kernel(int precision)
 {
     if (precision == HYGRO_FP64)
-        return cudaFuncSetAttribute(df2d_kernel<double, kTX64, kTY64, kH64, kNT64>,
+        return cudaFuncSetAttribute(df2d_kernel<double, kTX64, kTY64, kH64, kSeg64, kMinB64>,
                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg64::BYTES);
-    return cudaFuncSetAttribute(df2d_kernel<float, kTX32, kTY32, kH32, kNT32>,
+    return cudaFuncSetAttribute(df2d_kernel<float, kTX32, kTY32, kH32, kSeg32, kMinB32>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg32::BYTES);
 }
 
@@ -206,40 +221,58 @@ hygro_status upload_faces2d(hygro2d_ctx *c)
     return HYGRO_OK;
 }
 
-// Device field <-> absolute FP64 [G][ny][nx] host array.
-hygro_status download_field(hygro2d_ctx *c, const void *src, const std::vector<double> &ref, std::vector<double> &out)
+// Device level (pairs) <-> absolute FP64 [G][ny][nx] host arrays of T and P (either may be skipped).
+hygro_status download_level(hygro2d_ctx *c, const void *src, std::vector<double> *T, std::vector<double> *P)
 {
     const size_t n = c->cells();
-    std::vector<double> v(n);
+    std::vector<double> v(2 * n);
     if (c->precision == HYGRO_FP64) {
-        CUDA_TRY2(c, cudaMemcpy(v.data(), src, n * 8, cudaMemcpyDeviceToHost));
+        CUDA_TRY2(c, cudaMemcpy(v.data(), src, 2 * n * 8, cudaMemcpyDeviceToHost));
     } else {
-        std::vector<float> f(n);
-        CUDA_TRY2(c, cudaMemcpy(f.data(), src, n * 4, cudaMemcpyDeviceToHost));
-        for (size_t i = 0; i < n; ++i) v[i] = (double)f[i];
+        std::vector<float> f(2 * n);
+        CUDA_TRY2(c, cudaMemcpy(f.data(), src, 2 * n * 4, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < 2 * n; ++i) v[i] = (double)f[i];
     }
-    out.resize((size_t)c->G * c->ny * c->nx);
+    const size_t m = (size_t)c->G * c->ny * c->nx;
+    if (T) T->resize(m);
+    if (P) P->resize(m);
     for (int g = 0; g < c->G; ++g)
         for (int j = 0; j < c->ny; ++j)
-            for (int i = 0; i < c->nx; ++i)
-                out[((size_t)g * c->ny + j) * c->nx + i] = v[((size_t)g * c->ny + j) * c->pitch + i] + ref[g];
+            for (int i = 0; i < c->nx; ++i) {
+                const size_t a = ((size_t)g * c->ny + j) * c->nx + i, b = ((size_t)g * c->ny + j) * c->pitch + i;
+                if (T) (*T)[a] = v[2 * b] + c->Tref[g];
+                if (P) (*P)[a] = v[2 * b + 1] + c->Pref[g];
+            }
     return HYGRO_OK;
 }
 
-hygro_status upload_field(hygro2d_ctx *c, void *dst, const std::vector<double> &ref, const std::vector<double> &in)
+// Overwrite the T and / or P components of one device level (absent components keep their values).
+hygro_status upload_level(hygro2d_ctx *c, void *dst, const std::vector<double> *T, const std::vector<double> *P)
 {
     const size_t n = c->cells();
-    std::vector<double> v(n, 0.0);
+    std::vector<double> v(2 * n, 0.0);
+    if (!(T && P)) {
+        // read-modify-write: keep the component not given
+        if (c->precision == HYGRO_FP64) {
+            CUDA_TRY2(c, cudaMemcpy(v.data(), dst, 2 * n * 8, cudaMemcpyDeviceToHost));
+        } else {
+            std::vector<float> f(2 * n);
+            CUDA_TRY2(c, cudaMemcpy(f.data(), dst, 2 * n * 4, cudaMemcpyDeviceToHost));
+            for (size_t i = 0; i < 2 * n; ++i) v[i] = (double)f[i];
+        }
+    }
     for (int g = 0; g < c->G; ++g)
         for (int j = 0; j < c->ny; ++j)
-            for (int i = 0; i < c->nx; ++i)
-                v[((size_t)g * c->ny + j) * c->pitch + i] = in[((size_t)g * c->ny + j) * c->nx + i] - ref[g];
+            for (int i = 0; i < c->nx; ++i) {
+                const size_t a = ((size_t)g * c->ny + j) * c->nx + i, b = ((size_t)g * c->ny + j) * c->pitch + i;
+                if (T) v[2 * b] = (*T)[a] - c->Tref[g];
+                if (P) v[2 * b + 1] = (*P)[a] - c->Pref[g];
+            }
     if (c->precision == HYGRO_FP64) {
-        CUDA_TRY2(c, cudaMemcpy(dst, v.data(), n * 8, cudaMemcpyHostToDevice));
+        CUDA_TRY2(c, cudaMemcpy(dst, v.data(), 2 * n * 8, cudaMemcpyHostToDevice));
     } else {
-        std::vector<float> f(n);
-        for (size_t i = 0; i < n; ++i) f[i] = (float)v[i];
-        CUDA_TRY2(c, cudaMemcpy(dst, f.data(), n * 4, cudaMemcpyHostToDevice));
+        std::vector<float> f(v.begin(), v.end());
+        CUDA_TRY2(c, cudaMemcpy(dst, f.data(), 2 * n * 4, cudaMemcpyHostToDevice));
     }
     return HYGRO_OK;
 }
@@ -322,14 +355,14 @@ hygro_status hygro2d_create(const hygro2d_desc *desc, hygro2d_ctx **out)
     };
     CREATE2D_TRY(cu(cudaSetDevice(c->device), "cudaSetDevice"));
     CREATE2D_TRY(cu(prepare_kernel(c->precision), "cudaFuncSetAttribute(df2d_kernel)"));
-    const size_t bytes = c->cells() * c->rs;
+    const size_t bytes = c->cells() * 2 * c->rs;
     for (int s = 0; s < 2; ++s)
-        for (int f = 0; f < 4; ++f) {
-            CREATE2D_TRY(cu(cudaMalloc(&c->F[s][f], bytes), "cudaMalloc(fields)"));
-            CREATE2D_TRY(cu(cudaMemset(c->F[s][f], 0, bytes), "cudaMemset(fields)"));
+        for (int l = 0; l < 2; ++l) {
+            CREATE2D_TRY(cu(cudaMalloc(&c->F[s][l], bytes), "cudaMalloc(levels)"));
+            CREATE2D_TRY(cu(cudaMemset(c->F[s][l], 0, bytes), "cudaMemset(levels)"));
         }
-    CREATE2D_TRY(cu(cudaMalloc(&c->d_region, c->cells()), "cudaMalloc(region)"));
-    CREATE2D_TRY(cu(cudaMemset(c->d_region, 0, c->cells()), "cudaMemset(region)"));
+    CREATE2D_TRY(cu(cudaMalloc(&c->d_flags8, c->cells()), "cudaMalloc(node flags)"));
+    CREATE2D_TRY(cu(cudaMemset(c->d_flags8, 0, c->cells()), "cudaMemset(node flags)"));
     CREATE2D_TRY(cu(cudaMalloc(&c->d_faces, (size_t)c->G * 4 * sizeof(FaceInfo)), "cudaMalloc(faces)"));
     CREATE2D_TRY(cu(cudaMalloc(&c->d_flags, 2 * sizeof(int32_t)), "cudaMalloc(flags)"));
     CREATE2D_TRY(cu(cudaMemset(c->d_flags, 0, 2 * sizeof(int32_t)), "cudaMemset(flags)"));
@@ -396,13 +429,23 @@ hygro_status hygro2d_set_materials(hygro2d_ctx *c, int32_t n_regions, const uint
         std::vector<float> f(tab.begin(), tab.end());
         CUDA_TRY2(c, cudaMemcpy(c->d_tab, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
     }
-    std::vector<uint8_t> reg(c->cells(), 0);
+    // node flags: region, and one bit per neighbour that lies in another region
+    std::vector<uint8_t> fl(c->cells(), 0);
     for (int g = 0; g < c->G; ++g)
         for (int j = 0; j < c->ny; ++j)
-            memcpy(&reg[((size_t)g * c->ny + j) * c->pitch], &region[((size_t)g * c->ny + j) * c->nx], (size_t)c->nx);
-    CUDA_TRY2(c, cudaMemcpy(c->d_region, reg.data(), reg.size(), cudaMemcpyHostToDevice));
+            for (int i = 0; i < c->nx; ++i) {
+                const uint8_t *rg = region + (size_t)g * c->ny * c->nx;
+                const int r = rg[(size_t)j * c->nx + i];
+                uint32_t f = (uint32_t)r;
+                if (i > 0 && rg[(size_t)j * c->nx + i - 1] != r) f |= kDiffL;
+                if (i < c->nx - 1 && rg[(size_t)j * c->nx + i + 1] != r) f |= kDiffR;
+                if (j > 0 && rg[(size_t)(j - 1) * c->nx + i] != r) f |= kDiffU;
+                if (j < c->ny - 1 && rg[(size_t)(j + 1) * c->nx + i] != r) f |= kDiffD;
+                fl[((size_t)g * c->ny + j) * c->pitch + i] = (uint8_t)f;
+            }
+    CUDA_TRY2(c, cudaMemcpy(c->d_flags8, fl.data(), fl.size(), cudaMemcpyHostToDevice));
     // uniform initial state: zero deviation at both levels of the current set
-    for (int f = 0; f < 4; ++f) CUDA_TRY2(c, cudaMemset(c->F[c->set][f], 0, c->cells() * c->rs));
+    for (int l = 0; l < 2; ++l) CUDA_TRY2(c, cudaMemset(c->F[c->set][l], 0, c->cells() * 2 * c->rs));
     CUDA_TRY2(c, cudaMemset(c->d_flags, 0, 2 * sizeof(int32_t)));
     c->step = 0;
     c->have_materials = true;
@@ -444,8 +487,8 @@ hygro_status hygro2d_run(hygro2d_ctx *c, int64_t n_steps)
     for (int64_t done = 0; done < n_steps;) {
         const int sub = (int)std::min<int64_t>(c->k, n_steps - done);
         const cudaError_t e = c->precision == HYGRO_FP64
-                                  ? launch2d<double, kTX64, kTY64, kH64, kNT64>(c, c->step, sub)
-                                  : launch2d<float, kTX32, kTY32, kH32, kNT32>(c, c->step, sub);
+                                  ? launch2d<double, kTX64, kTY64, kH64, kSeg64, kMinB64>(c, c->step, sub)
+                                  : launch2d<float, kTX32, kTY32, kH32, kSeg32, kMinB32>(c, c->step, sub);
         if (e != cudaSuccess) return fail(c, HYGRO_E_CUDA, "2D DF launch: %s", cudaGetErrorString(e));
         c->set = 1 - c->set;
         c->step += sub;
@@ -474,14 +517,13 @@ hygro_status hygro2d_get_fields(hygro2d_ctx *c, int32_t level, double *T, double
     if (!c->have_materials) return fail(c, HYGRO_E_STATE, "hygro2d_set_materials must come first");
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
     CUDA_TRY2(c, cudaStreamSynchronize(c->stream));
-    std::vector<double> v;
-    for (int f = 0; f < 2; ++f) {
-        double *dst = f == 0 ? T : P;
-        if (dst == nullptr) continue;
-        const hygro_status st = download_field(c, c->F[c->set][2 * f + level], f == 0 ? c->Tref : c->Pref, v);
+    std::vector<double> vT, vP;
+    {
+        const hygro_status st = download_level(c, c->F[c->set][level], T ? &vT : nullptr, P ? &vP : nullptr);
         if (st != HYGRO_OK) return st;
-        CUDA_TRY2(c, cudaMemcpy(dst, v.data(), v.size() * sizeof(double), cudaMemcpyDefault));
     }
+    if (T) CUDA_TRY2(c, cudaMemcpy(T, vT.data(), vT.size() * sizeof(double), cudaMemcpyDefault));
+    if (P) CUDA_TRY2(c, cudaMemcpy(P, vP.data(), vP.size() * sizeof(double), cudaMemcpyDefault));
     return hygro2d_sync(c);
 }
 
@@ -501,13 +543,9 @@ hygro_status hygro2d_set_fields(hygro2d_ctx *c, int32_t level, const double *T, 
         for (double x : v[f])
             if (!std::isfinite(x)) return fail(c, HYGRO_E_INVALID, "non-finite field value");
     }
+    if (T == nullptr && P == nullptr) return HYGRO_OK;
     CUDA_TRY2(c, cudaStreamSynchronize(c->stream));
-    for (int f = 0; f < 2; ++f) {
-        if (v[f].empty()) continue;
-        const hygro_status st = upload_field(c, c->F[c->set][2 * f + level], f == 0 ? c->Tref : c->Pref, v[f]);
-        if (st != HYGRO_OK) return st;
-    }
-    return HYGRO_OK;
+    return upload_level(c, c->F[c->set][level], T ? &v[0] : nullptr, P ? &v[1] : nullptr);
 }
 
 hygro_status hygro2d_get_step(const hygro2d_ctx *c, int64_t *step)

@@ -90,7 +90,7 @@ def test_2d_desc_layout_and_rejections_before_touching_the_device(lib):
         with pytest.raises(H.HygroError) as e:
             H.hygro2d_create(d)
         assert e.value.status == H.HYGRO_E_INVALID, bad
-    d = H.hygro2d_desc(**{**good, "precision": H.HYGRO_FP64, "steps_per_launch": 5})
+    d = H.hygro2d_desc(**{**good, "precision": H.HYGRO_FP64, "steps_per_launch": 9})
     with pytest.raises(H.HygroError) as e:
         H.hygro2d_create(d)
     assert e.value.status == H.HYGRO_E_INVALID and "steps_per_launch" in str(e.value)
