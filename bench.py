@@ -7,7 +7,9 @@ One benchmark step = one hygro_run of the whole year on all walls with the
 persistent FP32 kernel (state carried over from step to step), inputs already
 resident in HBM; the L2 cache is flushed (512 MB write) between timed runs.
 Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle
-instead, on a bounded sample of the same workload.
+instead, on a bounded sample of the same workload. The line also carries the
+FP64 GPU comparators, the whole-building workload (64 rooms x 6 walls) and the
+2D thermal-bridge sections (64 x 512 x 512, 10000 steps) under other_workloads.
 
 Metric: DF cell-updates/s (one node advanced one step for both T and Pv).
 """
@@ -40,6 +42,13 @@ FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 KERNEL_SOURCES = ["paper_1703_10119_gb300/csrc/df1d_persistent.cuh", "paper_1703_10119_gb300/csrc/df1d_common.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "df1d_persistent_f32_traffic.json")
+# 2D sections: compulsory DRAM bytes of one cell-update when every step is a pass over memory (read the
+# (T, Pv) pairs of levels n and n-1, write the pair of level n+1, 4-byte reals)
+BYTES_PER_CELL_UPDATE_2D = 24
+STEPS_PER_LAUNCH_2D = 4
+KERNEL_SOURCES_2D = ["paper_1703_10119_gb300/csrc/df2d.cuh", "paper_1703_10119_gb300/csrc/df1d_common.cuh"]
+TRAFFIC_FILE_2D = os.path.join(ROOT, "profiles", "df2d_f32_traffic.json")
+FALLBACK_HBM_GBS = 6800.0
 
 
 def parse():
@@ -54,27 +63,39 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-2d", action="store_true")
+    p.add_argument("--only-2d", action="store_true", help="run only the 2D sections (profiling cases)")
+    p.add_argument("--sections", type=int, default=64, help="2D sections of 512 x 512")
+    p.add_argument("--section-steps", type=int, default=10000)
     return p.parse_args()
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(sources=None) -> str:
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources or KERNEL_SOURCES:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def measured_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel."""
+def measured_traffic(path=None, sources=None):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel source."""
     try:
-        with open(TRAFFIC_FILE) as fh:
+        with open(path or TRAFFIC_FILE) as fh:
             t = json.load(fh)
-        if t.get("kernel_source_sha") == kernel_source_hash():
+        if t.get("kernel_source_sha") == kernel_source_hash(sources):
             return t.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         pass
     return None
+
+
+def measured_hbm_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return FALLBACK_HBM_GBS
 
 
 class ClockSampler:
@@ -217,6 +238,60 @@ def bench_reference(args):
     print(json.dumps(line))
 
 
+def bench_sections(args, H, wk, stream, local, rank):
+    """The 2D thermal-bridge workload: throughput, its HBM roofline and parity on sampled sections."""
+    import torch
+
+    sec = wk.config4(seed=4 + rank, n_grids=args.sections, n_steps=args.section_steps)
+    h = H.Hygro2D(sec, precision="fp32", device=local, stream=stream.cuda_stream)
+    k = STEPS_PER_LAUNCH_2D
+    with torch.cuda.stream(stream):
+        h.run(100)
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h.run(sec.n_steps)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    h.sync()
+    h.close()
+    ms = e0.elapsed_time(e1)
+    units = sec.total_nodes * sec.n_steps
+    value = units / (ms / 1e3)
+    workload = f"{sec.n_grids} sections {sec.nx}x{sec.ny}, {sec.n_steps} steps, FP32, {k} fused steps per launch"
+    launches = -(-sec.n_steps // k)
+    ms_launch = ms / launches
+    achieved = BYTES_PER_CELL_UPDATE_2D * sec.total_nodes * k / (ms_launch / 1e3) / 1e9
+    peak = measured_hbm_gbs()
+    traffic = measured_traffic(TRAFFIC_FILE_2D, KERNEL_SOURCES_2D)
+    out = {"value": value, "unit": UNIT, "workload": workload, "ms_per_run": ms, "launches": launches,
+           "steps_per_launch": k,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                        "frac": achieved / peak if peak else None, "traffic": traffic,
+                        "note": (f"{BYTES_PER_CELL_UPDATE_2D} B of compulsory traffic per cell-update for one "
+                                 "step per pass (read T, Pv at n and n-1, write T, Pv at n+1, FP32) x cell-updates "
+                                 f"of one launch ({k} fused steps) / launch time; peak = measured copy bandwidth; "
+                                 "temporal blocking lets the fraction exceed 1; kernel df2d_kernel<float>")}}
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+
+        n = 200
+        pick = [0, sec.n_grids - 1]
+        sub = sec.subset(pick)
+        g2 = H.Hygro2D(sub, precision="fp32", device=local, stream=stream.cuda_stream)
+        g2.run(n)
+        T, P = g2.fields(0)
+        g2.close()
+        o = oracle.Oracle2D(sub)
+        o.run(n)
+        out["parity_vs_oracle"] = {"sections_checked": len(pick), "steps": n,
+                                   "rel_linf_T": float(np.abs(T - o.T_cur).max() / np.abs(o.T_cur).max()),
+                                   "rel_linf_P": float(np.abs(P - o.P_cur).max() / np.abs(o.P_cur).max())}
+    return out
+
+
 def bench_ours(args):
     import torch
 
@@ -229,6 +304,11 @@ def bench_ours(args):
     H.lib(build_if_missing=True)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
+    if args.only_2d:
+        out = bench_sections(args, H, wk, stream, local, rank)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "unit": UNIT, "only": "2d sections", **out}))
+        return
     wl = wk.config2(seed=2 + rank, n_walls=args.walls, n_steps=args.year_steps)
     units_per_run = wl.total_nodes * args.year_steps
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -348,6 +428,10 @@ def bench_ours(args):
         other["rooms_64x6_30days"] = {"value": wl3.total_nodes * wl3.n_steps / (ms3 / 1e3), "unit": UNIT,
                                       "ms_per_run": ms3, "walls": wl3.n_walls, "rooms": 64,
                                       "note": "wall cell-updates/s; one block per room, FP64 room nodes"}
+
+    # 2D sections (64 x 512 x 512, 10000 steps, FP32, 4 fused steps per TMA-tiled launch)
+    if not args.no_2d:
+        other["sections_64x512x512_10000steps"] = bench_sections(args, H, wk, stream, local, rank)
 
     # end to end through the C ABI with host buffers: inputs H2D, run, samples and fluxes D2H
     e2e = None

@@ -187,3 +187,46 @@ def test_uniform_invariance(oracle_mod):
     o.run(500)
     assert np.abs(o.T_cur - 293.0).max() <= 1e-12 * 293.0
     assert np.abs(o.P_cur - 1000.0).max() <= 1e-12 * 1000.0
+
+
+@pytest.mark.parametrize("axis", ["x", "y"])
+def test_steady_series_resistance_across_regions(oracle_mod, axis):
+    """Three regions in series along one axis (Robin faces at both ends of it, adiabatic faces along it):
+    the discrete steady state is uniform across the other axis and every node lies on the exact
+    series-resistance profile, with each region interface at the mid-face between its two nodes
+    (harmonic face means) -- the 1D steady state of the paper's scheme, reached in 2D."""
+    counts, L = [7, 9, 6], 0.1
+    ks, cs = [0.05, 1.5, 0.3], [1e6, 1.5e6, 8e5]
+    layers = [dict(kM0=1e-11, cM0=5e-2, kTT0=k, cTT0=c) for k, c in zip(ks, cs)]
+    N, M = sum(counts), 5
+    h = L / (N - 1)
+    dt = 0.5 * h ** 2 / max(k / c for k, c in zip(ks, cs))
+    h0, h1, T0, T1 = 25.0, 8.0, 303.0, 283.0
+    line = np.repeat(np.arange(3), counts).astype(np.uint8)
+    amb0, amb1, adi = dict(hT=h0, T_mean=T0), dict(hT=h1, T_mean=T1), dict()
+    if axis == "x":
+        region, nx, ny, bc, kinds = np.tile(line, (M, 1)), N, M, [amb0, amb1, adi, adi], (0, 0, 1, 1)
+    else:
+        region, nx, ny, bc, kinds = np.tile(line[:, None], (1, M)), M, N, [adi, adi, amb0, amb1], (1, 1, 0, 0)
+    sec = section(nx, ny, layers, bc, dt, region=region, kinds=kinds, Lv=0.0, h=h)
+    o = oracle_mod.Oracle2D(sec, 1)
+    for _ in range(100):
+        o.run(20000)
+        if np.abs(o.T_cur - o.T_prev).max() / np.abs(o.T_cur).max() < 1e-13:
+            break
+    else:
+        raise AssertionError("no steady state reached")
+    Ls = [(counts[0] - 0.5) * h, counts[1] * h, (counts[2] - 0.5) * h]
+    q = (T0 - T1) / (1 / h0 + sum(l / k for l, k in zip(Ls, ks)) + 1 / h1)
+    s = np.arange(N) * h
+    edges = np.cumsum([0.0] + Ls)
+    want = np.empty(N)
+    Ts = T0 - q / h0
+    for l in range(3):
+        m = (s >= edges[l] - 1e-12) & (s <= edges[l + 1] + 1e-12)
+        want[m] = Ts - q * (s[m] - edges[l]) / ks[l]
+        Ts = Ts - q * Ls[l] / ks[l]
+    got = o.T_cur[0] if axis == "x" else o.T_cur[0].T
+    for row in got:
+        np.testing.assert_allclose(row, want, rtol=0, atol=1e-9 * (T0 - T1))
+    np.testing.assert_allclose(o.P_cur[0], 1000.0, rtol=0, atol=1e-9)
