@@ -24,6 +24,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hygro_oracle.c")
 _SRC2 = os.path.join(_HERE, "hygro_oracle2d.c")
+_SRC3 = os.path.join(_HERE, "hygro_adjoint.c")
 _HDR = os.path.join(_HERE, "hygro_oracle.h")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
@@ -36,13 +37,13 @@ NROOM_PAR = 16
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (OpenMP if available); return the .so path."""
     os.makedirs(_BUILD, exist_ok=True)
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC2), os.path.getmtime(_HDR))
+    newest = max(os.path.getmtime(f) for f in (_SRC, _SRC2, _SRC3, _HDR))
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
         return _LIB
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         raise RuntimeError("no C compiler found to build the oracle")
-    base = [cc, "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", _LIB + ".tmp", _SRC, _SRC2, "-lm"]
+    base = [cc, "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", _LIB + ".tmp", _SRC, _SRC2, _SRC3, "-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
     except subprocess.CalledProcessError:
@@ -81,6 +82,11 @@ class _Problem2D(C.Structure):
     ]
 
 
+class _Misfit(C.Structure):
+    _fields_ = [("sample_every", C.c_int32), ("obs", C.c_void_p), ("wT", C.c_double), ("wP", C.c_double),
+                ("T_init", C.c_void_p), ("P_init", C.c_void_p)]
+
+
 class _State2D(C.Structure):
     _fields_ = [("step", C.c_int64), ("T_prev", C.c_void_p), ("T_cur", C.c_void_p), ("P_prev", C.c_void_p),
                 ("P_cur", C.c_void_p)]
@@ -101,6 +107,12 @@ def _load():
                                     C.POINTER(C.c_double), C.POINTER(C.c_double)]
         lib.orc2d_run.restype = C.c_int
         lib.orc2d_run.argtypes = [C.POINTER(_Problem2D), C.POINTER(_State2D), C.c_int64, C.c_int32]
+        lib.orc_loss_adjoint.restype = C.c_int
+        lib.orc_loss_adjoint.argtypes = [C.POINTER(_Problem), C.c_int64, C.POINTER(_Misfit), C.POINTER(C.c_double),
+                                         C.c_void_p, C.c_int32]
+        lib.orc_loss_tangent.restype = C.c_int
+        lib.orc_loss_tangent.argtypes = [C.POINTER(_Problem), C.c_int64, C.POINTER(_Misfit), C.c_void_p,
+                                         C.POINTER(C.c_double), C.POINTER(C.c_double)]
         lib.orc_coefficients.restype = None
         lib.orc_coefficients.argtypes = [C.POINTER(_Problem), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
         _lib = lib
@@ -231,6 +243,59 @@ class Oracle:
         face = np.zeros((N - 1, 3))
         _load().orc_coefficients(C.byref(self._p), int(w), _ptr(P), _ptr(node), _ptr(face))
         return node, face
+
+
+def _misfit(wl, obs, sample_every, wT, wP, keep):
+    m = _Misfit()
+    m.sample_every = int(sample_every)
+    m.obs = _ptr(keep(obs, np.float64))
+    m.wT, m.wP = float(wT), float(wP)
+    m.T_init = _ptr(keep(wl.T_init, np.float64))
+    m.P_init = _ptr(keep(wl.P_init, np.float64))
+    return m
+
+
+def loss_and_gradient(wl, n_steps: int, obs, sample_every: int, wT: float, wP: float, gradient: bool = True,
+                      n_threads: int | None = None):
+    """Sensor-misfit loss of the surface values of a fresh run of ``wl`` (uniform initial state) and its
+    gradient with respect to every layer's 9 parameters [sum layers, 9], by the reverse-time adjoint.
+    obs: [n_steps // sample_every, n_walls, 2 faces, 2 (T, Pv)]."""
+    o = Oracle(wl, n_threads=1)
+    kept = []
+
+    def keep(a, dt):
+        a = np.ascontiguousarray(a, dtype=dt)
+        kept.append(a)
+        return a
+
+    m = _misfit(wl, obs, sample_every, wT, wP, keep)
+    loss = C.c_double()
+    grad = np.zeros((len(wl.layer_par), NLAYER_PAR)) if gradient else None
+    rc = _load().orc_loss_adjoint(C.byref(o._p), int(n_steps), C.byref(m), C.byref(loss), _ptr(grad),
+                                  int(n_threads or default_threads()))
+    if rc != 0:
+        raise RuntimeError(f"oracle adjoint failed with code {rc}")
+    return loss.value, grad
+
+
+def loss_tangent(wl, n_steps: int, obs, sample_every: int, wT: float, wP: float, direction):
+    """Loss and its derivative along ``direction`` [sum layers, 9] by forward-mode dual numbers."""
+    o = Oracle(wl, n_threads=1)
+    kept = []
+
+    def keep(a, dt):
+        a = np.ascontiguousarray(a, dtype=dt)
+        kept.append(a)
+        return a
+
+    m = _misfit(wl, obs, sample_every, wT, wP, keep)
+    d = keep(direction, np.float64)
+    loss = C.c_double()
+    dl = C.c_double()
+    rc = _load().orc_loss_tangent(C.byref(o._p), int(n_steps), C.byref(m), _ptr(d), C.byref(loss), C.byref(dl))
+    if rc != 0:
+        raise RuntimeError(f"oracle tangent failed with code {rc}")
+    return loss.value, dl.value
 
 
 class Oracle2D:

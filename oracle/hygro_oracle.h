@@ -116,6 +116,25 @@ typedef struct {
 /* Advance n_steps DF steps of every grid (OpenMP over grids). 0 on success. */
 int orc2d_run(const orc2d_problem *p, orc2d_state *s, int64_t n_steps, int32_t n_threads);
 
+/* Sensor misfit of the surface values (hygro_adjoint.c): samples after every sample_every-th step,
+ * obs[k][w][f] = (T, Pv) observed at face f of wall w after step (k+1) * sample_every. */
+typedef struct {
+    int32_t sample_every;
+    const double *obs;           /* [n_steps / sample_every][n_walls][2][2] */
+    double wT, wP;               /* weights of the squared T and Pv mismatches */
+    const double *T_init;        /* [n_walls] uniform initial state of each wall */
+    const double *P_init;
+} orc_misfit;
+
+/* Loss and its gradient dL/d(layer_par) ([sum n_layers][ORC_NLAYER_PAR], or NULL for the loss alone)
+ * by the reverse-time adjoint of the DF step. Walls without room faces. 0 on success. */
+int orc_loss_adjoint(const orc_problem *p, int64_t n_steps, const orc_misfit *m, double *loss, double *grad,
+                     int32_t n_threads);
+
+/* Loss and its derivative along dir ([sum n_layers][ORC_NLAYER_PAR]) by forward-mode dual numbers. */
+int orc_loss_tangent(const orc_problem *p, int64_t n_steps, const orc_misfit *m, const double *dir, double *loss,
+                     double *dloss);
+
 #ifdef __cplusplus
 }
 #endif
