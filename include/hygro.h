@@ -227,6 +227,24 @@ HYGRO_API hygro_status hygro_set_state(hygro_ctx *ctx, const void *buf, size_t b
 HYGRO_API hygro_status hygro_run_noalloc(hygro_ctx *ctx, int64_t n_steps, int32_t sample_every, void *samples,
                                          size_t samples_bytes);
 
+/* Sensor misfit of a run and its gradient with respect to the material parameters, by the reverse-time
+ * adjoint of the DF step (the paper has no adjoint; this differentiates the scheme described above).
+ * The run starts from the uniform initial state given to hygro_set_materials (level -1 := level 0) at t0
+ * and lasts n_steps; the context's stored levels, step and flux sums are left as they were.
+ *   loss = sum over samples k (after every sample_every-th step, k = 0 .. n_steps / sample_every - 1),
+ *          walls w and faces f of  wT (T_f - obs[k][w][f][0])^2 + wP (Pv_f - obs[k][w][f][1])^2,
+ *   T_f, Pv_f the surface node values (node 0 for face 0, node N-1 for face 1); obs holds absolute values,
+ *   float, host or device memory, [n_steps / sample_every][n_walls][2][2].
+ * *loss (host) receives the loss, accumulated in FP64. grad (host or device memory, or NULL) receives
+ * dloss/dtheta, [total layers][9] in the order of hygro_layer (kM0, a, cM0, b, kTT0, aT, cTT0, bT, chi),
+ * accumulated in FP64. The forward saves (level n-1, level n) every checkpoint_every steps (0: about
+ * sqrt(n_steps)), and the reverse recomputes each stretch from its checkpoint. Device memory for the
+ * checkpoints is allocated by the call (walls x checkpoints x 4 x max N reals, plus a stretch of levels).
+ * Walls with a room face are not supported (HYGRO_E_UNSUPPORTED). The arithmetic runs in the context's
+ * precision. */
+HYGRO_API hygro_status hygro_loss_grad(hygro_ctx *ctx, int64_t n_steps, int32_t sample_every, const float *obs,
+                                       double wT, double wP, int32_t checkpoint_every, double *loss, double *grad);
+
 /* Message of the last failed call on ctx (or of the last failed
  * hygro_create when ctx is NULL). Never NULL. */
 HYGRO_API const char *hygro_last_error(const hygro_ctx *ctx);

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "hygro_internal.cuh"
+#include "adjoint.cuh"
 
 using namespace hygro;
 
@@ -1166,6 +1167,201 @@ hygro_status hygro_run_noalloc(hygro_ctx *c, int64_t n_steps, int32_t sample_eve
         return check_nonfinite(c);
     }
     return HYGRO_OK;
+}
+
+hygro_status hygro_loss_grad(hygro_ctx *c, int64_t n_steps, int32_t sample_every, const float *obs, double wT,
+                             double wP, int32_t checkpoint_every, double *loss, double *grad)
+{
+    if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    if (n_steps < 1) return fail(c, HYGRO_E_INVALID, "n_steps must be >= 1");
+    if (sample_every < 1) return fail(c, HYGRO_E_INVALID, "sample_every must be >= 1");
+    if (loss == nullptr) return fail(c, HYGRO_E_INVALID, "loss is NULL");
+    if (!std::isfinite(wT) || !std::isfinite(wP)) return fail(c, HYGRO_E_INVALID, "weights must be finite");
+    if (checkpoint_every < 0) return fail(c, HYGRO_E_INVALID, "checkpoint_every must be >= 0");
+    const int64_t K = n_steps / sample_every;
+    if (K > 0 && obs == nullptr) return fail(c, HYGRO_E_INVALID, "obs is NULL");
+    if (!(c->have_materials && c->have_bc[0] && c->have_bc[1]))
+        return fail(c, HYGRO_E_STATE, "hygro_set_materials and hygro_set_bc (both faces) must come first");
+    for (int w = 0; w < c->W; ++w)
+        for (int f = 0; f < 2; ++f)
+            if (c->bc[f][w].bc.kind == HYGRO_BC_ROOM)
+                return fail(c, HYGRO_E_UNSUPPORTED, "wall %d has a room face: the adjoint runs walls without rooms", w);
+    int64_t C = checkpoint_every > 0 ? checkpoint_every : (int64_t)std::ceil(std::sqrt((double)n_steps));
+    if (C > n_steps) C = n_steps;
+    if (C > (1 << 20)) return fail(c, HYGRO_E_UNSUPPORTED, "checkpoint stride too long");
+    const int64_t n_seg = (n_steps + C - 1) / C;
+    if (n_seg > INT32_MAX) return fail(c, HYGRO_E_UNSUPPORTED, "too many checkpoints");
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
+    const int W = c->W;
+    int Nmax = 0;
+    for (int w = 0; w < W; ++w) Nmax = std::max(Nmax, c->N[w]);
+    const size_t rs = c->real_size;
+    const size_t per_warp =
+        c->precision == HYGRO_FP64 ? adj_smem_per_warp<double>(Nmax) : adj_smem_per_warp<float>(Nmax);
+    int optin = 0;
+    CUDA_TRY(c, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+    const int warps = (int)std::min<size_t>((size_t)kAdjWarps, (size_t)optin / per_warp);
+    if (warps < 1) return fail(c, HYGRO_E_UNSUPPORTED, "walls of %d nodes need more shared memory than a block has", Nmax);
+    // lane layout: contiguous runs of nodes, one layer per lane (the smallest run length that fits 32 lanes)
+    std::vector<AdjWall> aw(W);
+    size_t lo = 0;
+    for (int w = 0; w < W; ++w) {
+        AdjWall &a = aw[w];
+        memset(&a, 0, sizeof a);
+        a.N = c->N[w];
+        a.node_off = c->walls[w].node_off;
+        a.layer_off = (int32_t)lo;
+        a.n_layers = c->n_layers[w];
+        a.dx = c->L[w] / (double)(a.N - 1);
+        std::vector<int> cnt(a.n_layers);
+        for (int l = 0; l < a.n_layers; ++l) {
+            const int j0 = c->layer_first[lo + l];
+            const int j1 = l + 1 < a.n_layers ? c->layer_first[lo + l + 1] : a.N;
+            cnt[l] = j1 - j0;
+        }
+        int K = 1;
+        for (;; ++K) {
+            int lanes = 0;
+            for (int l = 0; l < a.n_layers; ++l) lanes += (cnt[l] + K - 1) / K;
+            if (lanes <= 32) break;
+        }
+        int lane = 0, node = 0;
+        for (int l = 0; l < a.n_layers; ++l) {
+            const int m = (cnt[l] + K - 1) / K;
+            for (int i = 0; i < m; ++i) {
+                const int take = cnt[l] / m + (i < cnt[l] % m ? 1 : 0);
+                a.start[lane] = (int16_t)node;
+                a.layer[lane] = (int8_t)l;
+                node += take;
+                ++lane;
+            }
+        }
+        for (; lane < 32; ++lane) {
+            a.start[lane] = (int16_t)a.N;
+            a.layer[lane] = -1;
+        }
+        a.start[32] = (int16_t)a.N;
+        lo += c->n_layers[w];
+    }
+    const size_t total_layers = lo;
+    // physical laws of every layer, in the working precision
+    std::vector<double> phys(total_layers * 9);
+    for (size_t l = 0; l < total_layers; ++l) {
+        const hygro_layer &y = c->layers[l];
+        const double v[9] = {y.kM0, y.a, y.cM0, y.b, y.kTT0, y.aT, y.cTT0, y.bT, y.chi};
+        for (int k = 0; k < 9; ++k) phys[l * 9 + k] = v[k];
+    }
+    void *d_aw = nullptr, *d_phys = nullptr, *d_obs = nullptr, *d_ck = nullptr, *d_sg = nullptr;
+    double *d_loss = nullptr, *d_grad = nullptr;
+    hygro_status st = HYGRO_OK;
+    auto release = [&]() {
+        void *ps[] = {d_aw, d_phys, d_obs, d_ck, d_sg, d_loss, d_grad};
+        for (void *q : ps)
+            if (q) cudaFree(q);
+    };
+#define ADJ_TRY(call)                                                                                   \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess) {                                                                        \
+            st = fail(c, e_ == cudaErrorMemoryAllocation ? HYGRO_E_NOMEM : HYGRO_E_CUDA, "%s: %s", #call, \
+                      cudaGetErrorString(e_));                                                          \
+            release();                                                                                  \
+            return st;                                                                                  \
+        }                                                                                               \
+    } while (0)
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    ADJ_TRY(cudaMalloc(&d_aw, W * sizeof(AdjWall)));
+    ADJ_TRY(cudaMemcpy(d_aw, aw.data(), W * sizeof(AdjWall), cudaMemcpyHostToDevice));
+    ADJ_TRY(cudaMalloc(&d_phys, std::max<size_t>(1, phys.size()) * rs));
+    if ((st = upload_reals(c, d_phys, phys)) != HYGRO_OK) {
+        release();
+        return st;
+    }
+    const size_t obs_n = (size_t)K * W * 4;
+    if (K > 0) {
+        if (is_device_ptr(obs)) {
+            d_obs = nullptr;
+        } else {
+            ADJ_TRY(cudaMalloc(&d_obs, obs_n * sizeof(float)));
+            ADJ_TRY(cudaMemcpy(d_obs, obs, obs_n * sizeof(float), cudaMemcpyHostToDevice));
+        }
+    }
+    ADJ_TRY(cudaMalloc(&d_ck, (size_t)W * n_seg * 4 * Nmax * rs));
+    ADJ_TRY(cudaMalloc(&d_sg, (size_t)W * (C + 2) * 2 * Nmax * rs));
+    ADJ_TRY(cudaMalloc(&d_loss, W * sizeof(double)));
+    ADJ_TRY(cudaMalloc(&d_grad, std::max<size_t>(1, total_layers * 9) * sizeof(double)));
+    ADJ_TRY(cudaMemsetAsync(d_grad, 0, std::max<size_t>(1, total_layers * 9) * sizeof(double), c->stream));
+    cudaError_t le;
+    if (c->precision == HYGRO_FP64) {
+        AdjDev<double> d;
+        d.walls = (const AdjWall *)d_aw;
+        d.W = W;
+        d.Nmax = Nmax;
+        d.faces = c->d_faces;
+        d.layer_tab = (const double *)c->d_layer_tab;
+        d.phys = (const double *)d_phys;
+        d.Pref = (const double *)c->d_Pref;
+        d.Tref = (const double *)c->d_Tref;
+        d.noise = c->d_noise;
+        d.obs = K > 0 ? (d_obs ? (const float *)d_obs : obs) : nullptr;
+        d.wT = wT;
+        d.wP = wP;
+        d.se = sample_every;
+        d.K = (int32_t)K;
+        d.n_steps = n_steps;
+        d.C = (int32_t)C;
+        d.n_seg = (int32_t)n_seg;
+        d.ckpt = (double *)d_ck;
+        d.seg = (double *)d_sg;
+        d.loss = d_loss;
+        d.grad = d_grad;
+        d.nonfinite = c->d_nonfinite;
+        d.dt = c->dt;
+        d.t0 = c->t0;
+        d.Lv = c->Lv;
+        d.Psat = c->Psat;
+        le = launch_adjoint_f64(d, warps, c->stream);
+    } else {
+        AdjDev<float> d;
+        d.walls = (const AdjWall *)d_aw;
+        d.W = W;
+        d.Nmax = Nmax;
+        d.faces = c->d_faces;
+        d.layer_tab = (const float *)c->d_layer_tab;
+        d.phys = (const float *)d_phys;
+        d.Pref = (const float *)c->d_Pref;
+        d.Tref = (const float *)c->d_Tref;
+        d.noise = c->d_noise;
+        d.obs = K > 0 ? (d_obs ? (const float *)d_obs : obs) : nullptr;
+        d.wT = wT;
+        d.wP = wP;
+        d.se = sample_every;
+        d.K = (int32_t)K;
+        d.n_steps = n_steps;
+        d.C = (int32_t)C;
+        d.n_seg = (int32_t)n_seg;
+        d.ckpt = (float *)d_ck;
+        d.seg = (float *)d_sg;
+        d.loss = d_loss;
+        d.grad = d_grad;
+        d.nonfinite = c->d_nonfinite;
+        d.dt = c->dt;
+        d.t0 = c->t0;
+        d.Lv = c->Lv;
+        d.Psat = c->Psat;
+        le = launch_adjoint_f32(d, warps, c->stream);
+    }
+    ADJ_TRY(le);
+    std::vector<double> lw(W);
+    ADJ_TRY(cudaMemcpyAsync(lw.data(), d_loss, W * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (grad) ADJ_TRY(cudaMemcpyAsync(grad, d_grad, total_layers * 9 * sizeof(double), cudaMemcpyDefault, c->stream));
+    ADJ_TRY(cudaStreamSynchronize(c->stream));
+#undef ADJ_TRY
+    release();
+    double L = 0.0;
+    for (double x : lw) L += x;
+    *loss = L;
+    return check_nonfinite(c);
 }
 
 const char *hygro_last_error(const hygro_ctx *c) { return c ? c->err.c_str() : g_create_error.c_str(); }

@@ -134,6 +134,11 @@ cudaError_t launch_rooms_f32(const DevCtx<float> &d, int64_t n0, int32_t n_steps
 cudaError_t launch_rooms_f64(const DevCtx<double> &d, int64_t n0, int32_t n_steps, int32_t sample_every,
                              double *samples, int n_rooms, int warps, cudaStream_t s);
 
+template <typename real>
+struct AdjDev;
+cudaError_t launch_adjoint_f32(const AdjDev<float> &d, int warps, cudaStream_t s);
+cudaError_t launch_adjoint_f64(const AdjDev<double> &d, int warps, cudaStream_t s);
+
 cudaError_t launch_plain_step_f32(const DevCtx<float> &d, int64_t n, int32_t sample_idx, float *samples,
                                   cudaStream_t s);
 cudaError_t launch_plain_step_f64(const DevCtx<double> &d, int64_t n, int32_t sample_idx, double *samples,

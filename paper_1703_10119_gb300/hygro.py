@@ -36,7 +36,7 @@ STATUS_NAMES = {0: "HYGRO_OK", -1: "HYGRO_E_INVALID", -2: "HYGRO_E_NOMEM", -3: "
 ABI_FUNCTIONS = ("hygro_create", "hygro_set_materials", "hygro_set_bc", "hygro_run", "hygro_sync",
                  "hygro_fluxes", "hygro_get_fields", "hygro_set_fields", "hygro_get_step", "hygro_get_state",
                  "hygro_set_state", "hygro_last_error", "hygro_destroy", "hygro_run_noalloc", "hygro_set_rooms",
-                 "hygro_get_rooms")
+                 "hygro_get_rooms", "hygro_loss_grad")
 # Exported entry points of the 2D sections (names of include/hygro2d.h).
 ABI_FUNCTIONS_2D = ("hygro2d_create", "hygro2d_set_materials", "hygro2d_set_bc", "hygro2d_run", "hygro2d_sync",
                     "hygro2d_get_fields", "hygro2d_set_fields", "hygro2d_get_step", "hygro2d_last_error",
@@ -116,6 +116,7 @@ def lib(build_if_missing: bool = False) -> C.CDLL:
         "hygro_set_state": [P, P, C.c_size_t],
         "hygro_set_rooms": [P, C.c_int32, P, P],
         "hygro_get_rooms": [P, C.c_int32, P, P],
+        "hygro_loss_grad": [P, C.c_int64, C.c_int32, P, C.c_double, C.c_double, C.c_int32, C.POINTER(C.c_double), P],
         "hygro2d_create": [C.POINTER(hygro2d_desc), C.POINTER(P)],
         "hygro2d_set_materials": [P, C.c_int32, P, P, P, P],
         "hygro2d_set_bc": [P, C.c_int32, P],
@@ -237,6 +238,16 @@ def hygro_get_rooms(ctx, level: int, Ta=None, Pa=None):
     _check(lib().hygro_get_rooms(ctx, int(level), _ptr(Ta), _ptr(Pa)), ctx)
 
 
+def hygro_loss_grad(ctx, n_steps: int, sample_every: int, obs, wT: float, wP: float, checkpoint_every: int = 0,
+                    grad=None) -> float:
+    """Misfit loss of a run from the initial state; ``grad`` ([total layers, 9] float64, host or device)
+    receives its gradient. ``obs``: float32 [n_steps // sample_every, n_walls, 2, 2], host or device."""
+    loss = C.c_double()
+    _check(lib().hygro_loss_grad(ctx, int(n_steps), int(sample_every), _ptr(obs), float(wT), float(wP),
+                                 int(checkpoint_every), C.byref(loss), _ptr(grad)), ctx)
+    return loss.value
+
+
 def hygro_last_error(ctx) -> str:
     return lib().hygro_last_error(ctx).decode()
 
@@ -335,10 +346,13 @@ class Hygro:
             self.ctx = None
             raise
 
-    def set_materials(self):
+    def set_materials(self, layer_par=None):
+        """Materials of the workload, or the per-layer parameters ``layer_par`` [total layers, 9] in their
+        place (same layer map and initial state)."""
         wl = self.wl
-        lay = (hygro_layer * len(wl.layer_par))()
-        for i, row in enumerate(wl.layer_par):
+        par = wl.layer_par if layer_par is None else np.asarray(layer_par, np.float64)
+        lay = (hygro_layer * len(par))()
+        for i, row in enumerate(par):
             lay[i] = hygro_layer(*[float(x) for x in row])
         hygro_set_materials(self.ctx, np.ascontiguousarray(wl.n_layers, np.int32),
                             np.ascontiguousarray(wl.layer_first, np.int32), lay,
@@ -380,6 +394,13 @@ class Hygro:
 
     def sync(self):
         hygro_sync(self.ctx)
+
+    def loss_grad(self, n_steps: int, sample_every: int, obs, wT: float, wP: float, checkpoint_every: int = 0):
+        """Misfit loss and its gradient [total layers, 9] (hygro_loss_grad)."""
+        g = np.zeros((len(self.wl.layer_par), 9))
+        obs = np.ascontiguousarray(obs, np.float32)
+        L = hygro_loss_grad(self.ctx, n_steps, sample_every, obs, wT, wP, checkpoint_every, g)
+        return L, g
 
     def fields(self, level: int = 0):
         n = self.wl.total_nodes

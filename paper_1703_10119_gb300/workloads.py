@@ -433,3 +433,66 @@ def config4(seed: int = 4, n_grids: int = 64, nx: int = 512, ny: int = 512, h: f
                      h=h, region=region, region_par=par, bc_kind=bc_kind, bc_par=bc_par, noise=[nz, None, nz, None],
                      T_init=np.full(n_grids, 293.0), P_init=np.full(n_grids, 1000.0), dt=dt, t0=0.0,
                      n_steps=n_steps)
+
+
+@dataclasses.dataclass
+class Sensors:
+    """Synthetic sensor series for the misfit loss: obs[k][w][f] = (T, Pv) at face f of wall w after step
+    (k + 1) * sample_every, with the weights of the squared T and Pv mismatches."""
+    obs: np.ndarray              # float32 [n_steps // sample_every, n_walls, 2, 2]
+    sample_every: int
+    wT: float
+    wP: float
+
+
+def config5(seed: int = 5, n_walls: int = 1024, n_nodes: int = 200, n_steps: int = 43200, dt: float = 60.0,
+            sample_every: int = 10) -> tuple[Workload, Sensors]:
+    """Gradient workload: 1024 two-layer walls of 200 nodes, 30 days at dt = 60 s, surface sensors every
+    10 min.
+
+    Per wall: thickness ~ U[0.1, 0.3] m, the interface at a node drawn in [N/4, 3N/4]; per layer kM0
+    log-uniform in [1e-12, 1e-10] s, a, b ~ U[0, 2], cM0 log-uniform over Table 2's range, kTT ~ U[0.04, 2],
+    cTT ~ U[1e5, 2e6] (kTT, cTT independent of Pv, no cTM). Forcing as the batch workload (face 0 outdoor
+    air with hourly noise, face 1 constant indoor air). Sensors: seeded series at both faces,
+    T = 293 + 4 sin(2 pi t/86400 + psi) + N(0, 0.5^2) K and Pv = 1100 + 250 sin(2 pi t/86400 + psi') +
+    N(0, 30^2) Pa; weights wT = 1 K^-2, wP = 1e-4 Pa^-2.
+    """
+    walls = np.arange(n_walls)
+    keys = stream_key(seed, walls + (1 << 44))
+    u = uniform(keys[:, None], np.arange(10)[None, :])
+    N = np.full(n_walls, n_nodes, np.int32)
+    L = 0.1 + 0.2 * u[:, 0]
+    cut = (n_nodes // 4 + np.floor(u[:, 1] * (n_nodes // 2))).astype(np.int32)
+    firsts = np.stack([np.zeros(n_walls, np.int32), cut], axis=1).reshape(-1)
+    pars = []
+    for w in range(n_walls):
+        v = uniform(keys[w], np.arange(300, 312)).reshape(2, 6)
+        for l in range(2):
+            pars.append([10.0 ** (-12.0 + 2.0 * v[l, 0]), 2.0 * v[l, 1],
+                         10.0 ** (CM0_LOG10_RANGE[0] + (CM0_LOG10_RANGE[1] - CM0_LOG10_RANGE[0]) * v[l, 2]),
+                         2.0 * v[l, 3], 0.04 + 1.96 * v[l, 4], 0.0, 1e5 + 1.9e6 * v[l, 5], 0.0, 0.0])
+    noise_len = int(math.ceil(n_steps * dt / 3600.0)) + 2
+    bc_par = np.zeros((n_walls, 2, 12))
+    bc_par[:, 0] = _bc_row(25.0, 2e-8, 293.0, 10.0, 1200.0, 400.0)
+    bc_par[:, 0, 9] = 2 * np.pi * u[:, 2]
+    bc_par[:, 0, 10] = 2 * np.pi * u[:, 3]
+    bc_par[:, 1] = _bc_row(8.0, 3e-8, 293.0, 0.0, 1000.0, 0.0)
+    nkey = stream_key(seed, walls + (1 << 45))
+    z0, z1 = normal_pairs(nkey[:, None], np.arange(noise_len, dtype=np.uint64)[None, :])
+    nz0 = np.stack([1.0 * z0, 50.0 * z1], axis=-1).astype(np.float32)
+    wl = Workload(name=f"config5: {n_walls} two-layer walls N={n_nodes}, dt={dt:g} s x {n_steps}",
+                  n_nodes=N, thickness=L, n_layers=np.full(n_walls, 2, np.int32), layer_first=firsts,
+                  layer_par=np.array(pars, np.float64), T_init=np.full(n_walls, 293.0),
+                  P_init=np.full(n_walls, 1000.0), bc_kind=np.zeros((n_walls, 2), np.int32), bc_par=bc_par,
+                  bc_room=np.full((n_walls, 2), -1, np.int32), noise=[nz0, None], dt=dt, t0=0.0, n_steps=n_steps)
+    K = n_steps // sample_every
+    t = (np.arange(1, K + 1) * sample_every * dt)[:, None, None]
+    psiT = 2 * np.pi * u[:, 4:6][None]
+    psiP = 2 * np.pi * u[:, 6:8][None]
+    skey = stream_key(seed, walls + (1 << 46))
+    ctr = np.arange(K * 2, dtype=np.uint64).reshape(K, 1, 2)
+    n0, n1 = normal_pairs(skey[None, :, None], ctr)
+    T = 293.0 + 4.0 * np.sin(2 * np.pi * t / 86400.0 + psiT) + 0.5 * n0
+    P = 1100.0 + 250.0 * np.sin(2 * np.pi * t / 86400.0 + psiP) + 30.0 * n1
+    obs = np.stack([T, P], axis=-1).astype(np.float32)
+    return wl, Sensors(obs=obs, sample_every=sample_every, wT=1.0, wP=1e-4)
