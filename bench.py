@@ -9,7 +9,8 @@ resident in HBM; the L2 cache is flushed (512 MB write) between timed runs.
 Prints one JSON line (rank 0). ``--impl reference`` times the FP64 CPU oracle
 instead, on a bounded sample of the same workload. The line also carries the
 FP64 GPU comparators, the whole-building workload (64 rooms x 6 walls) and the
-2D thermal-bridge sections (64 x 512 x 512, 10000 steps) under other_workloads.
+2D thermal-bridge sections (64 x 512 x 512, 10000 steps) and the gradient workload (adjoint of 1024
+walls over 30 days) under other_workloads.
 
 Metric: DF cell-updates/s (one node advanced one step for both T and Pv).
 """
@@ -64,6 +65,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-2d", action="store_true")
+    p.add_argument("--no-adjoint", action="store_true")
     p.add_argument("--only-2d", action="store_true", help="run only the 2D sections (profiling cases)")
     p.add_argument("--sections", type=int, default=64, help="2D sections of 512 x 512")
     p.add_argument("--section-steps", type=int, default=10000)
@@ -292,6 +294,56 @@ def bench_sections(args, H, wk, stream, local, rank):
     return out
 
 
+def bench_adjoint(args, H, wk, stream, local, rank):
+    """Gradient workload: misfit loss and its gradient over 30 days of 1024 two-layer walls (FP32 adjoint,
+    sqrt(T) checkpoints), observations resident on the device; parity on sampled walls vs the oracle."""
+    import torch
+
+    wl, s = wk.config5(seed=5 + rank)
+    dev = torch.device("cuda", local)
+    obs = torch.from_numpy(s.obs).to(dev)
+    grad = torch.zeros((len(wl.layer_par), 9), dtype=torch.float64, device=dev)
+    h = H.Hygro(wl, precision="fp32", device=local, stream=stream.cuda_stream)
+    H.hygro_loss_grad(h.ctx, 600, s.sample_every, obs, s.wT, s.wP, 0, grad)   # warm-up (short run)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    with torch.cuda.stream(stream):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        L = H.hygro_loss_grad(h.ctx, wl.n_steps, s.sample_every, obs, s.wT, s.wP, 0, grad)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t
+    ms = e0.elapsed_time(e1)
+    g = grad.cpu().numpy()
+    h.close()
+    C = int(np.ceil(np.sqrt(wl.n_steps)))
+    out = {"value": wl.total_nodes * wl.n_steps / (ms / 1e3), "unit": UNIT + " (forward steps differentiated)",
+           "workload": f"{wl.n_walls} two-layer walls N=200, dt=60 s x {wl.n_steps} steps, sensors every "
+                       f"{s.sample_every} steps, FP32 adjoint, checkpoints every {C} steps",
+           "ms_per_gradient": ms, "seconds_call": el, "loss": L,
+           "note": "forward + recompute + reverse sweep in one launch; cell-updates of the forward run per second"}
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+
+        pick = [0, wl.n_walls - 1]
+        sub = wl.subset(pick)
+        t = time.perf_counter()
+        L0, g0 = oracle.loss_and_gradient(sub, wl.n_steps, s.obs[:, pick].astype(np.float64), s.sample_every,
+                                          s.wT, s.wP)
+        el0 = time.perf_counter() - t
+        h2 = H.Hygro(sub, precision="fp32", device=local, stream=stream.cuda_stream)
+        L2, _ = h2.loss_grad(wl.n_steps, s.sample_every, s.obs[:, pick], s.wT, s.wP)
+        h2.close()
+        rows = np.concatenate([np.arange(2 * w, 2 * w + 2) for w in pick])
+        big = np.max(np.abs(g0 * sub.layer_par))
+        out["parity_vs_oracle"] = {"walls_checked": len(pick), "loss_rel": abs(L2 - L0) / abs(L0),
+                                   "grad_scaled_max_rel": float(np.max(np.abs((g[rows] - g0) * sub.layer_par)) / big),
+                                   "oracle_seconds": el0}
+    return out
+
+
 def bench_ours(args):
     import torch
 
@@ -428,6 +480,10 @@ def bench_ours(args):
         other["rooms_64x6_30days"] = {"value": wl3.total_nodes * wl3.n_steps / (ms3 / 1e3), "unit": UNIT,
                                       "ms_per_run": ms3, "walls": wl3.n_walls, "rooms": 64,
                                       "note": "wall cell-updates/s; one block per room, FP64 room nodes"}
+
+    # gradient workload (1024 walls x 30 days, reverse-time adjoint)
+    if not args.no_adjoint:
+        other["adjoint_1024x200_30days"] = bench_adjoint(args, H, wk, stream, local, rank)
 
     # 2D sections (64 x 512 x 512, 10000 steps, FP32, 4 fused steps per TMA-tiled launch)
     if not args.no_2d:
