@@ -89,15 +89,9 @@ __device__ __forceinline__ void ambient_at(const FaceInfo &fi, const float2 *noi
         P = fmaf((float)fi.P_amp, sin_turns_fx(fi.phP0 + un * fi.pstep), P);
     }
     if (fi.noise_len > 0) {
-        // position = npos0 + n * nstep, saturated instead of wrapping
-        const double approx = (double)fi.npos0 + (double)n * (double)fi.nstep;
-        int64_t pos;
-        if (approx >= 9.0e18)
-            pos = (int64_t)fi.noise_len << 40;
-        else if (approx <= -9.0e18)
-            pos = -1;
-        else
-            pos = fi.npos0 + n * fi.nstep;
+        // position = npos0 + n * nstep up to the last table entry (from step n_hi on the table is held
+        // at its end, and the product is not formed, so it cannot overflow)
+        const int64_t pos = n >= fi.n_hi ? ((int64_t)(fi.noise_len - 1) << 40) : fi.npos0 + n * fi.nstep;
         const float2 v = noise_fx(noise + fi.noise_off, fi.noise_len, pos);
         T += v.x;
         P += v.y;

@@ -74,8 +74,13 @@ __device__ __forceinline__ void df_step(real (&Tp)[K], const real (&Tc)[K], real
     const real lastP = (K >= 2 && L.short_lane) ? Pc[K >= 2 ? K - 2 : 0] : Pc[K - 1];
     const real khM_first = fma(L.c0.kMb, Pc[0], L.c0.kMa);
     const real khM_last = fma(L.clkMb, lastP, L.clkMa);
-    const real rT = __shfl_down_sync(FULL, Tc[0], 1);
-    const real rP = __shfl_down_sync(FULL, Pc[0], 1);
+    // right neighbour of the lane's last node: the next lane's first node, or beyond the face-1 surface
+    // the ambient air, entering as a neighbour through a face of conductance hM1 / hT1 (the Robin
+    // exchange of [eq:HAM_BC] has the form of a face term)
+    real rT = __shfl_down_sync(FULL, Tc[0], 1);
+    real rP = __shfl_down_sync(FULL, Pc[0], 1);
+    rT = L.has_right ? rT : fT;
+    rP = L.has_right ? rP : fP;
     const real rkM = __shfl_down_sync(FULL, khM_first, 1);
     real FMb = khM_last + rkM;
     real FTb;
@@ -89,19 +94,22 @@ __device__ __forceinline__ void df_step(real (&Tp)[K], const real (&Tc)[K], real
         if (L.any_lb_iface && L.iface_right) FTb = face_harmonic(khT_last, rkT);
     }
     if (L.any_lb_iface && L.iface_right) FMb = face_harmonic(khM_last, rkM);
-    FMb = L.has_right ? FMb : real(0);
-    if (!SIMPLE) FTb = L.has_right ? FTb : real(0);
-    // left boundary: the previous lane's last node and its right face
-    const real lT = __shfl_up_sync(FULL, lastT, 1);
-    const real lP = __shfl_up_sync(FULL, lastP, 1);
+    FMb = L.has_right ? FMb : L.hM1;
+    if (!SIMPLE) FTb = L.has_right ? FTb : L.hT1;
+    // left boundary: the previous lane's last node and its right face, or before the face-0 surface
+    // the ambient air through hM0 / hT0
+    real lT = __shfl_up_sync(FULL, lastT, 1);
+    real lP = __shfl_up_sync(FULL, lastP, 1);
+    lT = L.has_left ? lT : fT;
+    lP = L.has_left ? lP : fP;
     real FMl0 = __shfl_up_sync(FULL, FMb, 1);
     real FTl0;
     if (SIMPLE)
         FTl0 = L.FTl0c;
     else
         FTl0 = __shfl_up_sync(FULL, FTb, 1);
-    FMl0 = L.has_left ? FMl0 : real(0);
-    if (!SIMPLE) FTl0 = L.has_left ? FTl0 : real(0);
+    FMl0 = L.has_left ? FMl0 : L.hM0;
+    if (!SIMPLE) FTl0 = L.has_left ? FTl0 : L.hT0;
 
     LayerC<real> c = L.c0;         // constants of the current slot's layer
     int lcur = L.l0;
@@ -174,21 +182,14 @@ __device__ __forceinline__ void df_step(real (&Tp)[K], const real (&Tc)[K], real
             }
         }
 
-        // vapour pressure: num = sum_f F (P_nb - P^{n-1}) [+ hM (Pinf - P^{n-1})], S = sum_f F [+ hM]
+        // vapour pressure: num = sum_f F (P_nb - P^{n-1}), S = sum_f F, the surface faces being the
+        // Robin exchanges with the ambient air as neighbour
         const real pp = Pp[k];
         real numP = fma(FMl, Pl - pp, FMr * (Pr - pp));
-        real S = FMl + FMr;
+        const real S = FMl + FMr;
         real gsrc = real(0);
-        if (k == 0) {
-            numP = fma(L.hM0, fP - pp, numP);
-            S += L.hM0;
-            gsrc = L.g0;
-        }
-        if (k == K - 1) {
-            numP = fma(L.hM1, fP - pp, numP);
-            S += L.hM1;
-            gsrc += L.g1;
-        }
+        if (k == 0) gsrc = L.g0;
+        if (k == K - 1) gsrc += L.g1;
         const real dP = fast_div(numP + gsrc, fma(half, S, A));
         // latent cross flux sum_f F (P_nb - Pbar) [+ hM (Pinf - Pbar)] = num - S dP / 2
         const real hdP = half * dP;
@@ -197,15 +198,9 @@ __device__ __forceinline__ void df_step(real (&Tp)[K], const real (&Tc)[K], real
         // temperature: conduction, Lv x cross flux, cTM storage
         const real tp = Tp[k];
         real numT = fma(FTl, Tl - tp, FTr * (Tr - tp));
-        real ST = SIMPLE ? real(0) : FTl + FTr;
-        if (k == 0) {
-            numT = fma(L.hT0, fT - tp, numT + L.q0);
-            if (!SIMPLE) ST += L.hT0;
-        }
-        if (k == K - 1) {
-            numT = fma(L.hT1, fT - tp, numT + L.q1);
-            if (!SIMPLE) ST += L.hT1;
-        }
+        const real ST = SIMPLE ? real(0) : FTl + FTr;
+        if (k == 0) numT += L.q0;
+        if (k == K - 1) numT += L.q1;
         numT = fma(Lv, X, numT);
         real dT;
         if (SIMPLE) {
@@ -381,8 +376,8 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
         real Fl = __shfl_up_sync(FULL, Fb, 1);
         Fl = L.has_left ? Fl : real(0);
         L.FTin = real(2) * khf;
-        L.FTl0c = Fl;
-        L.FTbc = Fb;
+        L.FTl0c = L.has_left ? Fl : L.hT0;    // the face-0 Robin exchange as the left face of lane 0
+        L.FTbc = L.has_right ? Fb : L.hT1;    // the face-1 Robin exchange as the right face of lane Wl-1
         if (!IFACE) {
             const real Bc = L.c0.Ba;
             // slot 0: right face FTin, or the boundary face when slot 0 is the last real slot (K = 1, or
@@ -426,7 +421,8 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
                     B *= L.w1;
                     hT += L.hT1;
                 }
-                sft[k * 32] = Fr;
+                // the last real slot of lane Wl-1 faces the ambient air: its right face is hT1
+                sft[k * 32] = (k + 1 == nreal && !L.has_right) ? L.hT1 : Fr;
                 srt[k * 32] = real(1) / (B + half * (Fl_k + Fr + hT));
                 Fleft = Fr;
             }
@@ -447,6 +443,10 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
     }
 
     double cum_q = 0.0, cum_g = 0.0;
+    // surface fluxes: FP32 within a batch of 16 steps, a compensated FP32 sum of 16 batches, then FP64
+    real kq = real(0), kq_c = real(0), kg = real(0), kg_c = real(0);
+    int kbatches = 0;
+    const real dt_r = (real)d.dt;
     if (my_face >= 0) {
         cum_q = d.cumul[(size_t)w * 4 + my_face * 2 + 0];
         cum_g = d.cumul[(size_t)w * 4 + my_face * 2 + 1];
@@ -533,9 +533,24 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
             one_step(Ta, Tb, Pa, Pb, bT, bP, src_base + i);
             flipped = true;
         }
-        cum_q += (double)acc_q * d.dt;
-        cum_g += (double)acc_g * d.dt;
+        {
+            const real xq = acc_q * dt_r, xg = acc_g * dt_r;
+            real t = kq + xq;
+            kq_c += fabs(kq) >= fabs(xq) ? (kq - t) + xq : (xq - t) + kq;
+            kq = t;
+            t = kg + xg;
+            kg_c += fabs(kg) >= fabs(xg) ? (kg - t) + xg : (xg - t) + kg;
+            kg = t;
+        }
         s += cnt;
+        if (++kbatches == 16 || s >= n_steps) {
+            if (my_face >= 0) {
+                cum_q += (double)kq + (double)kq_c;
+                cum_g += (double)kg + (double)kg_c;
+            }
+            kq = kq_c = kg = kg_c = real(0);
+            kbatches = 0;
+        }
     }
 
     // write back: level n into T[cur], level n-1 into T[1-cur]

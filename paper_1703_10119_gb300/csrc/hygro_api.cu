@@ -145,6 +145,16 @@ FaceInfo face_info(const hygro_bc &b, double T_ref, double P_ref, double t0, dou
         o.noise_off = noise_off;
         o.npos0 = (int64_t)std::llround(std::ldexp(t0 / b.noise_dt, 40));
         o.nstep = (int64_t)std::llround(std::ldexp(dt / b.noise_dt, 40));
+        // first step n >= 0 with npos0 + n nstep >= (len - 1) 2^40 (exact integer search; nstep > 0)
+        const __int128 target = (__int128)(noise_len - 1) << 40;
+        int64_t n_hi = 0;
+        if ((__int128)o.npos0 < target) {
+            const __int128 need = target - o.npos0;
+            n_hi = o.nstep > 0 ? (int64_t)((need + o.nstep - 1) / o.nstep) : INT64_MAX;
+        }
+        o.n_hi = n_hi;
+    } else {
+        o.n_hi = INT64_MAX;
     }
     return o;
 }

@@ -70,6 +70,7 @@ struct FaceInfo {
     uint64_t pstep;       // fraction of a period per step, scaled by 2^64
     int64_t npos0;        // noise table position at step 0, scaled by 2^40
     int64_t nstep;        // noise table positions per step, scaled by 2^40
+    int64_t n_hi;         // first step whose position reaches the last table entry (held from there on)
 };
 
 // A room and the walls facing it (room kernel: one block per room, one warp per wall).
