@@ -296,17 +296,25 @@ static __device__ __noinline__ void room_update(RoomShared &rs, const RoomInfo &
 // Everything one warp does for one wall over n_steps steps. ROOM: the wall is one of the walls of
 // the block's room (rs, its face room_face on the room); every step then ends with the room update
 // between two block barriers, which all warps of the block pass once per step.
-template <typename real, int K, bool IFACE, bool SIMPLE, bool ROOM = false>
-__device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi, int w, const real *tab, int64_t n0,
-                                      int32_t n_steps, int32_t sample_every, real *samples, real *sft, real *srt,
-                                      RoomShared *rs = nullptr, int room_face = -1)
+// Per-lane constants of a wall for the persistent kernel (layout, layer constants, surface exchange,
+// and for simple-heat walls the constant thermal faces and T denominators).
+template <typename real>
+struct WallLane {
+    LaneCtx<real> L;
+    int first, nreal, my_face;
+    const FaceInfo *fw;
+    real Tref, Pref;
+};
+
+template <typename real, int K, bool IFACE, bool SIMPLE>
+__device__ __forceinline__ void lane_setup(const DevCtx<real> &d, const WallInfo &wi, int w, const real *tab,
+                                           real *sft, real *srt, WallLane<real> &WLn)
 {
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int Wl = wi.Wl;
     const uint32_t smask = (uint32_t)wi.short_mask;
-
-    LaneCtx<real> L;
+    LaneCtx<real> &L = WLn.L;
     L.short_lane = (K >= 2) && ((smask >> lane) & 1u);
     const int first = lane * K - __popc(smask & ((1u << lane) - 1u));   // wall-local node of slot 0
     const int nreal = lane >= Wl ? 0 : (L.short_lane ? K - 1 : K);
@@ -428,6 +436,34 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
             }
         }
     }
+
+    WLn.first = first;
+    WLn.nreal = nreal;
+    WLn.my_face = my_face;
+    WLn.fw = fw;
+    WLn.Tref = Tref;
+    WLn.Pref = Pref;
+    (void)Lv;
+}
+
+template <typename real, int K, bool IFACE, bool SIMPLE, bool ROOM = false>
+__device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi, int w, const real *tab, int64_t n0,
+                                      int32_t n_steps, int32_t sample_every, real *samples, real *sft, real *srt,
+                                      RoomShared *rs = nullptr, int room_face = -1)
+{
+    constexpr unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int Wl = wi.Wl;
+    const uint32_t smask = (uint32_t)wi.short_mask;
+
+    WallLane<real> WLn;
+    lane_setup<real, K, IFACE, SIMPLE>(d, wi, w, tab, sft, srt, WLn);
+    const LaneCtx<real> &L = WLn.L;
+    const int first = WLn.first, nreal = WLn.nreal, my_face = WLn.my_face;
+    const FaceInfo *fw = WLn.fw;
+    const real Tref = WLn.Tref, Pref = WLn.Pref;
+    const real Lv = (real)d.Lv;
+    (void)smask;
 
     // load the two levels
     const int cur = d.cur;

@@ -89,77 +89,6 @@ struct Tile2D {
     static constexpr uint32_t TX_BYTES = (uint32_t)(2 * (size_t)BX * BY * sizeof(pair) + (size_t)FBX * BY);
 };
 
-// A (T, Pv) pair with component-wise arithmetic, in the order of the stored pairs (x = T, y = Pv):
-// FP32 pairs use the packed f32x2 instructions (one instruction for both components, each rounded as
-// the scalar operation), FP64 pairs scalar operations.
-template <typename real>
-struct P2;
-template <>
-struct P2<float> {
-    uint64_t v;
-};
-template <>
-struct P2<double> {
-    double x, y;
-};
-
-__device__ __forceinline__ P2<float> p2_make(float t, float p)
-{
-    P2<float> r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(t), "f"(p));
-    return r;
-}
-__device__ __forceinline__ float p2_t(P2<float> a) { return __uint_as_float((uint32_t)a.v); }
-__device__ __forceinline__ float p2_p(P2<float> a) { return __uint_as_float((uint32_t)(a.v >> 32)); }
-__device__ __forceinline__ P2<float> p2_add(P2<float> a, P2<float> b)
-{
-    P2<float> r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
-    return r;
-}
-__device__ __forceinline__ P2<float> p2_sub(P2<float> a, P2<float> b)
-{
-    P2<float> r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
-    return r;
-}
-__device__ __forceinline__ P2<float> p2_mul(P2<float> a, P2<float> b)
-{
-    P2<float> r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
-    return r;
-}
-__device__ __forceinline__ P2<float> p2_fma(P2<float> a, P2<float> b, P2<float> c)
-{
-    P2<float> r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
-    return r;
-}
-__device__ __forceinline__ P2<float> p2_load(const float2 *p)
-{
-    P2<float> r;
-    r.v = *reinterpret_cast<const uint64_t *>(p);
-    return r;
-}
-__device__ __forceinline__ void p2_store(float2 *p, P2<float> a) { *reinterpret_cast<uint64_t *>(p) = a.v; }
-
-__device__ __forceinline__ P2<double> p2_make(double t, double p) { return P2<double>{t, p}; }
-__device__ __forceinline__ double p2_t(P2<double> a) { return a.x; }
-__device__ __forceinline__ double p2_p(P2<double> a) { return a.y; }
-__device__ __forceinline__ P2<double> p2_add(P2<double> a, P2<double> b) { return P2<double>{a.x + b.x, a.y + b.y}; }
-__device__ __forceinline__ P2<double> p2_sub(P2<double> a, P2<double> b) { return P2<double>{a.x - b.x, a.y - b.y}; }
-__device__ __forceinline__ P2<double> p2_mul(P2<double> a, P2<double> b) { return P2<double>{a.x * b.x, a.y * b.y}; }
-__device__ __forceinline__ P2<double> p2_fma(P2<double> a, P2<double> b, P2<double> c)
-{
-    return P2<double>{fma(a.x, b.x, c.x), fma(a.y, b.y, c.y)};
-}
-__device__ __forceinline__ P2<double> p2_load(const double2 *p)
-{
-    const double2 v = *p;
-    return P2<double>{v.x, v.y};
-}
-__device__ __forceinline__ void p2_store(double2 *p, P2<double> a) { *p = make_double2(a.x, a.y); }
-
 // Constants of one region in pair form: (kTT, kM) / (2h) = ka + kb Pv', (cTT, cM) storage = sa + sb Pv'.
 template <typename real>
 struct RegionC {
