@@ -191,6 +191,18 @@ HYGRO_API hygro_status hygro_sync(hygro_ctx *ctx);
  * of dt * flux (J/m^2, kg/m^2), accumulated in FP64. Either may be NULL. */
 HYGRO_API hygro_status hygro_fluxes(hygro_ctx *ctx, double *flux, double *cumulative);
 
+/* Discrete balance of the next step n -> n+1, computed from the stored levels without advancing them
+ * (the step, the levels and the flux sums are left as they were). Per wall and field (0: T, 1: Pv):
+ * bal[w][f][0] storage S = sum_j w_j dx (c (u^{n+1} - u^{n-1}) [+ cTM (Pv^{n+1} - Pv^{n-1}) for T]) / (2 dt),
+ * bal[w][f][1] boundary B = the surface fluxes into the wall with the time-averaged surface values,
+ * bal[w][f][2] DF defect D = sum over interior faces of (k_f/dx)((u_{j+1}^n - ubar_{j+1}) + (u_j^n - ubar_j))
+ *              (plus the kTM terms for T), ubar = (u^{n+1} + u^{n-1}) / 2,
+ * bal[w][f][3] M = the sum of the magnitudes of every term.
+ * The scheme satisfies S = B + D exactly in exact arithmetic ([eq:DF_NL] summed over the nodes; D is the
+ * O(dt^2) conservation defect of DF). Sums in FP64; bal is [n_walls][2][4], host or device memory. Walls
+ * with a room face are not supported (HYGRO_E_UNSUPPORTED). */
+HYGRO_API hygro_status hygro_balance(hygro_ctx *ctx, double *bal);
+
 /* Stored levels as absolute values in FP64: level 0 is the newest (n),
  * level 1 the previous (n-1). T and P hold sum(n_nodes) values each. */
 HYGRO_API hygro_status hygro_get_fields(hygro_ctx *ctx, int32_t level, double *T, double *P);

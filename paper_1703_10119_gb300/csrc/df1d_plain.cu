@@ -102,6 +102,93 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// Discrete balance of one step n -> n+1 per wall and field (the identity S = B + D of the DF scheme):
+// storage S = sum_j w dx (c (u^{n+1} - u^{n-1}) [+ cTM (Pv^{n+1} - Pv^{n-1})]) / (2 dt), boundary B = the surface
+// fluxes into the wall with the time-averaged surface values ([eq:HAM_BC]), DF defect D = sum over interior
+// faces of (k_f / dx) ((u_{j+1}^n - ubar_{j+1}) + (u_j^n - ubar_j)) (plus the kTM cross terms for T), and M the
+// sum of the magnitudes of all terms. Levels: Tp, Pp = n-1, d.T[cur], d.P[cur] = n, Tn, Pn = n+1.
+// bal[w][field: 0 T, 1 Pv][4] = S, B, D, M, accumulated in FP64 (zeroed by the caller).
+template <typename real>
+__global__ void __launch_bounds__(256)
+    df1d_balance_kernel(const DevCtx<real> d, const real *Tp, const real *Pp, const real *Tn, const real *Pn,
+                        int64_t n, double *bal)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= d.total_nodes) return;
+    const int w = d.node_wall[g];
+    const WallInfo wi = d.walls[w];
+    const int j = g - wi.node_off;
+    const int N = wi.N;
+    const real *Tc = d.T[d.cur], *Pc = d.P[d.cur];
+    const real *tab = d.layer_tab + (size_t)wi.layer_off * kLayerStride;
+    const int l = d.node_layer[g];
+    const LayerC<real> c = load_layer(tab, l);
+    const real half = real(0.5), Lv = (real)d.Lv;
+    double *bT = bal + (size_t)w * 8, *bP = bT + 4;
+    const real wgt = (j == 0 || j == N - 1) ? half : real(1);
+    const real A = fma(c.Ab, Pc[g], c.Aa) * wgt, B = fma(c.Bb, Pc[g], c.Ba) * wgt;
+    const real dP = Pn[g] - Pp[g], dT = Tn[g] - Tp[g];
+    const double sP = (double)(A * dP), sT = (double)fma(B, dT, c.chi * A * dP);
+    atomicAdd(bP + 0, sP);
+    atomicAdd(bP + 3, fabs(sP));
+    atomicAdd(bT + 0, sT);
+    atomicAdd(bT + 3, fabs(sT));
+    if (j < N - 1) {
+        // the face (j, j+1), counted once, by node j
+        const int lr = d.node_layer[g + 1];
+        const LayerC<real> cr = (lr == l) ? c : load_layer(tab, lr);
+        const real a = fma(c.kMb, Pc[g], c.kMa), b = fma(cr.kMb, Pc[g + 1], cr.kMa);
+        const real at = fma(c.kTb, Pc[g], c.kTa), bt = fma(cr.kTb, Pc[g + 1], cr.kTa);
+        const real FM = lr == l ? a + b : face_harmonic(a, b);
+        const real FT = lr == l ? at + bt : face_harmonic(at, bt);
+        const real Pb0 = half * (Pn[g] + Pp[g]), Pb1 = half * (Pn[g + 1] + Pp[g + 1]);
+        const real Tb0 = half * (Tn[g] + Tp[g]), Tb1 = half * (Tn[g + 1] + Tp[g + 1]);
+        const real eP = (Pc[g + 1] - Pb1) + (Pc[g] - Pb0), eT = (Tc[g + 1] - Tb1) + (Tc[g] - Tb0);
+        atomicAdd(bP + 2, (double)(FM * eP));
+        atomicAdd(bT + 2, (double)fma(FT, eT, Lv * FM * eP));
+        atomicAdd(bP + 3, (double)(FM * (fabs(Pc[g + 1] - Pb0) + fabs(Pc[g] - Pb1))));
+        atomicAdd(bT + 3, (double)(FT * (fabs(Tc[g + 1] - Tb0) + fabs(Tc[g] - Tb1)) +
+                                   Lv * FM * (fabs(Pc[g + 1] - Pb0) + fabs(Pc[g] - Pb1))));
+    }
+    const int face = j == 0 ? 0 : (j == N - 1 ? 1 : -1);
+    if (face >= 0) {
+        const FaceInfo &fi = d.faces[(size_t)w * 2 + face];
+        if (fi.kind == HYGRO_BC_AMBIENT) {
+            real fT, fP;
+            ambient_at(fi, d.noise, n, d.t0, d.dt, fT, fP);
+            const real Tbar = half * (Tn[g] + Tp[g]), Pbar = half * (Pn[g] + Pp[g]);
+            const real hm = (real)fi.hM * (fP - Pbar);
+            const real gflux = hm + (real)fi.g_inf;
+            const real q = fma((real)fi.hT, fT - Tbar, fma(Lv, hm, (real)fi.q_inf));
+            atomicAdd(bP + 1, (double)gflux);
+            atomicAdd(bP + 3, fabs((double)gflux));
+            atomicAdd(bT + 1, (double)q);
+            atomicAdd(bT + 3, fabs((double)q));
+        }
+    }
+}
+
+template <typename real>
+static cudaError_t launch_balance(const DevCtx<real> &d, const real *Tp, const real *Pp, const real *Tn,
+                                  const real *Pn, int64_t n, double *bal, cudaStream_t s)
+{
+    const int grid = (d.total_nodes + 255) / 256;
+    df1d_balance_kernel<real><<<grid, 256, 0, s>>>(d, Tp, Pp, Tn, Pn, n, bal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_balance_f32(const DevCtx<float> &d, const float *Tp, const float *Pp, const float *Tn,
+                               const float *Pn, int64_t n, double *bal, cudaStream_t s)
+{
+    return launch_balance(d, Tp, Pp, Tn, Pn, n, bal, s);
+}
+
+cudaError_t launch_balance_f64(const DevCtx<double> &d, const double *Tp, const double *Pp, const double *Tn,
+                               const double *Pn, int64_t n, double *bal, cudaStream_t s)
+{
+    return launch_balance(d, Tp, Pp, Tn, Pn, n, bal, s);
+}
+
 cudaError_t launch_plain_step_f32(const DevCtx<float> &d, int64_t n, int32_t sample_idx, float *samples,
                                   cudaStream_t s)
 {

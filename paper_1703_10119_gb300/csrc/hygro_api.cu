@@ -983,6 +983,78 @@ hygro_status hygro_fluxes(hygro_ctx *c, double *flux, double *cumulative)
     return check_nonfinite(c);
 }
 
+hygro_status hygro_balance(hygro_ctx *c, double *bal)
+{
+    if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    if (bal == nullptr) return fail(c, HYGRO_E_INVALID, "bal is NULL");
+    if (!(c->have_materials && c->have_bc[0] && c->have_bc[1]))
+        return fail(c, HYGRO_E_STATE, "hygro_set_materials and hygro_set_bc (both faces) must come first");
+    for (int w = 0; w < c->W; ++w)
+        for (int f = 0; f < 2; ++f)
+            if (c->bc[f][w].bc.kind == HYGRO_BC_ROOM)
+                return fail(c, HYGRO_E_UNSUPPORTED, "wall %d has a room face: the balance covers walls without rooms", w);
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
+    const size_t nb = (size_t)c->total_nodes * c->real_size;
+    void *sT = nullptr, *sP = nullptr, *sc = nullptr, *sf = nullptr, *db = nullptr;
+    hygro_status st = HYGRO_OK;
+    auto release = [&]() {
+        void *ps[] = {sT, sP, sc, sf, db};
+        for (void *q : ps)
+            if (q) cudaFree(q);
+    };
+#define BAL_TRY(call)                                                                                   \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess) {                                                                        \
+            st = fail(c, e_ == cudaErrorMemoryAllocation ? HYGRO_E_NOMEM : HYGRO_E_CUDA, "%s: %s", #call, \
+                      cudaGetErrorString(e_));                                                          \
+            release();                                                                                  \
+            return st;                                                                                  \
+        }                                                                                               \
+    } while (0)
+    BAL_TRY(cudaMalloc(&sT, nb));
+    BAL_TRY(cudaMalloc(&sP, nb));
+    BAL_TRY(cudaMalloc(&sc, (size_t)c->W * 4 * sizeof(double)));
+    BAL_TRY(cudaMalloc(&sf, (size_t)c->W * 4 * sizeof(double)));
+    BAL_TRY(cudaMalloc(&db, (size_t)c->W * 8 * sizeof(double)));
+    BAL_TRY(cudaMemsetAsync(db, 0, (size_t)c->W * 8 * sizeof(double), c->stream));
+    BAL_TRY(cudaMemsetAsync(sc, 0, (size_t)c->W * 4 * sizeof(double), c->stream));
+    // pass 1: the step n -> n+1 into scratch copies of level n-1 (the plain kernel writes in place)
+    const int prv = 1 - c->cur;
+    BAL_TRY(cudaMemcpyAsync(sT, c->dT[prv], nb, cudaMemcpyDeviceToDevice, c->stream));
+    BAL_TRY(cudaMemcpyAsync(sP, c->dP[prv], nb, cudaMemcpyDeviceToDevice, c->stream));
+    cudaError_t e;
+    if (c->precision == HYGRO_FP64) {
+        DevCtx<double> d = make_dev<double>(c);
+        DevCtx<double> ds = d;
+        ds.T[prv] = (double *)sT;
+        ds.P[prv] = (double *)sP;
+        ds.cumul = (double *)sc;
+        ds.flast = (double *)sf;
+        e = launch_plain_step_f64(ds, c->step, -1, nullptr, c->stream);
+        if (e == cudaSuccess)
+            e = launch_balance_f64(d, (const double *)c->dT[prv], (const double *)c->dP[prv], (const double *)sT,
+                                   (const double *)sP, c->step, (double *)db, c->stream);
+    } else {
+        DevCtx<float> d = make_dev<float>(c);
+        DevCtx<float> ds = d;
+        ds.T[prv] = (float *)sT;
+        ds.P[prv] = (float *)sP;
+        ds.cumul = (double *)sc;
+        ds.flast = (double *)sf;
+        e = launch_plain_step_f32(ds, c->step, -1, nullptr, c->stream);
+        if (e == cudaSuccess)
+            e = launch_balance_f32(d, (const float *)c->dT[prv], (const float *)c->dP[prv], (const float *)sT,
+                                   (const float *)sP, c->step, (double *)db, c->stream);
+    }
+    BAL_TRY(e);
+    BAL_TRY(cudaMemcpyAsync(bal, db, (size_t)c->W * 8 * sizeof(double), cudaMemcpyDefault, c->stream));
+    BAL_TRY(cudaStreamSynchronize(c->stream));
+#undef BAL_TRY
+    release();
+    return check_nonfinite(c);
+}
+
 hygro_status hygro_get_fields(hygro_ctx *c, int32_t level, double *T, double *P)
 {
     if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");

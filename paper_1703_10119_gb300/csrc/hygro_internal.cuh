@@ -140,6 +140,11 @@ struct AdjDev;
 cudaError_t launch_adjoint_f32(const AdjDev<float> &d, int warps, cudaStream_t s);
 cudaError_t launch_adjoint_f64(const AdjDev<double> &d, int warps, cudaStream_t s);
 
+cudaError_t launch_balance_f32(const DevCtx<float> &d, const float *Tp, const float *Pp, const float *Tn,
+                               const float *Pn, int64_t n, double *bal, cudaStream_t s);
+cudaError_t launch_balance_f64(const DevCtx<double> &d, const double *Tp, const double *Pp, const double *Tn,
+                               const double *Pn, int64_t n, double *bal, cudaStream_t s);
+
 cudaError_t launch_plain_step_f32(const DevCtx<float> &d, int64_t n, int32_t sample_idx, float *samples,
                                   cudaStream_t s);
 cudaError_t launch_plain_step_f64(const DevCtx<double> &d, int64_t n, int32_t sample_idx, double *samples,

@@ -36,7 +36,7 @@ STATUS_NAMES = {0: "HYGRO_OK", -1: "HYGRO_E_INVALID", -2: "HYGRO_E_NOMEM", -3: "
 ABI_FUNCTIONS = ("hygro_create", "hygro_set_materials", "hygro_set_bc", "hygro_run", "hygro_sync",
                  "hygro_fluxes", "hygro_get_fields", "hygro_set_fields", "hygro_get_step", "hygro_get_state",
                  "hygro_set_state", "hygro_last_error", "hygro_destroy", "hygro_run_noalloc", "hygro_set_rooms",
-                 "hygro_get_rooms", "hygro_loss_grad")
+                 "hygro_get_rooms", "hygro_loss_grad", "hygro_balance")
 # Exported entry points of the 2D sections (names of include/hygro2d.h).
 ABI_FUNCTIONS_2D = ("hygro2d_create", "hygro2d_set_materials", "hygro2d_set_bc", "hygro2d_run", "hygro2d_sync",
                     "hygro2d_get_fields", "hygro2d_set_fields", "hygro2d_get_step", "hygro2d_last_error",
@@ -111,6 +111,7 @@ def lib(build_if_missing: bool = False) -> C.CDLL:
         "hygro_fluxes": [P, P, P],
         "hygro_get_fields": [P, C.c_int32, P, P],
         "hygro_set_fields": [P, C.c_int32, P, P],
+        "hygro_balance": [P, P],
         "hygro_get_step": [P, C.POINTER(C.c_int64)],
         "hygro_get_state": [P, P, C.POINTER(C.c_size_t)],
         "hygro_set_state": [P, P, C.c_size_t],
@@ -204,6 +205,11 @@ def hygro_fluxes(ctx, flux=None, cumulative=None):
 
 def hygro_get_fields(ctx, level: int, T=None, P=None):
     _check(lib().hygro_get_fields(ctx, int(level), _ptr(T), _ptr(P)), ctx)
+
+
+def hygro_balance(ctx, bal):
+    """bal: float64 [n_walls, 2, 4] (host or device) receives S, B, D, M of the next step per wall and field."""
+    _check(lib().hygro_balance(ctx, _ptr(bal)), ctx)
 
 
 def hygro_set_fields(ctx, level: int, T=None, P=None):
@@ -411,6 +417,12 @@ class Hygro:
 
     def set_fields(self, level: int, T, P):
         hygro_set_fields(self.ctx, level, np.ascontiguousarray(T, np.float64), np.ascontiguousarray(P, np.float64))
+
+    def balance(self) -> np.ndarray:
+        """Discrete balance (S, B, D, M) of the next step per wall and field (T, Pv), [n_walls, 2, 4]."""
+        b = np.zeros((self.wl.n_walls, 2, 4))
+        hygro_balance(self.ctx, b)
+        return b
 
     def fluxes(self):
         f = np.zeros((self.wl.n_walls, 2, 2))

@@ -230,3 +230,29 @@ def test_nonfinite_is_reported(H):
     assert e.value.status == H.HYGRO_E_NONFINITE
     g.sync()   # the flag is cleared once reported
     g.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_balance_of_the_next_step(H, oracle_mod, precision, tol):
+    """hygro_balance: storage, boundary flux and DF defect of the step n -> n+1 per wall, against the oracle's
+    balance of the same step (FP64), and the identity S = B + D on the GPU's own terms; the call changes
+    nothing."""
+    wl = ragged_batch([3, 5, 17, 33, 64, 100, 257, 400, 512], 40, dt=600.0)
+    with H.Hygro(wl, precision=precision, kernel="persistent") as g:
+        g.run(37)
+        before = g.fields(0), g.fields(1), g.fluxes()
+        bal = g.balance()
+        after = g.fields(0), g.fields(1), g.fluxes()
+        assert g.step == 37
+        for x, y in zip(before, after):
+            assert np.array_equal(x[0], y[0]) and np.array_equal(x[1], y[1])
+    S, B, D, M = bal[..., 0], bal[..., 1], bal[..., 2], bal[..., 3]
+    assert np.all(np.abs(S - B - D) <= tol * M)
+    if precision == "fp64":
+        o = oracle_mod.Oracle(wl, n_threads=1)
+        o.run(37)
+        ref = o.run(1, want_balance=True)["balance"]
+        # the terms are sums of differences of fields that agree to ~1e-12 of their own size, summed in
+        # another order: 1e-9 of M separates rounding from a wrong term (which would be off by O(M))
+        for k in range(3):
+            assert np.all(np.abs(bal[..., k] - ref[..., k]) <= 1e-9 * ref[..., 3]), k
