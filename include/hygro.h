@@ -149,6 +149,15 @@ typedef struct {
 /* Most walls one room may have (each wall has at most one face on a room). */
 #define HYGRO_MAX_ROOM_WALLS 8
 
+/* Options of a context (hygro_set_option). */
+enum { HYGRO_OPT_ROOM_SCHEME = 1 };
+/* HYGRO_OPT_ROOM_SCHEME values: how each room air node is advanced.
+ * HYGRO_ROOM_DF (default): one more DF node (its own level-n value in its balance replaced by the mean
+ *   of levels n+1 and n-1), explicit in the wall surface values; stable at the whole-building time steps.
+ * HYGRO_ROOM_EULER: the explicit Euler update of paper Sec. 5.2 (every term at level n); unstable when
+ *   dt exceeds twice the room's time constant (heat capacity over total exchange conductance). */
+enum { HYGRO_ROOM_DF = 0, HYGRO_ROOM_EULER = 1 };
+
 /* Create a context on desc->device. *out receives the context. */
 HYGRO_API hygro_status hygro_create(const hygro_desc *desc, hygro_ctx **out);
 
@@ -170,6 +179,9 @@ HYGRO_API hygro_status hygro_set_bc(hygro_ctx *ctx, int32_t face, const hygro_bc
  * air to (Ta0, Pa0). Rooms need the persistent kernel. */
 HYGRO_API hygro_status hygro_set_rooms(hygro_ctx *ctx, int32_t n_rooms, const hygro_room *rooms,
                                        const double *wall_area);
+
+/* Set an option (HYGRO_OPT_*) of the context; it applies from the next run. */
+HYGRO_API hygro_status hygro_set_option(hygro_ctx *ctx, int32_t option, int64_t value);
 
 /* Room air state of level 0 (n) or 1 (n-1): Ta[n_rooms], Pa[n_rooms] (host or device memory). */
 HYGRO_API hygro_status hygro_get_rooms(hygro_ctx *ctx, int32_t level, double *Ta, double *Pa);

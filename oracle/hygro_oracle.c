@@ -15,7 +15,7 @@
 enum { L_KM0, L_A, L_CM0, L_B, L_KTT0, L_AT, L_CTT0, L_BT, L_CHI };
 enum { B_HT, B_HM, B_QINF, B_GINF, B_TMEAN, B_TAMP, B_PMEAN, B_PAMP, B_PERIOD, B_PHT, B_PHP, B_NDT };
 enum { R_VOL, R_ACH, R_QGAIN, R_GVAP, R_TMEAN, R_TAMP, R_PMEAN, R_PAMP, R_PERIOD, R_PHT, R_PHP,
-       R_RHOA, R_CPA, R_CPV, R_PVREF };
+       R_RHOA, R_CPA, R_CPV, R_PVREF, R_SCHEME };
 
 static const double TWO_PI = 6.283185307179586476925286766559;
 
@@ -300,6 +300,19 @@ static void room_step(const orc_problem *p, int32_t r, double t, double *rs,
     }
     double Pref = q[R_PVREF];
     double w_out = P_out / Pref;
+    if (q[R_SCHEME] == 1.0) {
+        /* the explicit Euler update of Sec. 5.2: every term of both balances at level n */
+        double Pa_n = Pa_c + dt / (rhoV / Pref) * (q[R_GVAP] + gv * (w_out - Pa_c / Pref) + sum_AhMPs[r] - sum_AhM[r] * Pa_c);
+        double CT0 = rhoV * (q[R_CPA] + q[R_CPV] * Pa_c / Pref);
+        double rhs0 = q[R_QGAIN] + Lv * q[R_GVAP] + gv * q[R_CPA] * (T_out - Ta_c) + Lv * gv * (w_out - Pa_c / Pref) +
+                      sum_AhTTs[r] - sum_AhT[r] * Ta_c + Lv * (sum_AhMPs[r] - sum_AhM[r] * Pa_c);
+        double Ta_n = Ta_c + dt / CT0 * rhs0;
+        rs[0] = Ta_c;
+        rs[1] = Ta_n;
+        rs[2] = Pa_c;
+        rs[3] = Pa_n;
+        return;
+    }
     /* vapour: rhoV/Pref dPa/dt = g_vap + gv (w_out - Pa/Pref) + sum A hM (Ps - Pa) */
     double CP = rhoV / Pref;
     double a_p = CP / (2.0 * dt);

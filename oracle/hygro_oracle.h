@@ -44,7 +44,8 @@ extern "C" {
 #define ORC_NLAYER_PAR 9   /* kM0, a, cM0, b, kTT0, aT, cTT0, bT, chi */
 #define ORC_NBC_PAR 12     /* hT, hM, q_inf, g_inf, T_mean, T_amp, P_mean, P_amp, period, phase_T, phase_P, noise_dt */
 #define ORC_NROOM_PAR 16   /* volume, ach, Q_gain, g_vap, T_out_mean, T_out_amp, P_out_mean, P_out_amp,
-                              period, phase_T, phase_P, rho_a, cp_a, cp_v, Pv_ref, (unused) */
+                              period, phase_T, phase_P, rho_a, cp_a, cp_v, Pv_ref, scheme (0: the room
+                              as one more DF node, 1: the explicit Euler update of Sec. 5.2) */
 
 enum { ORC_BC_AMBIENT = 0, ORC_BC_ADIABATIC = 1, ORC_BC_ROOM = 2 };
 

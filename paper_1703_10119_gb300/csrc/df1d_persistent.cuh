@@ -278,6 +278,19 @@ static __device__ __noinline__ void room_update(RoomShared &rs, const RoomInfo &
     }
     const double Pref = q[RP_PVREF];
     const double w_out = P_out / Pref;
+    if (q[RP_SCHEME] == (double)HYGRO_ROOM_EULER) {
+        // explicit Euler of Sec. 5.2: every term at level n
+        const double Pa_n = rs.Pa_c + dt * Pref / rhoV * (q[RP_GVAP] + gv * (w_out - rs.Pa_c / Pref) + AhMPs - AhM * rs.Pa_c);
+        const double CT = rhoV * (q[RP_CPA] + q[RP_CPV] * rs.Pa_c / Pref);
+        const double rhs = q[RP_QGAIN] + Lv * q[RP_GVAP] + gv * q[RP_CPA] * (T_out - rs.Ta_c) +
+                           Lv * gv * (w_out - rs.Pa_c / Pref) + AhTTs - AhT * rs.Ta_c + Lv * (AhMPs - AhM * rs.Pa_c);
+        const double Ta_n = rs.Ta_c + dt / CT * rhs;
+        rs.Ta_p = rs.Ta_c;
+        rs.Ta_c = Ta_n;
+        rs.Pa_p = rs.Pa_c;
+        rs.Pa_c = Pa_n;
+        return;
+    }
     const double a_p = rhoV / Pref / (2.0 * dt);
     const double k_p = gv / Pref + AhM;
     const double Pa_n = ((a_p - 0.5 * k_p) * rs.Pa_p + q[RP_GVAP] + gv * w_out + AhMPs) / (a_p + 0.5 * k_p);

@@ -207,6 +207,7 @@ struct hygro_ctx {
     double *d_room_state = nullptr;
     bool any_room_walls = false;   // some wall has a face on a room (those walls run in the room kernel)
     int room_warps = 1;            // warps of the room kernel's blocks (most walls of one room)
+    int room_scheme = HYGRO_ROOM_DF;
     int n_free = 0;                // walls of the persistent kernel
     std::string room_issue;        // room configuration problem reported by hygro_run
     std::string trace_path;
@@ -467,6 +468,7 @@ hygro_status build_schedule(hygro_ctx *c)
             const double pv[15] = {q.volume, q.ach, q.Q_gain, q.g_vap, q.T_out_mean, q.T_out_amp, q.P_out_mean,
                                    q.P_out_amp, q.period, q.phase_T, q.phase_P, q.rho_a, q.cp_a, q.cp_v, q.Pv_ref};
             for (int k = 0; k < 15; ++k) o.par[k] = pv[k];
+            o.par[RP_SCHEME] = (double)c->room_scheme;
             c->room_warps = std::max(c->room_warps, (int)o.n_walls);
         }
         CUDA_TRY(c, cudaMemcpy(c->d_rooms, ri.data(), ri.size() * sizeof(RoomInfo), cudaMemcpyHostToDevice));
@@ -885,6 +887,20 @@ hygro_status hygro_set_rooms(hygro_ctx *c, int32_t n_rooms, const hygro_room *ro
         CUDA_TRY(c, cudaMemcpy(c->d_room_state, st.data(), st.size() * sizeof(double), cudaMemcpyHostToDevice));
     c->have_rooms = true;
     return build_schedule(c);
+}
+
+hygro_status hygro_set_option(hygro_ctx *c, int32_t option, int64_t value)
+{
+    if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    if (option == HYGRO_OPT_ROOM_SCHEME) {
+        if (value != HYGRO_ROOM_DF && value != HYGRO_ROOM_EULER)
+            return fail(c, HYGRO_E_INVALID, "room scheme must be HYGRO_ROOM_DF or HYGRO_ROOM_EULER");
+        if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        c->room_scheme = (int)value;
+        return build_schedule(c);   // rebuilds the device room descriptors
+    }
+    return fail(c, HYGRO_E_INVALID, "unknown option %d", option);
 }
 
 hygro_status hygro_get_rooms(hygro_ctx *c, int32_t level, double *Ta, double *Pa)

@@ -79,10 +79,10 @@ struct RoomInfo {
     int32_t wall[HYGRO_MAX_ROOM_WALLS];   // ascending wall indices
     int32_t face[HYGRO_MAX_ROOM_WALLS];   // which face of the wall is on the room
     double area[HYGRO_MAX_ROOM_WALLS];    // m^2
-    double par[16];                       // hygro_room fields volume .. Pv_ref (15 used)
+    double par[16];                       // hygro_room fields volume .. Pv_ref, then the room scheme
 };
 enum { RP_VOL = 0, RP_ACH, RP_QGAIN, RP_GVAP, RP_TMEAN, RP_TAMP, RP_PMEAN, RP_PAMP, RP_PERIOD, RP_PHT, RP_PHP,
-       RP_RHOA, RP_CPA, RP_CPV, RP_PVREF };
+       RP_RHOA, RP_CPA, RP_CPV, RP_PVREF, RP_SCHEME };
 
 template <typename real>
 struct DevCtx {

@@ -28,6 +28,8 @@ HYGRO_E_UNSUPPORTED = -7
 HYGRO_FP32, HYGRO_FP64 = 0, 1
 HYGRO_KERNEL_PERSISTENT, HYGRO_KERNEL_PLAIN = 0, 1
 HYGRO_BC_AMBIENT, HYGRO_BC_ADIABATIC, HYGRO_BC_ROOM = 0, 1, 2
+HYGRO_OPT_ROOM_SCHEME = 1
+HYGRO_ROOM_DF, HYGRO_ROOM_EULER = 0, 1
 HYGRO_NOALLOC_SCRATCH_BYTES = 8 << 20
 STATUS_NAMES = {0: "HYGRO_OK", -1: "HYGRO_E_INVALID", -2: "HYGRO_E_NOMEM", -3: "HYGRO_E_CUDA",
                 -4: "HYGRO_E_STATE", -5: "HYGRO_E_NONFINITE", -6: "HYGRO_E_TIMEOUT", -7: "HYGRO_E_UNSUPPORTED"}
@@ -36,7 +38,7 @@ STATUS_NAMES = {0: "HYGRO_OK", -1: "HYGRO_E_INVALID", -2: "HYGRO_E_NOMEM", -3: "
 ABI_FUNCTIONS = ("hygro_create", "hygro_set_materials", "hygro_set_bc", "hygro_run", "hygro_sync",
                  "hygro_fluxes", "hygro_get_fields", "hygro_set_fields", "hygro_get_step", "hygro_get_state",
                  "hygro_set_state", "hygro_last_error", "hygro_destroy", "hygro_run_noalloc", "hygro_set_rooms",
-                 "hygro_get_rooms", "hygro_loss_grad", "hygro_balance")
+                 "hygro_get_rooms", "hygro_loss_grad", "hygro_balance", "hygro_set_option")
 # Exported entry points of the 2D sections (names of include/hygro2d.h).
 ABI_FUNCTIONS_2D = ("hygro2d_create", "hygro2d_set_materials", "hygro2d_set_bc", "hygro2d_run", "hygro2d_sync",
                     "hygro2d_get_fields", "hygro2d_set_fields", "hygro2d_get_step", "hygro2d_last_error",
@@ -112,6 +114,7 @@ def lib(build_if_missing: bool = False) -> C.CDLL:
         "hygro_get_fields": [P, C.c_int32, P, P],
         "hygro_set_fields": [P, C.c_int32, P, P],
         "hygro_balance": [P, P],
+        "hygro_set_option": [P, C.c_int32, C.c_int64],
         "hygro_get_step": [P, C.POINTER(C.c_int64)],
         "hygro_get_state": [P, P, C.POINTER(C.c_size_t)],
         "hygro_set_state": [P, P, C.c_size_t],
@@ -238,6 +241,10 @@ def hygro_set_state(ctx, image: bytes):
 def hygro_set_rooms(ctx, n_rooms: int, rooms, wall_area):
     _check(lib().hygro_set_rooms(ctx, int(n_rooms), C.cast(rooms, C.c_void_p) if rooms is not None else None,
                                  _ptr(wall_area)), ctx)
+
+
+def hygro_set_option(ctx, option: int, value: int):
+    _check(lib().hygro_set_option(ctx, int(option), int(value)), ctx)
 
 
 def hygro_get_rooms(ctx, level: int, Ta=None, Pa=None):
@@ -380,6 +387,9 @@ class Hygro:
         for r in range(len(par)):
             arr[r] = hygro_room(*[float(x) for x in par[r, :15]], float(rm["Ta0"][r]), float(rm["Pa0"][r]))
         hygro_set_rooms(self.ctx, len(par), arr, np.ascontiguousarray(rm["wall_area"], np.float64))
+        if par.shape[1] > 15 and np.any(par[:, 15] == 1.0):
+            # the room rows' scheme slot (the oracle's layout): explicit Euler rooms
+            hygro_set_option(self.ctx, HYGRO_OPT_ROOM_SCHEME, HYGRO_ROOM_EULER)
 
     def rooms(self, level: int = 0):
         n = len(self.wl.rooms["par"]) if self.wl.rooms else 0

@@ -412,9 +412,12 @@ def test_ambient_forcing(oracle_mod):
     assert (T, P) == (293.0, 1000.0)
 
 
-def test_room_steady_state(oracle_mod):
+@pytest.mark.parametrize("scheme", [0, 1])
+def test_room_steady_state(oracle_mod, scheme):
     """One room, two walls, constant gains, Lv = 0: the steady room air state is the closed form
-    Ta = To + Q / (gv cpa + sum A / R), Pva = Po + g / (gv / Pref + sum A / R_M)."""
+    Ta = To + Q / (gv cpa + sum A / R), Pva = Po + g / (gv / Pref + sum A / R_M) -- for the room as a DF
+    node (scheme 0) and for the explicit Euler room update of Sec. 5.2 (scheme 1, stable at this dt): both
+    have the steady balance as their fixed point."""
     To, Po, Q, g, V, ach = 275.0, 600.0, 400.0, 1.5e-4, 30.0, 1.0
     rho, cpa, cpv, Pref = 1.2, 1006.0, 1860.0, 1.61e5
     walls = []
@@ -440,6 +443,7 @@ def test_room_steady_state(oracle_mod):
     wl.Lv = 0.0
     par = np.zeros((1, 16))
     par[0, :15] = [V, ach, Q, g, To, 0.0, Po, 0.0, 86400.0, 0.0, 0.0, rho, cpa, cpv, Pref]
+    par[0, 15] = scheme
     wl.rooms = dict(par=par, wall_area=np.array([s[3] for s in specs]), Ta0=np.array([291.0]), Pa0=np.array([950.0]))
     o, _ = _run_to_steady(oracle_mod, wl, chunk=20000, max_chunks=200, tol=1e-14)
     gv = rho * V * ach / 3600.0
@@ -447,3 +451,29 @@ def test_room_steady_state(oracle_mod):
     Pa = Po + g / (gv / Pref + sum(A / R for A, R in RMs))
     assert abs(o.room[0, 1] - Ta) <= 1e-9 * Ta
     assert abs(o.room[0, 3] - Pa) <= 1e-9 * Pa
+
+
+def test_room_euler_is_unstable_at_the_building_time_step(oracle_mod):
+    """Reading R26: with the whole-building workload's dt = 300 s, a small room's time constant (heat
+    capacity over exchange conductance) is below dt / 2, so the explicit Euler room update of Sec. 5.2
+    grows without bound, while the room as a DF node stays at physical values."""
+    wl = wk.config3(seed=3, n_rooms=2, walls_per_room=6, n_steps=400)
+    rooms = dict(wl.rooms)
+    par = np.array(rooms["par"], np.float64).copy()
+    par[:, 0] = 30.0          # 30 m^3 rooms
+    wl.rooms = dict(rooms, par=par)
+    rho_V_cp = par[:, 11] * par[:, 0] * par[:, 12]
+    tau = rho_V_cp / (np.bincount(np.where(wl.bc_room[:, 1] >= 0, wl.bc_room[:, 1], 0),
+                                  weights=wl.rooms["wall_area"] * wl.bc_par[:, 1, 0], minlength=2))
+    assert np.all(tau < wl.dt / 2)
+    o = oracle_mod.Oracle(wl, n_threads=1)
+    o.run(400)
+    assert np.all(np.abs(o.room[:, 1] - 293.0) < 60.0)
+    par_e = par.copy()
+    par_e[:, 15] = 1.0
+    wl.rooms = dict(rooms, par=par_e)
+    oe = oracle_mod.Oracle(wl, n_threads=1)
+    with np.errstate(all="ignore"):
+        oe.run(400)
+    Ta = oe.room[:, 1]
+    assert np.any(~np.isfinite(Ta)) or np.max(np.abs(Ta - 293.0)) > 1e3

@@ -104,3 +104,30 @@ def test_rooms_checkpoint_and_errors(H):
         h.run(1)
     assert e.value.status == H.HYGRO_E_UNSUPPORTED
     h.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-4)])
+def test_rooms_explicit_euler_option(H, oracle_mod, precision, tol):
+    """HYGRO_ROOM_EULER (the explicit room update of Sec. 5.2) against the oracle's Euler rooms, at a time
+    step where it is stable (dt = 20 s)."""
+    import dataclasses
+
+    wl = mixed_building(seed=6, n_steps=300)
+    wl = dataclasses.replace(wl, dt=20.0)
+    rooms = dict(wl.rooms)
+    rooms["par"] = np.array(rooms["par"], np.float64).copy()
+    rooms["par"][:, 15] = 1.0   # the scheme slot of the oracle's room rows: explicit Euler
+    wl.rooms = rooms
+    g = H.Hygro(wl, precision=precision)
+    s = g.run_sampled(300, 10)
+    Ta, Pa = g.rooms(0)
+    g.close()
+    o = oracle_mod.Oracle(wl)
+    r = o.run(300, 10)
+    assert relinf(s, r["samples"]) <= tol
+    assert relinf(Ta, o.room[:, 1]) <= tol and relinf(Pa, o.room[:, 3]) <= tol
+    # the DF room node gives a different trajectory (it is a different scheme)
+    rooms["par"][:, 15] = 0.0
+    o2 = oracle_mod.Oracle(wl)
+    o2.run(300, 10)
+    assert relinf(o2.room[:, 1], o.room[:, 1]) > 1e-8
