@@ -194,6 +194,18 @@ HYGRO_API hygro_status hygro_get_rooms(hygro_ctx *ctx, int32_t level, double *Ta
 HYGRO_API hygro_status hygro_run(hygro_ctx *ctx, int64_t n_steps, int32_t sample_every, void *samples,
                        size_t samples_bytes);
 
+/* Start option: the first step by explicit Euler substeps instead of the DF step with level -1 := level 0
+ * (DF is stated for n >= 1; the paper's explicit scheme is bounded by the stability condition it gives).
+ * Level 1 follows from level 0 by m explicit Euler substeps of dt / m per wall, the coefficients
+ * re-evaluated at every substep, Pv first and T with the substep's Pv change in the cTM storage term, the
+ * ambient air at each substep's time; m = ceil(dt / tau_max), tau_max = the wall's explicit stability
+ * bound at level 0 (min over nodes and both fields of w dx c / (sum of face conductances + h)). The flux
+ * sums receive dt / m times every substep's surface fluxes. Requires the context at step 0 (right after
+ * hygro_set_materials / hygro_set_fields); afterwards the step is 1 and the stored levels are (0, 1), and
+ * hygro_run continues with DF. A wall needing more than 2^24 substeps makes the call fail with
+ * HYGRO_E_UNSUPPORTED and no state changed. Walls with a room face: HYGRO_E_UNSUPPORTED. Synchronous. */
+HYGRO_API hygro_status hygro_start_euler(hygro_ctx *ctx);
+
 /* Wait for the context's stream; HYGRO_E_NONFINITE if any wall went
  * non-finite in the runs since the last check. */
 HYGRO_API hygro_status hygro_sync(hygro_ctx *ctx);

@@ -113,6 +113,8 @@ def _load():
         lib.orc_loss_tangent.restype = C.c_int
         lib.orc_loss_tangent.argtypes = [C.POINTER(_Problem), C.c_int64, C.POINTER(_Misfit), C.c_void_p,
                                          C.POINTER(C.c_double), C.POINTER(C.c_double)]
+        lib.orc_euler_start.restype = C.c_int
+        lib.orc_euler_start.argtypes = [C.POINTER(_Problem), C.POINTER(_State), C.c_double, C.c_int32]
         lib.orc_coefficients.restype = None
         lib.orc_coefficients.argtypes = [C.POINTER(_Problem), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
         _lib = lib
@@ -223,6 +225,15 @@ class Oracle:
         self.step = int(st.step)
         return dict(samples=samples, room_samples=room_samples, flux=flux if n_steps > 0 else None,
                     balance=bal)
+
+    def euler_start(self, refine: float = 1.0):
+        """The first step by explicit Euler substeps (state at step 0): levels become (0, 1), step 1."""
+        st = _State(self.step, _ptr(self.T_prev), _ptr(self.T_cur), _ptr(self.P_prev), _ptr(self.P_cur),
+                    _ptr(self.cumul), _ptr(self.room))
+        rc = _load().orc_euler_start(C.byref(self._p), C.byref(st), float(refine), int(self.n_threads))
+        if rc != 0:
+            raise RuntimeError(f"oracle Euler start failed with code {rc}")
+        self.step = int(st.step)
 
     def wall(self, w: int, field: str = "T", level: int = 0) -> np.ndarray:
         """Nodes of wall ``w``; level 0 is the newest (n), 1 the previous (n-1)."""

@@ -333,6 +333,137 @@ static void room_step(const orc_problem *p, int32_t r, double t, double *rs,
     rs[3] = Pa_n;
 }
 
+/* Start by explicit Euler substeps (an option of the first step): level 1 from level 0 by m explicit
+ * Euler steps of tau = dt / m, the coefficients of Sec. 2 re-evaluated at every substep, Pv first and T
+ * with the substep's Pv change in the cTM storage term, the ambient air at each substep's time. m is the
+ * smallest count with tau within the explicit stability bound of every node at level 0,
+ * tau <= w dx c / (sum of the face conductances k_f/dx + h) for both fields, times refine (>= 1).
+ * Afterwards level n-1 holds level 0, level n holds level 1, and the step is 1; the flux sums receive
+ * the sum over substeps of tau times the surface fluxes (surface values at each substep's start). */
+int orc_euler_start(const orc_problem *p, orc_state *s, double refine, int32_t n_threads)
+{
+    if (p == NULL || s == NULL || s->step != 0 || !(refine >= 1.0) || p->n_rooms > 0) return -1;
+    const int32_t W = p->n_walls;
+    int64_t *node_off = (int64_t *)calloc((size_t)W + 1, sizeof(int64_t));
+    int64_t *layer_off = (int64_t *)calloc((size_t)W + 1, sizeof(int64_t));
+    if (!node_off || !layer_off) {
+        free(node_off);
+        free(layer_off);
+        return -2;
+    }
+    int32_t Nmax = 3;
+    for (int32_t w = 0; w < W; ++w) {
+        node_off[w + 1] = node_off[w] + p->n_nodes[w];
+        layer_off[w + 1] = layer_off[w] + p->n_layers[w];
+        if (p->n_nodes[w] > Nmax) Nmax = p->n_nodes[w];
+    }
+    if (n_threads <= 0) n_threads = 1;
+    int rc = 0;
+#ifdef _OPENMP
+#pragma omp parallel for num_threads(n_threads) schedule(dynamic, 1)
+#endif
+    for (int32_t w = 0; w < W; ++w) {
+        double *buf = (double *)malloc(sizeof(double) * (size_t)Nmax * 13);
+        if (buf == NULL) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            rc = -2;
+            continue;
+        }
+        scratch sc;
+        sc.kM = buf; sc.cM = buf + Nmax; sc.kTT = buf + 2 * Nmax; sc.cTT = buf + 3 * Nmax;
+        sc.kTM = buf + 4 * Nmax; sc.cTM = buf + 5 * Nmax; sc.kMf = buf + 6 * Nmax;
+        sc.kTTf = buf + 7 * Nmax; sc.kTMf = buf + 8 * Nmax; sc.Pn = buf + 9 * Nmax; sc.Tn = buf + 10 * Nmax;
+        double *T = buf + 11 * Nmax, *P = buf + 12 * Nmax;
+        wall_view v = view_of(p, layer_off, w);
+        const int32_t N = v.N;
+        const double dx = v.dx, dt = p->dt, Lv = p->Lv;
+        const int64_t o = node_off[w];
+        for (int32_t j = 0; j < N; ++j) {
+            T[j] = s->T_cur[o + j];
+            P[j] = s->P_cur[o + j];
+        }
+        /* the stability bound at level 0 */
+        coefficients(p, &v, P, sc.kM, sc.cM, sc.kTT, sc.cTT, sc.kTM, sc.cTM, sc.kMf, sc.kTTf, sc.kTMf);
+        face_bc b0[2] = {face_of(p, w, 0, p->t0, NULL), face_of(p, w, 1, p->t0, NULL)};
+        double tmax = dt;
+        for (int32_t j = 0; j < N; ++j) {
+            const double wj = (j == 0 || j == N - 1) ? 0.5 : 1.0;
+            double GM = 0.0, GT = 0.0;
+            if (j > 0) {
+                GM += sc.kMf[j - 1] / dx;
+                GT += sc.kTTf[j - 1] / dx;
+            }
+            if (j < N - 1) {
+                GM += sc.kMf[j] / dx;
+                GT += sc.kTTf[j] / dx;
+            }
+            if (j == 0) {
+                GM += b0[0].hM;
+                GT += b0[0].hT;
+            }
+            if (j == N - 1) {
+                GM += b0[1].hM;
+                GT += b0[1].hT;
+            }
+            if (GM > 0.0 && wj * dx * sc.cM[j] / GM < tmax) tmax = wj * dx * sc.cM[j] / GM;
+            if (GT > 0.0 && wj * dx * sc.cTT[j] / GT < tmax) tmax = wj * dx * sc.cTT[j] / GT;
+        }
+        int64_t m = (int64_t)ceil(refine * dt / tmax);
+        if (m < 1) m = 1;
+        const double tau = dt / (double)m;
+        for (int64_t i = 0; i < m; ++i) {
+            const double t = p->t0 + (double)i * tau;
+            face_bc bc[2] = {face_of(p, w, 0, t, NULL), face_of(p, w, 1, t, NULL)};
+            coefficients(p, &v, P, sc.kM, sc.cM, sc.kTT, sc.cTT, sc.kTM, sc.cTM, sc.kMf, sc.kTTf, sc.kTMf);
+            /* surface fluxes with the values at the substep's start */
+            for (int f = 0; f < 2; ++f) {
+                const int32_t j = f == 0 ? 0 : N - 1;
+                const double g = bc[f].hM * (bc[f].P_inf - P[j]) + bc[f].g_inf;
+                const double q = bc[f].hT * (bc[f].T_inf - T[j]) + Lv * bc[f].hM * (bc[f].P_inf - P[j]) + bc[f].q_inf;
+                s->cumul[w * 4 + f * 2 + 0] += tau * q;
+                s->cumul[w * 4 + f * 2 + 1] += tau * g;
+            }
+            for (int32_t j = 0; j < N; ++j) {
+                const double wj = (j == 0 || j == N - 1) ? 0.5 : 1.0;
+                double rP = 0.0, rT = 0.0;
+                if (j > 0) {
+                    rP += sc.kMf[j - 1] / dx * (P[j - 1] - P[j]);
+                    rT += sc.kTTf[j - 1] / dx * (T[j - 1] - T[j]) + sc.kTMf[j - 1] / dx * (P[j - 1] - P[j]);
+                }
+                if (j < N - 1) {
+                    rP += sc.kMf[j] / dx * (P[j + 1] - P[j]);
+                    rT += sc.kTTf[j] / dx * (T[j + 1] - T[j]) + sc.kTMf[j] / dx * (P[j + 1] - P[j]);
+                }
+                for (int f = 0; f < 2; ++f)
+                    if ((f == 0 && j == 0) || (f == 1 && j == N - 1)) {
+                        rP += bc[f].hM * (bc[f].P_inf - P[j]) + bc[f].g_inf;
+                        rT += bc[f].hT * (bc[f].T_inf - T[j]) + Lv * bc[f].hM * (bc[f].P_inf - P[j]) + bc[f].q_inf;
+                    }
+                const double dP = tau * rP / (wj * dx * sc.cM[j]);
+                sc.Pn[j] = P[j] + dP;
+                sc.Tn[j] = T[j] + tau * rT / (wj * dx * sc.cTT[j]) - sc.cTM[j] / sc.cTT[j] * dP;
+            }
+            for (int32_t j = 0; j < N; ++j) {
+                T[j] = sc.Tn[j];
+                P[j] = sc.Pn[j];
+            }
+        }
+        for (int32_t j = 0; j < N; ++j) {
+            s->T_prev[o + j] = s->T_cur[o + j];
+            s->P_prev[o + j] = s->P_cur[o + j];
+            s->T_cur[o + j] = T[j];
+            s->P_cur[o + j] = P[j];
+        }
+        free(buf);
+    }
+    free(node_off);
+    free(layer_off);
+    if (rc == 0) s->step = 1;
+    return rc;
+}
+
 int orc_run(const orc_problem *p, orc_state *s, int64_t n_steps, int32_t sample_every,
             double *samples, double *room_samples, double *flux_last, double *balance_last,
             int32_t n_threads)

@@ -87,6 +87,11 @@ int orc_run(const orc_problem *p, orc_state *s, int64_t n_steps, int32_t sample_
             double *samples, double *room_samples, double *flux_last, double *balance_last,
             int32_t n_threads);
 
+/* The first step by explicit Euler substeps instead of DF with level -1 := level 0 (state at step 0, walls
+ * without rooms): level 1 from level 0 by m substeps of dt / m, m = ceil(refine * dt / tau_max) with
+ * tau_max the explicit stability bound at level 0. Afterwards the step is 1. 0 on success. */
+int orc_euler_start(const orc_problem *p, orc_state *s, double refine, int32_t n_threads);
+
 /* Ambient air state (T_inf, Pv_inf) seen by an ambient face at time t. */
 void orc_ambient(const orc_problem *p, int32_t wall, int32_t face, double t, double *T_inf, double *P_inf);
 

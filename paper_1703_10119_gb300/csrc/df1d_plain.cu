@@ -189,6 +189,183 @@ cudaError_t launch_balance_f64(const DevCtx<double> &d, const double *Tp, const 
     return launch_balance(d, Tp, Pp, Tn, Pn, n, bal, s);
 }
 
+// First step by explicit Euler substeps (hygro_start_euler): one block per wall, its levels in shared
+// memory. Level 1 from level 0 by m substeps of tau = dt / m, the coefficients re-evaluated at every
+// substep, Pv first and T with the substep's Pv change in the cTM storage term, the ambient air at each
+// substep's time; m = ceil(dt / tau_max) with tau_max the explicit stability bound of the wall at level 0,
+// min over nodes of C / (sum of the face conductances + h) for both fields (C = w dx c). In the kh form
+// of the layer table: C_Pv = 2 dt w (Aa + Ab P'), C_T = 2 dt w (Ba + Bb P'), C_TM = chi C_Pv. The flux sums
+// receive tau times the surface fluxes of every substep. Writes level 1 into the level n-1 buffer.
+// m_out[w] receives the substep count (0 if it exceeded max_sub: the wall is then left unchanged).
+template <typename real>
+__global__ void __launch_bounds__(128) df1d_euler_start_kernel(const DevCtx<real> d, int64_t max_sub, int64_t *m_out)
+{
+    extern __shared__ __align__(16) unsigned char es_raw[];
+    __shared__ double s_red[4];
+    const int w = blockIdx.x, tid = threadIdx.x;
+    const WallInfo wi = d.walls[w];
+    const int N = wi.N;
+    real *T = reinterpret_cast<real *>(es_raw), *P = T + N, *Tn = P + N, *Pn = Tn + N;
+    const real *tab = d.layer_tab + (size_t)wi.layer_off * kLayerStride;
+    const int8_t *lay = d.node_layer + wi.node_off;
+    const real *T0 = d.T[d.cur] + wi.node_off, *P0 = d.P[d.cur] + wi.node_off;
+    for (int j = tid; j < N; j += blockDim.x) {
+        T[j] = T0[j];
+        P[j] = P0[j];
+    }
+    const FaceInfo &f0 = d.faces[(size_t)w * 2], &f1 = d.faces[(size_t)w * 2 + 1];
+    const bool a0 = f0.kind == HYGRO_BC_AMBIENT, a1 = f1.kind == HYGRO_BC_AMBIENT;
+    const real hM0 = a0 ? (real)f0.hM : real(0), hT0 = a0 ? (real)f0.hT : real(0);
+    const real hM1 = a1 ? (real)f1.hM : real(0), hT1 = a1 ? (real)f1.hT : real(0);
+    const real g0 = a0 ? (real)f0.g_inf : real(0), q0 = a0 ? (real)f0.q_inf : real(0);
+    const real g1 = a1 ? (real)f1.g_inf : real(0), q1 = a1 ? (real)f1.q_inf : real(0);
+    const real Lv = (real)d.Lv, two_dt = (real)(2.0 * d.dt);
+    if (tid == 0) s_red[0] = d.dt;
+    __syncthreads();
+    // face conductances of node j (kh sums, harmonic across layers); left and right
+    auto faces = [&](int j, real &FMl, real &FTl, real &FMr, real &FTr) {
+        const LayerC<real> c = load_layer(tab, lay[j]);
+        const real khM = fma(c.kMb, P[j], c.kMa), khT = fma(c.kTb, P[j], c.kTa);
+        FMl = FTl = FMr = FTr = real(0);
+        if (j > 0) {
+            const LayerC<real> cl = load_layer(tab, lay[j - 1]);
+            const real a = fma(cl.kMb, P[j - 1], cl.kMa), b = fma(cl.kTb, P[j - 1], cl.kTa);
+            FMl = lay[j - 1] == lay[j] ? a + khM : face_harmonic(a, khM);
+            FTl = lay[j - 1] == lay[j] ? b + khT : face_harmonic(b, khT);
+        }
+        if (j < N - 1) {
+            const LayerC<real> cr = load_layer(tab, lay[j + 1]);
+            const real a = fma(cr.kMb, P[j + 1], cr.kMa), b = fma(cr.kTb, P[j + 1], cr.kTa);
+            FMr = lay[j + 1] == lay[j] ? khM + a : face_harmonic(khM, a);
+            FTr = lay[j + 1] == lay[j] ? khT + b : face_harmonic(khT, b);
+        }
+    };
+    // the stability bound at level 0
+    double tmin = d.dt;
+    for (int j = tid; j < N; j += blockDim.x) {
+        const LayerC<real> c = load_layer(tab, lay[j]);
+        const real wj = (j == 0 || j == N - 1) ? real(0.5) : real(1);
+        real FMl, FTl, FMr, FTr;
+        faces(j, FMl, FTl, FMr, FTr);
+        const real GM = FMl + FMr + (j == 0 ? hM0 : real(0)) + (j == N - 1 ? hM1 : real(0));
+        const real GT = FTl + FTr + (j == 0 ? hT0 : real(0)) + (j == N - 1 ? hT1 : real(0));
+        const double CP = (double)(two_dt * wj * fma(c.Ab, P[j], c.Aa)), CT = (double)(two_dt * wj * fma(c.Bb, P[j], c.Ba));
+        if (GM > real(0)) tmin = fmin(tmin, CP / (double)GM);
+        if (GT > real(0)) tmin = fmin(tmin, CT / (double)GT);
+    }
+    for (int o = 16; o > 0; o >>= 1) tmin = fmin(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
+    if ((tid & 31) == 0) atomicMin(reinterpret_cast<unsigned long long *>(&s_red[0]), __double_as_longlong(tmin));
+    __syncthreads();
+    const double tau_max = s_red[0];   // positive doubles order like their bit patterns
+    int64_t m = (int64_t)ceil(d.dt / tau_max);
+    if (m < 1) m = 1;
+    if (m > max_sub) {
+        if (tid == 0) m_out[w] = 0;
+        return;
+    }
+    const double tau = d.dt / (double)m;
+    const real tau_r = (real)tau;
+    double cq0 = 0.0, cg0 = 0.0, cq1 = 0.0, cg1 = 0.0, lq0 = 0.0, lg0 = 0.0, lq1 = 0.0, lg1 = 0.0;
+    for (int64_t i = 0; i < m; ++i) {
+        real aT0 = real(0), aP0 = real(0), aT1 = real(0), aP1 = real(0);
+        for (int j = tid; j < N; j += blockDim.x) {
+            const LayerC<real> c = load_layer(tab, lay[j]);
+            const real wj = (j == 0 || j == N - 1) ? real(0.5) : real(1);
+            real FMl, FTl, FMr, FTr;
+            faces(j, FMl, FTl, FMr, FTr);
+            real rP = real(0), rT = real(0);
+            if (j > 0) {
+                rP = fma(FMl, P[j - 1] - P[j], rP);
+                rT = fma(FTl, T[j - 1] - T[j], fma(Lv * FMl, P[j - 1] - P[j], rT));
+            }
+            if (j < N - 1) {
+                rP = fma(FMr, P[j + 1] - P[j], rP);
+                rT = fma(FTr, T[j + 1] - T[j], fma(Lv * FMr, P[j + 1] - P[j], rT));
+            }
+            if (j == 0 && a0) {
+                double x, y;
+                ambient_at(f0, d.noise, i, d.t0, tau, x, y);
+                aT0 = (real)x;
+                aP0 = (real)y;
+                const real hm = hM0 * (aP0 - P[j]);
+                const real gq = hm + g0, qq = fma(hT0, aT0 - T[j], fma(Lv, hm, q0));
+                rP += gq;
+                rT += qq;
+                cq0 += tau * (double)qq;
+                cg0 += tau * (double)gq;
+                lq0 = (double)qq;
+                lg0 = (double)gq;
+            }
+            if (j == N - 1 && a1) {
+                double x, y;
+                ambient_at(f1, d.noise, i, d.t0, tau, x, y);
+                aT1 = (real)x;
+                aP1 = (real)y;
+                const real hm = hM1 * (aP1 - P[j]);
+                const real gq = hm + g1, qq = fma(hT1, aT1 - T[j], fma(Lv, hm, q1));
+                rP += gq;
+                rT += qq;
+                cq1 += tau * (double)qq;
+                cg1 += tau * (double)gq;
+                lq1 = (double)qq;
+                lg1 = (double)gq;
+            }
+            const real CP = two_dt * wj * fma(c.Ab, P[j], c.Aa), CT = two_dt * wj * fma(c.Bb, P[j], c.Ba);
+            const real dP = tau_r * rP / CP;
+            Pn[j] = P[j] + dP;
+            Tn[j] = T[j] + tau_r * rT / CT - c.chi * CP / CT * dP;
+        }
+        __syncthreads();
+        for (int j = tid; j < N; j += blockDim.x) {
+            T[j] = Tn[j];
+            P[j] = Pn[j];
+        }
+        __syncthreads();
+    }
+    real *T1 = d.T[1 - d.cur] + wi.node_off, *P1 = d.P[1 - d.cur] + wi.node_off;
+    bool bad = false;
+    for (int j = tid; j < N; j += blockDim.x) {
+        T1[j] = T[j];
+        P1[j] = P[j];
+        bad |= !(isfinite(T[j]) && isfinite(P[j]));
+    }
+    if (bad) atomicExch(d.nonfinite, 1);
+    if (tid == 0) {
+        d.cumul[(size_t)w * 4 + 0] += cq0;
+        d.cumul[(size_t)w * 4 + 1] += cg0;
+        d.flast[(size_t)w * 4 + 0] = lq0;
+        d.flast[(size_t)w * 4 + 1] = lg0;
+        m_out[w] = m;
+    }
+    if (tid == (N - 1) % (int)blockDim.x) {
+        d.cumul[(size_t)w * 4 + 2] += cq1;
+        d.cumul[(size_t)w * 4 + 3] += cg1;
+        d.flast[(size_t)w * 4 + 2] = lq1;
+        d.flast[(size_t)w * 4 + 3] = lg1;
+    }
+}
+
+template <typename real>
+static cudaError_t launch_euler(const DevCtx<real> &d, int Nmax, int64_t max_sub, int64_t *m_out, cudaStream_t s)
+{
+    const size_t smem = (size_t)4 * Nmax * sizeof(real);
+    cudaError_t e = cudaFuncSetAttribute(df1d_euler_start_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    df1d_euler_start_kernel<real><<<d.W, 128, smem, s>>>(d, max_sub, m_out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_euler_start_f32(const DevCtx<float> &d, int Nmax, int64_t max_sub, int64_t *m_out, cudaStream_t s)
+{
+    return launch_euler(d, Nmax, max_sub, m_out, s);
+}
+
+cudaError_t launch_euler_start_f64(const DevCtx<double> &d, int Nmax, int64_t max_sub, int64_t *m_out, cudaStream_t s)
+{
+    return launch_euler(d, Nmax, max_sub, m_out, s);
+}
+
 cudaError_t launch_plain_step_f32(const DevCtx<float> &d, int64_t n, int32_t sample_idx, float *samples,
                                   cudaStream_t s)
 {

@@ -982,6 +982,78 @@ hygro_status hygro_run(hygro_ctx *c, int64_t n_steps, int32_t sample_every, void
     return HYGRO_OK;
 }
 
+hygro_status hygro_start_euler(hygro_ctx *c)
+{
+    if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    if (!(c->have_materials && c->have_bc[0] && c->have_bc[1]))
+        return fail(c, HYGRO_E_STATE, "hygro_set_materials and hygro_set_bc (both faces) must come first");
+    if (c->step != 0) return fail(c, HYGRO_E_STATE, "the Euler start applies at step 0 (the context is at %lld)",
+                                  (long long)c->step);
+    for (int w = 0; w < c->W; ++w)
+        for (int f = 0; f < 2; ++f)
+            if (c->bc[f][w].bc.kind == HYGRO_BC_ROOM)
+                return fail(c, HYGRO_E_UNSUPPORTED, "wall %d has a room face: the Euler start covers walls without rooms",
+                            w);
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
+    int Nmax = 0;
+    for (int w = 0; w < c->W; ++w) Nmax = std::max(Nmax, c->N[w]);
+    const int64_t max_sub = (int64_t)1 << 24;
+    const size_t nb = (size_t)c->total_nodes * c->real_size;
+    int64_t *dm = nullptr;
+    void *s1T = nullptr, *s1P = nullptr;
+    std::vector<double> cum_save((size_t)c->W * 4), fl_save((size_t)c->W * 4);
+    cudaError_t e = cudaMalloc(&dm, (size_t)c->W * sizeof(int64_t));
+    if (e == cudaSuccess) e = cudaMalloc(&s1T, nb);
+    if (e == cudaSuccess) e = cudaMalloc(&s1P, nb);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(cum_save.data(), c->d_cumul, cum_save.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(fl_save.data(), c->d_flast, fl_save.size() * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) {
+        // level 1 goes to scratch buffers; the stored levels change only if every wall is accepted
+        const int prv = 1 - c->cur;
+        if (c->precision == HYGRO_FP64) {
+            DevCtx<double> d = make_dev<double>(c);
+            d.T[prv] = (double *)s1T;
+            d.P[prv] = (double *)s1P;
+            e = launch_euler_start_f64(d, Nmax, max_sub, dm, c->stream);
+        } else {
+            DevCtx<float> d = make_dev<float>(c);
+            d.T[prv] = (float *)s1T;
+            d.P[prv] = (float *)s1P;
+            e = launch_euler_start_f32(d, Nmax, max_sub, dm, c->stream);
+        }
+    }
+    std::vector<int64_t> m((size_t)c->W, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(m.data(), dm, m.size() * sizeof(int64_t), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    bool refused = false;
+    int bad_wall = -1;
+    if (e == cudaSuccess)
+        for (int w = 0; w < c->W && !refused; ++w)
+            if (m[w] == 0) {
+                refused = true;
+                bad_wall = w;
+            }
+    if (e == cudaSuccess && !refused) {
+        const int prv = 1 - c->cur;
+        e = cudaMemcpy(c->dT[prv], s1T, nb, cudaMemcpyDeviceToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(c->dP[prv], s1P, nb, cudaMemcpyDeviceToDevice);
+    }
+    if (e == cudaSuccess && refused) {
+        e = cudaMemcpy(c->d_cumul, cum_save.data(), cum_save.size() * sizeof(double), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(c->d_flast, fl_save.data(), fl_save.size() * sizeof(double), cudaMemcpyHostToDevice);
+    }
+    cudaFree(dm);
+    cudaFree(s1T);
+    cudaFree(s1P);
+    if (e != cudaSuccess) return fail(c, HYGRO_E_CUDA, "Euler start: %s", cudaGetErrorString(e));
+    if (refused)
+        return fail(c, HYGRO_E_UNSUPPORTED, "wall %d needs more than %lld Euler substeps", bad_wall, (long long)max_sub);
+    c->cur = 1 - c->cur;
+    c->step = 1;
+    return check_nonfinite(c);
+}
+
 hygro_status hygro_sync(hygro_ctx *c)
 {
     if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");

@@ -145,6 +145,9 @@ cudaError_t launch_balance_f32(const DevCtx<float> &d, const float *Tp, const fl
 cudaError_t launch_balance_f64(const DevCtx<double> &d, const double *Tp, const double *Pp, const double *Tn,
                                const double *Pn, int64_t n, double *bal, cudaStream_t s);
 
+cudaError_t launch_euler_start_f32(const DevCtx<float> &d, int Nmax, int64_t max_sub, int64_t *m_out, cudaStream_t s);
+cudaError_t launch_euler_start_f64(const DevCtx<double> &d, int Nmax, int64_t max_sub, int64_t *m_out, cudaStream_t s);
+
 cudaError_t launch_plain_step_f32(const DevCtx<float> &d, int64_t n, int32_t sample_idx, float *samples,
                                   cudaStream_t s);
 cudaError_t launch_plain_step_f64(const DevCtx<double> &d, int64_t n, int32_t sample_idx, double *samples,

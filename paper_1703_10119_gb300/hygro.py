@@ -38,7 +38,8 @@ STATUS_NAMES = {0: "HYGRO_OK", -1: "HYGRO_E_INVALID", -2: "HYGRO_E_NOMEM", -3: "
 ABI_FUNCTIONS = ("hygro_create", "hygro_set_materials", "hygro_set_bc", "hygro_run", "hygro_sync",
                  "hygro_fluxes", "hygro_get_fields", "hygro_set_fields", "hygro_get_step", "hygro_get_state",
                  "hygro_set_state", "hygro_last_error", "hygro_destroy", "hygro_run_noalloc", "hygro_set_rooms",
-                 "hygro_get_rooms", "hygro_loss_grad", "hygro_balance", "hygro_set_option")
+                 "hygro_get_rooms", "hygro_loss_grad", "hygro_balance", "hygro_set_option",
+                 "hygro_start_euler")
 # Exported entry points of the 2D sections (names of include/hygro2d.h).
 ABI_FUNCTIONS_2D = ("hygro2d_create", "hygro2d_set_materials", "hygro2d_set_bc", "hygro2d_run", "hygro2d_sync",
                     "hygro2d_get_fields", "hygro2d_set_fields", "hygro2d_get_step", "hygro2d_last_error",
@@ -115,6 +116,7 @@ def lib(build_if_missing: bool = False) -> C.CDLL:
         "hygro_set_fields": [P, C.c_int32, P, P],
         "hygro_balance": [P, P],
         "hygro_set_option": [P, C.c_int32, C.c_int64],
+        "hygro_start_euler": [P],
         "hygro_get_step": [P, C.POINTER(C.c_int64)],
         "hygro_get_state": [P, P, C.POINTER(C.c_size_t)],
         "hygro_set_state": [P, P, C.c_size_t],
@@ -200,6 +202,10 @@ def hygro_run_noalloc(ctx, n_steps: int, sample_every: int = 0, samples=None):
 
 def hygro_sync(ctx):
     _check(lib().hygro_sync(ctx), ctx)
+
+
+def hygro_start_euler(ctx):
+    _check(lib().hygro_start_euler(ctx), ctx)
 
 
 def hygro_fluxes(ctx, flux=None, cumulative=None):
@@ -410,6 +416,10 @@ class Hygro:
 
     def sync(self):
         hygro_sync(self.ctx)
+
+    def start_euler(self):
+        """The first step by explicit Euler substeps (hygro_start_euler)."""
+        hygro_start_euler(self.ctx)
 
     def loss_grad(self, n_steps: int, sample_every: int, obs, wT: float, wP: float, checkpoint_every: int = 0):
         """Misfit loss and its gradient [total layers, 9] (hygro_loss_grad)."""

@@ -477,3 +477,69 @@ def test_room_euler_is_unstable_at_the_building_time_step(oracle_mod):
         oe.run(400)
     Ta = oe.room[:, 1]
     assert np.any(~np.isfinite(Ta)) or np.max(np.abs(Ta - 293.0)) > 1e3
+
+
+def test_euler_start_converges_to_the_semidiscrete_solution(oracle_mod):
+    """The start by explicit Euler substeps: level 1 tends to the exact solution at t = dt of the coupled
+    linear semi-discrete system (two layers, constant coefficients, latent cross flux, cTM storage, Robin
+    faces with sources), written as dy/dt = J y + c and solved by the matrix exponential. The error is first
+    order in the substep: it halves when the substep count doubles."""
+    counts, L = [3, 3], 0.1
+    lays = [dict(kM0=2e-11, cM0=5e-2, kTT0=0.8, cTT0=1.0e6, chi=8.0e4),
+            dict(kM0=6e-11, cM0=3e-2, kTT0=0.3, cTT0=1.6e6, chi=5.0e4)]
+    Lv, dt = wk.LV, 600.0
+    b0 = dict(hT=10.0, hM=2e-8, T_mean=300.0, P_mean=1400.0, q_inf=15.0, g_inf=3e-8)
+    b1 = dict(hT=6.0, hM=3e-8, T_mean=288.0, P_mean=800.0)
+    T0, P0 = 293.0, 1000.0
+    N = sum(counts)
+    dx = L / (N - 1)
+    lay_of = np.repeat([0, 1], counts)
+    w = np.ones(N)
+    w[0] = w[-1] = 0.5
+
+    def faces(key):
+        k = np.array([lays[l][key] for l in lay_of])
+        K = np.zeros((N, N))
+        for j in range(N - 1):
+            kf = 0.5 * (k[j] + k[j + 1]) if lay_of[j] == lay_of[j + 1] else 2 * k[j] * k[j + 1] / (k[j] + k[j + 1])
+            K[[j, j + 1], [j, j + 1]] += kf / dx
+            K[j, j + 1] -= kf / dx
+            K[j + 1, j] -= kf / dx
+        return K
+
+    KP, KT = faces("kM0"), faces("kTT0")
+    KP[0, 0] += b0["hM"]
+    KP[-1, -1] += b1["hM"]
+    KT[0, 0] += b0["hT"]
+    KT[-1, -1] += b1["hT"]
+    MP = w * dx * np.array([lays[l]["cM0"] for l in lay_of])
+    MT = w * dx * np.array([lays[l]["cTT0"] for l in lay_of])
+    CTM = w * dx * np.array([lays[l]["chi"] * lays[l]["cM0"] for l in lay_of])
+    bPh = np.zeros(N)
+    bPh[0], bPh[-1] = b0["hM"] * b0["P_mean"], b1["hM"] * b1["P_mean"]
+    bP = bPh.copy()
+    bP[0] += b0["g_inf"]
+    bT = np.zeros(N)
+    bT[0], bT[-1] = b0["hT"] * b0["T_mean"] + b0["q_inf"], b1["hT"] * b1["T_mean"]
+    # dP/dt = MP^-1 (-KP P + bP); MT dT/dt + CTM dP/dt = -KT T + bT + Lv (-KP P + bPh)
+    JPP = -KP / MP[:, None]
+    J = np.zeros((2 * N, 2 * N))
+    J[:N, :N] = JPP
+    J[N:, :N] = (-Lv * KP - CTM[:, None] * JPP) / MT[:, None]
+    J[N:, N:] = -KT / MT[:, None]
+    c = np.concatenate([bP / MP, (bT + Lv * bPh - CTM * bP / MP) / MT])
+    y0 = np.concatenate([np.full(N, P0), np.full(N, T0)])
+    ys = -np.linalg.solve(J, c)
+    exact = ys + expm(J * dt) @ (y0 - ys)
+    errs = []
+    for refine in (2.0, 4.0, 8.0, 16.0):
+        wl = wk.layered_wall(counts, L, lays, dt=dt, T0=T0, P0=P0, bc0=b0, bc1=b1, Lv=Lv)
+        o = oracle_mod.Oracle(wl, n_threads=1)
+        o.euler_start(refine)
+        assert o.step == 1
+        assert np.array_equal(o.wall(0, "T", 1), np.full(N, T0))
+        got = np.concatenate([o.wall(0, "P"), o.wall(0, "T")])
+        errs.append(np.max(np.abs(got - exact) / np.abs(exact - y0).max()))
+    ratios = [errs[i] / errs[i + 1] for i in range(3)]
+    assert all(1.8 < r < 2.2 for r in ratios), (errs, ratios)
+    assert errs[-1] < 0.05

@@ -256,3 +256,28 @@ def test_balance_of_the_next_step(H, oracle_mod, precision, tol):
         # another order: 1e-9 of M separates rounding from a wrong term (which would be off by O(M))
         for k in range(3):
             assert np.all(np.abs(bal[..., k] - ref[..., k]) <= 1e-9 * ref[..., 3]), k
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-4)])
+def test_euler_start_matches_oracle(H, oracle_mod, precision, tol):
+    """hygro_start_euler (the first step by explicit Euler substeps) then DF steps, against the oracle."""
+    wl = ragged_batch([3, 6, 17, 40, 65, 120], 30, dt=60.0)
+    with H.Hygro(wl, precision=precision, kernel="persistent") as g:
+        g.start_euler()
+        assert g.step == 1
+        T1, P1 = g.fields(0)
+        T0, P0 = g.fields(1)
+        s = g.run_sampled(24, 6)
+        T, P = g.fields(0)
+        _, cum = g.fluxes()
+        with pytest.raises(H.HygroError) as e:
+            g.start_euler()
+        assert e.value.status == H.HYGRO_E_STATE
+    o = oracle_mod.Oracle(wl, n_threads=1)
+    o.euler_start(1.0)
+    assert relinf(T0, o.T_prev) == 0.0 and relinf(P0, o.P_prev) == 0.0
+    assert relinf(T1, o.T_cur) <= tol and relinf(P1, o.P_cur) <= tol
+    r = o.run(24, 6)
+    assert relinf(T, o.T_cur) <= tol and relinf(P, o.P_cur) <= tol
+    assert relinf(s, r["samples"]) <= tol
+    assert np.max(np.abs(cum - o.cumul)) <= 50 * tol * np.max(np.abs(o.cumul))
