@@ -39,9 +39,13 @@ UNIT = "cell-updates/s"
 #                     coefficients 2, face 1, Pv 10, T 7 = 20 (+ 1 reciprocal)
 OPS_GENERAL = 27
 OPS_SIMPLE_HEAT = 20
+# adjoint, per differentiated cell-update: forward step 27, its recompute 27, reverse step 77 (the
+# recomputed forward quantities 26, the transposed step 36, the face chain 15)
+OPS_ADJOINT = 131
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
-KERNEL_SOURCES = ["paper_1703_10119_gb300/csrc/df1d_persistent.cuh", "paper_1703_10119_gb300/csrc/df1d_common.cuh"]
+KERNEL_SOURCES = ["paper_1703_10119_gb300/csrc/df1d_persistent.cuh", "paper_1703_10119_gb300/csrc/df1d_common.cuh",
+                  "paper_1703_10119_gb300/csrc/hygro_internal.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "df1d_persistent_f32_traffic.json")
 # 2D sections: compulsory DRAM bytes of one cell-update when every step is a pass over memory (read the
 # (T, Pv) pairs of levels n and n-1, write the pair of level n+1, 4-byte reals)
@@ -319,11 +323,21 @@ def bench_adjoint(args, H, wk, stream, local, rank):
     g = grad.cpu().numpy()
     h.close()
     C = int(np.ceil(np.sqrt(wl.n_steps)))
-    out = {"value": wl.total_nodes * wl.n_steps / (ms / 1e3), "unit": UNIT + " (forward steps differentiated)",
+    value = wl.total_nodes * wl.n_steps / (ms / 1e3)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = OPS_ADJOINT * value / 1e12
+    out = {"value": value, "unit": UNIT + " (forward steps differentiated)",
            "workload": f"{wl.n_walls} two-layer walls N=200, dt=60 s x {wl.n_steps} steps, sensors every "
                        f"{s.sample_every} steps, FP32 adjoint, checkpoints every {C} steps",
            "ms_per_gradient": ms, "seconds_call": el, "loss": L,
-           "note": "forward + recompute + reverse sweep in one launch; cell-updates of the forward run per second"}
+           "note": "forward + recompute + reverse sweep in one launch; cell-updates of the forward run per second; "
+                   "the time is the whole hygro_loss_grad call (buffer allocation and copies included)",
+           "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s", "frac": achieved / peak,
+                        "traffic": None,
+                        "note": f"FP32 FMA-pipe roof; {OPS_ADJOINT} algorithmic FP32 ops per differentiated "
+                                "cell-update (forward 27, recompute 27, reverse step 77) plus 6 reciprocals; "
+                                "kernel adjoint_reg_kernel<float>"}}
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
 

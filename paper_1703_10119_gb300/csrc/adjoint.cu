@@ -9,7 +9,7 @@ static cudaError_t launch_adjoint(const AdjDev<real> &d, int warps, cudaStream_t
     const size_t smem = (size_t)warps * adj_smem_per_warp<real>(d.Nmax);
     cudaError_t e = cudaFuncSetAttribute(adjoint_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int blocks = (d.W + warps - 1) / warps;
+    const int blocks = (d.n_list + warps - 1) / warps;
     adjoint_kernel<real><<<blocks, 32 * warps, smem, s>>>(d);
     return cudaGetLastError();
 }

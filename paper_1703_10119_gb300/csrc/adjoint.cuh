@@ -29,7 +29,9 @@ struct AdjWall {
     int32_t N, node_off, layer_off, n_layers;
     int16_t start[33];   // lane l owns nodes [start[l], start[l+1])
     int8_t layer[32];    // layer of lane l's nodes (-1: no nodes)
+    int32_t kt;          // register kernel: slots per lane (>= the longest run); 0: shared-memory kernel
     double dx;
+    int64_t ck_off, seg_off;   // first real of the wall's checkpoints and segment levels
 };
 
 template <typename real>
@@ -46,8 +48,12 @@ struct AdjDev {
     int32_t se, K;              // samples after every se-th step, K of them
     int64_t n_steps;
     int32_t C, n_seg;           // checkpoint stride and count
-    real *ckpt;                 // [W][n_seg][4][Nmax]: T(n-1), T(n), P(n-1), P(n) at n = c C
-    real *seg;                  // [W][C + 2][2][Nmax]: T, P of levels c C - 1 .. (c + 1) C
+    const int32_t *list;        // walls of this launch (one warp each)
+    int32_t n_list;
+    // Per wall, at ckpt + ck_off / seg + seg_off, with Ns = Nmax (shared-memory kernel, node-major) or
+    // kt x 32 (register kernel, slot-major: slot i of lane l at i * 32 + l):
+    real *ckpt;                 // [n_seg][4][Ns]: T(n-1), T(n), P(n-1), P(n) at n = c C
+    real *seg;                  // [C + 2][2][Ns]: T, P of levels c C - 1 .. (c + 1) C
     double *loss;               // [W]
     double *grad;               // [sum layers][9]
     int32_t *nonfinite;
@@ -376,14 +382,14 @@ __device__ __forceinline__ void adj_reverse_b(AdjWarp<real> &x)
 //   A-law = dx cM0 (1 + b r) / (2 dt):   dL/dcM0 = dx (S2 + b S3) / (2 dt), dL/db = dx cM0 S3 / (2 dt)
 //   kTT and cTT likewise (S4, S5; S6, S7); chi: S8.
 template <typename real>
-__device__ __forceinline__ void adj_fold(AdjWarp<real> &x, const AdjWall &aw)
+__device__ __forceinline__ void adj_fold(const AdjDev<real> &d, const AdjWall &aw, int lay, KSum<real> (&acc)[9])
 {
-    if (x.lay >= 0) {
-        const real *p = x.d->phys + (size_t)(aw.layer_off + x.lay) * 9;
-        double *g = x.d->grad + (size_t)(aw.layer_off + x.lay) * 9;
-        const double dx = aw.dx, dt = x.d->dt;
+    if (lay >= 0) {
+        const real *p = d.phys + (size_t)(aw.layer_off + lay) * 9;
+        double *g = d.grad + (size_t)(aw.layer_off + lay) * 9;
+        const double dx = aw.dx, dt = d.dt;
         double s[9];
-        for (int k = 0; k < 9; ++k) s[k] = (double)x.acc[k].value();
+        for (int k = 0; k < 9; ++k) s[k] = (double)acc[k].value();
         const double kM0 = p[0], a = p[1], cM0 = p[2], b = p[3], kTT0 = p[4], aT = p[5], cTT0 = p[6], bT = p[7];
         atomicAdd(g + 0, (s[0] + a * s[1]) / (2.0 * dx));
         atomicAdd(g + 1, kM0 * s[1] / (2.0 * dx));
@@ -395,7 +401,7 @@ __device__ __forceinline__ void adj_fold(AdjWarp<real> &x, const AdjWall &aw)
         atomicAdd(g + 7, dx * cTT0 * s[7] / (2.0 * dt));
         atomicAdd(g + 8, s[8]);
     }
-    for (int k = 0; k < 9; ++k) x.acc[k].s = x.acc[k].c = real(0);
+    for (int k = 0; k < 9; ++k) acc[k].s = acc[k].c = real(0);
 }
 
 template <typename real>
@@ -403,8 +409,9 @@ __global__ void __launch_bounds__(32 * kAdjWarps) adjoint_kernel(const AdjDev<re
 {
     extern __shared__ __align__(16) unsigned char adj_smem[];
     const int wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int w = blockIdx.x * (blockDim.x >> 5) + wib;
-    if (w >= d.W) return;   // the whole warp
+    const int wi = blockIdx.x * (blockDim.x >> 5) + wib;
+    if (wi >= d.n_list) return;   // the whole warp
+    const int w = d.list[wi];
     const AdjWall &aw = d.walls[w];
     AdjWarp<real> x;
     x.d = &d;
@@ -461,8 +468,8 @@ __global__ void __launch_bounds__(32 * kAdjWarps) adjoint_kernel(const AdjDev<re
     const real Tr = d.Tref[w];
     for (int k = 0; k < 9; ++k) x.acc[k].s = x.acc[k].c = real(0);
     const int N = x.N, Nm = d.Nmax;
-    real *ck = d.ckpt + (size_t)w * d.n_seg * 4 * Nm;
-    real *sg = d.seg + (size_t)w * (d.C + 2) * 2 * Nm;
+    real *ck = d.ckpt + aw.ck_off;
+    real *sg = d.seg + aw.seg_off;
 
     // 1. forward from the uniform initial state (zero deviations; level -1 := level 0)
     x.lp = 0;
@@ -605,7 +612,7 @@ __global__ void __launch_bounds__(32 * kAdjWarps) adjoint_kernel(const AdjDev<re
                 __syncwarp();
             }
         }
-        adj_fold(x, aw);
+        adj_fold(d, aw, x.lay, x.acc);
     }
     for (int j = x.s0; j < x.s1; ++j) bad |= !isfinite(x.AT(x.al)[j]) || !isfinite(x.AP(x.al)[j]);
     if (bad) atomicExch(d.nonfinite, 1);

@@ -8,10 +8,11 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "hygro_internal.cuh"
-#include "adjoint.cuh"
+#include "adjoint_reg.cuh"
 
 using namespace hygro;
 
@@ -488,14 +489,15 @@ hygro_status build_schedule(hygro_ctx *c)
         const int R = std::max(1, std::min(wpb, Wf / G));
         c->round_size = R;
         // code variant (as in the kernel) and time per step of a wall with K nodes per lane when an SM
-        // is shared by its full warp count, a + b K (nanoseconds, measured on GB300 with a wall trace)
+        // is shared by its full warp count, a + b K (nanoseconds, measured on GB300 with a wall trace at
+        // 16 warps per SM for variants 0 and 3; variants 1 and 2 scaled from an earlier 12-warp trace)
         auto kind_of = [&](const WallInfo &x) {
             const bool simple = x.simple && c->precision == HYGRO_FP32;
             return x.aligned ? (simple ? 0 : 1) : (simple ? 3 : 2);
         };
         auto cost = [&](const WallInfo &x) {
-            static const double a[4] = {162.0, 190.0, 127.0, 199.0};
-            static const double b[4] = {41.3, 62.0, 102.0, 61.7};
+            static const double a[4] = {107.0, 234.0, 156.0, 191.0};
+            static const double b[4] = {64.2, 76.0, 125.0, 77.2};
             const int k = kind_of(x);
             return a[k] + b[k] * x.K;
         };
@@ -1363,18 +1365,15 @@ hygro_status hygro_loss_grad(hygro_ctx *c, int64_t n_steps, int32_t sample_every
     if (n_seg > INT32_MAX) return fail(c, HYGRO_E_UNSUPPORTED, "too many checkpoints");
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
     const int W = c->W;
-    int Nmax = 0;
-    for (int w = 0; w < W; ++w) Nmax = std::max(Nmax, c->N[w]);
     const size_t rs = c->real_size;
-    const size_t per_warp =
-        c->precision == HYGRO_FP64 ? adj_smem_per_warp<double>(Nmax) : adj_smem_per_warp<float>(Nmax);
-    int optin = 0;
-    CUDA_TRY(c, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
-    const int warps = (int)std::min<size_t>((size_t)kAdjWarps, (size_t)optin / per_warp);
-    if (warps < 1) return fail(c, HYGRO_E_UNSUPPORTED, "walls of %d nodes need more shared memory than a block has", Nmax);
-    // lane layout: contiguous runs of nodes, one layer per lane (the smallest run length that fits 32 lanes)
+    const bool f64 = c->precision == HYGRO_FP64;
+    const int maxk = f64 ? adj_reg_max_k<double>() : adj_reg_max_k<float>();
+    // lane layout: contiguous runs of nodes, one layer per lane (the smallest run length that fits 32
+    // lanes). Runs up to maxk nodes take the register kernel, longer ones the shared-memory kernel.
     std::vector<AdjWall> aw(W);
+    std::vector<int32_t> reg_list, sm_list;
     size_t lo = 0;
+    int Nmax_sm = 0;
     for (int w = 0; w < W; ++w) {
         AdjWall &a = aw[w];
         memset(&a, 0, sizeof a);
@@ -1411,7 +1410,36 @@ hygro_status hygro_loss_grad(hygro_ctx *c, int64_t n_steps, int32_t sample_every
             a.layer[lane] = -1;
         }
         a.start[32] = (int16_t)a.N;
+        a.kt = K <= maxk ? adj_reg_slots(K) : 0;
+        if (a.kt > 0) {
+            reg_list.push_back(w);
+        } else {
+            sm_list.push_back(w);
+            Nmax_sm = std::max(Nmax_sm, a.N);
+        }
         lo += c->n_layers[w];
+    }
+    // checkpoint and segment storage of each wall: node-major (Nmax_sm nodes) for the shared-memory
+    // kernel, slot-major (kt x 32 slots) for the register kernel
+    size_t ck_total = 0, seg_total = 0;
+    for (int w = 0; w < W; ++w) {
+        AdjWall &a = aw[w];
+        const size_t ns = a.kt > 0 ? (size_t)a.kt * 32 : (size_t)Nmax_sm;
+        a.ck_off = (int64_t)ck_total;
+        a.seg_off = (int64_t)seg_total;
+        ck_total += (size_t)n_seg * 4 * ns;
+        seg_total += (size_t)(C + 2) * 2 * ns;
+    }
+    // heavier walls first (more slots per lane), so the block scheduler starts them early
+    std::stable_sort(reg_list.begin(), reg_list.end(), [&](int x, int y) { return aw[x].kt > aw[y].kt; });
+    int warps = 0;
+    if (!sm_list.empty()) {
+        const size_t per_warp = f64 ? adj_smem_per_warp<double>(Nmax_sm) : adj_smem_per_warp<float>(Nmax_sm);
+        int optin = 0;
+        CUDA_TRY(c, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->device));
+        warps = (int)std::min<size_t>((size_t)kAdjWarps, (size_t)optin / per_warp);
+        if (warps < 1)
+            return fail(c, HYGRO_E_UNSUPPORTED, "walls of %d nodes need more shared memory than a block has", Nmax_sm);
     }
     const size_t total_layers = lo;
     // physical laws of every layer, in the working precision
@@ -1421,11 +1449,11 @@ hygro_status hygro_loss_grad(hygro_ctx *c, int64_t n_steps, int32_t sample_every
         const double v[9] = {y.kM0, y.a, y.cM0, y.b, y.kTT0, y.aT, y.cTT0, y.bT, y.chi};
         for (int k = 0; k < 9; ++k) phys[l * 9 + k] = v[k];
     }
-    void *d_aw = nullptr, *d_phys = nullptr, *d_obs = nullptr, *d_ck = nullptr, *d_sg = nullptr;
+    void *d_aw = nullptr, *d_phys = nullptr, *d_obs = nullptr, *d_ck = nullptr, *d_sg = nullptr, *d_list = nullptr;
     double *d_loss = nullptr, *d_grad = nullptr;
     hygro_status st = HYGRO_OK;
     auto release = [&]() {
-        void *ps[] = {d_aw, d_phys, d_obs, d_ck, d_sg, d_loss, d_grad};
+        void *ps[] = {d_aw, d_phys, d_obs, d_ck, d_sg, d_list, d_loss, d_grad};
         for (void *q : ps)
             if (q) cudaFree(q);
     };
@@ -1442,6 +1470,10 @@ hygro_status hygro_loss_grad(hygro_ctx *c, int64_t n_steps, int32_t sample_every
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     ADJ_TRY(cudaMalloc(&d_aw, W * sizeof(AdjWall)));
     ADJ_TRY(cudaMemcpy(d_aw, aw.data(), W * sizeof(AdjWall), cudaMemcpyHostToDevice));
+    std::vector<int32_t> lists(reg_list);
+    lists.insert(lists.end(), sm_list.begin(), sm_list.end());
+    ADJ_TRY(cudaMalloc(&d_list, lists.size() * sizeof(int32_t)));
+    ADJ_TRY(cudaMemcpy(d_list, lists.data(), lists.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     ADJ_TRY(cudaMalloc(&d_phys, std::max<size_t>(1, phys.size()) * rs));
     if ((st = upload_reals(c, d_phys, phys)) != HYGRO_OK) {
         release();
@@ -1456,22 +1488,21 @@ hygro_status hygro_loss_grad(hygro_ctx *c, int64_t n_steps, int32_t sample_every
             ADJ_TRY(cudaMemcpy(d_obs, obs, obs_n * sizeof(float), cudaMemcpyHostToDevice));
         }
     }
-    ADJ_TRY(cudaMalloc(&d_ck, (size_t)W * n_seg * 4 * Nmax * rs));
-    ADJ_TRY(cudaMalloc(&d_sg, (size_t)W * (C + 2) * 2 * Nmax * rs));
+    ADJ_TRY(cudaMalloc(&d_ck, std::max<size_t>(1, ck_total) * rs));
+    ADJ_TRY(cudaMalloc(&d_sg, std::max<size_t>(1, seg_total) * rs));
     ADJ_TRY(cudaMalloc(&d_loss, W * sizeof(double)));
     ADJ_TRY(cudaMalloc(&d_grad, std::max<size_t>(1, total_layers * 9) * sizeof(double)));
     ADJ_TRY(cudaMemsetAsync(d_grad, 0, std::max<size_t>(1, total_layers * 9) * sizeof(double), c->stream));
-    cudaError_t le;
-    if (c->precision == HYGRO_FP64) {
-        AdjDev<double> d;
+    auto fill = [&](auto &d) {
+        using real = typename std::remove_pointer<decltype(d.ckpt)>::type;
         d.walls = (const AdjWall *)d_aw;
         d.W = W;
-        d.Nmax = Nmax;
+        d.Nmax = Nmax_sm;
         d.faces = c->d_faces;
-        d.layer_tab = (const double *)c->d_layer_tab;
-        d.phys = (const double *)d_phys;
-        d.Pref = (const double *)c->d_Pref;
-        d.Tref = (const double *)c->d_Tref;
+        d.layer_tab = (const real *)c->d_layer_tab;
+        d.phys = (const real *)d_phys;
+        d.Pref = (const real *)c->d_Pref;
+        d.Tref = (const real *)c->d_Tref;
         d.noise = c->d_noise;
         d.obs = K > 0 ? (d_obs ? (const float *)d_obs : obs) : nullptr;
         d.wT = wT;
@@ -1481,8 +1512,8 @@ hygro_status hygro_loss_grad(hygro_ctx *c, int64_t n_steps, int32_t sample_every
         d.n_steps = n_steps;
         d.C = (int32_t)C;
         d.n_seg = (int32_t)n_seg;
-        d.ckpt = (double *)d_ck;
-        d.seg = (double *)d_sg;
+        d.ckpt = (real *)d_ck;
+        d.seg = (real *)d_sg;
         d.loss = d_loss;
         d.grad = d_grad;
         d.nonfinite = c->d_nonfinite;
@@ -1490,36 +1521,26 @@ hygro_status hygro_loss_grad(hygro_ctx *c, int64_t n_steps, int32_t sample_every
         d.t0 = c->t0;
         d.Lv = c->Lv;
         d.Psat = c->Psat;
-        le = launch_adjoint_f64(d, warps, c->stream);
+    };
+    cudaError_t le = cudaSuccess;
+    if (f64) {
+        AdjDev<double> d;
+        fill(d);
+        d.list = (const int32_t *)d_list;
+        d.n_list = (int32_t)reg_list.size();
+        le = launch_adjoint_reg_f64(d, c->stream);
+        d.list = (const int32_t *)d_list + reg_list.size();
+        d.n_list = (int32_t)sm_list.size();
+        if (le == cudaSuccess && d.n_list > 0) le = launch_adjoint_f64(d, warps, c->stream);
     } else {
         AdjDev<float> d;
-        d.walls = (const AdjWall *)d_aw;
-        d.W = W;
-        d.Nmax = Nmax;
-        d.faces = c->d_faces;
-        d.layer_tab = (const float *)c->d_layer_tab;
-        d.phys = (const float *)d_phys;
-        d.Pref = (const float *)c->d_Pref;
-        d.Tref = (const float *)c->d_Tref;
-        d.noise = c->d_noise;
-        d.obs = K > 0 ? (d_obs ? (const float *)d_obs : obs) : nullptr;
-        d.wT = wT;
-        d.wP = wP;
-        d.se = sample_every;
-        d.K = (int32_t)K;
-        d.n_steps = n_steps;
-        d.C = (int32_t)C;
-        d.n_seg = (int32_t)n_seg;
-        d.ckpt = (float *)d_ck;
-        d.seg = (float *)d_sg;
-        d.loss = d_loss;
-        d.grad = d_grad;
-        d.nonfinite = c->d_nonfinite;
-        d.dt = c->dt;
-        d.t0 = c->t0;
-        d.Lv = c->Lv;
-        d.Psat = c->Psat;
-        le = launch_adjoint_f32(d, warps, c->stream);
+        fill(d);
+        d.list = (const int32_t *)d_list;
+        d.n_list = (int32_t)reg_list.size();
+        le = launch_adjoint_reg_f32(d, c->stream);
+        d.list = (const int32_t *)d_list + reg_list.size();
+        d.n_list = (int32_t)sm_list.size();
+        if (le == cudaSuccess && d.n_list > 0) le = launch_adjoint_f32(d, warps, c->stream);
     }
     ADJ_TRY(le);
     std::vector<double> lw(W);

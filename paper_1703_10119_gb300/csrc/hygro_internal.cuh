@@ -19,11 +19,13 @@ namespace hygro {
 constexpr int kMaxLayers = HYGRO_MAX_LAYERS;
 constexpr int kLayerStride = 12;   // reals per layer entry of a wall (9 used, padded)
 constexpr int kMaxK = 16;          // nodes per lane of the persistent kernel
-// Persistent kernel: one wall per warp; warps per block by precision (register budget:
-// FP32 fits 12 warps per SM without spills, FP64 needs the 255-register budget of 8 warps).
+// Persistent kernel: one wall per warp; warps per block by precision. FP32 runs 16 warps (four per SM
+// sub-partition, 128 registers): the variants with many nodes per lane spill a little, but the extra
+// warps hide more latency than 12 warps at 168 registers (measured on the yearly batch). FP64 needs
+// the 255-register budget of 8 warps.
 template <typename real>
 struct PersistCfg {
-    static constexpr int warps = sizeof(real) == 4 ? 12 : 8;
+    static constexpr int warps = sizeof(real) == 4 ? 16 : 8;
 };
 // Dynamic shared memory of the persistent kernel per warp (in reals): layer table, then two per-slot
 // tables of 32 lanes x kMaxK slots.
@@ -139,6 +141,8 @@ template <typename real>
 struct AdjDev;
 cudaError_t launch_adjoint_f32(const AdjDev<float> &d, int warps, cudaStream_t s);
 cudaError_t launch_adjoint_f64(const AdjDev<double> &d, int warps, cudaStream_t s);
+cudaError_t launch_adjoint_reg_f32(const AdjDev<float> &d, cudaStream_t s);
+cudaError_t launch_adjoint_reg_f64(const AdjDev<double> &d, cudaStream_t s);
 
 cudaError_t launch_balance_f32(const DevCtx<float> &d, const float *Tp, const float *Pp, const float *Tn,
                                const float *Pn, int64_t n, double *bal, cudaStream_t s);
