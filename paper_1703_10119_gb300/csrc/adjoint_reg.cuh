@@ -572,42 +572,33 @@ __device__ __noinline__ void adj_reg_wall(const AdjDev<real> &d, const int w, re
         reg_load(Pp, sg + (size_t)(end - start - 1) * lev + KT * 32, lane);
         reg_load(Tc, sg + (size_t)(end - start) * lev, lane);
         reg_load(Pc, sg + (size_t)(end - start) * lev + KT * 32, lane);
-        // rstep(n, p, c, l, m): p = level n-1, c = level n (replaced by level n-2), l = complete adjoint of
-        // level n+1 (replaced by the partial adjoint of level n-1), m = partial adjoint of level n (completed)
-        auto rstep = [&](int64_t n, real (&pT)[KT], real (&pP)[KT], real (&cT)[KT], real (&cP)[KT], real (&lT)[KT],
-                         real (&lP)[KT], real (&mT)[KT], real (&mP)[KT]) {
-            const bool more = n > start;
+        // reverse step n: (Tp, Pp) = level n-1, (Tc, Pc) = level n, (LT, LP) = complete adjoint of level
+        // n+1, (MT, MP) = partial adjoint of level n. The loop is not unrolled (its body is the largest code
+        // of the kernel: two copies of it missed in the instruction cache); the sets rotate by copies.
+        for (int64_t n = end - 1; n >= start; --n) {
+            // level n-2 (slot n-1-start), loaded ahead; at n = start it is not needed (slot 0 is read)
             real xT[KT], xP[KT];
-            if (more) {
-                const real *s2 = sg + (size_t)(n - 1 - start) * lev;
+            {
+                const real *s2 = sg + (size_t)(n - 1 - start > 0 ? n - 1 - start : 0) * lev;
                 reg_load(xT, s2, lane);
                 reg_load(xP, s2 + KT * 32, lane);
             }
-            direct(n, cT, cP, mT, mP);
+            direct(n, Tc, Pc, MT, MP);
             reg_air(d, f0, f1, air, chunk, n, lane);
             RegSums<real> gs;
-            reg_reverse(L, pT, pP, cT, cP, lT, lP, mT, mP, air + (n % kAdjAirChunk) * 4, gs);
+            reg_reverse(L, Tp, Pp, Tc, Pc, LT, LP, MT, MP, air + (n % kAdjAirChunk) * 4, gs);
 #pragma unroll
             for (int k = 0; k < 9; ++k) acc[k].add(gs.s[k]);
-            if (more) {
+            // levels move down one; the completed adjoint of level n becomes the complete one
 #pragma unroll
-                for (int i = 0; i < KT; ++i) {
-                    cT[i] = xT[i];
-                    cP[i] = xP[i];
-                }
+            for (int i = 0; i < KT; ++i) {
+                Tc[i] = Tp[i];
+                Pc[i] = Pp[i];
+                Tp[i] = xT[i];
+                Pp[i] = xP[i];
             }
-        };
-        {
-            int64_t n = end - 1;
-            for (; n - 1 >= start; n -= 2) {
-                rstep(n, Tp, Pp, Tc, Pc, LT, LP, MT, MP);
-                rstep(n - 1, Tc, Pc, Tp, Pp, MT, MP, LT, LP);
-            }
-            if (n >= start) {
-                rstep(n, Tp, Pp, Tc, Pc, LT, LP, MT, MP);
-                reg_swap(LT, MT);
-                reg_swap(LP, MP);
-            }
+            reg_swap(LT, MT);
+            reg_swap(LP, MP);
         }
         adj_fold(d, aw, L.lay, acc);
         __syncwarp();
