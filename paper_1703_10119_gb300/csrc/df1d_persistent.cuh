@@ -50,6 +50,7 @@ struct LaneCtx {
     // simple-heat walls (kTT, cTT independent of Pv and cTM = 0 in every layer): the thermal faces and the
     // T denominators do not change in time and are set up once per wall
     real FTin;                // in-lane thermal face kTT / dx (one layer per lane)
+    real m2FTin;              // -2 FTin
     real FTl0c, FTbc;         // thermal faces at the left / right lane boundary (0 at wall ends)
     real rT0, rTm, rTK2, rTK1; // 1 / T denominator of slot 0, interior slots, slot K-2, slot K-1
 };
@@ -182,23 +183,30 @@ __device__ __forceinline__ void df_step(real (&Tp)[K], const real (&Tc)[K], real
             }
         }
 
-        // vapour pressure: num = sum_f F (P_nb - P^{n-1}), S = sum_f F, the surface faces being the
-        // Robin exchanges with the ambient air as neighbour
+        // vapour pressure: num = sum_f F (P_nb - P^{n-1}) = sum_f F P_nb - S P^{n-1}, S = sum_f F, the
+        // surface faces being the Robin exchanges with the ambient air as neighbour
         const real pp = Pp[k];
-        real numP = fma(FMl, Pl - pp, FMr * (Pr - pp));
         const real S = FMl + FMr;
-        real gsrc = real(0);
-        if (k == 0) gsrc = L.g0;
-        if (k == K - 1) gsrc += L.g1;
-        const real dP = fast_div(numP + gsrc, fma(half, S, A));
+        const real numP = fma(FMl, Pl, fma(FMr, Pr, -S * pp));
+        real numPg = numP;   // + the surface source, on the surface slots only
+        if (k == 0) numPg += L.g0;
+        if (k == K - 1) numPg += L.g1;
+        const real dP = fast_div(numPg, fma(half, S, A));
         // latent cross flux sum_f F (P_nb - Pbar) [+ hM (Pinf - Pbar)] = num - S dP / 2
         const real hdP = half * dP;
         const real X = fma(-S, hdP, numP);
 
-        // temperature: conduction, Lv x cross flux, cTM storage
+        // temperature: conduction, Lv x cross flux, cTM storage. Inside a lane of a simple-heat wall
+        // without interfaces both thermal faces are FTin: FTin (T_l + T_r) - 2 FTin T^{n-1}.
         const real tp = Tp[k];
-        real numT = fma(FTl, Tl - tp, FTr * (Tr - tp));
         const real ST = SIMPLE ? real(0) : FTl + FTr;
+        real numT;
+        if (SIMPLE && !IFACE && k >= 1 && k + 2 < K)
+            numT = fma(L.m2FTin, tp, L.FTin * (Tl + Tr));
+        else if (SIMPLE)
+            numT = fma(FTl, Tl - tp, FTr * (Tr - tp));
+        else
+            numT = fma(FTl, Tl, fma(FTr, Tr, -ST * tp));
         if (k == 0) numT += L.q0;
         if (k == K - 1) numT += L.q1;
         numT = fma(Lv, X, numT);
@@ -384,7 +392,7 @@ __device__ __forceinline__ void lane_setup(const DevCtx<real> &d, const WallInfo
     L.gs = L.g0 + L.g1;
     const real Lv = (real)d.Lv;
     const real Tref = d.Tref[w], Pref = d.Pref[w];
-    L.FTin = L.FTl0c = L.FTbc = real(0);
+    L.FTin = L.m2FTin = L.FTl0c = L.FTbc = real(0);
     L.rT0 = L.rTm = L.rTK2 = L.rTK1 = real(1);
     if (SIMPLE) {
         // constant thermal faces and T denominators B w + (F_left + F_right + hT) / 2
@@ -397,6 +405,7 @@ __device__ __forceinline__ void lane_setup(const DevCtx<real> &d, const WallInfo
         real Fl = __shfl_up_sync(FULL, Fb, 1);
         Fl = L.has_left ? Fl : real(0);
         L.FTin = real(2) * khf;
+        L.m2FTin = real(-2) * L.FTin;
         L.FTl0c = L.has_left ? Fl : L.hT0;    // the face-0 Robin exchange as the left face of lane 0
         L.FTbc = L.has_right ? Fb : L.hT1;    // the face-1 Robin exchange as the right face of lane Wl-1
         if (!IFACE) {
