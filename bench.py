@@ -78,6 +78,8 @@ def parse():
     p.add_argument("--only-2d", action="store_true", help="run only the 2D sections (profiling cases)")
     p.add_argument("--sections", type=int, default=64, help="2D sections of 512 x 512")
     p.add_argument("--section-steps", type=int, default=10000)
+    p.add_argument("--only-adjoint", action="store_true", help="run only the gradient workload (profiling cases)")
+    p.add_argument("--adjoint-steps", type=int, default=43200, help="steps of the gradient workload")
     return p.parse_args()
 
 
@@ -308,12 +310,12 @@ def bench_adjoint(args, H, wk, stream, local, rank):
     sqrt(T) checkpoints), observations resident on the device; parity on sampled walls vs the oracle."""
     import torch
 
-    wl, s = wk.config5(seed=5 + rank)
+    wl, s = wk.config5(seed=5 + rank, n_steps=args.adjoint_steps)
     dev = torch.device("cuda", local)
     obs = torch.from_numpy(s.obs).to(dev)
     grad = torch.zeros((len(wl.layer_par), 9), dtype=torch.float64, device=dev)
     h = H.Hygro(wl, precision="fp32", device=local, stream=stream.cuda_stream)
-    H.hygro_loss_grad(h.ctx, 600, s.sample_every, obs, s.wT, s.wP, 0, grad)   # warm-up (short run)
+    H.hygro_loss_grad(h.ctx, min(600, wl.n_steps), s.sample_every, obs, s.wT, s.wP, 0, grad)   # warm-up (short run)
     torch.cuda.synchronize()
     t = time.perf_counter()
     with torch.cuda.stream(stream):
@@ -379,6 +381,11 @@ def bench_ours(args):
         out = bench_sections(args, H, wk, stream, local, rank)
         if rank == 0:
             print(json.dumps({"metric": METRIC, "unit": UNIT, "only": "2d sections", **out}))
+        return
+    if args.only_adjoint:
+        out = bench_adjoint(args, H, wk, stream, local, rank)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "unit": UNIT, "only": "gradient workload", **out}))
         return
     wl = wk.config2(seed=2 + rank, n_walls=args.walls, n_steps=args.year_steps)
     units_per_run = wl.total_nodes * args.year_steps
