@@ -463,12 +463,12 @@ __device__ __noinline__ void adj_reg_wall(const AdjDev<real> &d, const int w, re
 #pragma unroll
     for (int i = 0; i < KT; ++i) Tp[i] = Pp[i] = Tc[i] = Pc[i] = real(0);
 
-    // surface values of a new level against the observations (FP64 misfit)
+    // the misfit of sample k (FP64) from the surface values of its level
     double loss = 0.0;
     bool bad = false;
-    auto misfit = [&](int64_t levn, const real (&T)[KT], const real (&P)[KT]) {
-        if (levn < 1 || levn % d.se != 0 || levn / d.se > d.K) return;
-        const int64_t k = levn / d.se - 1;
+    const int se = d.se;
+    const int64_t Ks = d.K;
+    auto misfit = [&](int64_t k, const real (&T)[KT], const real (&P)[KT]) {
         const float *o = d.obs + ((size_t)k * d.W + w) * 4;
         if (L.lsurf && L.nl > 0) {
             const double eT = (double)T[0] + (double)L.Tr - (double)o[0];
@@ -484,10 +484,8 @@ __device__ __noinline__ void adj_reg_wall(const AdjDev<real> &d, const int w, re
             bad |= !isfinite(eT) || !isfinite(eP);
         }
     };
-    // the misfit's gradient at level levn, added to the adjoint (aT, aP) of that level
-    auto direct = [&](int64_t levn, const real (&T)[KT], const real (&P)[KT], real (&aT)[KT], real (&aP)[KT]) {
-        if (levn < 1 || levn % d.se != 0 || levn / d.se > d.K) return;
-        const int64_t k = levn / d.se - 1;
+    // the misfit's gradient of sample k, added to the adjoint (aT, aP) of its level
+    auto direct = [&](int64_t k, const real (&T)[KT], const real (&P)[KT], real (&aT)[KT], real (&aP)[KT]) {
         const float *o = d.obs + ((size_t)k * d.W + w) * 4;
         if (L.lsurf && L.nl > 0) {
             aT[0] += (real)(2.0 * d.wT * ((double)T[0] + (double)L.Tr - (double)o[0]));
@@ -500,28 +498,48 @@ __device__ __noinline__ void adj_reg_wall(const AdjDev<real> &d, const int w, re
         }
     };
 
-    // 1. forward from the uniform initial state (zero deviations; level -1 := level 0): checkpoints and
-    //    the misfit. fstep(n, a, b): a = level n-1 becomes level n+1, b = level n.
-    auto fstep1 = [&](int64_t n, real (&aT)[KT], real (&aP)[KT], real (&bT)[KT], real (&bP)[KT]) {
-        if (n % C == 0) {
-            real *c4 = ck + (size_t)(n / C) * 2 * lev;
-            reg_store(c4, aT, lane);
-            reg_store(c4 + KT * 32, bT, lane);
-            reg_store(c4 + 2 * KT * 32, aP, lane);
-            reg_store(c4 + 3 * KT * 32, bP, lane);
+    // Forward steps [n0, n1) from (Tp, Pp) = level n0-1, (Tc, Pc) = level n0, which end as levels n1-1, n1.
+    // With store = false (the first run, n0 = 0): checkpoints every C steps and the misfit; with store:
+    // each new level goes to the segment buffer (slot s = level start-1+s). One rolled loop serves both
+    // (the kernel's speed follows its code size: the hot loops must stay in the instruction cache);
+    // step positions are tracked by counters (no 64-bit division in the loop).
+    auto forward = [&](int64_t n0, int64_t n1, bool store, int64_t start) {
+        int cc = 0;            // steps to the next checkpoint (the first run starts on one)
+        int64_t ci = 0;        // next checkpoint
+        int sc = se;           // steps until the new level is a sample level
+        int64_t k = 0;         // next sample
+        real *s2 = sg + (size_t)(n0 + 1 - start + 1) * lev;
+        for (int64_t n = n0; n < n1; ++n) {
+            if (!store) {
+                if (cc == 0) {
+                    real *c4 = ck + (size_t)ci * 2 * lev;
+                    reg_store(c4, Tp, lane);
+                    reg_store(c4 + KT * 32, Tc, lane);
+                    reg_store(c4 + 2 * KT * 32, Pp, lane);
+                    reg_store(c4 + 3 * KT * 32, Pc, lane);
+                    ++ci;
+                    cc = C;
+                }
+                --cc;
+            }
+            reg_air(d, f0, f1, air, chunk, n, lane);
+            reg_forward(L, Tp, Pp, Tc, Pc, air + (int)(n & (kAdjAirChunk - 1)) * 4);
+            if (store) {
+                reg_store(s2, Tp, lane);
+                reg_store(s2 + KT * 32, Pp, lane);
+                s2 += lev;
+            } else if (--sc == 0) {
+                sc = se;
+                if (k < Ks) misfit(k, Tp, Pp);
+                ++k;
+            }
+            reg_swap(Tp, Tc);
+            reg_swap(Pp, Pc);
         }
-        reg_air(d, f0, f1, air, chunk, n, lane);
-        reg_forward(L, aT, aP, bT, bP, air + (n % kAdjAirChunk) * 4);
-        misfit(n + 1, aT, aP);
     };
-    {
-        int64_t n = 0;
-        for (; n + 1 < d.n_steps; n += 2) {
-            fstep1(n, Tp, Pp, Tc, Pc);
-            fstep1(n + 1, Tc, Pc, Tp, Pp);
-        }
-        if (n < d.n_steps) fstep1(n, Tp, Pp, Tc, Pc);
-    }
+
+    // 1. forward from the uniform initial state (zero deviations; level -1 := level 0)
+    forward(0, d.n_steps, false, 0);
     for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
     if (lane == 0) d.loss[w] = loss;
 
@@ -532,7 +550,7 @@ __device__ __noinline__ void adj_reg_wall(const AdjDev<real> &d, const int w, re
     for (int c = d.n_seg - 1; c >= 0; --c) {
         const int64_t start = (int64_t)c * C;
         const int64_t end = start + C < d.n_steps ? start + C : d.n_steps;
-        // recompute the segment's levels start + 1 .. end into the segment buffer (slot s = level start-1+s)
+        // recompute the segment's levels start + 1 .. end into the segment buffer
         {
             const real *c4 = ck + (size_t)c * 2 * lev;
             reg_load(Tp, c4, lane);
@@ -544,28 +562,17 @@ __device__ __noinline__ void adj_reg_wall(const AdjDev<real> &d, const int w, re
             reg_store(sg + lev, Tc, lane);
             reg_store(sg + lev + KT * 32, Pc, lane);
         }
-        auto fstep2 = [&](int64_t n, real (&aT)[KT], real (&aP)[KT], real (&bT)[KT], real (&bP)[KT]) {
-            reg_air(d, f0, f1, air, chunk, n, lane);
-            reg_forward(L, aT, aP, bT, bP, air + (n % kAdjAirChunk) * 4);
-            real *s2 = sg + (size_t)(n + 1 - start + 1) * lev;
-            reg_store(s2, aT, lane);
-            reg_store(s2 + KT * 32, aP, lane);
-        };
-        {
-            int64_t n = start;
-            for (; n + 1 < end; n += 2) {
-                fstep2(n, Tp, Pp, Tc, Pc);
-                fstep2(n + 1, Tc, Pc, Tp, Pp);
-            }
-            if (n < end) fstep2(n, Tp, Pp, Tc, Pc);
-        }
+        forward(start, end, true, start);
         __syncwarp();
+        // sample position of level end: end = kk se + rr
+        int64_t kk = end / se;
+        int rr = (int)(end - kk * se);
         // the last level's misfit gradient (level n_steps, only in the last segment)
         if (c == d.n_seg - 1) {
             const real *s2 = sg + (size_t)(end - start + 1) * lev;
             reg_load(Tc, s2, lane);
             reg_load(Pc, s2 + KT * 32, lane);
-            direct(end, Tc, Pc, LT, LP);
+            if (rr == 0 && kk >= 1 && kk <= Ks) direct(kk - 1, Tc, Pc, LT, LP);
         }
         // levels end-2 (slot end-start-1) and end-1 (slot end-start)
         reg_load(Tp, sg + (size_t)(end - start - 1) * lev, lane);
@@ -573,20 +580,31 @@ __device__ __noinline__ void adj_reg_wall(const AdjDev<real> &d, const int w, re
         reg_load(Tc, sg + (size_t)(end - start) * lev, lane);
         reg_load(Pc, sg + (size_t)(end - start) * lev + KT * 32, lane);
         // reverse step n: (Tp, Pp) = level n-1, (Tc, Pc) = level n, (LT, LP) = complete adjoint of level
-        // n+1, (MT, MP) = partial adjoint of level n. The loop is not unrolled (its body is the largest code
-        // of the kernel: two copies of it missed in the instruction cache); the sets rotate by copies.
+        // n+1, (MT, MP) = partial adjoint of level n. The loop is not unrolled; the sets rotate by copies.
+        if (rr == 0) {   // position of level end - 1
+            rr = se - 1;
+            --kk;
+        } else {
+            --rr;
+        }
         for (int64_t n = end - 1; n >= start; --n) {
             // level n-2 (slot n-1-start), loaded ahead; at n = start it is not needed (slot 0 is read)
             real xT[KT], xP[KT];
             {
-                const real *s2 = sg + (size_t)(n - 1 - start > 0 ? n - 1 - start : 0) * lev;
-                reg_load(xT, s2, lane);
-                reg_load(xP, s2 + KT * 32, lane);
+                const real *sx = sg + (size_t)(n > start ? n - 1 - start : 0) * lev;
+                reg_load(xT, sx, lane);
+                reg_load(xP, sx + KT * 32, lane);
             }
-            direct(n, Tc, Pc, MT, MP);
+            if (rr == 0 && kk >= 1 && kk <= Ks) direct(kk - 1, Tc, Pc, MT, MP);
+            if (rr == 0) {
+                rr = se - 1;
+                --kk;
+            } else {
+                --rr;
+            }
             reg_air(d, f0, f1, air, chunk, n, lane);
             RegSums<real> gs;
-            reg_reverse(L, Tp, Pp, Tc, Pc, LT, LP, MT, MP, air + (n % kAdjAirChunk) * 4, gs);
+            reg_reverse(L, Tp, Pp, Tc, Pc, LT, LP, MT, MP, air + (int)(n & (kAdjAirChunk - 1)) * 4, gs);
 #pragma unroll
             for (int k = 0; k < 9; ++k) acc[k].add(gs.s[k]);
             // levels move down one; the completed adjoint of level n becomes the complete one
