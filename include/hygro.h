@@ -274,8 +274,12 @@ HYGRO_API hygro_status hygro_run_noalloc(hygro_ctx *ctx, int64_t n_steps, int32_
  * *loss (host) receives the loss, accumulated in FP64. grad (host or device memory, or NULL) receives
  * dloss/dtheta, [total layers][9] in the order of hygro_layer (kM0, a, cM0, b, kTT0, aT, cTT0, bT, chi),
  * accumulated in FP64. The forward saves (level n-1, level n) every checkpoint_every steps (0: about
- * sqrt(n_steps)), and the reverse recomputes each stretch from its checkpoint. Device memory for the
- * checkpoints is allocated by the call (walls x checkpoints x 4 x max N reals, plus a stretch of levels).
+ * sqrt(n_steps)), and the reverse recomputes each stretch from its checkpoint. With checkpoint_every >=
+ * n_steps the forward keeps every level instead and nothing is recomputed (faster, at about
+ * walls x 2 x (n_steps + 2) x 32 x slots-per-lane reals of device memory). Device memory for the
+ * checkpoints and the stretch levels is allocated by the call, per wall about (checkpoints x 4 +
+ * (stride + 2) x 2) x 32 x slots-per-lane reals (slots per lane: the longest lane run of the wall,
+ * about N / 32); HYGRO_E_NOMEM if it does not fit.
  * Walls with a room face are not supported (HYGRO_E_UNSUPPORTED). The arithmetic runs in the context's
  * precision. */
 HYGRO_API hygro_status hygro_loss_grad(hygro_ctx *ctx, int64_t n_steps, int32_t sample_every, const float *obs,

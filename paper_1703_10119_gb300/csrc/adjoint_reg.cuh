@@ -499,18 +499,19 @@ __device__ __noinline__ void adj_reg_wall(const AdjDev<real> &d, const int w, re
     };
 
     // Forward steps [n0, n1) from (Tp, Pp) = level n0-1, (Tc, Pc) = level n0, which end as levels n1-1, n1.
-    // With store = false (the first run, n0 = 0): checkpoints every C steps and the misfit; with store:
-    // each new level goes to the segment buffer (slot s = level start-1+s). One rolled loop serves both
-    // (the kernel's speed follows its code size: the hot loops must stay in the instruction cache);
-    // step positions are tracked by counters (no 64-bit division in the loop).
-    auto forward = [&](int64_t n0, int64_t n1, bool store, int64_t start) {
+    // first (the first run, n0 = 0): checkpoints every C steps and the misfit; store: each new level goes
+    // to the segment buffer (slot s = level start-1+s). Both at once when the run is a single segment:
+    // every level is stored by the first run and nothing is recomputed. One rolled loop serves all
+    // cases (the kernel's speed follows its code size: the hot loops must stay in the instruction
+    // cache); step positions are tracked by counters (no 64-bit division in the loop).
+    auto forward = [&](int64_t n0, int64_t n1, bool first, bool store, int64_t start) {
         int cc = 0;            // steps to the next checkpoint (the first run starts on one)
         int64_t ci = 0;        // next checkpoint
         int sc = se;           // steps until the new level is a sample level
         int64_t k = 0;         // next sample
         real *s2 = sg + (size_t)(n0 + 1 - start + 1) * lev;
         for (int64_t n = n0; n < n1; ++n) {
-            if (!store) {
+            if (first) {
                 if (cc == 0) {
                     real *c4 = ck + (size_t)ci * 2 * lev;
                     reg_store(c4, Tp, lane);
@@ -528,7 +529,8 @@ __device__ __noinline__ void adj_reg_wall(const AdjDev<real> &d, const int w, re
                 reg_store(s2, Tp, lane);
                 reg_store(s2 + KT * 32, Pp, lane);
                 s2 += lev;
-            } else if (--sc == 0) {
+            }
+            if (first && --sc == 0) {
                 sc = se;
                 if (k < Ks) misfit(k, Tp, Pp);
                 ++k;
@@ -539,7 +541,14 @@ __device__ __noinline__ void adj_reg_wall(const AdjDev<real> &d, const int w, re
     };
 
     // 1. forward from the uniform initial state (zero deviations; level -1 := level 0)
-    forward(0, d.n_steps, false, 0);
+    const bool single = d.n_seg == 1;
+    if (single) {
+        reg_store(sg, Tp, lane);
+        reg_store(sg + KT * 32, Pp, lane);
+        reg_store(sg + lev, Tc, lane);
+        reg_store(sg + lev + KT * 32, Pc, lane);
+    }
+    forward(0, d.n_steps, true, single, 0);
     for (int o = 16; o > 0; o >>= 1) loss += __shfl_xor_sync(0xffffffffu, loss, o);
     if (lane == 0) d.loss[w] = loss;
 
@@ -550,8 +559,9 @@ __device__ __noinline__ void adj_reg_wall(const AdjDev<real> &d, const int w, re
     for (int c = d.n_seg - 1; c >= 0; --c) {
         const int64_t start = (int64_t)c * C;
         const int64_t end = start + C < d.n_steps ? start + C : d.n_steps;
-        // recompute the segment's levels start + 1 .. end into the segment buffer
-        {
+        // recompute the segment's levels start + 1 .. end into the segment buffer (a single segment was
+        // stored by the first run)
+        if (!single) {
             const real *c4 = ck + (size_t)c * 2 * lev;
             reg_load(Tp, c4, lane);
             reg_load(Tc, c4 + KT * 32, lane);
@@ -561,8 +571,8 @@ __device__ __noinline__ void adj_reg_wall(const AdjDev<real> &d, const int w, re
             reg_store(sg + KT * 32, Pp, lane);
             reg_store(sg + lev, Tc, lane);
             reg_store(sg + lev + KT * 32, Pc, lane);
+            forward(start, end, false, true, start);
         }
-        forward(start, end, true, start);
         __syncwarp();
         // sample position of level end: end = kk se + rr
         int64_t kk = end / se;
