@@ -19,10 +19,13 @@
 namespace hygro {
 
 constexpr int kMaxRegions2D = 8;
-// Node flags byte: region in bits 0-2; bit 4 / 5 / 6 / 7 set when the neighbour at x-1 / x+1 / y-1 / y+1
-// lies in another region (its face takes the harmonic mean).
+// Node flags byte: region in bits 0-2; bit 3 set on the section's edge nodes (half weights, Robin faces);
+// bit 4 / 5 / 6 / 7 set when the neighbour at x-1 / x+1 / y-1 / y+1 lies in another region (its face
+// takes the harmonic mean).
 constexpr uint32_t kRegionMask2D = 7u;
+constexpr uint32_t kEdge2D = 1u << 3;
 constexpr uint32_t kDiffL = 1u << 4, kDiffR = 1u << 5, kDiffU = 1u << 6, kDiffD = 1u << 7;
+constexpr uint32_t kDiffAny2D = kDiffL | kDiffR | kDiffU | kDiffD;
 
 template <typename real>
 struct PairOf;
@@ -230,7 +233,6 @@ __global__ void __launch_bounds__(Tile2D<real, TX, TY, H, SEG>::NT, MINB)
     const real *qx = fconst + (fcol > 0 ? 4 : 0);
     const real fxM = rx * qx[0], fxT = rx * qx[1], fxG = rx * qx[2], fxQ = rx * qx[3];
     const bool col_in = gx >= 0 && gx < d.nx;
-    const bool xedge = gx == 0 || gx == d.nx - 1;
     // rows of the section inside the box
     const int ylo = max(0, -y0), yhi = min(BY, d.ny - y0);
     // a launch of fewer than H steps only updates the cells its tile core depends on
@@ -243,6 +245,9 @@ __global__ void __launch_bounds__(Tile2D<real, TX, TY, H, SEG>::NT, MINB)
         const int yfirst = lo + seg * len;
         const int rlo = max(lo, ylo), rhi = min(BY - lo, yhi);   // rows stored at this step
         const bool col_ok = col_in && x >= lo && x < BX - lo;
+        // run indices i whose row is stored: i - ilo in [0, nst)
+        const int ilo = rlo - yfirst;
+        const unsigned nst = col_ok && rhi > rlo ? (unsigned)(rhi - rlo) : 0u;
         const real aTx = air[(s - 1) * 8 + (fcol > 0 ? 2 : 0)], aPx = air[(s - 1) * 8 + (fcol > 0 ? 3 : 1)];
         // prime the window: the cell above the first row and the first row (half-conductances
         // with each cell's own region), then the neighbours of the first row
@@ -263,7 +268,6 @@ __global__ void __launch_bounds__(Tile2D<real, TX, TY, H, SEG>::NT, MINB)
 #pragma unroll 2
         for (int i = 0; i < len; ++i, c += BX) {
             const int y = yfirst + i;
-            const int gy = y0 + y;
             // the next row's neighbours, read before this row's result is stored
             const P2<real> pdn = p2_load(cur + c + 2 * BX), pln = p2_load(cur + c + BX - 1);
             const P2<real> prn = p2_load(cur + c + BX + 1), pvn = p2_load(prv + c + BX);
@@ -274,36 +278,42 @@ __global__ void __launch_bounds__(Tile2D<real, TX, TY, H, SEG>::NT, MINB)
             const P2<real> kl = p2_fma(cc.kb, p2_make(p2_p(pl), p2_p(pl)), cc.ka);
             const P2<real> kr = p2_fma(cc.kb, p2_make(p2_p(pr), p2_p(pr)), cc.ka);
             P2<real> Fl = p2_add(kc, kl), Fr = p2_add(kc, kr), Fu = p2_add(kc, ku), Fd = p2_add(kc, kd);
-            if (fcen & (kDiffL | kDiffR | kDiffU | kDiffD)) {
-                // faces to another region: that region's constants, harmonic mean
-                if (fcen & kDiffL) {
-                    const P2<real> k = half_k(cc, false, flags[y * L::FBX + x - 1 + L::FOFF], p2_p(pl), tab);
-                    Fl = p2_make(face_harmonic(p2_t(kc), p2_t(k)), face_harmonic(p2_p(kc), p2_p(k)));
-                }
-                if (fcen & kDiffR) {
-                    const P2<real> k = half_k(cc, false, flags[y * L::FBX + x + 1 + L::FOFF], p2_p(pr), tab);
-                    Fr = p2_make(face_harmonic(p2_t(kc), p2_t(k)), face_harmonic(p2_p(kc), p2_p(k)));
-                }
-                if (fcen & kDiffU) Fu = p2_make(face_harmonic(p2_t(kc), p2_t(ku)), face_harmonic(p2_p(kc), p2_p(ku)));
-                if (fcen & kDiffD) {
-                    kd = half_k(cc, false, fd, p2_p(pd), tab);
-                    Fd = p2_make(face_harmonic(p2_t(kc), p2_t(kd)), face_harmonic(p2_p(kc), p2_p(kd)));
-                }
-            }
             P2<real> st = p2_fma(cc.sb, p2_make(Pk, Pk), cc.sa);   // (B, A) storage terms
-            const bool edge_y = gy == 0 || gy == d.ny - 1;
-            const bool edge = xedge || edge_y;
+            // rare nodes (faces to another region, section edges) in one test
+            const bool edge = fcen & kEdge2D;
+            bool edge_y = false;
+            int gy = 0;
             real wy = one;
-            if (edge) {
-                // section edges: half control areas and face lengths, absent faces weighted 0
-                wy = edge_y ? half : one;
-                const real wl = wy * mL, wr = wy * mR, wu = gy > 0 ? wx : zero, wd = gy < d.ny - 1 ? wx : zero;
-                Fl = p2_mul(Fl, p2_make(wl, wl));
-                Fr = p2_mul(Fr, p2_make(wr, wr));
-                Fu = p2_mul(Fu, p2_make(wu, wu));
-                Fd = p2_mul(Fd, p2_make(wd, wd));
-                const real wxy = wx * wy;
-                st = p2_mul(p2_make(wxy, wxy), st);
+            if (fcen & (kDiffAny2D | kEdge2D)) {
+                if (fcen & kDiffAny2D) {
+                    // faces to another region: that region's constants, harmonic mean
+                    if (fcen & kDiffL) {
+                        const P2<real> k = half_k(cc, false, flags[y * L::FBX + x - 1 + L::FOFF], p2_p(pl), tab);
+                        Fl = p2_make(face_harmonic(p2_t(kc), p2_t(k)), face_harmonic(p2_p(kc), p2_p(k)));
+                    }
+                    if (fcen & kDiffR) {
+                        const P2<real> k = half_k(cc, false, flags[y * L::FBX + x + 1 + L::FOFF], p2_p(pr), tab);
+                        Fr = p2_make(face_harmonic(p2_t(kc), p2_t(k)), face_harmonic(p2_p(kc), p2_p(k)));
+                    }
+                    if (fcen & kDiffU) Fu = p2_make(face_harmonic(p2_t(kc), p2_t(ku)), face_harmonic(p2_p(kc), p2_p(ku)));
+                    if (fcen & kDiffD) {
+                        kd = half_k(cc, false, fd, p2_p(pd), tab);
+                        Fd = p2_make(face_harmonic(p2_t(kc), p2_t(kd)), face_harmonic(p2_p(kc), p2_p(kd)));
+                    }
+                }
+                if (edge) {
+                    // section edges: half control areas and face lengths, absent faces weighted 0
+                    gy = y0 + y;
+                    edge_y = gy == 0 || gy == d.ny - 1;
+                    wy = edge_y ? half : one;
+                    const real wl = wy * mL, wr = wy * mR, wu = gy > 0 ? wx : zero, wd = gy < d.ny - 1 ? wx : zero;
+                    Fl = p2_mul(Fl, p2_make(wl, wl));
+                    Fr = p2_mul(Fr, p2_make(wr, wr));
+                    Fu = p2_mul(Fu, p2_make(wu, wu));
+                    Fd = p2_mul(Fd, p2_make(wd, wd));
+                    const real wxy = wx * wy;
+                    st = p2_mul(p2_make(wxy, wxy), st);
+                }
             }
             P2<real> num = p2_mul(Fl, p2_sub(pl, pv));
             num = p2_fma(Fr, p2_sub(pr, pv), num);
@@ -339,7 +349,7 @@ __global__ void __launch_bounds__(Tile2D<real, TX, TY, H, SEG>::NT, MINB)
             numT = fma(Lv, X, numT);
             numT = fma(-cc.chi * A, dP, numT);
             const real dT = fast_div(numT, fma(half, ST, p2_t(st)));
-            if (col_ok && y >= rlo && y < rhi) p2_store(prv + c, p2_add(pv, p2_make(dT, dP)));
+            if ((unsigned)(i - ilo) < nst) p2_store(prv + c, p2_add(pv, p2_make(dT, dP)));
             // roll the window down one row; a cell below in another region than the node was
             // evaluated with the node's constants, so a change of region recomputes it
             pu = pc;

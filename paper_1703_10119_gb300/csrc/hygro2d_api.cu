@@ -429,7 +429,7 @@ hygro_status hygro2d_set_materials(hygro2d_ctx *c, int32_t n_regions, const uint
         std::vector<float> f(tab.begin(), tab.end());
         CUDA_TRY2(c, cudaMemcpy(c->d_tab, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
     }
-    // node flags: region, and one bit per neighbour that lies in another region
+    // node flags: region, the section-edge bit, and one bit per neighbour that lies in another region
     std::vector<uint8_t> fl(c->cells(), 0);
     for (int g = 0; g < c->G; ++g)
         for (int j = 0; j < c->ny; ++j)
@@ -437,6 +437,7 @@ hygro_status hygro2d_set_materials(hygro2d_ctx *c, int32_t n_regions, const uint
                 const uint8_t *rg = region + (size_t)g * c->ny * c->nx;
                 const int r = rg[(size_t)j * c->nx + i];
                 uint32_t f = (uint32_t)r;
+                if (i == 0 || i == c->nx - 1 || j == 0 || j == c->ny - 1) f |= kEdge2D;
                 if (i > 0 && rg[(size_t)j * c->nx + i - 1] != r) f |= kDiffL;
                 if (i < c->nx - 1 && rg[(size_t)j * c->nx + i + 1] != r) f |= kDiffR;
                 if (j > 0 && rg[(size_t)(j - 1) * c->nx + i] != r) f |= kDiffU;
