@@ -36,17 +36,18 @@ UNIT = "cell-updates/s"
 # multiply-add counted once (they all issue to the FMA pipe); reciprocals run on the MUFU pipe apart.
 # The neighbour sums are counted in their shortest form, sum_f F u_nb - S u^{n-1} (3 operations for two
 # faces, S being needed for the denominator anyway):
-#   general wall:     coefficients 5 (kM, kTT, A, B, chi A), faces 2, Pv 9 (S, num 3, denominator,
-#                     dPv, X 2, update), T 9 (ST, num 3, latent, cTM, denominator, dT, update)
-#                     = 25 (+ 2 reciprocals)
+# The latent cross flux X = sum_f F (Pv_nb - Pv_bar) is the node's vapour balance A dPv - g (1 operation).
+#   general wall:     coefficients 5 (kM, kTT, A, B, chi A), faces 2, Pv 8 (S, num 3, denominator,
+#                     dPv, X, update), T 9 (ST, num 3, latent, cTM, denominator, dT, update)
+#                     = 24 (+ 2 reciprocals)
 #   simple-heat wall: (kTT, cTT independent of Pv, cTM = 0: constant thermal faces and T denominators)
-#                     coefficients 2, face 1, Pv 9, T 6 (num 3, latent, dT, update) = 18 (+ 1 reciprocal)
-OPS_GENERAL = 25
-OPS_SIMPLE_HEAT = 18
-# adjoint, per differentiated cell-update: forward step 25, its recompute 25, reverse step 76 (the
+#                     coefficients 2, face 1, Pv 8, T 6 (num 3, latent, dT, update) = 17 (+ 1 reciprocal)
+OPS_GENERAL = 24
+OPS_SIMPLE_HEAT = 17
+# adjoint, per differentiated cell-update: forward step 24, its recompute 24, reverse step 76 (the
 # recomputed forward quantities 25 with the neighbour differences the reverse needs, the transposed
 # step 36, the face chain 15)
-OPS_ADJOINT = 126
+OPS_ADJOINT = 124
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 KERNEL_SOURCES = ["paper_1703_10119_gb300/csrc/df1d_persistent.cuh", "paper_1703_10119_gb300/csrc/df1d_common.cuh",
@@ -365,7 +366,7 @@ def bench_adjoint(args, H, wk, stream, local, rank):
            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s", "frac": achieved / peak,
                         "traffic": None,
                         "note": f"FP32 FMA-pipe roof; {OPS_ADJOINT} algorithmic FP32 ops per differentiated "
-                                "cell-update (forward 25, recompute 25, reverse step 76) plus 6 reciprocals; "
+                                "cell-update (forward 24, recompute 24, reverse step 76) plus 6 reciprocals; "
                                 "kernel adjoint_reg_kernel<float>"}}
     if rank == 0 and not args.no_cpu_baseline:
         import oracle

@@ -192,9 +192,11 @@ __device__ __forceinline__ void df_step(real (&Tp)[K], const real (&Tc)[K], real
         if (k == 0) numPg += L.g0;
         if (k == K - 1) numPg += L.g1;
         const real dP = fast_div(numPg, fma(half, S, A));
-        // latent cross flux sum_f F (P_nb - Pbar) [+ hM (Pinf - Pbar)] = num - S dP / 2
-        const real hdP = half * dP;
-        const real X = fma(-S, hdP, numP);
+        // latent cross flux sum_f F (P_nb - Pbar) [+ hM (Pinf - Pbar)] = num - S dP / 2, which the vapour
+        // balance of the node, (A + S / 2) dP = num + g, turns into A dP - g
+        real X = A * dP;
+        if (k == 0) X -= L.g0;
+        if (k == K - 1) X -= L.g1;
 
         // temperature: conduction, Lv x cross flux, cTM storage. Inside a lane of a simple-heat wall
         // without interfaces both thermal faces are FTin: FTin (T_l + T_r) - 2 FTin T^{n-1}.
@@ -230,11 +232,11 @@ __device__ __forceinline__ void df_step(real (&Tp)[K], const real (&Tc)[K], real
         Tp[k] = tp + dT;
 
         if (k == 0) {
-            sPbar = pp + hdP;
+            sPbar = fma(half, dP, pp);
             sTbar = fma(half, dT, tp);
         }
         if (k == K - 1) {
-            sPbar = L.face1 ? pp + hdP : sPbar;
+            sPbar = L.face1 ? fma(half, dP, pp) : sPbar;
             sTbar = L.face1 ? fma(half, dT, tp) : sTbar;
         }
 
