@@ -30,6 +30,7 @@ struct AdjWall {
     int16_t start[33];   // lane l owns nodes [start[l], start[l+1])
     int8_t layer[32];    // layer of lane l's nodes (-1: no nodes)
     int32_t kt;          // register kernel: slots per lane (>= the longest run); 0: shared-memory kernel
+    int32_t dense;       // every run that holds nodes has kt - 1 or kt of them
     double dx;
     int64_t ck_off, seg_off;   // first real of the wall's checkpoints and segment levels
 };

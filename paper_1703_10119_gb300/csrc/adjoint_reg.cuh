@@ -47,6 +47,30 @@ __device__ __forceinline__ double adj_rcp<double>(double x)
     return 1.0 / x;
 }
 
+// Slot predicates. A lane's run holds slots [0, nl). DENSE walls have every run that holds nodes at KT - 1
+// or KT nodes, so only the last two slots depend on nl there; lanes without nodes then compute values
+// that no other lane reads (the last lane with nodes takes the ambient air on its right).
+template <int KT, bool DENSE>
+__device__ __forceinline__ bool s_fixed(int i)
+{
+    return DENSE && i + 2 < KT;
+}
+template <int KT, bool DENSE>
+__device__ __forceinline__ bool s_act(int i, int nl)
+{
+    return s_fixed<KT, DENSE>(i) || i < nl;
+}
+template <int KT, bool DENSE>
+__device__ __forceinline__ bool s_last(int i, int nl)
+{
+    return !s_fixed<KT, DENSE>(i) && i == nl - 1;
+}
+template <int KT, bool DENSE>
+__device__ __forceinline__ bool s_inR(int i, int nl)
+{
+    return s_fixed<KT, DENSE>(i) || i + 1 < nl;
+}
+
 // Constants of one lane.
 template <typename real>
 struct RegLane {
@@ -71,7 +95,7 @@ struct RegEdge {
     real pcl, khlM, khlT;         // the last slot's Pv and kh
 };
 
-template <typename real, int KT>
+template <typename real, int KT, bool DENSE>
 __device__ __forceinline__ void reg_edges(const RegLane<real> &L, const real (&tc)[KT], const real (&pc)[KT],
                                           const real (&khM)[KT], const real (&khT)[KT], const real *air,
                                           RegEdge<real> &e)
@@ -79,8 +103,8 @@ __device__ __forceinline__ void reg_edges(const RegLane<real> &L, const real (&t
     real pcl = pc[0], tcl = tc[0];
 #pragma unroll
     for (int i = 1; i < KT; ++i) {
-        pcl = i == L.nl - 1 ? pc[i] : pcl;
-        tcl = i == L.nl - 1 ? tc[i] : tcl;
+        pcl = s_last<KT, DENSE>(i, L.nl) ? pc[i] : pcl;
+        tcl = s_last<KT, DENSE>(i, L.nl) ? tc[i] : tcl;
     }
     const unsigned full = 0xffffffffu;
     const real pLn = __shfl_up_sync(full, pcl, 1), tLn = __shfl_up_sync(full, tcl, 1);
@@ -116,13 +140,13 @@ struct RegSlot {
     real w, A, S, ST, numP, numT0, src, pl, pr, tl, tr, FML, FMR, FTL, FTR, D, rD, dP, E, rE, dT;
 };
 
-template <typename real, int KT>
+template <typename real, int KT, bool DENSE>
 __device__ __forceinline__ void reg_slot(const RegLane<real> &L, const RegEdge<real> &e, const real (&tp)[KT],
                                          const real (&pp)[KT], const real (&tc)[KT], const real (&pc)[KT],
                                          const real (&khM)[KT], const real (&khT)[KT], const int i, RegSlot<real> &o)
 {
     const real half = real(0.5);
-    const bool lastslot = i == L.nl - 1, inR = i + 1 < L.nl;
+    const bool lastslot = s_last<KT, DENSE>(i, L.nl), inR = s_inR<KT, DENSE>(i, L.nl);
     const int im = i > 0 ? i - 1 : 0, ip = i + 1 < KT ? i + 1 : i;
     if (i == 0) {
         o.pl = e.XLP;
@@ -171,19 +195,19 @@ __device__ __forceinline__ void reg_kh(const RegLane<real> &L, const real (&pc)[
 }
 
 // One DF step of the lane's slots: (tp, pp) = level n-1 is overwritten with level n+1.
-template <typename real, int KT>
+template <typename real, int KT, bool DENSE>
 __device__ __forceinline__ void reg_forward(const RegLane<real> &L, real (&tp)[KT], real (&pp)[KT],
                                             const real (&tc)[KT], const real (&pc)[KT], const real *air)
 {
     real khM[KT], khT[KT];
     reg_kh(L, pc, khM, khT);
     RegEdge<real> e;
-    reg_edges(L, tc, pc, khM, khT, air, e);
+    reg_edges<real, KT, DENSE>(L, tc, pc, khM, khT, air, e);
 #pragma unroll
     for (int i = 0; i < KT; ++i) {
         RegSlot<real> o;
-        reg_slot(L, e, tp, pp, tc, pc, khM, khT, i, o);
-        const bool act = i < L.nl;
+        reg_slot<real, KT, DENSE>(L, e, tp, pp, tc, pc, khM, khT, i, o);
+        const bool act = s_act<KT, DENSE>(i, L.nl);
         pp[i] = act ? pp[i] + o.dP : real(0);
         tp[i] = act ? tp[i] + o.dT : real(0);
     }
@@ -198,7 +222,7 @@ struct RegSums {
 // Reverse of the step n -> n+1. In: (tp, pp) level n-1, (tc, pc) level n, (lT, lP) the complete adjoint
 // of level n+1, (mT, mP) the partial adjoint of level n. Out: (lT, lP) the partial adjoint of level n-1
 // (from this step), (mT, mP) complete.
-template <typename real, int KT>
+template <typename real, int KT, bool DENSE>
 __device__ __forceinline__ void reg_reverse(const RegLane<real> &L, const real (&tp)[KT], const real (&pp)[KT],
                                             const real (&tc)[KT], const real (&pc)[KT], real (&lT)[KT],
                                             real (&lP)[KT], real (&mT)[KT], real (&mP)[KT], const real *air,
@@ -208,7 +232,7 @@ __device__ __forceinline__ void reg_reverse(const RegLane<real> &L, const real (
     real khM[KT], khT[KT];
     reg_kh(L, pc, khM, khT);
     RegEdge<real> e;
-    reg_edges(L, tc, pc, khM, khT, air, e);
+    reg_edges<real, KT, DENSE>(L, tc, pc, khM, khT, air, e);
 #pragma unroll
     for (int k = 0; k < 9; ++k) g.s[k] = real(0);
     // carried between slots: the previous slot's right-face adjoints and right-neighbour contributions
@@ -218,8 +242,8 @@ __device__ __forceinline__ void reg_reverse(const RegLane<real> &L, const real (
 #pragma unroll
     for (int i = 0; i < KT; ++i) {
         RegSlot<real> o;
-        reg_slot(L, e, tp, pp, tc, pc, khM, khT, i, o);
-        const bool act = i < L.nl;
+        reg_slot<real, KT, DENSE>(L, e, tp, pp, tc, pc, khM, khT, i, o);
+        const bool act = s_act<KT, DENSE>(i, L.nl);
         // T+ = t- + numT / E
         const real gdT = lT[i];
         const real gnumT = gdT * o.rE;
@@ -277,7 +301,7 @@ __device__ __forceinline__ void reg_reverse(const RegLane<real> &L, const real (
                 g.s[5] = fma(tT, pr_i + r, g.s[5]);
             }
         }
-        if (i == L.nl - 1) {
+        if (s_last<KT, DENSE>(i, L.nl)) {
             rLT = gtr;
             rLP = gpr;
             rLFM = gFMR;
@@ -328,8 +352,8 @@ __device__ __forceinline__ void reg_reverse(const RegLane<real> &L, const real (
         const real addT = fromR_T, addP = fromR_P + fma(eM, L.c.kMb, eT * L.c.kTb);
 #pragma unroll
         for (int i = 0; i < KT; ++i) {
-            mT[i] += i == L.nl - 1 ? addT : real(0);
-            mP[i] += i == L.nl - 1 ? addP : real(0);
+            mT[i] += s_last<KT, DENSE>(i, L.nl) ? addT : real(0);
+            mP[i] += s_last<KT, DENSE>(i, L.nl) ? addP : real(0);
         }
         g.s[0] += eM;
         g.s[1] = fma(eM, rl, g.s[1]);
@@ -359,20 +383,20 @@ __device__ __forceinline__ void reg_air(const AdjDev<real> &d, const FaceInfo &f
 }
 
 // The value of slot nl - 1 (a run of selects: register arrays take no run-time index).
-template <typename real, int KT>
+template <typename real, int KT, bool DENSE>
 __device__ __forceinline__ real reg_last(const real (&v)[KT], int nl)
 {
     real x = v[0];
 #pragma unroll
-    for (int i = 1; i < KT; ++i) x = i == nl - 1 ? v[i] : x;
+    for (int i = 1; i < KT; ++i) x = s_last<KT, DENSE>(i, nl) ? v[i] : x;
     return x;
 }
 
-template <typename real, int KT>
+template <typename real, int KT, bool DENSE>
 __device__ __forceinline__ void reg_add_last(real (&v)[KT], int nl, real a)
 {
 #pragma unroll
-    for (int i = 0; i < KT; ++i) v[i] += i == nl - 1 ? a : real(0);
+    for (int i = 0; i < KT; ++i) v[i] += s_last<KT, DENSE>(i, nl) ? a : real(0);
 }
 
 template <typename real, int KT>
@@ -401,7 +425,7 @@ __device__ __forceinline__ void reg_swap(real (&a)[KT], real (&b)[KT])
 }
 
 // Loss and gradient of one wall (the whole warp).
-template <typename real, int KT>
+template <typename real, int KT, bool DENSE>
 __device__ __noinline__ void adj_reg_wall(const AdjDev<real> &d, const int w, real *air)
 {
     const AdjWall &aw = d.walls[w];
@@ -476,7 +500,7 @@ __device__ __noinline__ void adj_reg_wall(const AdjDev<real> &d, const int w, re
             loss += d.wT * eT * eT + d.wP * eP * eP;
             bad |= !isfinite(eT) || !isfinite(eP);
         }
-        const real Tl = reg_last(T, L.nl), Plv = reg_last(P, L.nl);
+        const real Tl = reg_last<real, KT, DENSE>(T, L.nl), Plv = reg_last<real, KT, DENSE>(P, L.nl);
         if (L.rsurf && L.nl > 0) {
             const double eT = (double)Tl + (double)L.Tr - (double)o[2];
             const double eP = (double)Plv + (double)L.Pr - (double)o[3];
@@ -491,10 +515,10 @@ __device__ __noinline__ void adj_reg_wall(const AdjDev<real> &d, const int w, re
             aT[0] += (real)(2.0 * d.wT * ((double)T[0] + (double)L.Tr - (double)o[0]));
             aP[0] += (real)(2.0 * d.wP * ((double)P[0] + (double)L.Pr - (double)o[1]));
         }
-        const real Tl = reg_last(T, L.nl), Plv = reg_last(P, L.nl);
+        const real Tl = reg_last<real, KT, DENSE>(T, L.nl), Plv = reg_last<real, KT, DENSE>(P, L.nl);
         if (L.rsurf && L.nl > 0) {
-            reg_add_last(aT, L.nl, (real)(2.0 * d.wT * ((double)Tl + (double)L.Tr - (double)o[2])));
-            reg_add_last(aP, L.nl, (real)(2.0 * d.wP * ((double)Plv + (double)L.Pr - (double)o[3])));
+            reg_add_last<real, KT, DENSE>(aT, L.nl, (real)(2.0 * d.wT * ((double)Tl + (double)L.Tr - (double)o[2])));
+            reg_add_last<real, KT, DENSE>(aP, L.nl, (real)(2.0 * d.wP * ((double)Plv + (double)L.Pr - (double)o[3])));
         }
     };
 
@@ -524,7 +548,7 @@ __device__ __noinline__ void adj_reg_wall(const AdjDev<real> &d, const int w, re
                 --cc;
             }
             reg_air(d, f0, f1, air, chunk, n, lane);
-            reg_forward(L, Tp, Pp, Tc, Pc, air + (int)(n & (kAdjAirChunk - 1)) * 4);
+            reg_forward<real, KT, DENSE>(L, Tp, Pp, Tc, Pc, air + (int)(n & (kAdjAirChunk - 1)) * 4);
             if (store) {
                 reg_store(s2, Tp, lane);
                 reg_store(s2 + KT * 32, Pp, lane);
@@ -614,7 +638,7 @@ __device__ __noinline__ void adj_reg_wall(const AdjDev<real> &d, const int w, re
             }
             reg_air(d, f0, f1, air, chunk, n, lane);
             RegSums<real> gs;
-            reg_reverse(L, Tp, Pp, Tc, Pc, LT, LP, MT, MP, air + (int)(n & (kAdjAirChunk - 1)) * 4, gs);
+            reg_reverse<real, KT, DENSE>(L, Tp, Pp, Tc, Pc, LT, LP, MT, MP, air + (int)(n & (kAdjAirChunk - 1)) * 4, gs);
 #pragma unroll
             for (int k = 0; k < 9; ++k) acc[k].add(gs.s[k]);
             // levels move down one; the completed adjoint of level n becomes the complete one
@@ -643,25 +667,45 @@ __global__ void __launch_bounds__(32, 8) adjoint_reg_kernel(const __grid_constan
     __shared__ __align__(16) real air[kAdjAirChunk * 4];
     if ((int)blockIdx.x >= d.n_list) return;
     const int w = d.list[blockIdx.x];
-    switch (d.walls[w].kt) {
-    case 2: adj_reg_wall<real, 2>(d, w, air); break;
-    case 3: adj_reg_wall<real, 3>(d, w, air); break;
-    case 4: adj_reg_wall<real, 4>(d, w, air); break;
-    case 5: adj_reg_wall<real, 5>(d, w, air); break;
-    case 6: adj_reg_wall<real, 6>(d, w, air); break;
-    case 7: adj_reg_wall<real, 7>(d, w, air); break;
-    case 8: adj_reg_wall<real, 8>(d, w, air); break;
-    case 10:
-        if constexpr (adj_reg_max_k<real>() >= 10) adj_reg_wall<real, 10>(d, w, air);
+    const AdjWall &aw = d.walls[w];
+    switch (aw.kt * 2 + (aw.dense ? 1 : 0)) {
+    case 4: adj_reg_wall<real, 2, false>(d, w, air); break;
+    case 5: adj_reg_wall<real, 2, true>(d, w, air); break;
+    case 6: adj_reg_wall<real, 3, false>(d, w, air); break;
+    case 7: adj_reg_wall<real, 3, true>(d, w, air); break;
+    case 8: adj_reg_wall<real, 4, false>(d, w, air); break;
+    case 9: adj_reg_wall<real, 4, true>(d, w, air); break;
+    case 10: adj_reg_wall<real, 5, false>(d, w, air); break;
+    case 11: adj_reg_wall<real, 5, true>(d, w, air); break;
+    case 12: adj_reg_wall<real, 6, false>(d, w, air); break;
+    case 13: adj_reg_wall<real, 6, true>(d, w, air); break;
+    case 14: adj_reg_wall<real, 7, false>(d, w, air); break;
+    case 15: adj_reg_wall<real, 7, true>(d, w, air); break;
+    case 16: adj_reg_wall<real, 8, false>(d, w, air); break;
+    case 17: adj_reg_wall<real, 8, true>(d, w, air); break;
+    case 20:
+        if constexpr (adj_reg_max_k<real>() >= 10) adj_reg_wall<real, 10, false>(d, w, air);
         break;
-    case 12:
-        if constexpr (adj_reg_max_k<real>() >= 12) adj_reg_wall<real, 12>(d, w, air);
+    case 21:
+        if constexpr (adj_reg_max_k<real>() >= 10) adj_reg_wall<real, 10, true>(d, w, air);
         break;
-    case 14:
-        if constexpr (adj_reg_max_k<real>() >= 14) adj_reg_wall<real, 14>(d, w, air);
+    case 24:
+        if constexpr (adj_reg_max_k<real>() >= 12) adj_reg_wall<real, 12, false>(d, w, air);
         break;
-    case 16:
-        if constexpr (adj_reg_max_k<real>() >= 16) adj_reg_wall<real, 16>(d, w, air);
+    case 25:
+        if constexpr (adj_reg_max_k<real>() >= 12) adj_reg_wall<real, 12, true>(d, w, air);
+        break;
+    case 28:
+        if constexpr (adj_reg_max_k<real>() >= 14) adj_reg_wall<real, 14, false>(d, w, air);
+        break;
+    case 29:
+        if constexpr (adj_reg_max_k<real>() >= 14) adj_reg_wall<real, 14, true>(d, w, air);
+        break;
+    case 32:
+        if constexpr (adj_reg_max_k<real>() >= 16) adj_reg_wall<real, 16, false>(d, w, air);
+        break;
+    case 33:
+        if constexpr (adj_reg_max_k<real>() >= 16) adj_reg_wall<real, 16, true>(d, w, air);
         break;
     default: break;
     }

@@ -1411,6 +1411,11 @@ hygro_status hygro_loss_grad(hygro_ctx *c, int64_t n_steps, int32_t sample_every
         }
         a.start[32] = (int16_t)a.N;
         a.kt = K <= maxk ? adj_reg_slots(K) : 0;
+        a.dense = 1;
+        for (int l = 0; l < 32; ++l) {
+            const int nl = a.start[l + 1] - a.start[l];
+            if (nl > 0 && nl < a.kt - 1) a.dense = 0;
+        }
         if (a.kt > 0) {
             reg_list.push_back(w);
         } else {
