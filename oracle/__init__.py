@@ -30,8 +30,8 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 
 NLAYER_PAR = 9
-NBC_PAR = 12
-NROOM_PAR = 16
+NBC_PAR = 13
+NROOM_PAR = 21
 
 
 def build(force: bool = False) -> str:
@@ -61,6 +61,7 @@ class _Problem(C.Structure):
         ("noise", C.c_void_p * 2), ("noise_len", C.c_int32 * 2),
         ("dt", C.c_double), ("t0", C.c_double), ("Lv", C.c_double), ("Psat", C.c_double),
         ("n_rooms", C.c_int32), ("room_par", C.c_void_p), ("wall_area", C.c_void_p),
+        ("vapour_frac", C.c_void_p),
     ]
 
 
@@ -174,12 +175,16 @@ class Oracle:
         rooms = wl.rooms
         if rooms:
             p.n_rooms = len(rooms["par"])
-            p.room_par = _ptr(keep(rooms["par"], np.float64))
+            par = np.asarray(rooms["par"], np.float64)
+            assert par.shape[1] == NROOM_PAR, "room rows hold ROOM_FIELDS"
+            p.room_par = _ptr(keep(par, np.float64))
             p.wall_area = _ptr(keep(rooms["wall_area"], np.float64))
         else:
             p.n_rooms = 0
             p.room_par = None
             p.wall_area = _ptr(keep(np.zeros(max(W, 1)), np.float64))
+        vf = getattr(wl, "vapour_frac", None)
+        p.vapour_frac = None if vf is None else _ptr(keep(vf, np.float64))
         self._p = p
 
         self.T_prev = np.repeat(np.asarray(wl.T_init, np.float64), wl.n_nodes)

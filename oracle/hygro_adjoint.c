@@ -301,6 +301,9 @@ int orc_loss_adjoint(const orc_problem *p, int64_t n_steps, const orc_misfit *m,
 {
     if (p == NULL || m == NULL || loss_out == NULL || n_steps < 0 || m->sample_every < 1) return -1;
     if (p->n_rooms > 0) return -1;
+    if (p->vapour_frac != NULL)
+        for (int32_t w = 0; w < p->n_walls; ++w)
+            if (p->vapour_frac[w] != 1.0) return -1;   /* the adjoint takes kTM = Lv kM */
     int64_t *loff = layer_offsets(p);
     if (loff == NULL) return -2;
     const int64_t total_layers = loff[p->n_walls];
@@ -418,6 +421,9 @@ int orc_loss_tangent(const orc_problem *p, int64_t n_steps, const orc_misfit *m,
                      double *dloss_out)
 {
     if (p == NULL || m == NULL || dir == NULL || n_steps < 0 || m->sample_every < 1 || p->n_rooms > 0) return -1;
+    if (p->vapour_frac != NULL)
+        for (int32_t w = 0; w < p->n_walls; ++w)
+            if (p->vapour_frac[w] != 1.0) return -1;
     int64_t *loff = layer_offsets(p);
     if (loff == NULL) return -2;
     const int32_t K = (int32_t)(n_steps / m->sample_every);

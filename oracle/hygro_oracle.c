@@ -13,9 +13,9 @@
 #endif
 
 enum { L_KM0, L_A, L_CM0, L_B, L_KTT0, L_AT, L_CTT0, L_BT, L_CHI };
-enum { B_HT, B_HM, B_QINF, B_GINF, B_TMEAN, B_TAMP, B_PMEAN, B_PAMP, B_PERIOD, B_PHT, B_PHP, B_NDT };
+enum { B_HT, B_HM, B_QINF, B_GINF, B_TMEAN, B_TAMP, B_PMEAN, B_PAMP, B_PERIOD, B_PHT, B_PHP, B_NDT, B_PERIODP };
 enum { R_VOL, R_ACH, R_QGAIN, R_GVAP, R_TMEAN, R_TAMP, R_PMEAN, R_PAMP, R_PERIOD, R_PHT, R_PHP,
-       R_RHOA, R_CPA, R_CPV, R_PVREF, R_SCHEME };
+       R_RHOA, R_CPA, R_CPV, R_PVREF, R_SCHEME, R_PERIODP, R_GPULSE, R_PON, R_POFF, R_PPER };
 
 static const double TWO_PI = 6.283185307179586476925286766559;
 
@@ -42,10 +42,9 @@ void orc_ambient(const orc_problem *p, int32_t w, int32_t face, double t, double
     if (p->noise[face] != NULL && p->noise_len[face] > 0)
         tab = p->noise[face] + (size_t)w * (size_t)p->noise_len[face] * 2;
     double T = b[B_TMEAN], P = b[B_PMEAN];
-    if (b[B_PERIOD] > 0.0) {
-        T += b[B_TAMP] * sin(TWO_PI * t / b[B_PERIOD] + b[B_PHT]);
-        P += b[B_PAMP] * sin(TWO_PI * t / b[B_PERIOD] + b[B_PHP]);
-    }
+    const double period_P = b[B_PERIODP] > 0.0 ? b[B_PERIODP] : b[B_PERIOD];
+    if (b[B_PERIOD] > 0.0) T += b[B_TAMP] * sin(TWO_PI * t / b[B_PERIOD] + b[B_PHT]);
+    if (period_P > 0.0) P += b[B_PAMP] * sin(TWO_PI * t / period_P + b[B_PHP]);
     T += noise_at(tab, p->noise_len[face], b[B_NDT], t, 0);
     P += noise_at(tab, p->noise_len[face], b[B_NDT], t, 1);
     *T_inf = T;
@@ -58,6 +57,7 @@ typedef struct {
     int32_t nl;
     const int32_t *first;
     const double *par;
+    double nu;             /* kTM = nu Lv kM */
 } wall_view;
 
 static wall_view view_of(const orc_problem *p, const int64_t *layer_off, int32_t w)
@@ -68,6 +68,7 @@ static wall_view view_of(const orc_problem *p, const int64_t *layer_off, int32_t
     v.nl = p->n_layers[w];
     v.first = p->layer_first + layer_off[w];
     v.par = p->layer_par + (size_t)layer_off[w] * ORC_NLAYER_PAR;
+    v.nu = p->vapour_frac != NULL ? p->vapour_frac[w] : 1.0;
     return v;
 }
 
@@ -82,7 +83,7 @@ static int32_t layer_of(const wall_view *v, int32_t j)
  * paper prescribes for the DF scheme in Sec. 3.1), then their face values:
  * arithmetic mean of the two nodes inside a layer (for coefficients affine
  * in Pv this equals the coefficient at the face-mean Pv, Sec. 3.1) and the
- * harmonic mean across an interface between two layers. kTM_f = Lv kM_f. */
+ * harmonic mean across an interface between two layers. kTM_f = nu Lv kM_f. */
 static void coefficients(const orc_problem *p, const wall_view *v, const double *P,
                          double *kM, double *cM, double *kTT, double *cTT, double *kTM, double *cTM,
                          double *kMf, double *kTTf, double *kTMf)
@@ -94,7 +95,7 @@ static void coefficients(const orc_problem *p, const wall_view *v, const double 
         cM[j] = q[L_CM0] * (1.0 + q[L_B] * r);
         kTT[j] = q[L_KTT0] * (1.0 + q[L_AT] * r);
         cTT[j] = q[L_CTT0] * (1.0 + q[L_BT] * r);
-        kTM[j] = p->Lv * kM[j];
+        kTM[j] = v->nu * p->Lv * kM[j];
         cTM[j] = q[L_CHI] * cM[j];
     }
     for (int32_t j = 0; j + 1 < v->N; ++j) {
@@ -105,7 +106,7 @@ static void coefficients(const orc_problem *p, const wall_view *v, const double 
             kMf[j] = 2.0 * kM[j] * kM[j + 1] / (kM[j] + kM[j + 1]);
             kTTf[j] = 2.0 * kTT[j] * kTT[j + 1] / (kTT[j] + kTT[j + 1]);
         }
-        kTMf[j] = p->Lv * kMf[j];
+        kTMf[j] = v->nu * p->Lv * kMf[j];
     }
 }
 
@@ -294,17 +295,22 @@ static void room_step(const orc_problem *p, int32_t r, double t, double *rs,
     double rhoV = q[R_RHOA] * q[R_VOL];
     double gv = rhoV * q[R_ACH] / 3600.0;                        /* kg/s of exchanged air */
     double T_out = q[R_TMEAN], P_out = q[R_PMEAN];
-    if (q[R_PERIOD] > 0.0) {
-        T_out += q[R_TAMP] * sin(TWO_PI * t / q[R_PERIOD] + q[R_PHT]);
-        P_out += q[R_PAMP] * sin(TWO_PI * t / q[R_PERIOD] + q[R_PHP]);
+    const double period_P = q[R_PERIODP] > 0.0 ? q[R_PERIODP] : q[R_PERIOD];
+    if (q[R_PERIOD] > 0.0) T_out += q[R_TAMP] * sin(TWO_PI * t / q[R_PERIOD] + q[R_PHT]);
+    if (period_P > 0.0) P_out += q[R_PAMP] * sin(TWO_PI * t / period_P + q[R_PHP]);
+    /* vapour production of the occupants (Sec. 5.1): base load plus the daily pulse */
+    double g_vap = q[R_GVAP];
+    if (q[R_PPER] > 0.0) {
+        const double ph = fmod(t, q[R_PPER]);
+        if (ph >= q[R_PON] && ph < q[R_POFF]) g_vap += q[R_GPULSE];
     }
     double Pref = q[R_PVREF];
     double w_out = P_out / Pref;
     if (q[R_SCHEME] == 1.0) {
         /* the explicit Euler update of Sec. 5.2: every term of both balances at level n */
-        double Pa_n = Pa_c + dt / (rhoV / Pref) * (q[R_GVAP] + gv * (w_out - Pa_c / Pref) + sum_AhMPs[r] - sum_AhM[r] * Pa_c);
+        double Pa_n = Pa_c + dt / (rhoV / Pref) * (g_vap + gv * (w_out - Pa_c / Pref) + sum_AhMPs[r] - sum_AhM[r] * Pa_c);
         double CT0 = rhoV * (q[R_CPA] + q[R_CPV] * Pa_c / Pref);
-        double rhs0 = q[R_QGAIN] + Lv * q[R_GVAP] + gv * q[R_CPA] * (T_out - Ta_c) + Lv * gv * (w_out - Pa_c / Pref) +
+        double rhs0 = q[R_QGAIN] + Lv * g_vap + gv * q[R_CPA] * (T_out - Ta_c) + Lv * gv * (w_out - Pa_c / Pref) +
                       sum_AhTTs[r] - sum_AhT[r] * Ta_c + Lv * (sum_AhMPs[r] - sum_AhM[r] * Pa_c);
         double Ta_n = Ta_c + dt / CT0 * rhs0;
         rs[0] = Ta_c;
@@ -317,14 +323,14 @@ static void room_step(const orc_problem *p, int32_t r, double t, double *rs,
     double CP = rhoV / Pref;
     double a_p = CP / (2.0 * dt);
     double k_p = gv / Pref + sum_AhM[r];
-    double Pa_n = ((a_p - 0.5 * k_p) * Pa_p + q[R_GVAP] + gv * w_out + sum_AhMPs[r]) / (a_p + 0.5 * k_p);
+    double Pa_n = ((a_p - 0.5 * k_p) * Pa_p + g_vap + gv * w_out + sum_AhMPs[r]) / (a_p + 0.5 * k_p);
     double Pa_bar = 0.5 * (Pa_n + Pa_p);
     /* heat: rhoV (cpa + cpv w) dTa/dt = Q + Lv g_vap + gv cpa (T_out - Ta) + Lv gv (w_out - w)
      *       + sum A [hT (Ts - Ta) + Lv hM (Ps - Pa)] */
     double CT = rhoV * (q[R_CPA] + q[R_CPV] * Pa_c / Pref);
     double a_t = CT / (2.0 * dt);
     double k_t = gv * q[R_CPA] + sum_AhT[r];
-    double rhs = q[R_QGAIN] + Lv * q[R_GVAP] + gv * q[R_CPA] * T_out + Lv * gv * (w_out - Pa_bar / Pref) +
+    double rhs = q[R_QGAIN] + Lv * g_vap + gv * q[R_CPA] * T_out + Lv * gv * (w_out - Pa_bar / Pref) +
                  sum_AhTTs[r] + Lv * (sum_AhMPs[r] - sum_AhM[r] * Pa_bar);
     double Ta_n = ((a_t - 0.5 * k_t) * Ta_p + rhs) / (a_t + 0.5 * k_t);
     rs[0] = Ta_c;

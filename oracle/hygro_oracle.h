@@ -13,7 +13,8 @@
  *     with coefficients kM, cM, kTT, cTT, kTM, cTM (Sec. 2) taken in the
  *     affine form kM = kM0 (1 + a Pv/Psat), cM = cM0 (1 + b Pv/Psat),
  *     kTT = kTT0 (1 + aT Pv/Psat), cTT = cTT0 (1 + bT Pv/Psat),
- *     kTM = Lv kM, cTM = chi cM;
+ *     kTM = nu Lv kM (nu = 1 unless a wall's vapour fraction says otherwise:
+ *     Sec. 2 defines kTM = Lv delta_v with delta_v the vapour part of kM), cTM = chi cM;
  *   - Robin surface exchanges [eq:HAM_BC] (fluxes counted positive INTO the
  *     wall at both faces), uniform initial state [eq:HAM_ic];
  *   - the nonlinear DF scheme [eq:DF_NL], [eq:DF_NL_RHS]: coefficients
@@ -42,10 +43,14 @@ extern "C" {
 #endif
 
 #define ORC_NLAYER_PAR 9   /* kM0, a, cM0, b, kTT0, aT, cTT0, bT, chi */
-#define ORC_NBC_PAR 12     /* hT, hM, q_inf, g_inf, T_mean, T_amp, P_mean, P_amp, period, phase_T, phase_P, noise_dt */
-#define ORC_NROOM_PAR 16   /* volume, ach, Q_gain, g_vap, T_out_mean, T_out_amp, P_out_mean, P_out_amp,
+#define ORC_NBC_PAR 13     /* hT, hM, q_inf, g_inf, T_mean, T_amp, P_mean, P_amp, period, phase_T, phase_P, noise_dt,
+                              period_P (period of the Pv sinusoid; <= 0: period) */
+#define ORC_NROOM_PAR 21   /* volume, ach, Q_gain, g_vap, T_out_mean, T_out_amp, P_out_mean, P_out_amp,
                               period, phase_T, phase_P, rho_a, cp_a, cp_v, Pv_ref, scheme (0: the room
-                              as one more DF node, 1: the explicit Euler update of Sec. 5.2) */
+                              as one more DF node, 1: the explicit Euler update of Sec. 5.2), period_P
+                              (outdoor Pv; <= 0: period), g_pulse, pulse_on, pulse_off, pulse_period (the
+                              vapour production is g_vap + g_pulse while pulse_on <= t mod pulse_period
+                              < pulse_off; no pulse when pulse_period <= 0) */
 
 enum { ORC_BC_AMBIENT = 0, ORC_BC_ADIABATIC = 1, ORC_BC_ROOM = 2 };
 
@@ -65,6 +70,7 @@ typedef struct {
     int32_t n_rooms;
     const double *room_par;      /* [n_rooms][ORC_NROOM_PAR] */
     const double *wall_area;     /* [n_walls], m^2, used by room faces */
+    const double *vapour_frac;   /* [n_walls] nu of kTM = nu Lv kM inside the wall, or NULL (all 1) */
 } orc_problem;
 
 typedef struct {
@@ -133,7 +139,7 @@ typedef struct {
 } orc_misfit;
 
 /* Loss and its gradient dL/d(layer_par) ([sum n_layers][ORC_NLAYER_PAR], or NULL for the loss alone)
- * by the reverse-time adjoint of the DF step. Walls without room faces. 0 on success. */
+ * by the reverse-time adjoint of the DF step. Walls without room faces, kTM = Lv kM. 0 on success. */
 int orc_loss_adjoint(const orc_problem *p, int64_t n_steps, const orc_misfit *m, double *loss, double *grad,
                      int32_t n_threads);
 

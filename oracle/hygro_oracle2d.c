@@ -53,10 +53,9 @@ static void grid_step(const orc2d_problem *p, int32_t g, double t, double *Tp, c
         qs[f] = b[2];
         gs[f] = b[3];
         double T = b[4], P = b[6];
-        if (b[8] > 0.0) {
-            T += b[5] * sin(6.283185307179586476925286766559 * t / b[8] + b[9]);
-            P += b[7] * sin(6.283185307179586476925286766559 * t / b[8] + b[10]);
-        }
+        const double period_P = b[12] > 0.0 ? b[12] : b[8];   /* Pv sinusoid period (<= 0: the T period) */
+        if (b[8] > 0.0) T += b[5] * sin(6.283185307179586476925286766559 * t / b[8] + b[9]);
+        if (period_P > 0.0) P += b[7] * sin(6.283185307179586476925286766559 * t / period_P + b[10]);
         if (p->noise[f] != NULL && p->noise_len[f] > 0 && b[11] > 0.0) {
             const float *tab = p->noise[f] + (size_t)g * p->noise_len[f] * 2;
             double x = t / b[11];

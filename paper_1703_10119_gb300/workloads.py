@@ -42,7 +42,7 @@ BC_ROOM = 2              # face exposed to a room air node
 
 # Column order of a boundary parameter row.
 BC_FIELDS = ("hT", "hM", "q_inf", "g_inf", "T_mean", "T_amp", "P_mean",
-             "P_amp", "period", "phase_T", "phase_P", "noise_dt")
+             "P_amp", "period", "phase_T", "phase_P", "noise_dt", "period_P")
 # Column order of a layer parameter row.
 LAYER_FIELDS = ("kM0", "a", "cM0", "b", "kTT0", "aT", "cTT0", "bT", "chi")
 
@@ -92,7 +92,7 @@ class Workload:
     T_init: np.ndarray           # float64 [n_walls], K
     P_init: np.ndarray           # float64 [n_walls], Pa
     bc_kind: np.ndarray          # int32 [n_walls, 2]
-    bc_par: np.ndarray           # float64 [n_walls, 2, 12] (BC_FIELDS)
+    bc_par: np.ndarray           # float64 [n_walls, 2, 13] (BC_FIELDS)
     bc_room: np.ndarray          # int32 [n_walls, 2], room index for BC_ROOM faces, else -1
     noise: list                  # per face: float32 [n_walls, noise_len, 2] (T, Pv) or None
     dt: float
@@ -101,6 +101,7 @@ class Workload:
     Lv: float = LV
     Psat: float = PSAT_REF
     rooms: dict | None = None    # room description (whole-building workloads)
+    vapour_frac: np.ndarray | None = None   # float64 [n_walls]: kTM = nu Lv kM inside the wall (None: 1)
 
     @property
     def n_walls(self) -> int:
@@ -128,13 +129,14 @@ class Workload:
             layer_par=self.layer_par[rows].copy(), T_init=self.T_init[walls].copy(),
             P_init=self.P_init[walls].copy(), bc_kind=self.bc_kind[walls].copy(),
             bc_par=self.bc_par[walls].copy(), bc_room=self.bc_room[walls].copy(),
-            noise=noise, rooms=None)
+            noise=noise, rooms=None,
+            vapour_frac=None if self.vapour_frac is None else self.vapour_frac[walls].copy())
 
 
 def _bc_row(hT, hM, T_mean, T_amp, P_mean, P_amp, period=86400.0, phase_T=0.0,
-            phase_P=0.0, noise_dt=3600.0, q_inf=0.0, g_inf=0.0) -> np.ndarray:
+            phase_P=0.0, noise_dt=3600.0, q_inf=0.0, g_inf=0.0, period_P=0.0) -> np.ndarray:
     return np.array([hT, hM, q_inf, g_inf, T_mean, T_amp, P_mean, P_amp, period,
-                     phase_T, phase_P, noise_dt], dtype=np.float64)
+                     phase_T, phase_P, noise_dt, period_P], dtype=np.float64)
 
 
 def uniform_wall(N: int, L: float, layer: dict, **kw) -> Workload:
@@ -157,7 +159,7 @@ def layered_wall(counts, L: float, layers, *, T0=293.0, P0=1000.0,
                             bc.get("T_amp", 0.0), bc.get("P_mean", P0), bc.get("P_amp", 0.0),
                             bc.get("period", 86400.0), bc.get("phase_T", 0.0),
                             bc.get("phase_P", 0.0), bc.get("noise_dt", 3600.0),
-                            bc.get("q_inf", 0.0), bc.get("g_inf", 0.0)))
+                            bc.get("q_inf", 0.0), bc.get("g_inf", 0.0), bc.get("period_P", 0.0)))
     return Workload(
         name=name, n_nodes=np.array([N], np.int32), thickness=np.array([L], np.float64),
         n_layers=np.array([len(counts)], np.int32), layer_first=first, layer_par=par,
@@ -195,7 +197,9 @@ def concat(workloads: list[Workload], name="batch") -> Workload:
         bc_kind=np.concatenate([w.bc_kind for w in workloads]),
         bc_par=np.concatenate([w.bc_par for w in workloads]),
         bc_room=np.concatenate([w.bc_room for w in workloads]),
-        noise=noise, rooms=None)
+        noise=noise, rooms=None,
+        vapour_frac=None if all(w.vapour_frac is None for w in workloads) else np.concatenate(
+            [np.ones(w.n_walls) if w.vapour_frac is None else w.vapour_frac for w in workloads]))
 
 
 def config1(seed: int = 1) -> Workload:
@@ -272,7 +276,7 @@ def config2(seed: int = 2, n_walls: int = 4096, n_steps: int = 52560, dt: float 
             pars.append([kM0, a, cM0, b, kTT, 0.0, cTT, 0.0, 0.0])
     horizon = n_steps * dt
     noise_len = int(math.ceil(horizon / 3600.0)) + 2
-    bc_par = np.zeros((n_walls, 2, 12))
+    bc_par = np.zeros((n_walls, 2, len(BC_FIELDS)))
     bc_par[:, 0] = _bc_row(25.0, 2e-8, 293.0, 10.0, 1200.0, 400.0)
     bc_par[:, 0, 9] = phase_T
     bc_par[:, 0, 10] = phase_P
@@ -294,7 +298,8 @@ def config2(seed: int = 2, n_walls: int = 4096, n_steps: int = 52560, dt: float 
 
 # Column order of a room parameter row (whole-building workloads).
 ROOM_FIELDS = ("volume", "ach", "Q_gain", "g_vap", "T_out_mean", "T_out_amp", "P_out_mean", "P_out_amp",
-               "period", "phase_T", "phase_P", "rho_a", "cp_a", "cp_v", "Pv_ref", "unused")
+               "period", "phase_T", "phase_P", "rho_a", "cp_a", "cp_v", "Pv_ref", "scheme", "period_P",
+               "g_pulse", "pulse_on", "pulse_off", "pulse_period")
 
 
 def config3(seed: int = 3, n_rooms: int = 64, walls_per_room: int = 6, n_steps: int = 8640,
@@ -321,7 +326,7 @@ def config3(seed: int = 3, n_rooms: int = 64, walls_per_room: int = 6, n_steps: 
     rk = stream_key(seed, rooms + (1 << 41))
     u = uniform(rk[:, None], np.arange(4)[None, :])
     V = 30.0 + 170.0 * u[:, 0]
-    par = np.zeros((n_rooms, 16))
+    par = np.zeros((n_rooms, len(ROOM_FIELDS)))
     par[:, 0] = V
     par[:, 1] = 0.5 + 1.5 * u[:, 1]
     par[:, 2] = 100.0 + 500.0 * u[:, 2]
@@ -349,7 +354,7 @@ class Section2D:
     region: np.ndarray           # uint8 [G, ny, nx] material region of every node
     region_par: np.ndarray       # float64 [G, n_regions, 9] (LAYER_FIELDS)
     bc_kind: np.ndarray          # int32 [G, 4] faces 0: x = 0, 1: x = Lx, 2: y = 0, 3: y = Ly
-    bc_par: np.ndarray           # float64 [G, 4, 12] (BC_FIELDS)
+    bc_par: np.ndarray           # float64 [G, 4, 13] (BC_FIELDS)
     noise: list                  # per face: float32 [G, noise_len, 2] or None
     T_init: np.ndarray           # float64 [G]
     P_init: np.ndarray           # float64 [G]
@@ -420,7 +425,7 @@ def config4(seed: int = 4, n_grids: int = 64, nx: int = 512, ny: int = 512, h: f
                          10.0 ** (CM0_LOG10_RANGE[0] + (CM0_LOG10_RANGE[1] - CM0_LOG10_RANGE[0]) * v[k, 2]),
                          2.0 * v[k, 3], 0.04 + 1.96 * v[k, 4], 0.0, 1e5 + 1.9e6 * v[k, 5], 0.0, 0.0]
     bc_kind = np.tile(np.array([BC_AMBIENT, BC_ADIABATIC, BC_AMBIENT, BC_ADIABATIC], np.int32), (n_grids, 1))
-    bc_par = np.zeros((n_grids, 4, 12))
+    bc_par = np.zeros((n_grids, 4, len(BC_FIELDS)))
     for f in (0, 2):
         bc_par[:, f] = _bc_row(25.0, 2e-8, 293.0, 10.0, 1200.0, 400.0)
         bc_par[:, f, 9] = 2 * np.pi * u[:, 6]
@@ -472,7 +477,7 @@ def config5(seed: int = 5, n_walls: int = 1024, n_nodes: int = 200, n_steps: int
                          10.0 ** (CM0_LOG10_RANGE[0] + (CM0_LOG10_RANGE[1] - CM0_LOG10_RANGE[0]) * v[l, 2]),
                          2.0 * v[l, 3], 0.04 + 1.96 * v[l, 4], 0.0, 1e5 + 1.9e6 * v[l, 5], 0.0, 0.0])
     noise_len = int(math.ceil(n_steps * dt / 3600.0)) + 2
-    bc_par = np.zeros((n_walls, 2, 12))
+    bc_par = np.zeros((n_walls, 2, len(BC_FIELDS)))
     bc_par[:, 0] = _bc_row(25.0, 2e-8, 293.0, 10.0, 1200.0, 400.0)
     bc_par[:, 0, 9] = 2 * np.pi * u[:, 2]
     bc_par[:, 0, 10] = 2 * np.pi * u[:, 3]
@@ -496,3 +501,54 @@ def config5(seed: int = 5, n_walls: int = 1024, n_nodes: int = 200, n_steps: int
     P = 1100.0 + 250.0 * np.sin(2 * np.pi * t / 86400.0 + psiP) + 30.0 * n1
     obs = np.stack([T, P], axis=-1).astype(np.float32)
     return wl, Sensors(obs=obs, sample_every=sample_every, wT=1.0, wP=1e-4)
+
+
+# The one-zone case of Sec. 5.2 (Table 2 walls; dimensionless data of Appendix B), in SI units.
+ONE_ZONE_WALLS = {  # cM, kM, cTT, kTT, cTM, kTM, hT outside, hM outside, area
+    "north": (1.82e-2, 5.89e-9, 7.7e5, 0.294, 1.52e3, 1.59e-2, 5.0, 2e-7, 18.0),
+    "south": (1.18e-1, 2.92e-8, 1.28e6, 0.841, 9.88e3, 2.96e-3, 25.0, 8e-7, 18.0),
+    "east": (6.09e-2, 5.47e-9, 8.61e5, 0.387, 5.09e3, 1.53e-2, 12.0, 4e-7, 9.0),
+    "west": (6.09e-2, 5.47e-9, 8.61e5, 0.387, 5.09e3, 1.53e-2, 12.0, 4e-7, 9.0),
+}
+
+
+def one_zone(N: int = 101, dt: float = 3.6, hours: float = 80.0) -> Workload:
+    """The paper's one-zone building (Sec. 5.2, Table 2, Appendix B): four 10 cm walls of linear
+    materials around one air zone, 80 h at dt = 3.6 s (dx = 1 mm with N = 101).
+
+    * walls north, south (18 m2 each), east, west (9 m2 each); constant coefficients from Table 2 with
+      cTM = chi cM and the cross conductivity kTM entering as the vapour fraction nu = kTM / (Lv kM)
+      (Lv = 2.5e6 J/kg; Appendix B's BiTM values follow from it with Pref = Pvi and Tref = Ti);
+    * face 0 outdoors with Table 2's hT, hM, face 1 on the zone with hT = 8 W/m2/K, hM = 3e-8 s/m;
+    * outdoor air (Appendix B): T = Ti (1 - 0.02 sin^2(2 pi t / 24 h)) = Ti (0.99 + 0.01 sin(2 pi t / 12 h
+      + pi/2)), Pv = Pvi (1 + 0.06 sin(2 pi t / 24 h)); the zone's ventilation (0.5 1/h) takes the same air;
+    * zone of 54 m3, vapour load 25 g/h plus 400 g/h from 6 h to 9 h each day (its latent heat Lv g
+      enters the air's heat balance, Sec. 5.1), no other gains;
+    * everything starts at Ti = 20 C, Pvi = 50 % of Psat(20 C) = 1168.5 Pa.
+    """
+    Ti, Pvi = 293.15, 0.5 * PSAT_REF
+    n_steps = int(round(hours * 3600.0 / dt))
+    walls = []
+    areas = []
+    nu = []
+    for name, (cM, kM, cTT, kTT, cTM, kTM, hT, hM, A) in ONE_ZONE_WALLS.items():
+        layer = dict(kM0=kM, a=0.0, cM0=cM, b=0.0, kTT0=kTT, aT=0.0, cTT0=cTT, bT=0.0, chi=cTM / cM)
+        bc0 = dict(hT=hT, hM=hM, T_mean=0.99 * Ti, T_amp=0.01 * Ti, period=43200.0, phase_T=0.5 * math.pi,
+                   P_mean=Pvi, P_amp=0.06 * Pvi, period_P=86400.0, phase_P=0.0)
+        bc1 = dict(hT=8.0, hM=3e-8, T_mean=Ti, P_mean=Pvi)
+        walls.append(uniform_wall(N, 0.1, layer, T0=Ti, P0=Pvi, bc0=bc0, bc1=bc1, dt=dt, n_steps=n_steps,
+                                  kinds=(BC_AMBIENT, BC_ROOM), name=name))
+        areas.append(A)
+        nu.append(kTM / (LV * kM))
+    wl = concat(walls, name=f"one-zone case: 4 walls N={N}, dt={dt:g} s x {n_steps}")
+    par = np.zeros((1, len(ROOM_FIELDS)))
+    row = dict(volume=54.0, ach=0.5, Q_gain=0.0, g_vap=25e-3 / 3600.0, T_out_mean=0.99 * Ti, T_out_amp=0.01 * Ti,
+               P_out_mean=Pvi, P_out_amp=0.06 * Pvi, period=43200.0, phase_T=0.5 * math.pi, phase_P=0.0,
+               rho_a=1.2, cp_a=1006.0, cp_v=1860.0, Pv_ref=1.61e5, scheme=0.0, period_P=86400.0,
+               g_pulse=400e-3 / 3600.0, pulse_on=6 * 3600.0, pulse_off=9 * 3600.0, pulse_period=86400.0)
+    par[0] = [row[k] for k in ROOM_FIELDS]
+    bc_room = np.full((4, 2), -1, np.int32)
+    bc_room[:, 1] = 0
+    return dataclasses.replace(wl, bc_room=bc_room, vapour_frac=np.array(nu),
+                               rooms=dict(par=par, wall_area=np.array(areas), Ta0=np.array([Ti]),
+                                          Pa0=np.array([Pvi])))

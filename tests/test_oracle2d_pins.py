@@ -24,12 +24,13 @@ def section(nx, ny, layer, bc, dt, n_steps=10, region=None, kinds=(0, 1, 0, 1), 
     layers = layer if isinstance(layer, list) else [layer]
     par = np.array([[[lay.get(k, 0.0) for k in wk.LAYER_FIELDS] for lay in layers]], np.float64)
     reg = np.zeros((1, ny, nx), np.uint8) if region is None else region[None].astype(np.uint8)
-    bc_par = np.zeros((1, 4, 12))
+    bc_par = np.zeros((1, 4, len(wk.BC_FIELDS)))
     for f in range(4):
         b = bc if isinstance(bc, dict) else bc[f]
         bc_par[0, f] = [b.get("hT", 0.0), b.get("hM", 0.0), b.get("q_inf", 0.0), b.get("g_inf", 0.0),
                         b.get("T_mean", T0), b.get("T_amp", 0.0), b.get("P_mean", P0), b.get("P_amp", 0.0),
-                        b.get("period", 86400.0), b.get("phase_T", 0.0), b.get("phase_P", 0.0), 3600.0]
+                        b.get("period", 86400.0), b.get("phase_T", 0.0), b.get("phase_P", 0.0), 3600.0,
+                        b.get("period_P", 0.0)]
     return wk.Section2D(name="test", h=h, region=reg, region_par=par, bc_kind=np.array([kinds], np.int32),
                         bc_par=bc_par, noise=[None] * 4, T_init=np.array([T0]), P_init=np.array([P0]),
                         dt=dt, t0=0.0, n_steps=n_steps, Lv=Lv)

@@ -441,7 +441,7 @@ def test_room_steady_state(oracle_mod, scheme):
         RMs.append((A, 1 / hM_out + sum(l / lay["kM0"] for l, lay in zip(Ls, layers)) + 1 / hM_in))
     wl = wk.concat(walls)
     wl.Lv = 0.0
-    par = np.zeros((1, 16))
+    par = np.zeros((1, len(wk.ROOM_FIELDS)))
     par[0, :15] = [V, ach, Q, g, To, 0.0, Po, 0.0, 86400.0, 0.0, 0.0, rho, cpa, cpv, Pref]
     par[0, 15] = scheme
     wl.rooms = dict(par=par, wall_area=np.array([s[3] for s in specs]), Ta0=np.array([291.0]), Pa0=np.array([950.0]))
