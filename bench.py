@@ -530,6 +530,42 @@ def bench_ours(args):
                                       "ms_per_run": ms3, "walls": wl3.n_walls, "rooms": 64,
                                       "note": "wall cell-updates/s; one block per room, FP64 room nodes"}
 
+    # the paper's one-zone case (Sec. 5.2: 4 walls + 1 zone, 80 h at dt = 3.6 s), FP32 and FP64; parity of
+    # the hourly surface samples against the oracle
+    if not args.no_fp64:
+        wl5 = wk.one_zone()
+        res = {}
+        for prec in ("fp32", "fp64"):
+            h = H.Hygro(wl5, precision=prec, device=local, stream=stream.cuda_stream)
+            smp = np.zeros((wl5.n_steps // 1000, wl5.n_walls, 2, 2), np.float32 if prec == "fp32" else np.float64)
+            with torch.cuda.stream(stream):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                h.run(wl5.n_steps, 1000, smp)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            ms5 = e0.elapsed_time(e1)
+            h.close()
+            res[prec] = {"value": wl5.total_nodes * wl5.n_steps / (ms5 / 1e3), "ms_per_run": ms5, "samples": smp}
+        out5 = {"value": res["fp32"]["value"], "unit": UNIT, "ms_per_run_fp32": res["fp32"]["ms_per_run"],
+                "ms_per_run_fp64": res["fp64"]["ms_per_run"],
+                "workload": "4 walls N=101 around one zone, 80 h at dt = 3.6 s (80 000 steps), FP32",
+                "note": "one block (the zone's); latency-bound, reported, not roofline-graded; the time includes the "
+                        "hourly samples copied to the host"}
+        if rank == 0 and not args.no_cpu_baseline:
+            import oracle
+
+            t = time.perf_counter()
+            r5 = oracle.Oracle(wl5).run(wl5.n_steps, 1000)
+            el5 = time.perf_counter() - t
+            ref = r5["samples"]
+            out5["parity_vs_oracle"] = {
+                prec: {f: float(np.max(np.abs(res[prec]["samples"][..., i] - ref[..., i])) / np.max(np.abs(ref[..., i])))
+                       for i, f in enumerate(("rel_linf_T", "rel_linf_P"))} for prec in ("fp32", "fp64")}
+            out5["oracle_seconds"] = el5
+        other["one_zone_80h"] = out5
+
     # gradient workload (1024 walls x 30 days, reverse-time adjoint)
     if not args.no_adjoint:
         other["adjoint_1024x200_30days"] = bench_adjoint(args, H, wk, stream, local, rank)

@@ -113,11 +113,11 @@ typedef struct {
 
 /* One face of one wall ([eq:HAM_BC]). For HYGRO_BC_AMBIENT the air state is
  *   T_inf(t)  = T_mean + T_amp sin(2 pi t/period + phase_T) + noise_T(t)
- *   Pv_inf(t) = P_mean + P_amp sin(2 pi t/period + phase_P) + noise_P(t)
- * (the sinusoid is dropped when period <= 0), noise(t) being the linear
- * interpolation at t/noise_dt of the table noise[k][2] = (T, Pv), k = 0 ..
- * noise_len-1, held at its end values outside it. HYGRO_BC_ROOM faces see
- * the air of room `room` at level n (paper Sec. 5.2 [eq:wbse_tn_exp]).
+ *   Pv_inf(t) = P_mean + P_amp sin(2 pi t/period_P + phase_P) + noise_P(t)
+ * (the T sinusoid is dropped when period <= 0; period_P <= 0 means period_P = period, and the Pv
+ * sinusoid is dropped when that is <= 0), noise(t) being the linear interpolation at t/noise_dt of the
+ * table noise[k][2] = (T, Pv), k = 0 .. noise_len-1, held at its end values outside it. HYGRO_BC_ROOM
+ * faces see the air of room `room` at level n (paper Sec. 5.2 [eq:wbse_tn_exp]).
  * HYGRO_BC_ADIABATIC faces exchange nothing. */
 typedef struct {
     int32_t kind;
@@ -128,22 +128,27 @@ typedef struct {
     const float *noise;        /* host memory, [noise_len][2], or NULL (copied) */
     int32_t noise_len;
     double noise_dt;
+    double period_P;           /* period of the Pv sinusoid, s (<= 0: period) */
 } hygro_bc;
 
 /* One room: a perfectly mixed air zone (paper Sec. 5.1, [eq:LAV_equation], [eq:LAV_couplage]).
  * Air state Ta (K) and Pva (Pa), humidity ratio w = Pva / Pv_ref. Per step, with the wall surface
  * values Ts, Pvs of the room's walls at level n (explicit coupling, Sec. 5.2 [eq:wbse_tn_exp]):
- *   rho V / Pv_ref dPva/dt = g_vap + gv (w_out - w) + sum_walls A hM (Pvs - Pva)
- *   rho V (cp_a + cp_v w) dTa/dt = Q_gain + Lv g_vap + gv cp_a (T_out - Ta) + Lv gv (w_out - w)
+ *   rho V / Pv_ref dPva/dt = g(t) + gv (w_out - w) + sum_walls A hM (Pvs - Pva)
+ *   rho V (cp_a + cp_v w) dTa/dt = Q_gain + Lv g(t) + gv cp_a (T_out - Ta) + Lv gv (w_out - w)
  *                                  + sum_walls A [hT (Ts - Ta) + Lv hM (Pvs - Pva)]
- * gv = rho V ach / 3600 (kg/s), outdoor air T_out, Pv_out as the ambient sinusoid of hygro_bc
- * (no noise). Each room equation is advanced as one more DF node (its own value at level n replaced
- * by the mean of levels n+1 and n-1; the heat capacity at level n), vapour first. */
+ * gv = rho V ach / 3600 (kg/s), outdoor air T_out, Pv_out as the ambient sinusoids of hygro_bc
+ * (no noise). The vapour production g(t) = g_vap, plus g_pulse while pulse_on <= (t mod pulse_period)
+ * < pulse_off (no pulse when pulse_period <= 0): the occupants' load of Sec. 5.1, whose latent heat
+ * Q_o = Lv g enters the heat balance. Each room equation is advanced as one more DF node (its own value
+ * at level n replaced by the mean of levels n+1 and n-1; the heat capacity at level n), vapour first. */
 typedef struct {
     double volume, ach, Q_gain, g_vap;   /* m^3, 1/h, W, kg/s */
     double T_out_mean, T_out_amp, P_out_mean, P_out_amp, period, phase_T, phase_P;
     double rho_a, cp_a, cp_v, Pv_ref;    /* kg/m^3, J/kg/K, J/kg/K, Pa */
     double Ta0, Pa0;                     /* initial air state (both stored levels) */
+    double period_P;                     /* period of the outdoor Pv sinusoid, s (<= 0: period) */
+    double g_pulse, pulse_on, pulse_off, pulse_period;   /* kg/s, s, s, s */
 } hygro_room;
 
 /* Most walls one room may have (each wall has at most one face on a room). */
@@ -182,6 +187,13 @@ HYGRO_API hygro_status hygro_set_rooms(hygro_ctx *ctx, int32_t n_rooms, const hy
 
 /* Set an option (HYGRO_OPT_*) of the context; it applies from the next run. */
 HYGRO_API hygro_status hygro_set_option(hygro_ctx *ctx, int32_t option, int64_t value);
+
+/* Share of the moisture permeability that carries latent heat, per wall: the cross conductivity of
+ * the heat equation is kTM = nu Lv kM at the faces inside the wall (paper Sec. 2: kTM = Lv delta_v with
+ * delta_v the vapour part of kM), while the surface exchange keeps Lv hM ([eq:HAM_BC]). nu[w] >= 0,
+ * finite; the default is 1 (kTM = Lv kM). nu (host memory, [n_walls]) is copied; it may be set at any
+ * time and applies from the next step. The adjoint (hygro_loss_grad) supports nu = 1 only. */
+HYGRO_API hygro_status hygro_set_vapour_fraction(hygro_ctx *ctx, const double *nu);
 
 /* Room air state of level 0 (n) or 1 (n-1): Ta[n_rooms], Pa[n_rooms] (host or device memory). */
 HYGRO_API hygro_status hygro_get_rooms(hygro_ctx *ctx, int32_t level, double *Ta, double *Pa);

@@ -154,11 +154,9 @@ __device__ __forceinline__ void ambient_at(const FaceInfo &fi, const float2 *noi
 {
     T = (float)fi.T_mean_dev;
     P = (float)fi.P_mean_dev;
-    if (fi.period > 0.0) {
-        const uint64_t un = (uint64_t)n;
-        T = fmaf((float)fi.T_amp, sin_turns_fx(fi.phT0 + un * fi.pstep), T);
-        P = fmaf((float)fi.P_amp, sin_turns_fx(fi.phP0 + un * fi.pstep), P);
-    }
+    const uint64_t un = (uint64_t)n;
+    if (fi.period > 0.0) T = fmaf((float)fi.T_amp, sin_turns_fx(fi.phT0 + un * fi.pstep), T);
+    if (fi.period_P > 0.0) P = fmaf((float)fi.P_amp, sin_turns_fx(fi.phP0 + un * fi.pstepP), P);
     if (fi.noise_len > 0) {
         // position = npos0 + n * nstep up to the last table entry (from step n_hi on the table is held
         // at its end, and the product is not formed, so it cannot overflow)
@@ -178,10 +176,8 @@ __device__ __forceinline__ void ambient_at(const FaceInfo &fi, const float2 *noi
     const double two_pi = 6.283185307179586476925286766559;
     T = fi.T_mean_dev;
     P = fi.P_mean_dev;
-    if (fi.period > 0.0) {
-        T += fi.T_amp * sin(two_pi * t / fi.period + fi.phase_T);
-        P += fi.P_amp * sin(two_pi * t / fi.period + fi.phase_P);
-    }
+    if (fi.period > 0.0) T += fi.T_amp * sin(two_pi * t / fi.period + fi.phase_T);
+    if (fi.period_P > 0.0) P += fi.P_amp * sin(two_pi * t / fi.period_P + fi.phase_P);
     if (fi.noise_len > 0 && fi.noise_dt > 0.0) {
         const float2 *tab = noise + fi.noise_off;
         const double x = t / fi.noise_dt;

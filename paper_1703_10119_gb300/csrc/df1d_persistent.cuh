@@ -38,6 +38,9 @@ struct LaneCtx {
     real hM0, hT0, q0, g0;    // face-0 exchange (lane 0 only, else 0)
     real hM1, hT1, q1, g1;    // face-1 exchange (lane Wl-1 only, else 0)
     real hMs, hTs, qs, gs;    // this lane's face exchange (sum of the two sets above)
+    real Lvn;                 // Lv nu: latent heat carried by the moisture flux inside the wall (kTM = nu Lv kM)
+    real cs0, cs1;            // Lv (1 - nu) hM of the face-0 / face-1 surface (0 elsewhere and when nu = 1)
+    bool nu_corr;             // nu != 1 (warp-uniform)
     uint32_t imask;           // bit k: slot k is the first node of a layer >= 1 (its left face is an interface)
     uint32_t wimask;          // OR of imask bits 1.. over the warp (warp-uniform)
     int l0;                   // layer of slot 0
@@ -211,7 +214,12 @@ __device__ __forceinline__ void df_step(real (&Tp)[K], const real (&Tc)[K], real
             numT = fma(FTl, Tl, fma(FTr, Tr, -ST * tp));
         if (k == 0) numT += L.q0;
         if (k == K - 1) numT += L.q1;
-        numT = fma(Lv, X, numT);
+        numT = fma(L.Lvn, X, numT);
+        if (L.nu_corr) {
+            // X holds the surface exchange too, whose latent heat is Lv hM (Pinf - Pbar) whatever nu
+            if (k == 0) numT = fma(L.cs0, fP - fma(half, dP, pp), numT);
+            if (k == K - 1) numT = fma(L.cs1, fP - fma(half, dP, pp), numT);
+        }
         real dT;
         if (SIMPLE) {
             real r;
@@ -282,17 +290,21 @@ static __device__ __noinline__ void room_update(RoomShared &rs, const RoomInfo &
     const double rhoV = q[RP_RHOA] * q[RP_VOL];
     const double gv = rhoV * q[RP_ACH] / 3600.0;
     double T_out = q[RP_TMEAN], P_out = q[RP_PMEAN];
-    if (q[RP_PERIOD] > 0.0) {
-        T_out += q[RP_TAMP] * sin(two_pi * t / q[RP_PERIOD] + q[RP_PHT]);
-        P_out += q[RP_PAMP] * sin(two_pi * t / q[RP_PERIOD] + q[RP_PHP]);
+    if (q[RP_PERIOD] > 0.0) T_out += q[RP_TAMP] * sin(two_pi * t / q[RP_PERIOD] + q[RP_PHT]);
+    if (q[RP_PERIODP] > 0.0) P_out += q[RP_PAMP] * sin(two_pi * t / q[RP_PERIODP] + q[RP_PHP]);
+    // vapour production: the base load plus the daily pulse (occupants' load of Sec. 5.1)
+    double g = q[RP_GVAP];
+    if (q[RP_PPER] > 0.0) {
+        const double ph = fmod(t, q[RP_PPER]);
+        if (ph >= q[RP_PON] && ph < q[RP_POFF]) g += q[RP_GPULSE];
     }
     const double Pref = q[RP_PVREF];
     const double w_out = P_out / Pref;
     if (q[RP_SCHEME] == (double)HYGRO_ROOM_EULER) {
         // explicit Euler of Sec. 5.2: every term at level n
-        const double Pa_n = rs.Pa_c + dt * Pref / rhoV * (q[RP_GVAP] + gv * (w_out - rs.Pa_c / Pref) + AhMPs - AhM * rs.Pa_c);
+        const double Pa_n = rs.Pa_c + dt * Pref / rhoV * (g + gv * (w_out - rs.Pa_c / Pref) + AhMPs - AhM * rs.Pa_c);
         const double CT = rhoV * (q[RP_CPA] + q[RP_CPV] * rs.Pa_c / Pref);
-        const double rhs = q[RP_QGAIN] + Lv * q[RP_GVAP] + gv * q[RP_CPA] * (T_out - rs.Ta_c) +
+        const double rhs = q[RP_QGAIN] + Lv * g + gv * q[RP_CPA] * (T_out - rs.Ta_c) +
                            Lv * gv * (w_out - rs.Pa_c / Pref) + AhTTs - AhT * rs.Ta_c + Lv * (AhMPs - AhM * rs.Pa_c);
         const double Ta_n = rs.Ta_c + dt / CT * rhs;
         rs.Ta_p = rs.Ta_c;
@@ -303,11 +315,11 @@ static __device__ __noinline__ void room_update(RoomShared &rs, const RoomInfo &
     }
     const double a_p = rhoV / Pref / (2.0 * dt);
     const double k_p = gv / Pref + AhM;
-    const double Pa_n = ((a_p - 0.5 * k_p) * rs.Pa_p + q[RP_GVAP] + gv * w_out + AhMPs) / (a_p + 0.5 * k_p);
+    const double Pa_n = ((a_p - 0.5 * k_p) * rs.Pa_p + g + gv * w_out + AhMPs) / (a_p + 0.5 * k_p);
     const double Pa_bar = 0.5 * (Pa_n + rs.Pa_p);
     const double a_t = rhoV * (q[RP_CPA] + q[RP_CPV] * rs.Pa_c / Pref) / (2.0 * dt);
     const double k_t = gv * q[RP_CPA] + AhT;
-    const double rhs = q[RP_QGAIN] + Lv * q[RP_GVAP] + gv * q[RP_CPA] * T_out + Lv * gv * (w_out - Pa_bar / Pref) +
+    const double rhs = q[RP_QGAIN] + Lv * g + gv * q[RP_CPA] * T_out + Lv * gv * (w_out - Pa_bar / Pref) +
                        AhTTs + Lv * (AhMPs - AhM * Pa_bar);
     const double Ta_n = ((a_t - 0.5 * k_t) * rs.Ta_p + rhs) / (a_t + 0.5 * k_t);
     rs.Ta_p = rs.Ta_c;
@@ -393,6 +405,10 @@ __device__ __forceinline__ void lane_setup(const DevCtx<real> &d, const WallInfo
     L.qs = L.q0 + L.q1;
     L.gs = L.g0 + L.g1;
     const real Lv = (real)d.Lv;
+    L.Lvn = (real)(d.Lv * wi.nu);
+    L.nu_corr = wi.nu != 1.0;
+    L.cs0 = (real)(d.Lv * (1.0 - wi.nu)) * L.hM0;
+    L.cs1 = (real)(d.Lv * (1.0 - wi.nu)) * L.hM1;
     const real Tref = d.Tref[w], Pref = d.Pref[w];
     L.FTin = L.m2FTin = L.FTl0c = L.FTbc = real(0);
     L.rT0 = L.rTm = L.rTK2 = L.rTK1 = real(1);

@@ -74,7 +74,8 @@ __global__ void __launch_bounds__(256)
     const real Lv = (real)d.Lv;
     const real hm = hM * (fP - Pbar);
     real numT = fma(FTl, Tl - tp, FTr * (Tr - tp));
-    numT = fma(Lv, fma(FMl, Pl - Pbar, FMr * (Pr - Pbar)), numT);
+    // latent heat of the moisture flux inside the wall (kTM = nu Lv kM); the surface keeps Lv hM
+    numT = fma((real)(d.Lv * wi.nu), fma(FMl, Pl - Pbar, FMr * (Pr - Pbar)), numT);
     numT = fma(-c.chi * A, dP, numT);
     numT = fma(hT, fT - tp, fma(Lv, hm, numT + qi));
     const real denT = fma(half, FTl + FTr + hT, B);
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(256)
     const real *tab = d.layer_tab + (size_t)wi.layer_off * kLayerStride;
     const int l = d.node_layer[g];
     const LayerC<real> c = load_layer(tab, l);
-    const real half = real(0.5), Lv = (real)d.Lv;
+    const real half = real(0.5), Lv = (real)d.Lv, LvN = (real)(d.Lv * wi.nu);
     double *bT = bal + (size_t)w * 8, *bP = bT + 4;
     const real wgt = (j == 0 || j == N - 1) ? half : real(1);
     const real A = fma(c.Ab, Pc[g], c.Aa) * wgt, B = fma(c.Bb, Pc[g], c.Ba) * wgt;
@@ -145,10 +146,10 @@ __global__ void __launch_bounds__(256)
         const real Tb0 = half * (Tn[g] + Tp[g]), Tb1 = half * (Tn[g + 1] + Tp[g + 1]);
         const real eP = (Pc[g + 1] - Pb1) + (Pc[g] - Pb0), eT = (Tc[g + 1] - Tb1) + (Tc[g] - Tb0);
         atomicAdd(bP + 2, (double)(FM * eP));
-        atomicAdd(bT + 2, (double)fma(FT, eT, Lv * FM * eP));
+        atomicAdd(bT + 2, (double)fma(FT, eT, LvN * FM * eP));
         atomicAdd(bP + 3, (double)(FM * (fabs(Pc[g + 1] - Pb0) + fabs(Pc[g] - Pb1))));
         atomicAdd(bT + 3, (double)(FT * (fabs(Tc[g + 1] - Tb0) + fabs(Tc[g] - Tb1)) +
-                                   Lv * FM * (fabs(Pc[g + 1] - Pb0) + fabs(Pc[g] - Pb1))));
+                                   LvN * FM * (fabs(Pc[g + 1] - Pb0) + fabs(Pc[g] - Pb1))));
     }
     const int face = j == 0 ? 0 : (j == N - 1 ? 1 : -1);
     if (face >= 0) {
@@ -219,7 +220,7 @@ __global__ void __launch_bounds__(128) df1d_euler_start_kernel(const DevCtx<real
     const real hM1 = a1 ? (real)f1.hM : real(0), hT1 = a1 ? (real)f1.hT : real(0);
     const real g0 = a0 ? (real)f0.g_inf : real(0), q0 = a0 ? (real)f0.q_inf : real(0);
     const real g1 = a1 ? (real)f1.g_inf : real(0), q1 = a1 ? (real)f1.q_inf : real(0);
-    const real Lv = (real)d.Lv, two_dt = (real)(2.0 * d.dt);
+    const real Lv = (real)d.Lv, LvN = (real)(d.Lv * wi.nu), two_dt = (real)(2.0 * d.dt);
     if (tid == 0) s_red[0] = d.dt;
     __syncthreads();
     // face conductances of node j (kh sums, harmonic across layers); left and right
@@ -276,11 +277,11 @@ __global__ void __launch_bounds__(128) df1d_euler_start_kernel(const DevCtx<real
             real rP = real(0), rT = real(0);
             if (j > 0) {
                 rP = fma(FMl, P[j - 1] - P[j], rP);
-                rT = fma(FTl, T[j - 1] - T[j], fma(Lv * FMl, P[j - 1] - P[j], rT));
+                rT = fma(FTl, T[j - 1] - T[j], fma(LvN * FMl, P[j - 1] - P[j], rT));
             }
             if (j < N - 1) {
                 rP = fma(FMr, P[j + 1] - P[j], rP);
-                rT = fma(FTr, T[j + 1] - T[j], fma(Lv * FMr, P[j + 1] - P[j], rT));
+                rT = fma(FTr, T[j + 1] - T[j], fma(LvN * FMr, P[j + 1] - P[j], rT));
             }
             if (j == 0 && a0) {
                 double x, y;

@@ -85,8 +85,8 @@ hygro_status check_bc(const hygro_bc &b, bool allow_room, double t0, double dt, 
             *why = "non-finite value";
             return HYGRO_E_INVALID;
         }
-    if (!finite_nonneg(b.period)) {
-        *why = "period must be >= 0";
+    if (!finite_nonneg(b.period) || !finite_nonneg(b.period_P)) {
+        *why = "period and period_P must be >= 0";
         return HYGRO_E_INVALID;
     }
     if (b.noise_len < 0) {
@@ -131,15 +131,20 @@ FaceInfo face_info(const hygro_bc &b, double T_ref, double P_ref, double t0, dou
     o.T_amp = b.T_amp;
     o.P_mean_dev = b.P_mean - P_ref;
     o.P_amp = b.P_amp;
-    o.period = b.period;
+    o.period = b.period > 0 ? b.period : 0.0;
+    const double pP = b.period_P > 0 ? b.period_P : b.period;
+    o.period_P = pP > 0 ? pP : 0.0;
     o.phase_T = b.phase_T;
     o.phase_P = b.phase_P;
     o.noise_dt = b.noise_dt;
     const double two_pi = 6.283185307179586476925286766559;
-    if (b.period > 0) {
-        o.phT0 = turns_fixed(t0 / b.period + b.phase_T / two_pi);
-        o.phP0 = turns_fixed(t0 / b.period + b.phase_P / two_pi);
-        o.pstep = turns_fixed(dt / b.period);
+    if (o.period > 0) {
+        o.phT0 = turns_fixed(t0 / o.period + b.phase_T / two_pi);
+        o.pstep = turns_fixed(dt / o.period);
+    }
+    if (o.period_P > 0) {
+        o.phP0 = turns_fixed(t0 / o.period_P + b.phase_P / two_pi);
+        o.pstepP = turns_fixed(dt / o.period_P);
     }
     if (noise_len > 0) {
         o.noise_len = (int32_t)noise_len;
@@ -469,6 +474,11 @@ hygro_status build_schedule(hygro_ctx *c)
             const double pv[15] = {q.volume, q.ach, q.Q_gain, q.g_vap, q.T_out_mean, q.T_out_amp, q.P_out_mean,
                                    q.P_out_amp, q.period, q.phase_T, q.phase_P, q.rho_a, q.cp_a, q.cp_v, q.Pv_ref};
             for (int k = 0; k < 15; ++k) o.par[k] = pv[k];
+            o.par[RP_PERIODP] = q.period_P > 0 ? q.period_P : q.period;
+            o.par[RP_GPULSE] = q.g_pulse;
+            o.par[RP_PON] = q.pulse_on;
+            o.par[RP_POFF] = q.pulse_off;
+            o.par[RP_PPER] = q.pulse_period;
             o.par[RP_SCHEME] = (double)c->room_scheme;
             c->room_warps = std::max(c->room_warps, (int)o.n_walls);
         }
@@ -649,6 +659,7 @@ hygro_status hygro_create(const hygro_desc *desc, hygro_ctx **out)
         WallInfo &wi = c->walls[w];
         memset(&wi, 0, sizeof wi);
         wi.N = c->N[w];
+        wi.nu = 1.0;
         const int32_t zero = 0;
         wall_layout(wi.N, &zero, 1, wi);
         wi.node_off = (int32_t)off;
@@ -854,11 +865,14 @@ hygro_status hygro_set_rooms(hygro_ctx *c, int32_t n_rooms, const hygro_room *ro
     for (int r = 0; r < n_rooms; ++r) {
         const hygro_room &q = rooms[r];
         const double v[] = {q.volume, q.ach, q.Q_gain, q.g_vap, q.T_out_mean, q.T_out_amp, q.P_out_mean, q.P_out_amp,
-                            q.period, q.phase_T, q.phase_P, q.rho_a, q.cp_a, q.cp_v, q.Pv_ref, q.Ta0, q.Pa0};
+                            q.period, q.phase_T, q.phase_P, q.rho_a, q.cp_a, q.cp_v, q.Pv_ref, q.Ta0, q.Pa0,
+                            q.period_P, q.g_pulse, q.pulse_on, q.pulse_off, q.pulse_period};
         for (double x : v)
             if (!std::isfinite(x)) return fail(c, HYGRO_E_INVALID, "room %d: non-finite value", r);
-        if (!(q.volume > 0 && q.rho_a > 0 && q.cp_a > 0 && q.Pv_ref > 0 && q.ach >= 0 && q.period >= 0))
-            return fail(c, HYGRO_E_INVALID, "room %d: volume, rho_a, cp_a, Pv_ref must be > 0, ach, period >= 0", r);
+        if (!(q.volume > 0 && q.rho_a > 0 && q.cp_a > 0 && q.Pv_ref > 0 && q.ach >= 0 && q.period >= 0 &&
+              q.period_P >= 0 && q.pulse_period >= 0))
+            return fail(c, HYGRO_E_INVALID,
+                        "room %d: volume, rho_a, cp_a, Pv_ref must be > 0, ach, period, period_P, pulse_period >= 0", r);
     }
     if (n_rooms > 0)
         for (int w = 0; w < c->W; ++w)
@@ -889,6 +903,19 @@ hygro_status hygro_set_rooms(hygro_ctx *c, int32_t n_rooms, const hygro_room *ro
         CUDA_TRY(c, cudaMemcpy(c->d_room_state, st.data(), st.size() * sizeof(double), cudaMemcpyHostToDevice));
     c->have_rooms = true;
     return build_schedule(c);
+}
+
+hygro_status hygro_set_vapour_fraction(hygro_ctx *c, const double *nu)
+{
+    if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    if (nu == nullptr) return fail(c, HYGRO_E_INVALID, "nu is NULL");
+    for (int w = 0; w < c->W; ++w)
+        if (!finite_nonneg(nu[w])) return fail(c, HYGRO_E_INVALID, "wall %d: nu must be finite and >= 0", w);
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (int w = 0; w < c->W; ++w) c->walls[w].nu = nu[w];
+    CUDA_TRY(c, cudaMemcpy(c->d_walls, c->walls.data(), c->walls.size() * sizeof(WallInfo), cudaMemcpyHostToDevice));
+    return HYGRO_OK;
 }
 
 hygro_status hygro_set_option(hygro_ctx *c, int32_t option, int64_t value)
@@ -1354,10 +1381,13 @@ hygro_status hygro_loss_grad(hygro_ctx *c, int64_t n_steps, int32_t sample_every
     if (K > 0 && obs == nullptr) return fail(c, HYGRO_E_INVALID, "obs is NULL");
     if (!(c->have_materials && c->have_bc[0] && c->have_bc[1]))
         return fail(c, HYGRO_E_STATE, "hygro_set_materials and hygro_set_bc (both faces) must come first");
-    for (int w = 0; w < c->W; ++w)
+    for (int w = 0; w < c->W; ++w) {
         for (int f = 0; f < 2; ++f)
             if (c->bc[f][w].bc.kind == HYGRO_BC_ROOM)
                 return fail(c, HYGRO_E_UNSUPPORTED, "wall %d has a room face: the adjoint runs walls without rooms", w);
+        if (c->walls[w].nu != 1.0)
+            return fail(c, HYGRO_E_UNSUPPORTED, "wall %d: the adjoint takes kTM = Lv kM (vapour fraction 1)", w);
+    }
     int64_t C = checkpoint_every > 0 ? checkpoint_every : (int64_t)std::ceil(std::sqrt((double)n_steps));
     if (C > n_steps) C = n_steps;
     if (C > (1 << 20)) return fail(c, HYGRO_E_UNSUPPORTED, "checkpoint stride too long");

@@ -55,6 +55,7 @@ struct WallInfo {
     int32_t layer_off;    // first layer entry of this wall
     int16_t aligned;      // 1 when every layer interface falls on a lane boundary
     int16_t simple;       // 1 when kTT, cTT do not depend on Pv and cTM = 0 in every layer
+    double nu;            // latent share of kM: kTM = nu Lv kM at the faces inside the wall
 };
 
 struct FaceInfo {
@@ -67,9 +68,11 @@ struct FaceInfo {
     double T_mean_dev, T_amp;        // T_mean - T_ref
     double P_mean_dev, P_amp;        // P_mean - P_ref
     double period, phase_T, phase_P, noise_dt;
+    double period_P;      // period of the Pv sinusoid (0: none)
     // fixed-point forms used by the FP32 kernels:
     uint64_t phT0, phP0;  // fraction of a period at step 0, scaled by 2^64 (sinusoid phase incl. phase_T/P)
-    uint64_t pstep;       // fraction of a period per step, scaled by 2^64
+    uint64_t pstep;       // fraction of the T period per step, scaled by 2^64
+    uint64_t pstepP;      // fraction of the Pv period per step, scaled by 2^64
     int64_t npos0;        // noise table position at step 0, scaled by 2^40
     int64_t nstep;        // noise table positions per step, scaled by 2^40
     int64_t n_hi;         // first step whose position reaches the last table entry (held from there on)
@@ -81,10 +84,11 @@ struct RoomInfo {
     int32_t wall[HYGRO_MAX_ROOM_WALLS];   // ascending wall indices
     int32_t face[HYGRO_MAX_ROOM_WALLS];   // which face of the wall is on the room
     double area[HYGRO_MAX_ROOM_WALLS];    // m^2
-    double par[16];                       // hygro_room fields volume .. Pv_ref, then the room scheme
+    double par[21];                       // hygro_room fields volume .. Pv_ref, the room scheme, then
+                                          // period_P, g_pulse, pulse_on, pulse_off, pulse_period
 };
 enum { RP_VOL = 0, RP_ACH, RP_QGAIN, RP_GVAP, RP_TMEAN, RP_TAMP, RP_PMEAN, RP_PAMP, RP_PERIOD, RP_PHT, RP_PHP,
-       RP_RHOA, RP_CPA, RP_CPV, RP_PVREF, RP_SCHEME };
+       RP_RHOA, RP_CPA, RP_CPV, RP_PVREF, RP_SCHEME, RP_PERIODP, RP_GPULSE, RP_PON, RP_POFF, RP_PPER };
 
 template <typename real>
 struct DevCtx {

@@ -39,7 +39,7 @@ ABI_FUNCTIONS = ("hygro_create", "hygro_set_materials", "hygro_set_bc", "hygro_r
                  "hygro_fluxes", "hygro_get_fields", "hygro_set_fields", "hygro_get_step", "hygro_get_state",
                  "hygro_set_state", "hygro_last_error", "hygro_destroy", "hygro_run_noalloc", "hygro_set_rooms",
                  "hygro_get_rooms", "hygro_loss_grad", "hygro_balance", "hygro_set_option",
-                 "hygro_start_euler")
+                 "hygro_start_euler", "hygro_set_vapour_fraction")
 # Exported entry points of the 2D sections (names of include/hygro2d.h).
 ABI_FUNCTIONS_2D = ("hygro2d_create", "hygro2d_set_materials", "hygro2d_set_bc", "hygro2d_run", "hygro2d_sync",
                     "hygro2d_get_fields", "hygro2d_set_fields", "hygro2d_get_step", "hygro2d_last_error",
@@ -69,13 +69,14 @@ class hygro_bc(C.Structure):
                 ("q_inf", C.c_double), ("g_inf", C.c_double), ("T_mean", C.c_double), ("T_amp", C.c_double),
                 ("P_mean", C.c_double), ("P_amp", C.c_double), ("period", C.c_double), ("phase_T", C.c_double),
                 ("phase_P", C.c_double), ("noise", C.c_void_p), ("noise_len", C.c_int32),
-                ("noise_dt", C.c_double)]
+                ("noise_dt", C.c_double), ("period_P", C.c_double)]
 
 
 class hygro_room(C.Structure):
     _fields_ = [(n, C.c_double) for n in ("volume", "ach", "Q_gain", "g_vap", "T_out_mean", "T_out_amp",
                                           "P_out_mean", "P_out_amp", "period", "phase_T", "phase_P", "rho_a",
-                                          "cp_a", "cp_v", "Pv_ref", "Ta0", "Pa0")]
+                                          "cp_a", "cp_v", "Pv_ref", "Ta0", "Pa0", "period_P", "g_pulse",
+                                          "pulse_on", "pulse_off", "pulse_period")]
 
 
 class HygroError(RuntimeError):
@@ -116,6 +117,7 @@ def lib(build_if_missing: bool = False) -> C.CDLL:
         "hygro_set_fields": [P, C.c_int32, P, P],
         "hygro_balance": [P, P],
         "hygro_set_option": [P, C.c_int32, C.c_int64],
+        "hygro_set_vapour_fraction": [P, P],
         "hygro_start_euler": [P],
         "hygro_get_step": [P, C.POINTER(C.c_int64)],
         "hygro_get_state": [P, P, C.POINTER(C.c_size_t)],
@@ -253,6 +255,10 @@ def hygro_set_option(ctx, option: int, value: int):
     _check(lib().hygro_set_option(ctx, int(option), int(value)), ctx)
 
 
+def hygro_set_vapour_fraction(ctx, nu):
+    _check(lib().hygro_set_vapour_fraction(ctx, _ptr(np.ascontiguousarray(nu, np.float64))), ctx)
+
+
 def hygro_get_rooms(ctx, level: int, Ta=None, Pa=None):
     _check(lib().hygro_get_rooms(ctx, int(level), _ptr(Ta), _ptr(Pa)), ctx)
 
@@ -323,15 +329,15 @@ def hygro2d_destroy(ctx):
 
 
 def _bc_array(n: int, kind, par, noise):
-    """hygro_bc[n] from kinds [n], rows [n, 12] and an optional noise table [n, len, 2] (kept alive by
-    the caller)."""
+    """hygro_bc[n] from kinds [n], rows [n, 13] (BC_FIELDS) and an optional noise table [n, len, 2] (kept
+    alive by the caller)."""
     arr = (hygro_bc * n)()
     for i in range(n):
         p = par[i]
         b = arr[i]
         b.kind = int(kind[i])
         (b.hT, b.hM, b.q_inf, b.g_inf, b.T_mean, b.T_amp, b.P_mean, b.P_amp, b.period, b.phase_T,
-         b.phase_P, b.noise_dt) = [float(x) for x in p]
+         b.phase_P, b.noise_dt, b.period_P) = [float(x) for x in p]
         if noise is not None:
             b.noise = noise[i].ctypes.data
             b.noise_len = noise.shape[1]
@@ -360,6 +366,8 @@ class Hygro:
             self.set_bc()
             if wl.rooms:
                 self.set_rooms()
+            if wl.vapour_frac is not None:
+                hygro_set_vapour_fraction(self.ctx, wl.vapour_frac)
         except Exception:
             hygro_destroy(self.ctx)
             self.ctx = None
@@ -391,7 +399,8 @@ class Hygro:
         par = np.asarray(rm["par"], np.float64)
         arr = (hygro_room * len(par))()
         for r in range(len(par)):
-            arr[r] = hygro_room(*[float(x) for x in par[r, :15]], float(rm["Ta0"][r]), float(rm["Pa0"][r]))
+            arr[r] = hygro_room(*[float(x) for x in par[r, :15]], float(rm["Ta0"][r]), float(rm["Pa0"][r]),
+                                *[float(x) for x in par[r, 16:21]])
         hygro_set_rooms(self.ctx, len(par), arr, np.ascontiguousarray(rm["wall_area"], np.float64))
         if par.shape[1] > 15 and np.any(par[:, 15] == 1.0):
             # the room rows' scheme slot (the oracle's layout): explicit Euler rooms

@@ -50,13 +50,14 @@ def mixed_sections(G, nx, ny, n_steps, seed=5, n_regions=4, dt=60.0, h=1e-3):
                          rng.uniform(0, 2), rng.uniform(0.04, 2), rng.uniform(0, 0.3), rng.uniform(1e5, 2e6),
                          rng.uniform(0, 0.3), 8.36e4]
     kinds = np.zeros((G, 4), np.int32)
-    bc = np.zeros((G, 4, 12))
+    bc = np.zeros((G, 4, len(wk.BC_FIELDS)))
     for g in range(G):
         for f in range(4):
             kinds[g, f] = wk.BC_AMBIENT if f in (0, 2) or (g + f) % 3 == 0 else wk.BC_ADIABATIC
             bc[g, f] = [rng.uniform(5, 25), rng.uniform(1e-8, 3e-8), rng.uniform(-20, 20), rng.uniform(-1e-7, 1e-7),
                         rng.uniform(285, 300), rng.uniform(2, 10), rng.uniform(900, 1300), rng.uniform(100, 400),
-                        rng.choice([86400.0, 3600.0 * 7]), rng.uniform(0, 6.28), rng.uniform(0, 6.28), 1800.0]
+                        rng.choice([86400.0, 3600.0 * 7]), rng.uniform(0, 6.28), rng.uniform(0, 6.28), 1800.0,
+                        rng.choice([0.0, 3600.0 * 5])]
     nl = int(np.ceil(n_steps * dt / 1800.0)) + 2
     nz0 = np.stack([rng.normal(0, 1.0, (G, nl)), rng.normal(0, 50.0, (G, nl))], -1).astype(np.float32)
     nz2 = np.stack([rng.normal(0, 1.0, (G, nl)), rng.normal(0, 50.0, (G, nl))], -1).astype(np.float32)

@@ -49,7 +49,36 @@ def test_exports_nothing_else(lib):
 def test_struct_sizes_match_header_layout():
     assert C.sizeof(H.hygro_layer) == 9 * 8
     assert C.sizeof(H.hygro_desc) == 4 + 4 + 8 + 8 + 8 * 4 + 4 * 3 + 4 + 8
-    assert C.sizeof(H.hygro_bc) == 8 + 8 * 11 + 8 + 8 + 8
+    assert C.sizeof(H.hygro_bc) == 8 + 8 * 11 + 8 + 8 + 8 + 8
+    assert C.sizeof(H.hygro_room) == 22 * 8
+
+
+def test_struct_layout_matches_the_c_compiler(tmp_path):
+    """Size and field offsets of the binding's structs against the C compiler's reading of the header."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {"hygro_desc": H.hygro_desc, "hygro_layer": H.hygro_layer, "hygro_bc": H.hygro_bc,
+               "hygro_room": H.hygro_room}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "hygro.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for f in cls._fields_:
+            lines.append(f'printf("{name} {f[0]} %zu\\n", offsetof({name}, {f[0]}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = {tuple(l.split()[:2]): int(l.split()[2]) for l in out if l.strip()}
+    for name, cls in structs.items():
+        assert got[(name, "size")] == C.sizeof(cls), name
+        for f in cls._fields_:
+            assert got[(name, f[0])] == getattr(cls, f[0]).offset, (name, f[0])
 
 
 def test_create_rejects_bad_arguments_before_touching_the_device(lib):
