@@ -588,7 +588,7 @@ def bench_ours(args):
                 b = arr[w]
                 b.kind = int(wl.bc_kind[w, f])
                 (b.hT, b.hM, b.q_inf, b.g_inf, b.T_mean, b.T_amp, b.P_mean, b.P_amp, b.period, b.phase_T,
-                 b.phase_P, b.noise_dt) = map(float, wl.bc_par[w, f])
+                 b.phase_P, b.noise_dt, b.period_P) = map(float, wl.bc_par[w, f])
                 if noise[f] is not None:
                     b.noise = noise[f][w].ctypes.data
                     b.noise_len = noise[f].shape[1]

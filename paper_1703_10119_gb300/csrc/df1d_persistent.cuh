@@ -38,8 +38,8 @@ struct LaneCtx {
     real hM0, hT0, q0, g0;    // face-0 exchange (lane 0 only, else 0)
     real hM1, hT1, q1, g1;    // face-1 exchange (lane Wl-1 only, else 0)
     real hMs, hTs, qs, gs;    // this lane's face exchange (sum of the two sets above)
-    real Lvn;                 // Lv nu: latent heat carried by the moisture flux inside the wall (kTM = nu Lv kM)
-    real cs0, cs1;            // Lv (1 - nu) hM of the face-0 / face-1 surface (0 elsewhere and when nu = 1)
+    real Lvn;                 // Lv nu: latent heat carried by the moisture flux inside the wall (kTM = nu Lv kM;
+                              // simple-heat variants are only used with nu = 1)
     bool nu_corr;             // nu != 1 (warp-uniform)
     uint32_t imask;           // bit k: slot k is the first node of a layer >= 1 (its left face is an interface)
     uint32_t wimask;          // OR of imask bits 1.. over the warp (warp-uniform)
@@ -214,11 +214,15 @@ __device__ __forceinline__ void df_step(real (&Tp)[K], const real (&Tc)[K], real
             numT = fma(FTl, Tl, fma(FTr, Tr, -ST * tp));
         if (k == 0) numT += L.q0;
         if (k == K - 1) numT += L.q1;
-        numT = fma(L.Lvn, X, numT);
-        if (L.nu_corr) {
-            // X holds the surface exchange too, whose latent heat is Lv hM (Pinf - Pbar) whatever nu
-            if (k == 0) numT = fma(L.cs0, fP - fma(half, dP, pp), numT);
-            if (k == K - 1) numT = fma(L.cs1, fP - fma(half, dP, pp), numT);
+        if (SIMPLE) {
+            numT = fma(Lv, X, numT);   // simple-heat walls have nu = 1
+        } else {
+            numT = fma(L.Lvn, X, numT);
+            if (L.nu_corr) {
+                // X holds the surface exchange too, whose latent heat is Lv hM (Pinf - Pbar) whatever nu
+                if (k == 0) numT = fma((Lv - L.Lvn) * L.hM0, fP - fma(half, dP, pp), numT);
+                if (k == K - 1) numT = fma((Lv - L.Lvn) * L.hM1, fP - fma(half, dP, pp), numT);
+            }
         }
         real dT;
         if (SIMPLE) {
@@ -407,8 +411,6 @@ __device__ __forceinline__ void lane_setup(const DevCtx<real> &d, const WallInfo
     const real Lv = (real)d.Lv;
     L.Lvn = (real)(d.Lv * wi.nu);
     L.nu_corr = wi.nu != 1.0;
-    L.cs0 = (real)(d.Lv * (1.0 - wi.nu)) * L.hM0;
-    L.cs1 = (real)(d.Lv * (1.0 - wi.nu)) * L.hM1;
     const real Tref = d.Tref[w], Pref = d.Pref[w];
     L.FTin = L.m2FTin = L.FTl0c = L.FTbc = real(0);
     L.rT0 = L.rTm = L.rTK2 = L.rTK1 = real(1);

@@ -776,7 +776,7 @@ hygro_status hygro_set_materials(hygro_ctx *c, const int32_t *n_layers, const in
         wi.n_layers = n_layers[w];
         wi.layer_off = (int32_t)lo;
         wall_layout(wi.N, layer_first + lo, wi.n_layers, wi);
-        wi.simple = 1;
+        wi.simple = wi.nu == 1.0 ? 1 : 0;
         for (int l = 0; l < wi.n_layers; ++l) {
             const hygro_layer &y = layers[lo + l];
             if (y.aT != 0.0 || y.bT != 0.0 || y.chi != 0.0) wi.simple = 0;
@@ -913,8 +913,25 @@ hygro_status hygro_set_vapour_fraction(hygro_ctx *c, const double *nu)
         if (!finite_nonneg(nu[w])) return fail(c, HYGRO_E_INVALID, "wall %d: nu must be finite and >= 0", w);
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
     CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    for (int w = 0; w < c->W; ++w) c->walls[w].nu = nu[w];
+    size_t lo = 0;
+    for (int w = 0; w < c->W; ++w) {
+        WallInfo &wi = c->walls[w];
+        wi.nu = nu[w];
+        // the simple-heat code variant assumes nu = 1
+        if (c->have_materials) {
+            wi.simple = wi.nu == 1.0 ? 1 : 0;
+            for (int l = 0; l < c->n_layers[w]; ++l) {
+                const hygro_layer &y = c->layers[lo + l];
+                if (y.aT != 0.0 || y.bT != 0.0 || y.chi != 0.0) wi.simple = 0;
+            }
+            lo += c->n_layers[w];
+        }
+    }
     CUDA_TRY(c, cudaMemcpy(c->d_walls, c->walls.data(), c->walls.size() * sizeof(WallInfo), cudaMemcpyHostToDevice));
+    if (c->have_materials) {
+        const hygro_status st = build_schedule(c);
+        if (st != HYGRO_OK) return st;
+    }
     return HYGRO_OK;
 }
 

@@ -54,7 +54,7 @@ struct WallInfo {
     int32_t n_layers;
     int32_t layer_off;    // first layer entry of this wall
     int16_t aligned;      // 1 when every layer interface falls on a lane boundary
-    int16_t simple;       // 1 when kTT, cTT do not depend on Pv and cTM = 0 in every layer
+    int16_t simple;       // 1 when kTT, cTT do not depend on Pv and cTM = 0 in every layer, and nu = 1
     double nu;            // latent share of kM: kTM = nu Lv kM at the faces inside the wall
 };
 
