@@ -266,33 +266,25 @@ __device__ __forceinline__ void df_step(real (&Tp)[K], const real (&Tc)[K], real
     fg = hm + L.gs;
 }
 
-// Air state of a room and the level-n surface values of its walls, shared by the room's warps.
+constexpr int kRoomAirChunk = 32;   // steps of outdoor air and vapour production computed at a time
+
+// Air state of a room and the level-n surface values of its walls, shared by the room's warps; the
+// outdoor air and vapour production of the current chunk of steps.
 struct RoomShared {
     double Ta_p, Ta_c, Pa_p, Pa_c;        // levels n-1 and n
     double surfT[HYGRO_MAX_ROOM_WALLS];   // room-side surface T of each wall at level n
     double surfP[HYGRO_MAX_ROOM_WALLS];
+    double airT[kRoomAirChunk], airP[kRoomAirChunk], gvap[kRoomAirChunk];
 };
 
-// Room air node of Sec. 5.1 advanced from level n to n+1 in FP64 with the walls' level-n surface
-// values (explicit coupling of [eq:wbse_tn_exp]); the room's own value in its balance is the mean of
-// levels n+1 and n-1 (one more DF node), vapour first, heat capacity at level n.
-static __device__ __noinline__ void room_update(RoomShared &rs, const RoomInfo &ri, const FaceInfo *faces, int64_t n,
-                                         double t0, double dt, double Lv)
+// Outdoor air (T_out, Pv_out) and vapour production g of the steps n_first .. n_first + 31 (lane i: step
+// n_first + i; the whole warp).
+static __device__ __forceinline__ void room_air_chunk(RoomShared &rs, const RoomInfo &ri, int64_t n_first, double t0,
+                                                      double dt, int lane)
 {
     const double *q = ri.par;
-    double AhT = 0.0, AhM = 0.0, AhTTs = 0.0, AhMPs = 0.0;
-    for (int i = 0; i < ri.n_walls; ++i) {
-        const FaceInfo &fc = faces[(size_t)ri.wall[i] * 2 + ri.face[i]];
-        const double A = ri.area[i];
-        AhT += A * fc.hT;
-        AhM += A * fc.hM;
-        AhTTs += A * fc.hT * rs.surfT[i];
-        AhMPs += A * fc.hM * rs.surfP[i];
-    }
     const double two_pi = 6.283185307179586476925286766559;
-    const double t = t0 + (double)n * dt;
-    const double rhoV = q[RP_RHOA] * q[RP_VOL];
-    const double gv = rhoV * q[RP_ACH] / 3600.0;
+    const double t = t0 + (double)(n_first + lane) * dt;
     double T_out = q[RP_TMEAN], P_out = q[RP_PMEAN];
     if (q[RP_PERIOD] > 0.0) T_out += q[RP_TAMP] * sin(two_pi * t / q[RP_PERIOD] + q[RP_PHT]);
     if (q[RP_PERIODP] > 0.0) P_out += q[RP_PAMP] * sin(two_pi * t / q[RP_PERIODP] + q[RP_PHP]);
@@ -302,7 +294,50 @@ static __device__ __noinline__ void room_update(RoomShared &rs, const RoomInfo &
         const double ph = fmod(t, q[RP_PPER]);
         if (ph >= q[RP_PON] && ph < q[RP_POFF]) g += q[RP_GPULSE];
     }
-    const double Pref = q[RP_PVREF];
+    rs.airT[lane] = T_out;
+    rs.airP[lane] = P_out;
+    rs.gvap[lane] = g;
+}
+
+// Time-independent parts of a room's update.
+struct RoomConst {
+    double AhT, AhM;          // sums over the room's walls of A hT, A hM
+    double rhoV, gv, Pref;
+};
+
+static __device__ __forceinline__ RoomConst room_const(const RoomInfo &ri, const FaceInfo *faces)
+{
+    RoomConst k;
+    const double *q = ri.par;
+    k.AhT = 0.0;
+    k.AhM = 0.0;
+    for (int i = 0; i < ri.n_walls; ++i) {
+        const FaceInfo &fc = faces[(size_t)ri.wall[i] * 2 + ri.face[i]];
+        k.AhT += ri.area[i] * fc.hT;
+        k.AhM += ri.area[i] * fc.hM;
+    }
+    k.rhoV = q[RP_RHOA] * q[RP_VOL];
+    k.gv = k.rhoV * q[RP_ACH] / 3600.0;
+    k.Pref = q[RP_PVREF];
+    return k;
+}
+
+// Room air node of Sec. 5.1 advanced from level n to n+1 in FP64 with the walls' level-n surface
+// values (explicit coupling of [eq:wbse_tn_exp]); the room's own value in its balance is the mean of
+// levels n+1 and n-1 (one more DF node), vapour first, heat capacity at level n. T_out, P_out, g: the
+// outdoor air and vapour production at t^n.
+static __device__ void room_update(RoomShared &rs, const RoomConst &k, const RoomInfo &ri, const FaceInfo *faces,
+                                   double T_out, double P_out, double g, double dt, double Lv)
+{
+    const double *q = ri.par;
+    double AhTTs = 0.0, AhMPs = 0.0;
+    for (int i = 0; i < ri.n_walls; ++i) {
+        const FaceInfo &fc = faces[(size_t)ri.wall[i] * 2 + ri.face[i]];
+        const double A = ri.area[i];
+        AhTTs += A * fc.hT * rs.surfT[i];
+        AhMPs += A * fc.hM * rs.surfP[i];
+    }
+    const double AhT = k.AhT, AhM = k.AhM, rhoV = k.rhoV, gv = k.gv, Pref = k.Pref;
     const double w_out = P_out / Pref;
     if (q[RP_SCHEME] == (double)HYGRO_ROOM_EULER) {
         // explicit Euler of Sec. 5.2: every term at level n
@@ -557,7 +592,6 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
     const double Tref_d = (double)Tref, Pref_d = (double)Pref;
     const int wib = threadIdx.x >> 5;
     real acc_q = real(0), acc_g = real(0);
-    int64_t n_cur = n0;
     auto one_step = [&](auto &Tp_, auto &Tc_, auto &Pp_, auto &Pc_, real bT, real bP, int src) {
         real fT = __shfl_sync(FULL, bT, src);
         real fP = __shfl_sync(FULL, bP, src);
@@ -586,11 +620,9 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
                 rs->surfT[wib] = Tref_d + (double)ts;
                 rs->surfP[wib] = Pref_d + (double)ps;
             }
-            __syncthreads();
-            if (threadIdx.x == 0) room_update(*rs, d.rooms[blockIdx.x], d.faces, n_cur, d.t0, d.dt, d.Lv);
+            __syncthreads();   // the room warp advances the room air between the two barriers
             __syncthreads();
         }
-        ++n_cur;
     };
 
     int s = 0;

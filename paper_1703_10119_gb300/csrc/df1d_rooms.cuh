@@ -1,8 +1,10 @@
-// Room kernel of the whole-building model: one block per room, one warp per wall facing the room.
-// Each step every wall advances with the room air at level n on its room face, then the walls
-// publish their level-n surface values, the block synchronises, thread 0 advances the room air node
-// in FP64 (paper Sec. 5.1-5.2), and the block synchronises again. Every thread passes exactly two
-// block barriers per step (warps without a wall run an empty loop of the same barriers).
+// Room kernel of the whole-building model: one block per room, one warp per wall facing the room, and
+// one more warp (the last) for the room air. Each step every wall advances with the room air at level n
+// on its room face, then the walls publish their level-n surface values, the block synchronises, the
+// room warp advances the room air node in FP64 (paper Sec. 5.1-5.2), and the block synchronises again.
+// The room warp computes the outdoor air and vapour production of 32 steps at a time, one step per
+// lane, while the walls compute. Every thread passes exactly two block barriers per step (warps
+// without a wall run an empty loop of the same barriers).
 #pragma once
 
 #include "df1d_persistent.cuh"
@@ -10,7 +12,7 @@
 namespace hygro {
 
 template <typename real>
-__global__ void __launch_bounds__(HYGRO_MAX_ROOM_WALLS * 32, 1)
+__global__ void __launch_bounds__((HYGRO_MAX_ROOM_WALLS + 1) * 32, 1)
     df1d_room_kernel(const DevCtx<real> d, int64_t n0, int32_t n_steps, int32_t sample_every, real *samples)
 {
     __shared__ RoomShared rs;
@@ -27,7 +29,23 @@ __global__ void __launch_bounds__(HYGRO_MAX_ROOM_WALLS * 32, 1)
     }
     __syncthreads();
     bool ran = false;
-    if (wib < ri.n_walls) {
+    const int room_warp = (int)(blockDim.x >> 5) - 1;
+    if (wib == room_warp) {
+        const RoomConst k = room_const(ri, d.faces);
+        for (int s = 0; s < n_steps; ++s) {
+            if (s % kRoomAirChunk == 0) {
+                room_air_chunk(rs, ri, n0 + s, d.t0, d.dt, lane);
+                __syncwarp();
+            }
+            __syncthreads();   // the walls' level-n surface values are in rs
+            if (lane == 0) {
+                const int i = s % kRoomAirChunk;
+                room_update(rs, k, ri, d.faces, rs.airT[i], rs.airP[i], rs.gvap[i], d.dt, d.Lv);
+            }
+            __syncthreads();
+        }
+        ran = true;
+    } else if (wib < ri.n_walls) {
         const int w = ri.wall[wib];
         const WallInfo wi = d.walls[w];
         for (int i = lane; i < wi.n_layers * kLayerStride; i += 32)
