@@ -269,18 +269,53 @@ __device__ __forceinline__ void df_step(real (&Tp)[K], const real (&Tc)[K], real
 constexpr int kRoomAirChunk = 32;   // steps of outdoor air and vapour production computed at a time
 
 // Air state of a room and the level-n surface values of its walls, shared by the room's warps; the
-// outdoor air and vapour production of the current chunk of steps.
+// time-dependent sources of the current chunk of steps.
 struct RoomShared {
     double Ta_p, Ta_c, Pa_p, Pa_c;        // levels n-1 and n
     double surfT[HYGRO_MAX_ROOM_WALLS];   // room-side surface T of each wall at level n
     double surfP[HYGRO_MAX_ROOM_WALLS];
-    double airT[kRoomAirChunk], airP[kRoomAirChunk], gvap[kRoomAirChunk];
+    double srcP[kRoomAirChunk];           // g + gv w_out
+    double srcT[kRoomAirChunk];           // Q_gain + Lv g + gv cp_a T_out + Lv gv w_out (w_out = Pv_out / Pv_ref)
 };
 
-// Outdoor air (T_out, Pv_out) and vapour production g of the steps n_first .. n_first + 31 (lane i: step
-// n_first + i; the whole warp).
-static __device__ __forceinline__ void room_air_chunk(RoomShared &rs, const RoomInfo &ri, int64_t n_first, double t0,
-                                                      double dt, int lane)
+// Time-independent parts of a room's update (FP64).
+struct RoomConst {
+    double AhT[HYGRO_MAX_ROOM_WALLS], AhM[HYGRO_MAX_ROOM_WALLS];   // A hT, A hM of each wall
+    double sAhT, sAhM;        // their sums
+    double rhoV, gv, Pref;
+    double a_p, k_p;          // vapour node: capacity rho V / Pv_ref / (2 dt), conductance gv / Pv_ref + sum A hM
+    double at0, at1;          // heat capacity rho V (cp_a + cp_v Pv / Pv_ref) / (2 dt) = at0 + at1 Pv
+    double k_t;               // gv cp_a + sum A hT
+};
+
+static __device__ __forceinline__ RoomConst room_const(const RoomInfo &ri, const FaceInfo *faces, double dt)
+{
+    RoomConst k;
+    const double *q = ri.par;
+    k.sAhT = 0.0;
+    k.sAhM = 0.0;
+    for (int i = 0; i < ri.n_walls; ++i) {
+        const FaceInfo &fc = faces[(size_t)ri.wall[i] * 2 + ri.face[i]];
+        k.AhT[i] = ri.area[i] * fc.hT;
+        k.AhM[i] = ri.area[i] * fc.hM;
+        k.sAhT += k.AhT[i];
+        k.sAhM += k.AhM[i];
+    }
+    k.rhoV = q[RP_RHOA] * q[RP_VOL];
+    k.gv = k.rhoV * q[RP_ACH] / 3600.0;
+    k.Pref = q[RP_PVREF];
+    k.a_p = k.rhoV / k.Pref / (2.0 * dt);
+    k.k_p = k.gv / k.Pref + k.sAhM;
+    k.at0 = k.rhoV * q[RP_CPA] / (2.0 * dt);
+    k.at1 = k.rhoV * q[RP_CPV] / k.Pref / (2.0 * dt);
+    k.k_t = k.gv * q[RP_CPA] + k.sAhT;
+    return k;
+}
+
+// Outdoor air and vapour production of the steps n_first .. n_first + 31 (lane i: step n_first + i; the
+// whole warp), as the time-dependent sources of the room balances.
+static __device__ __forceinline__ void room_air_chunk(RoomShared &rs, const RoomInfo &ri, const RoomConst &k,
+                                                      int64_t n_first, double t0, double dt, double Lv, int lane)
 {
     const double *q = ri.par;
     const double two_pi = 6.283185307179586476925286766559;
@@ -294,57 +329,31 @@ static __device__ __forceinline__ void room_air_chunk(RoomShared &rs, const Room
         const double ph = fmod(t, q[RP_PPER]);
         if (ph >= q[RP_PON] && ph < q[RP_POFF]) g += q[RP_GPULSE];
     }
-    rs.airT[lane] = T_out;
-    rs.airP[lane] = P_out;
-    rs.gvap[lane] = g;
-}
-
-// Time-independent parts of a room's update.
-struct RoomConst {
-    double AhT, AhM;          // sums over the room's walls of A hT, A hM
-    double rhoV, gv, Pref;
-};
-
-static __device__ __forceinline__ RoomConst room_const(const RoomInfo &ri, const FaceInfo *faces)
-{
-    RoomConst k;
-    const double *q = ri.par;
-    k.AhT = 0.0;
-    k.AhM = 0.0;
-    for (int i = 0; i < ri.n_walls; ++i) {
-        const FaceInfo &fc = faces[(size_t)ri.wall[i] * 2 + ri.face[i]];
-        k.AhT += ri.area[i] * fc.hT;
-        k.AhM += ri.area[i] * fc.hM;
-    }
-    k.rhoV = q[RP_RHOA] * q[RP_VOL];
-    k.gv = k.rhoV * q[RP_ACH] / 3600.0;
-    k.Pref = q[RP_PVREF];
-    return k;
+    const double w_out = P_out / k.Pref;
+    rs.srcP[lane] = g + k.gv * w_out;
+    rs.srcT[lane] = q[RP_QGAIN] + Lv * g + k.gv * q[RP_CPA] * T_out + Lv * k.gv * w_out;
 }
 
 // Room air node of Sec. 5.1 advanced from level n to n+1 in FP64 with the walls' level-n surface
 // values (explicit coupling of [eq:wbse_tn_exp]); the room's own value in its balance is the mean of
-// levels n+1 and n-1 (one more DF node), vapour first, heat capacity at level n. T_out, P_out, g: the
-// outdoor air and vapour production at t^n.
-static __device__ void room_update(RoomShared &rs, const RoomConst &k, const RoomInfo &ri, const FaceInfo *faces,
-                                   double T_out, double P_out, double g, double dt, double Lv)
+// levels n+1 and n-1 (one more DF node), vapour first, heat capacity at level n:
+//   a_p (Pa+ - Pa-) = srcP + sum A hM Pvs - k_p Pabar,   k_p = gv / Pv_ref + sum A hM
+//   a_t (Ta+ - Ta-) = srcT + sum A hT Ts + Lv sum A hM Pvs - Lv k_p Pabar - k_t Tabar,  k_t = gv cp_a + sum A hT
+// i is the step's entry in the chunk.
+static __device__ void room_update(RoomShared &rs, const RoomConst &k, const RoomInfo &ri, int i, double dt,
+                                   double Lv)
 {
     const double *q = ri.par;
     double AhTTs = 0.0, AhMPs = 0.0;
-    for (int i = 0; i < ri.n_walls; ++i) {
-        const FaceInfo &fc = faces[(size_t)ri.wall[i] * 2 + ri.face[i]];
-        const double A = ri.area[i];
-        AhTTs += A * fc.hT * rs.surfT[i];
-        AhMPs += A * fc.hM * rs.surfP[i];
+    for (int w = 0; w < ri.n_walls; ++w) {
+        AhTTs = fma(k.AhT[w], rs.surfT[w], AhTTs);
+        AhMPs = fma(k.AhM[w], rs.surfP[w], AhMPs);
     }
-    const double AhT = k.AhT, AhM = k.AhM, rhoV = k.rhoV, gv = k.gv, Pref = k.Pref;
-    const double w_out = P_out / Pref;
     if (q[RP_SCHEME] == (double)HYGRO_ROOM_EULER) {
         // explicit Euler of Sec. 5.2: every term at level n
-        const double Pa_n = rs.Pa_c + dt * Pref / rhoV * (g + gv * (w_out - rs.Pa_c / Pref) + AhMPs - AhM * rs.Pa_c);
-        const double CT = rhoV * (q[RP_CPA] + q[RP_CPV] * rs.Pa_c / Pref);
-        const double rhs = q[RP_QGAIN] + Lv * g + gv * q[RP_CPA] * (T_out - rs.Ta_c) +
-                           Lv * gv * (w_out - rs.Pa_c / Pref) + AhTTs - AhT * rs.Ta_c + Lv * (AhMPs - AhM * rs.Pa_c);
+        const double Pa_n = rs.Pa_c + dt * k.Pref / k.rhoV * (rs.srcP[i] + AhMPs - k.k_p * rs.Pa_c);
+        const double CT = 2.0 * dt * fma(k.at1, rs.Pa_c, k.at0);
+        const double rhs = rs.srcT[i] + AhTTs + Lv * AhMPs - Lv * k.k_p * rs.Pa_c - k.k_t * rs.Ta_c;
         const double Ta_n = rs.Ta_c + dt / CT * rhs;
         rs.Ta_p = rs.Ta_c;
         rs.Ta_c = Ta_n;
@@ -352,15 +361,11 @@ static __device__ void room_update(RoomShared &rs, const RoomConst &k, const Roo
         rs.Pa_c = Pa_n;
         return;
     }
-    const double a_p = rhoV / Pref / (2.0 * dt);
-    const double k_p = gv / Pref + AhM;
-    const double Pa_n = ((a_p - 0.5 * k_p) * rs.Pa_p + g + gv * w_out + AhMPs) / (a_p + 0.5 * k_p);
+    const double Pa_n = (fma(k.a_p - 0.5 * k.k_p, rs.Pa_p, rs.srcP[i]) + AhMPs) / (k.a_p + 0.5 * k.k_p);
     const double Pa_bar = 0.5 * (Pa_n + rs.Pa_p);
-    const double a_t = rhoV * (q[RP_CPA] + q[RP_CPV] * rs.Pa_c / Pref) / (2.0 * dt);
-    const double k_t = gv * q[RP_CPA] + AhT;
-    const double rhs = q[RP_QGAIN] + Lv * g + gv * q[RP_CPA] * T_out + Lv * gv * (w_out - Pa_bar / Pref) +
-                       AhTTs + Lv * (AhMPs - AhM * Pa_bar);
-    const double Ta_n = ((a_t - 0.5 * k_t) * rs.Ta_p + rhs) / (a_t + 0.5 * k_t);
+    const double a_t = fma(k.at1, rs.Pa_c, k.at0);
+    const double rhs = rs.srcT[i] + AhTTs + Lv * (AhMPs - k.k_p * Pa_bar);
+    const double Ta_n = fma(a_t - 0.5 * k.k_t, rs.Ta_p, rhs) / (a_t + 0.5 * k.k_t);
     rs.Ta_p = rs.Ta_c;
     rs.Ta_c = Ta_n;
     rs.Pa_p = rs.Pa_c;

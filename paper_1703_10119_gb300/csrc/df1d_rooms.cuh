@@ -31,17 +31,14 @@ __global__ void __launch_bounds__((HYGRO_MAX_ROOM_WALLS + 1) * 32, 1)
     bool ran = false;
     const int room_warp = (int)(blockDim.x >> 5) - 1;
     if (wib == room_warp) {
-        const RoomConst k = room_const(ri, d.faces);
+        const RoomConst k = room_const(ri, d.faces, d.dt);
         for (int s = 0; s < n_steps; ++s) {
             if (s % kRoomAirChunk == 0) {
-                room_air_chunk(rs, ri, n0 + s, d.t0, d.dt, lane);
+                room_air_chunk(rs, ri, k, n0 + s, d.t0, d.dt, d.Lv, lane);
                 __syncwarp();
             }
             __syncthreads();   // the walls' level-n surface values are in rs
-            if (lane == 0) {
-                const int i = s % kRoomAirChunk;
-                room_update(rs, k, ri, d.faces, rs.airT[i], rs.airP[i], rs.gvap[i], d.dt, d.Lv);
-            }
+            if (lane == 0) room_update(rs, k, ri, s % kRoomAirChunk, d.dt, d.Lv);
             __syncthreads();
         }
         ran = true;
