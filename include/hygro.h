@@ -68,7 +68,7 @@ typedef enum {
     HYGRO_E_STATE = -4,        /* call out of order (e.g. run before set_materials / set_bc) */
     HYGRO_E_NONFINITE = -5,    /* a wall produced a NaN or infinity */
     HYGRO_E_TIMEOUT = -6,      /* a bounded device wait gave up */
-    HYGRO_E_UNSUPPORTED = -7   /* valid request this build does not handle (e.g. N too large) */
+    HYGRO_E_UNSUPPORTED = -7   /* valid request the library does not handle (e.g. N too large) */
 } hygro_status;
 
 enum { HYGRO_FP32 = 0, HYGRO_FP64 = 1 };
