@@ -271,9 +271,10 @@ constexpr int kRoomAirChunk = 32;   // steps of outdoor air and vapour productio
 // Air state of a room and the level-n surface values of its walls, shared by the room's warps; the
 // time-dependent sources of the current chunk of steps.
 struct RoomShared {
-    double Ta_p, Ta_c, Pa_p, Pa_c;        // levels n-1 and n
-    double surfT[HYGRO_MAX_ROOM_WALLS];   // room-side surface T of each wall at level n
-    double surfP[HYGRO_MAX_ROOM_WALLS];
+    double Ta_p, Ta_c, Pa_p, Pa_c;        // levels n-1 and n (the room warp's own history)
+    double airT[2], airP[2];              // room air of level n for the walls, slot n & 1
+    double surfT[2][HYGRO_MAX_ROOM_WALLS];   // room-side surface T of each wall at level n, slot n & 1
+    double surfP[2][HYGRO_MAX_ROOM_WALLS];
     double srcP[kRoomAirChunk];           // g + gv w_out
     double srcT[kRoomAirChunk];           // Q_gain + Lv g + gv cp_a T_out + Lv gv w_out (w_out = Pv_out / Pv_ref)
 };
@@ -339,15 +340,15 @@ static __device__ __forceinline__ void room_air_chunk(RoomShared &rs, const Room
 // levels n+1 and n-1 (one more DF node), vapour first, heat capacity at level n:
 //   a_p (Pa+ - Pa-) = srcP + sum A hM Pvs - k_p Pabar,   k_p = gv / Pv_ref + sum A hM
 //   a_t (Ta+ - Ta-) = srcT + sum A hT Ts + Lv sum A hM Pvs - Lv k_p Pabar - k_t Tabar,  k_t = gv cp_a + sum A hT
-// i is the step's entry in the chunk.
-static __device__ void room_update(RoomShared &rs, const RoomConst &k, const RoomInfo &ri, int i, double dt,
+// i is the step's entry in the chunk, b the buffer of the level-n surface values.
+static __device__ void room_update(RoomShared &rs, const RoomConst &k, const RoomInfo &ri, int i, int b, double dt,
                                    double Lv)
 {
     const double *q = ri.par;
     double AhTTs = 0.0, AhMPs = 0.0;
     for (int w = 0; w < ri.n_walls; ++w) {
-        AhTTs = fma(k.AhT[w], rs.surfT[w], AhTTs);
-        AhMPs = fma(k.AhM[w], rs.surfP[w], AhMPs);
+        AhTTs = fma(k.AhT[w], rs.surfT[b][w], AhTTs);
+        AhMPs = fma(k.AhM[w], rs.surfP[b][w], AhMPs);
     }
     if (q[RP_SCHEME] == (double)HYGRO_ROOM_EULER) {
         // explicit Euler of Sec. 5.2: every term at level n
@@ -592,18 +593,34 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
     const bool f_ambient = ff.kind == HYGRO_BC_AMBIENT;
 
     // room coupling: the lane of the room face takes the room air at level n as its ambient air and
-    // publishes its level-n surface values for the room update
+    // publishes its surface values for the room update. Step n reads the room air of level n and writes
+    // the wall's level-n+1 surface values, while the room warp advances the room from the level-n
+    // values (both double-buffered by level parity); one block barrier per step.
     const int room_lane = room_face == 0 ? 0 : Wl - 1;
     const double Tref_d = (double)Tref, Pref_d = (double)Pref;
     const int wib = threadIdx.x >> 5;
     real acc_q = real(0), acc_g = real(0);
+    int64_t n_cur = n0;
+    auto publish = [&](const real (&T_)[K], const real (&P_)[K], int b) {
+        if (lane == room_lane) {
+            const int slot = room_face == 0 ? 0 : K - 1;
+            real ts = T_[0], ps = P_[0];
+#pragma unroll
+            for (int k = 1; k < K; ++k) {
+                ts = k == slot ? T_[k] : ts;
+                ps = k == slot ? P_[k] : ps;
+            }
+            rs->surfT[b][wib] = Tref_d + (double)ts;
+            rs->surfP[b][wib] = Pref_d + (double)ps;
+        }
+    };
     auto one_step = [&](auto &Tp_, auto &Tc_, auto &Pp_, auto &Pc_, real bT, real bP, int src) {
         real fT = __shfl_sync(FULL, bT, src);
         real fP = __shfl_sync(FULL, bP, src);
         if (ROOM) {
             if (lane == room_lane) {
-                fT = (real)(rs->Ta_c - Tref_d);
-                fP = (real)(rs->Pa_c - Pref_d);
+                fT = (real)(rs->airT[n_cur & 1] - Tref_d);
+                fP = (real)(rs->airP[n_cur & 1] - Pref_d);
             }
         }
         real fq, fg;
@@ -614,21 +631,15 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
         last_g = fg;
         sample(Tp_, Pp_);
         if (ROOM) {
-            if (lane == room_lane) {
-                const int slot = room_face == 0 ? 0 : K - 1;
-                real ts = Tc_[0], ps = Pc_[0];
-#pragma unroll
-                for (int k = 1; k < K; ++k) {
-                    ts = k == slot ? Tc_[k] : ts;
-                    ps = k == slot ? Pc_[k] : ps;
-                }
-                rs->surfT[wib] = Tref_d + (double)ts;
-                rs->surfP[wib] = Pref_d + (double)ps;
-            }
-            __syncthreads();   // the room warp advances the room air between the two barriers
+            publish(Tp_, Pp_, (int)((n_cur + 1) & 1));   // level n+1
             __syncthreads();
         }
+        ++n_cur;
     };
+    if (ROOM) {
+        publish(Tb, Pb, (int)(n0 & 1));   // level n0, before the first step
+        __syncthreads();
+    }
 
     int s = 0;
     bool flipped = false;

@@ -1,10 +1,12 @@
 // Room kernel of the whole-building model: one block per room, one warp per wall facing the room, and
-// one more warp (the last) for the room air. Each step every wall advances with the room air at level n
-// on its room face, then the walls publish their level-n surface values, the block synchronises, the
-// room warp advances the room air node in FP64 (paper Sec. 5.1-5.2), and the block synchronises again.
-// The room warp computes the outdoor air and vapour production of 32 steps at a time, one step per
-// lane, while the walls compute. Every thread passes exactly two block barriers per step (warps
-// without a wall run an empty loop of the same barriers).
+// one more warp (the last) for the room air. The coupling is explicit (paper Sec. 5.2): step n of a wall
+// takes the room air of level n, and the room's step takes the walls' level-n surface values, so both
+// run at the same time. Step n: every wall advances with the room air of level n and publishes its
+// level-n+1 surface values, while the room warp advances the room air node in FP64 (Sec. 5.1) from the
+// level-n surface values; room air and surface values are double-buffered by level parity, and the
+// block synchronises once per step. The room warp computes the outdoor air and vapour production of 32
+// steps at a time, one step per lane. Every thread passes one block barrier before the first step and
+// one per step (warps without a wall run an empty loop of the same barriers).
 #pragma once
 
 #include "df1d_persistent.cuh"
@@ -26,19 +28,26 @@ __global__ void __launch_bounds__((HYGRO_MAX_ROOM_WALLS + 1) * 32, 1)
         rs.Ta_c = d.room_state[(size_t)r * 4 + 1];
         rs.Pa_p = d.room_state[(size_t)r * 4 + 2];
         rs.Pa_c = d.room_state[(size_t)r * 4 + 3];
+        rs.airT[n0 & 1] = rs.Ta_c;
+        rs.airP[n0 & 1] = rs.Pa_c;
     }
     __syncthreads();
     bool ran = false;
     const int room_warp = (int)(blockDim.x >> 5) - 1;
     if (wib == room_warp) {
         const RoomConst k = room_const(ri, d.faces, d.dt);
+        __syncthreads();   // the walls' level-n0 surface values are in rs
         for (int s = 0; s < n_steps; ++s) {
             if (s % kRoomAirChunk == 0) {
                 room_air_chunk(rs, ri, k, n0 + s, d.t0, d.dt, d.Lv, lane);
                 __syncwarp();
             }
-            __syncthreads();   // the walls' level-n surface values are in rs
-            if (lane == 0) room_update(rs, k, ri, s % kRoomAirChunk, d.dt, d.Lv);
+            const int b = (int)((n0 + s) & 1);
+            if (lane == 0) {
+                room_update(rs, k, ri, s % kRoomAirChunk, b, d.dt, d.Lv);
+                rs.airT[b ^ 1] = rs.Ta_c;   // level n+1 for the walls' next step
+                rs.airP[b ^ 1] = rs.Pa_c;
+            }
             __syncthreads();
         }
         ran = true;
@@ -64,11 +73,10 @@ __global__ void __launch_bounds__((HYGRO_MAX_ROOM_WALLS + 1) * 32, 1)
             default: break;
         }
     }
-    if (!ran)
-        for (int s = 0; s < n_steps; ++s) {
-            __syncthreads();
-            __syncthreads();
-        }
+    if (!ran) {
+        __syncthreads();
+        for (int s = 0; s < n_steps; ++s) __syncthreads();
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         d.room_state[(size_t)r * 4 + 0] = rs.Ta_p;
