@@ -59,12 +59,19 @@ __global__ void __launch_bounds__((HYGRO_MAX_ROOM_WALLS + 1) * 32, 1)
         __syncwarp();
         const real *tab = s_tab[wib];
         const int face = ri.face[wib];
-        switch (wi.K) {
-#define HYGRO_CASE(KK)                                                                                            \
-    case KK:                                                                                                      \
-        run_wall<real, KK, true, false, true>(d, wi, w, tab, n0, n_steps, sample_every, samples, nullptr, nullptr, \
-                                              &rs, face);                                                         \
-        ran = true;                                                                                               \
+        // simple-heat walls with one layer per lane (FP32) take the simple variant, the others the general one
+        const bool simple = kSimpleVariant<real> && wi.simple && wi.aligned;
+        switch (wi.K * 2 + (simple ? 1 : 0)) {
+#define HYGRO_CASE(KK)                                                                                             \
+    case 2 * KK:                                                                                                   \
+        run_wall<real, KK, true, false, true>(d, wi, w, tab, n0, n_steps, sample_every, samples, nullptr, nullptr,  \
+                                              &rs, face);                                                          \
+        ran = true;                                                                                                \
+        break;                                                                                                     \
+    case 2 * KK + 1:                                                                                               \
+        run_wall<real, KK, false, kSimpleVariant<real>, true>(d, wi, w, tab, n0, n_steps, sample_every, samples,   \
+                                                              nullptr, nullptr, &rs, face);                       \
+        ran = true;                                                                                                \
         break;
             HYGRO_CASE(1) HYGRO_CASE(2) HYGRO_CASE(3) HYGRO_CASE(4) HYGRO_CASE(5) HYGRO_CASE(6)
             HYGRO_CASE(7) HYGRO_CASE(8) HYGRO_CASE(9) HYGRO_CASE(10) HYGRO_CASE(11) HYGRO_CASE(12)
