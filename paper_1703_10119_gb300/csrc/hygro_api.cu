@@ -8,6 +8,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -22,7 +23,9 @@ thread_local std::string g_create_error = "no error";
 
 struct RawBc {
     hygro_bc bc;                 // noise pointer not kept
-    std::vector<float> noise;    // copied table [noise_len][2]
+    int64_t noise_off = 0;       // first (T, Pv) pair of this wall's table in its face's region of the
+                                 // context's noise array
+    int64_t noise_len = 0;       // pairs (0: no table, or not an ambient face)
 };
 
 template <typename T>
@@ -60,7 +63,7 @@ uint64_t turns_fixed(double x)
 
 namespace hygro {
 
-hygro_status check_bc(const hygro_bc &b, bool allow_room, double t0, double dt, std::string *why)
+hygro_status check_bc(const hygro_bc &b, bool allow_room, double t0, double dt, std::string *why, bool scan_noise)
 {
     if (b.kind == HYGRO_BC_ROOM && !allow_room) {
         *why = "room faces are not accepted here";
@@ -106,11 +109,19 @@ hygro_status check_bc(const hygro_bc &b, bool allow_room, double t0, double dt, 
             *why = "noise table too long for its time step";
             return HYGRO_E_UNSUPPORTED;
         }
-        for (int64_t k = 0; k < 2 * (int64_t)b.noise_len; ++k)
-            if (!std::isfinite(b.noise[k])) {
-                *why = "non-finite noise";
-                return HYGRO_E_INVALID;
-            }
+        // branch-free scan, which the compiler vectorises: a float is finite unless its exponent bits
+        // are all ones
+        const int64_t n = scan_noise ? 2 * (int64_t)b.noise_len : 0;
+        uint32_t bad = 0;
+        for (int64_t k = 0; k < n; ++k) {
+            uint32_t u;
+            memcpy(&u, b.noise + k, sizeof u);
+            bad |= (uint32_t)((u & 0x7f800000u) == 0x7f800000u);
+        }
+        if (bad) {
+            *why = "non-finite noise";
+            return HYGRO_E_INVALID;
+        }
     }
     return HYGRO_OK;
 }
@@ -196,8 +207,17 @@ struct hygro_ctx {
     FaceInfo *d_faces = nullptr;
     void *d_layer_tab = nullptr;
     int32_t *d_layer_first = nullptr;
-    float2 *d_noise = nullptr;
-    size_t noise_cap = 0;
+    float2 *d_noise = nullptr;         // noise tables: face 0's region, then face 1's
+    size_t noise_reg[2] = {0, 0};      // pairs reserved for each face's region
+    size_t noise_used[2] = {0, 0};     // pairs in use
+    // noise upload pipeline: two host chunks (pinned when the allocation succeeds), their copy events,
+    // and a device staging area that receives a face's tables before they are known to be finite
+    float *h_stage[2] = {nullptr, nullptr};
+    bool stage_pinned = false;
+    size_t stage_pairs = 0;            // pairs per host chunk
+    cudaEvent_t stage_ev[2] = {nullptr, nullptr};
+    float2 *d_stage = nullptr;
+    size_t stage_cap = 0;              // pairs
     void *d_Tref = nullptr, *d_Pref = nullptr;
     double *d_cumul = nullptr, *d_flast = nullptr;
     int32_t *d_nonfinite = nullptr;
@@ -252,6 +272,16 @@ void free_all(hygro_ctx *c)
                     c->d_nonfinite, c->d_order, c->d_block_off, c->d_trace, c->d_rooms, c->d_room_state, c->d_node_wall, c->d_node_layer, c->d_samples};
     for (void *p : ptrs)
         if (p) cudaFree(p);
+    if (c->d_stage) cudaFree(c->d_stage);
+    for (int i = 0; i < 2; ++i) {
+        if (c->h_stage[i]) {
+            if (c->stage_pinned)
+                cudaFreeHost(c->h_stage[i]);
+            else
+                free(c->h_stage[i]);
+        }
+        if (c->stage_ev[i]) cudaEventDestroy(c->stage_ev[i]);
+    }
 }
 
 template <typename real>
@@ -316,35 +346,179 @@ hygro_status download_reals(hygro_ctx *c, const void *src, std::vector<double> &
 }
 
 // Face descriptors in the deviation variables of each wall; needs the
-// materials (for T_ref, P_ref) and both faces.
+// materials (for T_ref, P_ref) and both faces. The noise tables are already
+// on the device (upload_noise); only their offsets enter the descriptors.
 hygro_status upload_faces(hygro_ctx *c)
 {
     if (!(c->have_materials && c->have_bc[0] && c->have_bc[1])) return HYGRO_OK;
     const int W = c->W;
     std::vector<FaceInfo> fi((size_t)W * 2);
-    size_t total_noise = 0;
-    for (int f = 0; f < 2; ++f)
-        for (int w = 0; w < W; ++w) total_noise += c->bc[f][w].noise.size() / 2;
-    std::vector<float2> noise(total_noise > 0 ? total_noise : 1);
-    size_t off = 0;
     for (int w = 0; w < W; ++w)
         for (int f = 0; f < 2; ++f) {
             const RawBc &r = c->bc[f][w];
-            const int64_t nl = (int64_t)r.noise.size() / 2;
-            fi[(size_t)w * 2 + f] = face_info(r.bc, c->Tref[w], c->Pref[w], c->t0, c->dt, (int64_t)off, nl);
-            if (r.bc.kind == HYGRO_BC_ADIABATIC) continue;
-            for (int64_t k = 0; k < nl; ++k) noise[off + k] = make_float2(r.noise[2 * k], r.noise[2 * k + 1]);
-            off += (size_t)nl;
+            const int64_t base = f == 0 ? 0 : (int64_t)c->noise_reg[0];
+            fi[(size_t)w * 2 + f] =
+                face_info(r.bc, c->Tref[w], c->Pref[w], c->t0, c->dt, base + r.noise_off, r.noise_len);
         }
-    if (noise.size() > c->noise_cap) {
-        if (c->d_noise) cudaFree(c->d_noise);
-        c->d_noise = nullptr;
-        c->noise_cap = 0;
-        CUDA_TRY(c, dalloc(&c->d_noise, noise.size()));
-        c->noise_cap = noise.size();
-    }
-    CUDA_TRY(c, cudaMemcpy(c->d_noise, noise.data(), noise.size() * sizeof(float2), cudaMemcpyHostToDevice));
     CUDA_TRY(c, cudaMemcpy(c->d_faces, fi.data(), fi.size() * sizeof(FaceInfo), cudaMemcpyHostToDevice));
+    return HYGRO_OK;
+}
+
+constexpr size_t kStagePairs = size_t(1) << 23;   // (T, Pv) pairs per host chunk of the noise upload (64 MB)
+
+// Copies pairs [p0, p1) of a face's concatenated tables into dst (wall wid[k]'s table starts at pair
+// start[k] and has len[k] pairs, read from its hygro_bc), with up to `threads` host threads, each checking
+// the values it copies. Returns the index of the first non-finite pair, or -1.
+int64_t gather_tables(const hygro_bc *bc, const std::vector<int> &wid, const std::vector<int64_t> &start,
+                      const std::vector<int64_t> &len, int64_t p0, int64_t p1, float *dst, int threads)
+{
+    auto part = [&](int64_t a, int64_t b) -> int64_t {
+        if (a >= b) return -1;
+        size_t k = (size_t)(std::upper_bound(start.begin(), start.end(), a) - start.begin()) - 1;
+        int64_t x = a;
+        while (x < b) {
+            const int64_t s = start[k], e = std::min(b, s + len[k]);
+            const float *src = bc[wid[k]].noise + 2 * (x - s);
+            float *out = dst + 2 * (x - p0);
+            const int64_t n = 2 * (e - x);
+            uint32_t bad = 0;
+            for (int64_t i = 0; i < n; ++i) {   // branch-free copy and check (vectorises)
+                uint32_t u;
+                memcpy(&u, src + i, sizeof u);
+                memcpy(out + i, &u, sizeof u);
+                bad |= (uint32_t)((u & 0x7f800000u) == 0x7f800000u);
+            }
+            if (bad)
+                for (int64_t i = 0; i < n; ++i)
+                    if (!std::isfinite(src[i])) return x + i / 2;
+            x = e;
+            ++k;
+        }
+        return -1;
+    };
+    const int64_t n = p1 - p0;
+    const int T = (int)std::max<int64_t>(1, std::min<int64_t>(threads, n / (int64_t(1) << 18)));
+    std::vector<int64_t> first_bad(T, -1);
+    std::vector<std::thread> pool;
+    for (int t = 1; t < T; ++t) {
+        try {
+            pool.emplace_back([&, t] { first_bad[t] = part(p0 + n * t / T, p0 + n * (t + 1) / T); });
+        } catch (...) {   // no thread: this part on the calling thread
+            first_bad[t] = part(p0 + n * t / T, p0 + n * (t + 1) / T);
+        }
+    }
+    first_bad[0] = part(p0, p0 + n / T);
+    for (auto &th : pool) th.join();
+    for (int t = 0; t < T; ++t)
+        if (first_bad[t] >= 0) return first_bad[t];
+    return -1;
+}
+
+// Uploads the noise tables of one face (hygro_bc array, validated except for the table values) and
+// records each wall's offset and length in v. Host threads gather the per-wall tables into two host
+// chunks (pinned when possible), checking each value as they copy, while the previous chunk's copy to
+// the device runs; the chunks land in a device staging area, which reaches the face's region of the
+// context's noise array only when every value was finite, so a refused call leaves the face as it was.
+// The array grows when the region is too small (the other face's tables move with a device copy).
+hygro_status upload_noise(hygro_ctx *c, int face, const hygro_bc *bc, std::vector<RawBc> &v)
+{
+    const int W = c->W;
+    std::vector<int> wid;
+    std::vector<int64_t> start, len;
+    int64_t total = 0;
+    for (int w = 0; w < W; ++w) {
+        const bool has = bc[w].kind == HYGRO_BC_AMBIENT && bc[w].noise_len > 0;
+        v[w].noise_off = total;
+        v[w].noise_len = has ? bc[w].noise_len : 0;
+        if (!has) continue;
+        wid.push_back(w);
+        start.push_back(total);
+        len.push_back(bc[w].noise_len);
+        total += bc[w].noise_len;
+    }
+    if (total > 0) {
+        if ((size_t)total > c->stage_cap) {
+            if (c->d_stage) cudaFree(c->d_stage);
+            c->d_stage = nullptr;
+            c->stage_cap = 0;
+            CUDA_TRY(c, dalloc(&c->d_stage, (size_t)total));
+            c->stage_cap = (size_t)total;
+        }
+        const size_t want = std::min(kStagePairs, (size_t)total);
+        if (want > c->stage_pairs) {   // host chunks sized to the need, up to kStagePairs
+            for (int i = 0; i < 2; ++i) {
+                if (c->h_stage[i]) {
+                    if (c->stage_pinned)
+                        cudaFreeHost(c->h_stage[i]);
+                    else
+                        free(c->h_stage[i]);
+                }
+                c->h_stage[i] = nullptr;
+            }
+            c->stage_pairs = 0;
+            const size_t bytes = want * 2 * sizeof(float);
+            c->stage_pinned = cudaHostAlloc((void **)&c->h_stage[0], bytes, cudaHostAllocDefault) == cudaSuccess &&
+                              cudaHostAlloc((void **)&c->h_stage[1], bytes, cudaHostAllocDefault) == cudaSuccess;
+            if (!c->stage_pinned) {   // pageable chunks: the same pipeline, with synchronous copies
+                for (int i = 0; i < 2; ++i) {
+                    if (c->h_stage[i]) cudaFreeHost(c->h_stage[i]);
+                    c->h_stage[i] = (float *)malloc(bytes);
+                }
+                if (!c->h_stage[0] || !c->h_stage[1]) return fail(c, HYGRO_E_NOMEM, "noise upload buffers");
+            }
+            c->stage_pairs = want;
+        }
+        for (int i = 0; i < 2; ++i)
+            if (c->stage_ev[i] == nullptr)
+                CUDA_TRY(c, cudaEventCreateWithFlags(&c->stage_ev[i], cudaEventDisableTiming));
+        const int threads = (int)std::min(8u, std::max(1u, std::thread::hardware_concurrency()));
+        int64_t bad = -1;
+        int chunk = 0;
+        for (int64_t p0 = 0; p0 < total; p0 += (int64_t)c->stage_pairs, ++chunk) {
+            const int64_t p1 = std::min(total, p0 + (int64_t)c->stage_pairs);
+            const int slot = chunk & 1;
+            if (chunk >= 2) CUDA_TRY(c, cudaEventSynchronize(c->stage_ev[slot]));
+            bad = gather_tables(bc, wid, start, len, p0, p1, c->h_stage[slot], threads);
+            if (bad >= 0) break;
+            CUDA_TRY(c, cudaMemcpyAsync(c->d_stage + p0, c->h_stage[slot], (size_t)(p1 - p0) * sizeof(float2),
+                                        cudaMemcpyHostToDevice, c->stream));
+            CUDA_TRY(c, cudaEventRecord(c->stage_ev[slot], c->stream));
+        }
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+        if (bad >= 0) {
+            const size_t k = (size_t)(std::upper_bound(start.begin(), start.end(), bad) - start.begin()) - 1;
+            return fail(c, HYGRO_E_INVALID, "wall %d face %d: non-finite noise", wid[k], face);
+        }
+    }
+    const int other = 1 - face;
+    if ((size_t)total > c->noise_reg[face] || c->d_noise == nullptr) {
+        size_t reg[2];
+        reg[face] = (size_t)total;
+        reg[other] = c->noise_reg[other];
+        float2 *fresh = nullptr;
+        CUDA_TRY(c, dalloc(&fresh, reg[0] + reg[1]));
+        const size_t old_base = other == 0 ? 0 : c->noise_reg[0];
+        const size_t new_base = other == 0 ? 0 : reg[0];
+        if (c->noise_used[other] > 0) {
+            const cudaError_t e = cudaMemcpy(fresh + new_base, c->d_noise + old_base,
+                                             c->noise_used[other] * sizeof(float2), cudaMemcpyDeviceToDevice);
+            if (e != cudaSuccess) {
+                cudaFree(fresh);
+                return fail(c, HYGRO_E_CUDA, "noise table copy: %s", cudaGetErrorString(e));
+            }
+        }
+        if (c->d_noise) cudaFree(c->d_noise);
+        c->d_noise = fresh;
+        c->noise_reg[0] = reg[0];
+        c->noise_reg[1] = reg[1];
+    }
+    if (total > 0) {
+        float2 *dst = c->d_noise + (face == 0 ? 0 : c->noise_reg[0]);
+        CUDA_TRY(c, cudaMemcpyAsync(dst, c->d_stage, (size_t)total * sizeof(float2), cudaMemcpyDeviceToDevice,
+                                    c->stream));
+        CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    }
+    c->noise_used[face] = (size_t)total;
     return HYGRO_OK;
 }
 
@@ -665,7 +839,6 @@ hygro_status hygro_create(const hygro_desc *desc, hygro_ctx **out)
         wi.node_off = (int32_t)off;
         off += wi.N;
     }
-    hygro_status st = HYGRO_OK;
     auto bail = [&](hygro_status s) {
         g_create_error = c->err;
         free_all(c);
@@ -726,7 +899,6 @@ hygro_status hygro_create(const hygro_desc *desc, hygro_ctx **out)
         CREATE_TRY(cudaMemset(c->d_trace, 0, (size_t)c->W * 4 * sizeof(unsigned long long)));
     }
 #undef CREATE_TRY
-    (void)st;
     *out = c;
     return HYGRO_OK;
 }
@@ -837,7 +1009,8 @@ hygro_status hygro_set_bc(hygro_ctx *c, int32_t face, const hygro_bc *bc)
     if (bc == nullptr) return fail(c, HYGRO_E_INVALID, "bc is NULL");
     for (int w = 0; w < c->W; ++w) {
         std::string why;
-        const hygro_status st = check_bc(bc[w], true, c->t0, c->dt, &why);
+        // the table values are checked by upload_noise as they are copied
+        const hygro_status st = check_bc(bc[w], true, c->t0, c->dt, &why, false);
         if (st != HYGRO_OK) return fail(c, st, "wall %d face %d: %s", w, face, why.c_str());
     }
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
@@ -846,8 +1019,10 @@ hygro_status hygro_set_bc(hygro_ctx *c, int32_t face, const hygro_bc *bc)
     for (int w = 0; w < c->W; ++w) {
         v[w].bc = bc[w];
         v[w].bc.noise = nullptr;
-        if (bc[w].kind == HYGRO_BC_AMBIENT && bc[w].noise_len > 0)
-            v[w].noise.assign(bc[w].noise, bc[w].noise + 2 * (size_t)bc[w].noise_len);
+    }
+    {
+        const hygro_status nst = upload_noise(c, face, bc, v);
+        if (nst != HYGRO_OK) return nst;
     }
     c->bc[face].swap(v);
     c->have_bc[face] = true;

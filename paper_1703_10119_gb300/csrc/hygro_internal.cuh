@@ -120,9 +120,11 @@ struct DevCtx {
 };
 
 // Host helpers shared by the 1D and 2D entry points (hygro_api.cu).
-// Validates one face description (kind, coefficients, noise table against the time step); room faces
-// only where allow_room. Returns HYGRO_OK, or an error status with the reason in *why.
-hygro_status check_bc(const hygro_bc &b, bool allow_room, double t0, double dt, std::string *why);
+// Validates one face description (kind, coefficients, noise table against the time step, and the
+// table's values finite unless scan_noise is false, for a caller that checks them while copying);
+// room faces only where allow_room. Returns HYGRO_OK, or an error status with the reason in *why.
+hygro_status check_bc(const hygro_bc &b, bool allow_room, double t0, double dt, std::string *why,
+                      bool scan_noise = true);
 // Device form of one face in the deviation variables of its wall or section (reference T_ref, P_ref),
 // with its noise table at noise_off of the context's noise array.
 FaceInfo face_info(const hygro_bc &b, double T_ref, double P_ref, double t0, double dt, int64_t noise_off,
