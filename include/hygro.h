@@ -176,7 +176,11 @@ HYGRO_API hygro_status hygro_set_materials(hygro_ctx *ctx, const int32_t *n_laye
                                  const hygro_layer *layers, const double *T_init, const double *P_init);
 
 /* Boundary description of one face (0: x = 0, 1: x = L) for every wall;
- * bc[w] for w in 0..n_walls-1, host memory. */
+ * bc[w] for w in 0..n_walls-1, host memory. The noise tables of the ambient faces are copied to the
+ * device during the call (the caller's tables may be freed afterwards); each value is checked on the
+ * way. A non-finite value gives HYGRO_E_INVALID naming the wall, as does any other invalid field, and
+ * a refused call leaves the face's previous description and tables in place. Setting one face does not
+ * copy the other face's tables again, nor does hygro_set_materials. */
 HYGRO_API hygro_status hygro_set_bc(hygro_ctx *ctx, int32_t face, const hygro_bc *bc);
 
 /* Rooms of the whole-building model: rooms[r] for r in 0..n_rooms-1, wall_area[w] (m^2) the area
