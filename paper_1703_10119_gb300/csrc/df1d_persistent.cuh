@@ -21,8 +21,11 @@
 // which is the DF balance of [eq:DF_NL] solved for u^{n+1} - u^{n-1}. The
 // latent cross flux of the T equation, sum_f F_f (Pv_nb - Pvbar), reuses the
 // Pv numerator: num_P - (S / 2) dPv.
-// Surface fluxes are summed in the working precision over batches of 16
-// steps and then added to FP64 running sums.
+// Surface fluxes are linear in the time-averaged surface values and the air
+// values, so a step only adds its surface values to batch sums; the fluxes
+// of a batch of 16 steps follow from those sums and the batch's air sums
+// ([eq:HAM_BC] summed over the batch), and go to compensated sums that are
+// added to FP64 running sums every 16 batches.
 #pragma once
 
 #include "df1d_common.cuh"
@@ -60,7 +63,8 @@ struct LaneCtx {
 
 // One DF step of the lane's K slots: level n+1 is written into Tp / Pp.
 // fT, fP: ambient air of this lane's surface face (if any) at level n.
-// fq, fg: receive this lane's surface heat / moisture flux of the step.
+// sT, sP: receive the time-averaged values (u^{n+1} + u^{n-1}) / 2 of this lane's surface node, which
+// the Robin exchange of [eq:HAM_BC] uses.
 // IFACE: the wall has layer interfaces inside lanes. SIMPLE: simple-heat
 // wall (see LaneCtx; only with one layer per lane).
 // With IFACE && SIMPLE, sft / srt hold this lane's per-slot right thermal face and reciprocal T
@@ -68,7 +72,7 @@ struct LaneCtx {
 template <typename real, int K, bool IFACE, bool SIMPLE>
 __device__ __forceinline__ void df_step(real (&Tp)[K], const real (&Tc)[K], real (&Pp)[K], const real (&Pc)[K],
                                         const LaneCtx<real> &L, const real *tab, const real fT, const real fP,
-                                        const real Lv, real &fq, real &fg, const real *sft, const real *srt)
+                                        const real Lv, real &sT, real &sP, const real *sft, const real *srt)
 {
     constexpr unsigned FULL = 0xffffffffu;
     const real half = real(0.5);
@@ -260,10 +264,8 @@ __device__ __forceinline__ void df_step(real (&Tp)[K], const real (&Tc)[K], real
         khM = khMn;
         khT = khTn;
     }
-    // surface fluxes into the wall with the time-averaged surface values ([eq:HAM_BC])
-    const real hm = L.hMs * (fP - sPbar);
-    fq = fma(L.hTs, fT - sTbar, fma(Lv, hm, L.qs));
-    fg = hm + L.gs;
+    sT = sTbar;
+    sP = sPbar;
 }
 
 constexpr int kRoomAirChunk = 32;   // steps of outdoor air and vapour production computed at a time
@@ -570,7 +572,8 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
         cum_q = d.cumul[(size_t)w * 4 + my_face * 2 + 0];
         cum_g = d.cumul[(size_t)w * 4 + my_face * 2 + 1];
     }
-    real last_q = real(0), last_g = real(0);
+    // values of the last step, for its flux
+    real last_sT = real(0), last_sP = real(0), last_fT = real(0), last_fP = real(0);
     int scount = sample_every;
     int64_t sidx = 0;
     const int W = d.W;
@@ -599,7 +602,8 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
     const int room_lane = room_face == 0 ? 0 : Wl - 1;
     const double Tref_d = (double)Tref, Pref_d = (double)Pref;
     const int wib = threadIdx.x >> 5;
-    real acc_q = real(0), acc_g = real(0);
+    // sums over the current batch of the lane's time-averaged surface values, and (room walls) of its air
+    real acc_sT = real(0), acc_sP = real(0), acc_fT = real(0), acc_fP = real(0);
     int64_t n_cur = n0;
     auto publish = [&](const real (&T_)[K], const real (&P_)[K], int b) {
         if (lane == room_lane) {
@@ -622,13 +626,17 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
                 fT = (real)(rs->airT[n_cur & 1] - Tref_d);
                 fP = (real)(rs->airP[n_cur & 1] - Pref_d);
             }
+            acc_fT += fT;
+            acc_fP += fP;
+            last_fT = fT;
+            last_fP = fP;
         }
-        real fq, fg;
-        df_step<real, K, IFACE, SIMPLE>(Tp_, Tc_, Pp_, Pc_, L, tab, fT, fP, Lv, fq, fg, sft, srt);
-        acc_q += fq;
-        acc_g += fg;
-        last_q = fq;
-        last_g = fg;
+        real sT, sP;
+        df_step<real, K, IFACE, SIMPLE>(Tp_, Tc_, Pp_, Pc_, L, tab, fT, fP, Lv, sT, sP, sft, srt);
+        acc_sT += sT;
+        acc_sP += sP;
+        last_sT = sT;
+        last_sP = sP;
         sample(Tp_, Pp_);
         if (ROOM) {
             publish(Tp_, Pp_, (int)((n_cur + 1) & 1));   // level n+1
@@ -643,13 +651,16 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
 
     int s = 0;
     bool flipped = false;
+    real bT = real(0), bP = real(0);
+    int last_src = 0;
     while (s < n_steps) {
         const int cnt = min(kForcingBatch, n_steps - s);
         // ambient air for steps n0+s .. n0+s+15: lane i<16 computes face 0 at step i, lane 16+i face 1
-        real bT = real(0), bP = real(0);
+        bT = real(0);
+        bP = real(0);
         if (f_ambient) ambient_at(ff, d.noise, n0 + s + (lane % kForcingBatch), d.t0, d.dt, bT, bP);
-        acc_q = real(0);
-        acc_g = real(0);
+        acc_sT = acc_sP = real(0);
+        if (ROOM) acc_fT = acc_fP = real(0);
         int i = 0;
         for (; i + 1 < cnt; i += 2) {
             one_step(Ta, Tb, Pa, Pb, bT, bP, src_base + i);
@@ -660,6 +671,30 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
             flipped = true;
         }
         {
+            // the batch's air sums of the lane's face: room walls summed them per step; otherwise lanes
+            // 0..cnt-1 (face 0) and 16..15+cnt (face 1) hold the batch's air, summed within each half-warp
+            real sfT, sfP;
+            if (ROOM) {
+                sfT = acc_fT;
+                sfP = acc_fP;
+            } else {
+                real xT = (lane % kForcingBatch) < cnt ? bT : real(0);
+                real xP = (lane % kForcingBatch) < cnt ? bP : real(0);
+#pragma unroll
+                for (int o = kForcingBatch / 2; o >= 1; o >>= 1) {
+                    xT += __shfl_xor_sync(FULL, xT, o);
+                    xP += __shfl_xor_sync(FULL, xP, o);
+                }
+                sfT = __shfl_sync(FULL, xT, src_base);
+                sfP = __shfl_sync(FULL, xP, src_base);
+                last_src = src_base + cnt - 1;
+            }
+            // [eq:HAM_BC] summed over the batch: q = hT (T_inf - Tbar) + Lv hM (Pv_inf - Pvbar) + q_inf,
+            // g = hM (Pv_inf - Pvbar) + g_inf
+            const real rc = (real)cnt;
+            const real hm = L.hMs * (sfP - acc_sP);
+            const real acc_q = fma(L.hTs, sfT - acc_sT, fma(Lv, hm, rc * L.qs));
+            const real acc_g = fma(rc, L.gs, hm);
             const real xq = acc_q * dt_r, xg = acc_g * dt_r;
             real t = kq + xq;
             kq_c += fabs(kq) >= fabs(xq) ? (kq - t) + xq : (xq - t) + kq;
@@ -694,6 +729,14 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
         }
     }
     if (__any_sync(FULL, bad) && lane == 0) atomicExch(d.nonfinite, 1);
+    // flux of the last step
+    if (!ROOM) {
+        last_fT = __shfl_sync(FULL, bT, last_src);
+        last_fP = __shfl_sync(FULL, bP, last_src);
+    }
+    const real last_hm = L.hMs * (last_fP - last_sP);
+    const real last_q = fma(L.hTs, last_fT - last_sT, fma(Lv, last_hm, L.qs));
+    const real last_g = last_hm + L.gs;
     if (my_face >= 0 && n_steps > 0) {
         d.cumul[(size_t)w * 4 + my_face * 2 + 0] = cum_q;
         d.cumul[(size_t)w * 4 + my_face * 2 + 1] = cum_g;
