@@ -229,7 +229,7 @@ def bench_reference(args):
     from paper_1703_10119_gb300 import workloads as wk
     import oracle
 
-    wl = wk.config2(n_walls=args.walls, n_steps=args.year_steps)
+    wl = wk.wall_batch(n_walls=args.walls, n_steps=args.year_steps)
     pick, sub = cpu_sample(wl, max(8, args.cpu_walls // 8))
     units = sub.total_nodes * args.year_steps
     for _ in range(args.warmup):
@@ -256,7 +256,7 @@ def bench_sections(args, H, wk, stream, local, rank):
     """The 2D thermal-bridge workload: throughput, its HBM roofline and parity on sampled sections."""
     import torch
 
-    sec = wk.config4(seed=4 + rank, n_grids=args.sections, n_steps=args.section_steps)
+    sec = wk.sections_2d(seed=4 + rank, n_grids=args.sections, n_steps=args.section_steps)
     h = H.Hygro2D(sec, precision="fp32", device=local, stream=stream.cuda_stream)
     k = STEPS_PER_LAUNCH_2D
     with torch.cuda.stream(stream):
@@ -311,7 +311,7 @@ def bench_adjoint(args, H, wk, stream, local, rank):
     sqrt(T) checkpoints), observations resident on the device; parity on sampled walls vs the oracle."""
     import torch
 
-    wl, s = wk.config5(seed=5 + rank, n_steps=args.adjoint_steps)
+    wl, s = wk.gradient_walls(seed=5 + rank, n_steps=args.adjoint_steps)
     dev = torch.device("cuda", local)
     obs = torch.from_numpy(s.obs).to(dev)
     grad = torch.zeros((len(wl.layer_par), 9), dtype=torch.float64, device=dev)
@@ -410,7 +410,7 @@ def bench_ours(args):
         if rank == 0:
             print(json.dumps({"metric": METRIC, "unit": UNIT, "only": "gradient workload", **out}))
         return
-    wl = wk.config2(seed=2 + rank, n_walls=args.walls, n_steps=args.year_steps)
+    wl = wk.wall_batch(seed=2 + rank, n_walls=args.walls, n_steps=args.year_steps)
     units_per_run = wl.total_nodes * args.year_steps
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
@@ -509,7 +509,7 @@ def bench_ours(args):
     # whole-building workload (64 rooms x 6 walls, FP64 room nodes, 30 days): walls + rooms per run
     other = {}
     if not args.no_fp64:
-        wl3 = wk.config3(seed=3 + rank)
+        wl3 = wk.building(seed=3 + rank)
         h = H.Hygro(wl3, precision="fp32", kernel="persistent", device=local, stream=stream.cuda_stream)
         with torch.cuda.stream(stream):
             h.run(wl3.n_steps)

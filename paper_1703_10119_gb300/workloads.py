@@ -12,8 +12,8 @@ Gaussian noise uses the Box-Muller transform.
 
 Workloads (their shapes follow the paper's wall problems, Sec. 2 and Sec. 4,
 with the ranges of the standard benchmark configurations):
-  * ``config1``: one 10 cm wall, 101 nodes, dt = 60 s, one day.
-  * ``config2``: a batch of ragged multi-layer walls (default 4096 walls of
+  * ``single_wall``: one 10 cm wall, 101 nodes, dt = 60 s, one day.
+  * ``wall_batch``: a batch of ragged multi-layer walls (default 4096 walls of
     50..400 nodes, dt = 600 s, one year, hourly Gaussian noise on face 0).
 """
 from __future__ import annotations
@@ -202,7 +202,7 @@ def concat(workloads: list[Workload], name="batch") -> Workload:
             [np.ones(w.n_walls) if w.vapour_frac is None else w.vapour_frac for w in workloads]))
 
 
-def config1(seed: int = 1) -> Workload:
+def single_wall(seed: int = 1) -> Workload:
     """One 10 cm wall, N = 101, dt = 60 s, 1440 steps (one day), FP64 case.
 
     kM = kM0 (1 + a Pv/Psat), cM = cM0 (1 + b Pv/Psat) with a, b ~ U[0, 1]
@@ -218,7 +218,7 @@ def config1(seed: int = 1) -> Workload:
                phase_P=2.0 * math.pi * u[2])
     bc1 = dict(hT=8.0, hM=3e-8, T_mean=293.0, P_mean=1000.0)
     return uniform_wall(101, 0.1, layer, bc0=bc0, bc1=bc1, dt=60.0, n_steps=1440,
-                        name="config1: 1 wall, N=101, dt=60 s x 1440")
+                        name="single_wall: 1 wall, N=101, dt=60 s x 1440")
 
 
 def _layer_split(key, N: int, n_layers: int) -> list[int]:
@@ -234,7 +234,7 @@ def _layer_split(key, N: int, n_layers: int) -> list[int]:
     return [n0, n1, N - n0 - n1]
 
 
-def config2(seed: int = 2, n_walls: int = 4096, n_steps: int = 52560, dt: float = 600.0,
+def wall_batch(seed: int = 2, n_walls: int = 4096, n_steps: int = 52560, dt: float = 600.0,
             n_min: int = 50, n_max: int = 400, noise: bool = True,
             name: str | None = None) -> Workload:
     """Batch of ragged 1..3-layer walls, per-wall seeded forcing.
@@ -287,7 +287,7 @@ def config2(seed: int = 2, n_walls: int = 4096, n_steps: int = 52560, dt: float 
         z0, z1 = normal_pairs(nkey[:, None], np.arange(noise_len, dtype=np.uint64)[None, :])
         nz0 = np.stack([1.0 * z0, 50.0 * z1], axis=-1).astype(np.float32)
     return Workload(
-        name=name or f"config2: {n_walls} ragged walls N {n_min}-{n_max}, dt={dt:g} s x {n_steps}",
+        name=name or f"wall_batch: {n_walls} ragged walls N {n_min}-{n_max}, dt={dt:g} s x {n_steps}",
         n_nodes=N, thickness=L, n_layers=nl, layer_first=np.concatenate(firsts),
         layer_par=np.array(pars, dtype=np.float64),
         T_init=np.full(n_walls, 293.0), P_init=np.full(n_walls, 1000.0),
@@ -302,7 +302,7 @@ ROOM_FIELDS = ("volume", "ach", "Q_gain", "g_vap", "T_out_mean", "T_out_amp", "P
                "g_pulse", "pulse_on", "pulse_off", "pulse_period")
 
 
-def config3(seed: int = 3, n_rooms: int = 64, walls_per_room: int = 6, n_steps: int = 8640,
+def building(seed: int = 3, n_rooms: int = 64, walls_per_room: int = 6, n_steps: int = 8640,
             dt: float = 300.0, n_min: int = 80, n_max: int = 300) -> Workload:
     """Whole building: rooms of six walls each, FP64 room air balances.
 
@@ -317,8 +317,8 @@ def config3(seed: int = 3, n_rooms: int = 64, walls_per_room: int = 6, n_steps: 
     dt = 300 s x 8640 (30 days).
     """
     n_walls = n_rooms * walls_per_room
-    base = config2(seed=seed, n_walls=n_walls, n_steps=n_steps, dt=dt, n_min=n_min, n_max=n_max,
-                   name=f"config3: {n_rooms} rooms x {walls_per_room} walls, dt={dt:g} s x {n_steps}")
+    base = wall_batch(seed=seed, n_walls=n_walls, n_steps=n_steps, dt=dt, n_min=n_min, n_max=n_max,
+                   name=f"building: {n_rooms} rooms x {walls_per_room} walls, dt={dt:g} s x {n_steps}")
     key = stream_key(seed, 1 << 40)
     g = uniform(key, np.arange(2))
     phase_T, phase_P = 2 * np.pi * g[0], 2 * np.pi * g[1]
@@ -389,7 +389,7 @@ class Section2D:
             T_init=self.T_init[g].copy(), P_init=self.P_init[g].copy())
 
 
-def config4(seed: int = 4, n_grids: int = 64, nx: int = 512, ny: int = 512, h: float = 1e-3, dt: float = 60.0,
+def sections_2d(seed: int = 4, n_grids: int = 64, nx: int = 512, ny: int = 512, h: float = 1e-3, dt: float = 60.0,
             n_steps: int = 10000) -> Section2D:
     """Thermal-bridge corners: 2D sections with an L-shaped outer leaf and an optional inner column.
 
@@ -434,7 +434,7 @@ def config4(seed: int = 4, n_grids: int = 64, nx: int = 512, ny: int = 512, h: f
     nkey = stream_key(seed, grids + (1 << 43))
     z0, z1 = normal_pairs(nkey[:, None], np.arange(noise_len, dtype=np.uint64)[None, :])
     nz = np.stack([1.0 * z0, 50.0 * z1], axis=-1).astype(np.float32)
-    return Section2D(name=f"config4: {n_grids} sections {nx}x{ny}, h={h:g} m, dt={dt:g} s x {n_steps}",
+    return Section2D(name=f"sections_2d: {n_grids} sections {nx}x{ny}, h={h:g} m, dt={dt:g} s x {n_steps}",
                      h=h, region=region, region_par=par, bc_kind=bc_kind, bc_par=bc_par, noise=[nz, None, nz, None],
                      T_init=np.full(n_grids, 293.0), P_init=np.full(n_grids, 1000.0), dt=dt, t0=0.0,
                      n_steps=n_steps)
@@ -450,7 +450,7 @@ class Sensors:
     wP: float
 
 
-def config5(seed: int = 5, n_walls: int = 1024, n_nodes: int = 200, n_steps: int = 43200, dt: float = 60.0,
+def gradient_walls(seed: int = 5, n_walls: int = 1024, n_nodes: int = 200, n_steps: int = 43200, dt: float = 60.0,
             sample_every: int = 10) -> tuple[Workload, Sensors]:
     """Gradient workload: 1024 two-layer walls of 200 nodes, 30 days at dt = 60 s, surface sensors every
     10 min.
@@ -485,7 +485,7 @@ def config5(seed: int = 5, n_walls: int = 1024, n_nodes: int = 200, n_steps: int
     nkey = stream_key(seed, walls + (1 << 45))
     z0, z1 = normal_pairs(nkey[:, None], np.arange(noise_len, dtype=np.uint64)[None, :])
     nz0 = np.stack([1.0 * z0, 50.0 * z1], axis=-1).astype(np.float32)
-    wl = Workload(name=f"config5: {n_walls} two-layer walls N={n_nodes}, dt={dt:g} s x {n_steps}",
+    wl = Workload(name=f"gradient_walls: {n_walls} two-layer walls N={n_nodes}, dt={dt:g} s x {n_steps}",
                   n_nodes=N, thickness=L, n_layers=np.full(n_walls, 2, np.int32), layer_first=firsts,
                   layer_par=np.array(pars, np.float64), T_init=np.full(n_walls, 293.0),
                   P_init=np.full(n_walls, 1000.0), bc_kind=np.zeros((n_walls, 2), np.int32), bc_par=bc_par,

@@ -125,7 +125,7 @@ def test_edge_shapes(H, oracle_mod, shape):
 
 def test_corner_workload_reduced_matches_oracle(H, oracle_mod):
     # the thermal-bridge generator at 4 sections of 192 x 160 (ragged tiles), 64 steps
-    sec = wk.config4(n_grids=4, nx=192, ny=160, n_steps=64)
+    sec = wk.sections_2d(n_grids=4, nx=192, ny=160, n_steps=64)
     ref = run_oracle(oracle_mod, sec, 64)
     for precision in ("fp64", "fp32"):
         check(run_gpu(H, sec, precision, 64), ref, TOL[precision], f"corner {precision}")
@@ -135,7 +135,7 @@ def test_full_size_corner_batch_on_sampled_sections(H, oracle_mod):
     """All 64 sections of 512 x 512 on the GPU in the benchmark's launch configuration (4 fused
     steps, FP32); the oracle advances three of them (the first, a middle and the last)."""
     n = 48
-    sec = wk.config4(n_steps=n)
+    sec = wk.sections_2d(n_steps=n)
     got = run_gpu(H, sec, "fp32", n)
     pick = [0, 31, 63]
     ref = run_oracle(oracle_mod, sec.subset(pick), n)

@@ -129,7 +129,7 @@ def test_invalid_calls(H):
         g.loss_grad(120, 10, obs, 1.0, 1e-4)
         after = g.fields(0)
         assert np.array_equal(before[0], after[0]) and g.step == 5
-    wl3 = wk.config3(n_rooms=1, walls_per_room=2, n_steps=10)
+    wl3 = wk.building(n_rooms=1, walls_per_room=2, n_steps=10)
     with H.Hygro(wl3, precision="fp32") as g:
         with pytest.raises(H.HygroError) as e:
             g.loss_grad(10, 5, np.zeros((2, wl3.n_walls, 2, 2), np.float32), 1.0, 1e-4)
@@ -139,7 +139,7 @@ def test_invalid_calls(H):
 def test_gradient_workload_full_size_sampled_walls(H, oracle_mod):
     """All 1024 walls over the 30 days in FP32 with sqrt(T) checkpoints; the oracle adjoint runs two of
     them (their layers' gradient rows depend on those walls alone)."""
-    wl, s = wk.config5()
+    wl, s = wk.gradient_walls()
     with H.Hygro(wl, precision="fp32") as g:
         L, grad = g.loss_grad(wl.n_steps, s.sample_every, s.obs, s.wT, s.wP)
     assert np.isfinite(L) and np.all(np.isfinite(grad))

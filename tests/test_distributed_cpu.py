@@ -32,7 +32,7 @@ def _worker(rank, world, port, out_dir):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
                       LOCAL_RANK=str(rank))
     dist.init_process_group("gloo", rank=rank, world_size=world)
-    wl = wk.config2(seed=21, n_walls=12, n_steps=60, n_min=5, n_max=40)
+    wl = wk.wall_batch(seed=21, n_walls=12, n_steps=60, n_min=5, n_max=40)
     sub, idx = shard.shard(wl, rank, world)
     o = oracle.Oracle(sub, n_threads=1)
     r = o.run(60, 20)
@@ -72,7 +72,7 @@ def test_two_rank_split_equals_single_process(tmp_path, oracle_mod):
     got = np.load(tmp_path / "rank0.npz")
     from paper_1703_10119_gb300 import workloads as wk
 
-    wl = wk.config2(seed=21, n_walls=12, n_steps=60, n_min=5, n_max=40)
+    wl = wk.wall_batch(seed=21, n_walls=12, n_steps=60, n_min=5, n_max=40)
     o = oracle_mod.Oracle(wl, n_threads=1)
     r = o.run(60, 20)
     assert np.array_equal(got["flux"], r["flux"])

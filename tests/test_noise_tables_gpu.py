@@ -31,7 +31,7 @@ def H():
 
 def two_face_noise_batch():
     """A small ragged batch (64 walls, 50-400 nodes) with noise tables on both faces."""
-    wl = wk.config2(seed=11, n_walls=64, n_steps=N_STEPS, noise=True)
+    wl = wk.wall_batch(seed=11, n_walls=64, n_steps=N_STEPS, noise=True)
     z0 = wl.noise[0]
     key = wk.stream_key(11, np.arange(64) + (1 << 33))
     a, b = wk.normal_pairs(key[:, None], np.arange(z0.shape[1], dtype=np.uint64)[None, :])
@@ -134,7 +134,7 @@ def long_table_batch(n_steps=140000):
     """64 thin walls (50-60 nodes) whose face-0 tables hold one entry per step (noise_dt = dt), so every
     entry enters the cumulative fluxes; 64 x (n_steps + 2) pairs exceed one 2^23-pair upload chunk, the
     chunk boundary falling inside wall 59's table."""
-    wl = wk.config2(seed=12, n_walls=64, n_min=50, n_max=60, n_steps=n_steps, dt=600.0, noise=False)
+    wl = wk.wall_batch(seed=12, n_walls=64, n_min=50, n_max=60, n_steps=n_steps, dt=600.0, noise=False)
     L = n_steps + 2
     key = wk.stream_key(12, np.arange(64) + (1 << 34))
     a, b = wk.normal_pairs(key[:, None], np.arange(L, dtype=np.uint64)[None, :])

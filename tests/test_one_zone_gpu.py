@@ -91,7 +91,7 @@ def test_vapour_fraction_balance_and_start(H, oracle_mod):
 
 
 def test_vapour_fraction_validation_and_adjoint(H):
-    wl = wk.config1()
+    wl = wk.single_wall()
     with H.Hygro(wl, precision="fp64") as g:
         for bad in (np.array([-0.1]), np.array([np.nan])):
             with pytest.raises(H.HygroError) as e:

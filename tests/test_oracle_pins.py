@@ -301,7 +301,7 @@ def test_second_order_in_time_semidiscrete(oracle_mod):
 
 
 def _rich_batch(n_walls=24, steps=200, seed=5):
-    wl = wk.config2(seed=seed, n_walls=n_walls, n_steps=steps, n_min=5, n_max=60)
+    wl = wk.wall_batch(seed=seed, n_walls=n_walls, n_steps=steps, n_min=5, n_max=60)
     lp = wl.layer_par.copy()
     rng = np.random.default_rng(seed)
     lp[:, 5] = rng.uniform(0, 0.5, len(lp))          # aT
@@ -395,7 +395,7 @@ def test_dimensionless_similarity(oracle_mod):
 
 def test_ambient_forcing(oracle_mod):
     """Face air state: daily sinusoid plus a linearly interpolated noise table held at its ends."""
-    wl = wk.config2(seed=3, n_walls=2, n_steps=100)
+    wl = wk.wall_batch(seed=3, n_walls=2, n_steps=100)
     o = oracle_mod.Oracle(wl, n_threads=1)
     nz = wl.noise[0][1].astype(np.float64)
     bp = wl.bc_par[1, 0]
@@ -457,7 +457,7 @@ def test_room_euler_is_unstable_at_the_building_time_step(oracle_mod):
     """Reading R26: with the whole-building workload's dt = 300 s, a small room's time constant (heat
     capacity over exchange conductance) is below dt / 2, so the explicit Euler room update of Sec. 5.2
     grows without bound, while the room as a DF node stays at physical values."""
-    wl = wk.config3(seed=3, n_rooms=2, walls_per_room=6, n_steps=400)
+    wl = wk.building(seed=3, n_rooms=2, walls_per_room=6, n_steps=400)
     rooms = dict(wl.rooms)
     par = np.array(rooms["par"], np.float64).copy()
     par[:, 0] = 30.0          # 30 m^3 rooms

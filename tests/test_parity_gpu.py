@@ -103,8 +103,8 @@ def _compare(H, oracle_mod, wl, precision, kernel, n_steps, sample_every, splits
 
 
 @pytest.mark.parametrize("precision,kernel", COMBOS)
-def test_config1_single_wall(H, oracle_mod, precision, kernel):
-    wl = wk.config1()
+def test_single_wall(H, oracle_mod, precision, kernel):
+    wl = wk.single_wall()
     _compare(H, oracle_mod, wl, precision, kernel, 1440, 60)
 
 
@@ -118,10 +118,10 @@ def test_ragged_batch_all_lane_layouts(H, oracle_mod, precision, kernel, simple_
     _compare(H, oracle_mod, wl, precision, kernel, 401, 7, splits=[200, 201])
 
 
-def test_config2_full_size_sampled(H, oracle_mod):
+def test_wall_batch_full_size_sampled(H, oracle_mod):
     """Full configuration (4096 walls, 52560 steps, FP32 persistent, the benchmark launch) against
     the oracle on a sample of walls (walls are independent, so the subset is exact)."""
-    wl = wk.config2()
+    wl = wk.wall_batch()
     g = H.Hygro(wl, precision="fp32", kernel="persistent")
     samples = g.run_sampled(wl.n_steps, 1440)
     T, P = g.fields(0)
@@ -141,9 +141,9 @@ def test_config2_full_size_sampled(H, oracle_mod):
 
 
 @pytest.mark.parametrize("kernel", ["plain", "persistent"])
-def test_config2_full_size_fp64_sampled(H, oracle_mod, kernel):
+def test_wall_batch_full_size_fp64_sampled(H, oracle_mod, kernel):
     """The FP64 kernels at full size against the oracle on a sample of walls, to 1e-12."""
-    wl = wk.config2()
+    wl = wk.wall_batch()
     g = H.Hygro(wl, precision="fp64", kernel=kernel)
     g.run(wl.n_steps)
     T, P = g.fields(0)

@@ -30,7 +30,7 @@ def relinf(x, ref):
 
 def mixed_building(seed=4, n_steps=600):
     """8 rooms of 1..8 walls (N 3..300, some multi-layer) plus free walls without rooms."""
-    base = wk.config3(seed=seed, n_rooms=8, walls_per_room=8, n_steps=n_steps, n_min=3, n_max=300)
+    base = wk.building(seed=seed, n_rooms=8, walls_per_room=8, n_steps=n_steps, n_min=3, n_max=300)
     counts = [1, 2, 3, 4, 5, 6, 7, 8]
     keep = []
     for r, c in enumerate(counts):
@@ -39,7 +39,7 @@ def mixed_building(seed=4, n_steps=600):
     sub.bc_kind = base.bc_kind[keep].copy()
     sub.bc_room = base.bc_room[keep].copy()
     # three more walls on room 2 become free walls (ambient on both faces)
-    free = wk.config2(seed=seed + 1, n_walls=5, n_steps=n_steps, n_min=3, n_max=200)
+    free = wk.wall_batch(seed=seed + 1, n_walls=5, n_steps=n_steps, n_min=3, n_max=200)
     wl = wk.concat([sub, free])
     wl.bc_kind = np.concatenate([sub.bc_kind, free.bc_kind])
     wl.bc_room = np.concatenate([sub.bc_room, free.bc_room])
@@ -70,7 +70,7 @@ def test_rooms_mixed_building(H, oracle_mod, precision, tol):
 
 def test_rooms_full_building_fp32(H, oracle_mod):
     """The whole-building configuration (64 rooms x 6 walls, 30 days at dt = 300 s), FP32."""
-    wl = wk.config3()
+    wl = wk.building()
     g = H.Hygro(wl, precision="fp32")
     s = g.run_sampled(wl.n_steps, 288)
     T, P = g.fields(0)

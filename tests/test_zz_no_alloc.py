@@ -39,7 +39,7 @@ def test_noalloc_matches_run_two_calls(H, kernel):
 
     from paper_1703_10119_gb300 import workloads as wk
 
-    wl = wk.config2(seed=21, n_walls=96, n_steps=300, n_min=3, n_max=512)
+    wl = wk.wall_batch(seed=21, n_walls=96, n_steps=300, n_min=3, n_max=512)
     a = H.Hygro(wl, precision="fp32", kernel=kernel)
     b = H.Hygro(wl, precision="fp32", kernel=kernel)
     for call in range(2):
@@ -69,7 +69,7 @@ def test_noalloc_matches_run_two_calls(H, kernel):
 def test_noalloc_refuses_oversized_samples(H):
     from paper_1703_10119_gb300 import workloads as wk
 
-    wl = wk.config2(seed=22, n_walls=64, n_steps=100, n_min=3, n_max=100)
+    wl = wk.wall_batch(seed=22, n_walls=64, n_steps=100, n_min=3, n_max=100)
     g = H.Hygro(wl, precision="fp32")
     g.run(3)
     T0, P0 = g.fields(0)
