@@ -13,9 +13,12 @@
 #include <vector>
 
 #include "hygro_internal.cuh"
+#include "host_layout.h"
 #include "adjoint_reg.cuh"
 
 using namespace hygro;
+
+static_assert(kLayoutMaxK == kMaxK, "lane layout and kernel disagree on the most nodes per lane");
 
 namespace {
 
@@ -536,54 +539,14 @@ hygro_status check_nonfinite(hygro_ctx *c)
 
 const uint64_t kStateMagic = 0x6879677273746174ull;  // "hygrstat"
 
-// Lane layout of one wall for the persistent kernel: K nodes per lane, Wl lanes, lanes of K or K-1
-// nodes (short_mask), the last lane full. Preferred: every layer interface on a lane boundary
-// (each layer split into lanes of K or K-1 nodes, its short lanes first), trying K from
-// ceil(N/32) up while the lanes fit in a warp. Otherwise the plain split (short lanes first).
+// Lane layout of one wall for the persistent kernel (host_layout.h).
 void wall_layout(int N, const int32_t *first, int nl, WallInfo &wi)
 {
-    const int K0 = (N + 31) / 32;
-    for (int K = K0; K <= kMaxK; ++K) {
-        int lanes = 0;
-        uint32_t mask = 0;
-        bool ok = true;
-        for (int l = 0; l < nl && ok; ++l) {
-            const int Nl = (l + 1 < nl ? first[l + 1] : N) - first[l];
-            const int c = (Nl + K - 1) / K;
-            const int sh = c * K - Nl;
-            const bool last = l + 1 == nl;
-            if (sh > c - (last ? 1 : 0) || lanes + c > 32) {
-                ok = false;
-                break;
-            }
-            for (int i = 0; i < sh; ++i) mask |= 1u << (lanes + i);
-            lanes += c;
-        }
-        if (ok) {
-            wi.K = K;
-            wi.Wl = lanes;
-            wi.short_mask = mask;
-            wi.aligned = 1;
-            return;
-        }
-    }
-    wi.K = K0;
-    wi.Wl = (N + K0 - 1) / K0;
-    const int m = wi.Wl * K0 - N;
-    wi.short_mask = m > 0 ? ((1u << m) - 1u) : 0u;
-    // aligned by chance when every interface is a lane start
-    int aligned = 1;
-    for (int l = 1; l < nl; ++l) {
-        int start = 0, lane = 0;
-        bool hit = false;
-        while (lane < wi.Wl && start <= first[l]) {
-            if (start == first[l]) hit = true;
-            start += ((wi.short_mask >> lane) & 1u) ? K0 - 1 : K0;
-            ++lane;
-        }
-        if (!hit) aligned = 0;
-    }
-    wi.aligned = aligned;
+    const LaneLayout o = hygro::wall_layout(N, first, nl);
+    wi.K = o.K;
+    wi.Wl = o.Wl;
+    wi.short_mask = o.short_mask;
+    wi.aligned = o.aligned;
 }
 
 
@@ -659,62 +622,22 @@ hygro_status build_schedule(hygro_ctx *c)
         CUDA_TRY(c, cudaMemcpy(c->d_rooms, ri.data(), ri.size() * sizeof(RoomInfo), cudaMemcpyHostToDevice));
     }
     {
-        // Persistent blocks: walls sorted by nodes per lane and code variant, cut into rounds of
-        // round_size walls (one per warp of a block); rounds dealt to blocks largest estimated cost
-        // first, each to the least loaded block (LPT); a block runs its rounds largest first. Cost
-        // per step ~ K * (cost of a slot) + fixed part.
-        std::vector<int32_t> srt;
-        for (int w = 0; w < W; ++w)
-            if (!in_room[w]) srt.push_back(w);
-        const int Wf = (int)srt.size();
+        // Persistent blocks: rounds of same-size walls dealt to blocks by estimated cost (host_layout.h)
+        std::vector<SchedWall> sw;
+        for (int w = 0; w < W; ++w) {
+            if (in_room[w]) continue;
+            const WallInfo &x = c->walls[w];
+            const bool simple = x.simple && c->precision == HYGRO_FP32;
+            sw.push_back({w, x.K, x.aligned ? (simple ? 0 : 1) : (simple ? 3 : 2), x.N});
+        }
+        const int Wf = (int)sw.size();
         c->n_free = Wf;
         const int G = c->grid_persistent;
         const int wpb = c->precision == HYGRO_FP64 ? PersistCfg<double>::warps : PersistCfg<float>::warps;
         const int R = std::max(1, std::min(wpb, Wf / G));
         c->round_size = R;
-        // code variant (as in the kernel) and time per step of a wall with K nodes per lane when an SM
-        // is shared by its full warp count, a + b K (nanoseconds, measured on GB300 with a wall trace at
-        // 16 warps per SM for variants 0 and 3; variants 1 and 2 scaled from an earlier 12-warp trace)
-        auto kind_of = [&](const WallInfo &x) {
-            const bool simple = x.simple && c->precision == HYGRO_FP32;
-            return x.aligned ? (simple ? 0 : 1) : (simple ? 3 : 2);
-        };
-        auto cost = [&](const WallInfo &x) {
-            static const double a[4] = {107.0, 234.0, 156.0, 191.0};
-            static const double b[4] = {64.2, 76.0, 125.0, 77.2};
-            const int k = kind_of(x);
-            return a[k] + b[k] * x.K;
-        };
-        std::stable_sort(srt.begin(), srt.end(), [&](int a, int b) {
-            const WallInfo &x = c->walls[a], &y = c->walls[b];
-            if (x.K != y.K) return x.K > y.K;
-            if (kind_of(x) != kind_of(y)) return kind_of(x) < kind_of(y);
-            return x.N > y.N;
-        });
-        const int n_rounds = (Wf + R - 1) / R;
-        std::vector<double> rcost(n_rounds, 0.0);
-        for (int i = 0; i < Wf; ++i) rcost[i / R] = std::max(rcost[i / R], cost(c->walls[srt[i]]));
-        std::vector<int32_t> ridx(n_rounds);
-        for (int r = 0; r < n_rounds; ++r) ridx[r] = r;
-        std::stable_sort(ridx.begin(), ridx.end(), [&](int a, int b) { return rcost[a] > rcost[b]; });
-        std::vector<double> load(G, 0.0);
-        std::vector<std::vector<int32_t>> lists(G);
-        for (int r : ridx) {
-            int best = 0;
-            for (int g = 1; g < G; ++g)
-                if (load[g] < load[best]) best = g;
-            load[best] += rcost[r];
-            lists[best].push_back(r);
-        }
-        std::vector<int32_t> order;
-        std::vector<int32_t> boff(G + 1, 0);
-        order.reserve((size_t)n_rounds * R);
-        for (int g = 0; g < G; ++g) {
-            boff[g] = (int32_t)order.size();
-            for (int r : lists[g])
-                for (int i = 0; i < R; ++i) order.push_back(r * R + i < Wf ? srt[r * R + i] : -1);
-        }
-        boff[G] = (int32_t)order.size();
+        std::vector<int32_t> order, boff;
+        lpt_rounds(std::move(sw), G, R, order, boff);
         if (!order.empty())
             CUDA_TRY(c, cudaMemcpy(c->d_order, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
         CUDA_TRY(c, cudaMemcpy(c->d_block_off, boff.data(), boff.size() * sizeof(int32_t), cudaMemcpyHostToDevice));

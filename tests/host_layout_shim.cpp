@@ -1,0 +1,38 @@
+// Test shim: the persistent kernel's host-side work partition (paper_1703_10119_gb300/csrc/host_layout.h)
+// behind a C ABI, built with g++ by tests/test_host_layout.py. No CUDA.
+#include "host_layout.h"
+
+extern "C" {
+
+// out: K, Wl, short_mask, aligned
+void shim_wall_layout(int N, const int32_t *first, int nl, int64_t *out)
+{
+    const hygro::LaneLayout o = hygro::wall_layout(N, first, nl);
+    out[0] = o.K;
+    out[1] = o.Wl;
+    out[2] = (int64_t)o.short_mask;
+    out[3] = o.aligned;
+}
+
+double shim_sched_cost(int K, int kind)
+{
+    return hygro::sched_cost({0, K, kind, 0});
+}
+
+// Returns the number of order entries written (at most cap), or -1 when cap is too small.
+int shim_lpt_rounds(int n, const int32_t *wall, const int32_t *K, const int32_t *kind, const int32_t *N, int G,
+                    int R, int32_t *order, int cap, int32_t *boff, double *load)
+{
+    std::vector<hygro::SchedWall> w(n);
+    for (int i = 0; i < n; ++i) w[i] = {wall[i], K[i], kind[i], N[i]};
+    std::vector<int32_t> o, b;
+    std::vector<double> l;
+    hygro::lpt_rounds(w, G, R, o, b, &l);
+    if ((int)o.size() > cap) return -1;
+    for (size_t i = 0; i < o.size(); ++i) order[i] = o[i];
+    for (int g = 0; g <= G; ++g) boff[g] = b[g];
+    for (int g = 0; g < G; ++g) load[g] = l[g];
+    return (int)o.size();
+}
+
+}  // extern "C"
