@@ -225,6 +225,13 @@ def run_oracle_sample(sub, n_steps: int):
     return o, el
 
 
+def batch_config(wl, n_steps: int) -> dict:
+    """The benchmark workload as both arms name it."""
+    return {"workload": (f"{wl.n_walls} ragged 1D walls per GPU (1-3 layers, 50-400 nodes), "
+                         f"dt=600 s x {n_steps} steps (one year)"),
+            "nodes_per_gpu": int(wl.total_nodes), "cell_updates_per_gpu_per_step": int(wl.total_nodes) * int(n_steps)}
+
+
 def bench_reference(args):
     from paper_1703_10119_gb300 import workloads as wk
     import oracle
@@ -246,7 +253,8 @@ def bench_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl.name, "sample": sample},
+            "config": {**batch_config(wl, args.year_steps), "path": "FP64 oracle on the host cores",
+                       "sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -628,9 +636,7 @@ def bench_ours(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": (f"{wl.n_walls} ragged 1D walls per GPU (1-3 layers, 50-400 nodes), "
-                                        f"dt=600 s x {args.year_steps} steps (one year), FP32 persistent kernel"),
-                           "nodes_per_gpu": int(wl.total_nodes), "cell_updates_per_step": int(units_total),
+                "config": {**batch_config(wl, args.year_steps), "path": "FP32 persistent kernel",
                            "l2": "flushed between timed runs (512 MB write)", "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,
                 "gpu_launches": args.steps, "clocks": cs.summary(), "parity_vs_oracle": parity,
