@@ -8,12 +8,12 @@
 #include <cstring>
 #include <mutex>
 #include <string>
-#include <thread>
 #include <type_traits>
 #include <vector>
 
 #include "hygro_internal.cuh"
 #include "host_layout.h"
+#include "host_noise.h"
 #include "adjoint_reg.cuh"
 
 using namespace hygro;
@@ -369,54 +369,6 @@ hygro_status upload_faces(hygro_ctx *c)
 
 constexpr size_t kStagePairs = size_t(1) << 23;   // (T, Pv) pairs per host chunk of the noise upload (64 MB)
 
-// Copies pairs [p0, p1) of a face's concatenated tables into dst (wall wid[k]'s table starts at pair
-// start[k] and has len[k] pairs, read from its hygro_bc), with up to `threads` host threads, each checking
-// the values it copies. Returns the index of the first non-finite pair, or -1.
-int64_t gather_tables(const hygro_bc *bc, const std::vector<int> &wid, const std::vector<int64_t> &start,
-                      const std::vector<int64_t> &len, int64_t p0, int64_t p1, float *dst, int threads)
-{
-    auto part = [&](int64_t a, int64_t b) -> int64_t {
-        if (a >= b) return -1;
-        size_t k = (size_t)(std::upper_bound(start.begin(), start.end(), a) - start.begin()) - 1;
-        int64_t x = a;
-        while (x < b) {
-            const int64_t s = start[k], e = std::min(b, s + len[k]);
-            const float *src = bc[wid[k]].noise + 2 * (x - s);
-            float *out = dst + 2 * (x - p0);
-            const int64_t n = 2 * (e - x);
-            uint32_t bad = 0;
-            for (int64_t i = 0; i < n; ++i) {   // branch-free copy and check (vectorises)
-                uint32_t u;
-                memcpy(&u, src + i, sizeof u);
-                memcpy(out + i, &u, sizeof u);
-                bad |= (uint32_t)((u & 0x7f800000u) == 0x7f800000u);
-            }
-            if (bad)
-                for (int64_t i = 0; i < n; ++i)
-                    if (!std::isfinite(src[i])) return x + i / 2;
-            x = e;
-            ++k;
-        }
-        return -1;
-    };
-    const int64_t n = p1 - p0;
-    const int T = (int)std::max<int64_t>(1, std::min<int64_t>(threads, n / (int64_t(1) << 18)));
-    std::vector<int64_t> first_bad(T, -1);
-    std::vector<std::thread> pool;
-    for (int t = 1; t < T; ++t) {
-        try {
-            pool.emplace_back([&, t] { first_bad[t] = part(p0 + n * t / T, p0 + n * (t + 1) / T); });
-        } catch (...) {   // no thread: this part on the calling thread
-            first_bad[t] = part(p0 + n * t / T, p0 + n * (t + 1) / T);
-        }
-    }
-    first_bad[0] = part(p0, p0 + n / T);
-    for (auto &th : pool) th.join();
-    for (int t = 0; t < T; ++t)
-        if (first_bad[t] >= 0) return first_bad[t];
-    return -1;
-}
-
 // Uploads the noise tables of one face (hygro_bc array, validated except for the table values) and
 // records each wall's offset and length in v. Host threads gather the per-wall tables into two host
 // chunks (pinned when possible), checking each value as they copy, while the previous chunk's copy to
@@ -427,6 +379,7 @@ hygro_status upload_noise(hygro_ctx *c, int face, const hygro_bc *bc, std::vecto
 {
     const int W = c->W;
     std::vector<int> wid;
+    std::vector<const float *> src;
     std::vector<int64_t> start, len;
     int64_t total = 0;
     for (int w = 0; w < W; ++w) {
@@ -435,6 +388,7 @@ hygro_status upload_noise(hygro_ctx *c, int face, const hygro_bc *bc, std::vecto
         v[w].noise_len = has ? bc[w].noise_len : 0;
         if (!has) continue;
         wid.push_back(w);
+        src.push_back(bc[w].noise);
         start.push_back(total);
         len.push_back(bc[w].noise_len);
         total += bc[w].noise_len;
@@ -481,7 +435,7 @@ hygro_status upload_noise(hygro_ctx *c, int face, const hygro_bc *bc, std::vecto
             const int64_t p1 = std::min(total, p0 + (int64_t)c->stage_pairs);
             const int slot = chunk & 1;
             if (chunk >= 2) CUDA_TRY(c, cudaEventSynchronize(c->stage_ev[slot]));
-            bad = gather_tables(bc, wid, start, len, p0, p1, c->h_stage[slot], threads);
+            bad = gather_tables(src, start, len, p0, p1, c->h_stage[slot], threads);
             if (bad >= 0) break;
             CUDA_TRY(c, cudaMemcpyAsync(c->d_stage + p0, c->h_stage[slot], (size_t)(p1 - p0) * sizeof(float2),
                                         cudaMemcpyHostToDevice, c->stream));

@@ -1,6 +1,8 @@
-// Test shim: the persistent kernel's host-side work partition (paper_1703_10119_gb300/csrc/host_layout.h)
-// behind a C ABI, built with g++ by tests/test_host_layout.py. No CUDA.
+// Test shim: the library's CUDA-free host logic behind a C ABI, built with g++ by the CPU tests
+// (tests/test_host_layout.py, tests/test_host_noise.py): the persistent kernel's work partition
+// (paper_1703_10119_gb300/csrc/host_layout.h) and the noise-table gather (csrc/host_noise.h).
 #include "host_layout.h"
+#include "host_noise.h"
 
 extern "C" {
 
@@ -33,6 +35,20 @@ int shim_lpt_rounds(int n, const int32_t *wall, const int32_t *K, const int32_t 
     for (int g = 0; g <= G; ++g) boff[g] = b[g];
     for (int g = 0; g < G; ++g) load[g] = l[g];
     return (int)o.size();
+}
+
+// n tables of len[k] pairs at src[k] (back to back in the order given); gathers pairs [p0, p1) into dst.
+int64_t shim_gather_tables(int n, const float *const *src, const int64_t *len, int64_t p0, int64_t p1, float *dst,
+                           int threads, int64_t min_pairs)
+{
+    std::vector<const float *> s(src, src + n);
+    std::vector<int64_t> start(n), l(len, len + n);
+    int64_t off = 0;
+    for (int k = 0; k < n; ++k) {
+        start[k] = off;
+        off += l[k];
+    }
+    return hygro::gather_tables(s, start, l, p0, p1, dst, threads, min_pairs);
 }
 
 }  // extern "C"

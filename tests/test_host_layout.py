@@ -24,7 +24,7 @@ def shim(tmp_path_factory):
     out = str(tmp_path_factory.mktemp("host_layout") / "libhost_layout.so")
     subprocess.run([gxx, "-O2", "-std=c++17", "-shared", "-fPIC",
                     "-I", os.path.join(ROOT, "paper_1703_10119_gb300", "csrc"),
-                    os.path.join(ROOT, "tests", "host_layout_shim.cpp"), "-o", out], check=True)
+                    os.path.join(ROOT, "tests", "host_logic_shim.cpp"), "-o", out], check=True)
     lib = C.CDLL(out)
     lib.shim_sched_cost.restype = C.c_double
     return lib
