@@ -180,7 +180,9 @@ HYGRO_API hygro_status hygro_set_materials(hygro_ctx *ctx, const int32_t *n_laye
  * device during the call (the caller's tables may be freed afterwards); each value is checked on the
  * way. A non-finite value gives HYGRO_E_INVALID naming the wall, as does any other invalid field, and
  * a refused call leaves the face's previous description and tables in place. Setting one face does not
- * copy the other face's tables again, nor does hygro_set_materials. */
+ * copy the other face's tables again, nor does hygro_set_materials. The copy uses up to 8 host threads
+ * and two host staging chunks of up to 64 MB each (pinned when the allocation succeeds), which the
+ * context keeps for its next uploads; the call returns when the tables are on the device. */
 HYGRO_API hygro_status hygro_set_bc(hygro_ctx *ctx, int32_t face, const hygro_bc *bc);
 
 /* Rooms of the whole-building model: rooms[r] for r in 0..n_rooms-1, wall_area[w] (m^2) the area
