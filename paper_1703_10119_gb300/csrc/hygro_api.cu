@@ -14,6 +14,7 @@
 #include "hygro_internal.cuh"
 #include "host_layout.h"
 #include "host_noise.h"
+#include "host_forcing.h"
 #include "adjoint_reg.cuh"
 
 using namespace hygro;
@@ -51,16 +52,6 @@ bool is_device_ptr(const void *p)
 }
 
 bool finite_nonneg(double x) { return std::isfinite(x) && x >= 0.0; }
-
-uint64_t turns_fixed(double x)
-{
-    // fraction of x in [0, 1) scaled by 2^64
-    double f = x - std::floor(x);
-    double s = std::ldexp(f, 64);
-    if (!(s < 18446744073709551616.0)) return 0;
-    if (s < 0) return 0;
-    return (uint64_t)s;
-}
 
 }  // namespace
 
@@ -163,16 +154,10 @@ FaceInfo face_info(const hygro_bc &b, double T_ref, double P_ref, double t0, dou
     if (noise_len > 0) {
         o.noise_len = (int32_t)noise_len;
         o.noise_off = noise_off;
-        o.npos0 = (int64_t)std::llround(std::ldexp(t0 / b.noise_dt, 40));
-        o.nstep = (int64_t)std::llround(std::ldexp(dt / b.noise_dt, 40));
-        // first step n >= 0 with npos0 + n nstep >= (len - 1) 2^40 (exact integer search; nstep > 0)
-        const __int128 target = (__int128)(noise_len - 1) << 40;
-        int64_t n_hi = 0;
-        if ((__int128)o.npos0 < target) {
-            const __int128 need = target - o.npos0;
-            n_hi = o.nstep > 0 ? (int64_t)((need + o.nstep - 1) / o.nstep) : INT64_MAX;
-        }
-        o.n_hi = n_hi;
+        const NoiseFixed nf = noise_fixed(t0, dt, b.noise_dt, noise_len);   // host_forcing.h
+        o.npos0 = nf.npos0;
+        o.nstep = nf.nstep;
+        o.n_hi = nf.n_hi;
     } else {
         o.n_hi = INT64_MAX;
     }

@@ -1,6 +1,8 @@
 // Test shim: the library's CUDA-free host logic behind a C ABI, built with g++ by the CPU tests
-// (tests/test_host_layout.py, tests/test_host_noise.py): the persistent kernel's work partition
-// (paper_1703_10119_gb300/csrc/host_layout.h) and the noise-table gather (csrc/host_noise.h).
+// (tests/test_host_layout.py, tests/test_host_noise.py, tests/test_host_forcing.py): the persistent
+// kernel's work partition (paper_1703_10119_gb300/csrc/host_layout.h), the noise-table gather
+// (csrc/host_noise.h) and the fixed-point forcing accumulators (csrc/host_forcing.h).
+#include "host_forcing.h"
 #include "host_layout.h"
 #include "host_noise.h"
 
@@ -49,6 +51,17 @@ int64_t shim_gather_tables(int n, const float *const *src, const int64_t *len, i
         off += l[k];
     }
     return hygro::gather_tables(s, start, l, p0, p1, dst, threads, min_pairs);
+}
+
+uint64_t shim_turns_fixed(double x) { return hygro::turns_fixed(x); }
+
+// out: npos0, nstep, n_hi
+void shim_noise_fixed(double t0, double dt, double noise_dt, int64_t len, int64_t *out)
+{
+    const hygro::NoiseFixed o = hygro::noise_fixed(t0, dt, noise_dt, len);
+    out[0] = o.npos0;
+    out[1] = o.nstep;
+    out[2] = o.n_hi;
 }
 
 }  // extern "C"
