@@ -15,6 +15,8 @@ import pytest
 from paper_1703_10119_gb300 import workloads as wk
 from test_oracle_pins import _run_to_steady
 
+import golden_data
+
 
 @pytest.mark.parametrize("nu", [0.3, 1.0, 1.7])
 def test_vapour_fraction_steady_state_is_exact(oracle_mod, nu):
@@ -91,3 +93,39 @@ def test_zone_vapour_pulse_sum(oracle_mod):
     mean = 0.5 * (o.room[0, 2] + o.room[0, 3])
     assert abs(mean - expect) <= 1e-12 * expect
     assert 100 < np.count_nonzero(g > g0) < n   # the window opened and closed inside the run
+
+
+def test_one_zone_workload_takes_the_printed_set_up():
+    """The one-zone inputs carry the printed values of tests/golden/one_zone_table2_appendix_b.txt (Sec. 5.2
+    and its Table 2): per wall the linear coefficients (cTM as chi cM, kTM as the vapour fraction
+    nu = kTM / (Lv kM)), area and outdoor exchange; the zone's volume, exchange, load and ventilation."""
+    g = golden_data.load("one_zone_table2_appendix_b.txt")
+    z = g["zone"]["zone"]
+    wl = wk.one_zone()
+    Lv = wl.Lv
+    table = [g["table2"][n] for n in ("north", "south", "east", "east")]   # west = east (one column)
+    lp = wl.layer_par                                                      # one layer per wall
+    col = {k: i for i, k in enumerate(wk.LAYER_FIELDS)}
+    bcol = {k: i for i, k in enumerate(wk.BC_FIELDS)}
+    rcol = {k: i for i, k in enumerate(wk.ROOM_FIELDS)}
+    assert wl.n_walls == 4 and lp.shape[0] == 4
+    for w, t in enumerate(table):
+        assert lp[w, col["cM0"]] == t["cM"] and lp[w, col["kM0"]] == t["kM"]
+        assert lp[w, col["cTT0"]] == t["cTT"] and lp[w, col["kTT0"]] == t["kTT"]
+        assert lp[w, col["a"]] == lp[w, col["b"]] == lp[w, col["aT"]] == lp[w, col["bT"]] == 0.0
+        assert abs(lp[w, col["chi"]] * t["cM"] - t["cTM"]) <= 1e-12 * t["cTM"]
+        assert abs(wl.vapour_frac[w] * Lv * t["kM"] - t["kTM"]) <= 1e-12 * t["kTM"]
+        assert wl.rooms["wall_area"][w] == t["A"]
+        assert wl.bc_par[w, 0, bcol["hT"]] == t["hT"] and wl.bc_par[w, 0, bcol["hM"]] == t["hM"]
+        assert wl.bc_par[w, 1, bcol["hT"]] == z["hT_in"] and wl.bc_par[w, 1, bcol["hM"]] == z["hM_in"]
+        assert wl.bc_kind[w, 0] == wk.BC_AMBIENT and wl.bc_kind[w, 1] == wk.BC_ROOM
+        assert abs(wl.thickness[w] - z["L"]) < 1e-15
+    r = wl.rooms["par"][0]
+    assert r[rcol["volume"]] == z["volume"] and r[rcol["ach"]] == z["ach"]
+    assert abs(r[rcol["g_vap"]] * 3.6e6 - z["g_base"]) < 1e-9            # kg/s -> g/h
+    assert abs(r[rcol["g_pulse"]] * 3.6e6 - z["g_extra"]) < 1e-9
+    assert r[rcol["pulse_on"]] == 3600.0 * z["extra_on"] and r[rcol["pulse_off"]] == 3600.0 * z["extra_off"]
+    assert r[rcol["pulse_period"]] == 86400.0
+    Ti = 273.15 + z["Ti_C"]
+    assert np.all(wl.T_init == Ti) and abs(wl.rooms["Ta0"][0] - Ti) < 1e-12
+    assert np.allclose(wl.P_init, z["phi_i"] * wk.PSAT_REF, rtol=1e-15)

@@ -20,6 +20,8 @@ from scipy.optimize import brentq
 
 from paper_1703_10119_gb300 import workloads as wk
 
+import golden_data
+
 PS = wk.PSAT_REF
 
 
@@ -351,29 +353,26 @@ def test_uniform_invariance(oracle_mod):
 
 def test_appendix_b_dimensionless_numbers():
     """Table 2 (one-zone walls) with t0 = 1 h, L = 0.1 m, Ti = 293.15 K and Pvi = Psat/2 reproduce
-    the Fourier, gamma and Biot numbers printed in Appendix B (within their 2-3 printed digits)."""
-    t0, L, Ti, Lv = 3600.0, 0.1, 293.15, 2.5e6
-    Pvi = 0.5 * PS
-    walls = {  # cM, kM, cTT, kTT, cTM, kTM, hT_out, hM_out (Table 2)
-        "north": (1.82e-2, 5.89e-9, 7.7e5, 0.294, 1.52e3, 1.59e-2, 5.0, 2e-7),
-        "south": (1.18e-1, 2.92e-8, 1.28e6, 0.841, 9.88e3, 2.96e-3, 25.0, 8e-7),
-        "east": (6.09e-2, 5.47e-9, 8.61e5, 0.387, 5.09e3, 1.53e-2, 12.0, 4e-7),
-    }
-    printed = {  # FoM, FoTT, FoTM, gamma, BiM, BiTT, BiTM at x = 0, BiM, BiTT, BiTM at x = 1
-        "north": (1.16e-1, 1.37e-1, 3.76, 7.87e-3, 3.39, 1.7, 6.78e-1, 5.09e-1, 2.72, 1.01e-1),
-        "south": (8.9e-2, 2.36e-1, 0.107, 3.07e-2, 2.73, 2.97, 9.48e-1, 1.02e-1, 9.5e-1, 3.55e-2),
-        "east": (3.23e-2, 1.61e-1, 1.08, 2.35e-2, 7.31, 3.1, 1.03, 5.48e-1, 2.06, 7.72e-2),
-    }
-    hT_in, hM_in = 8.0, 3e-8
-    for name, (cM, kM, cTT, kTT, cTM, kTM, hT, hM) in walls.items():
+    the Fourier, gamma and Biot numbers printed in Appendix B (within their 2-3 printed digits); both
+    tables as printed in tests/golden/one_zone_table2_appendix_b.txt."""
+    g = golden_data.load("one_zone_table2_appendix_b.txt")
+    z = g["zone"]["zone"]
+    t0, L, Ti, Lv = 3600.0, z["L"], 273.15 + z["Ti_C"], 2.5e6
+    Pvi = z["phi_i"] * PS
+    hT_in, hM_in = z["hT_in"], z["hM_in"]
+    cols = ("FoM", "FoTT", "FoTM", "gamma", "BiM_0", "BiTT_0", "BiTM_0", "BiM_1", "BiTT_1", "BiTM_1")
+    for name, w in g["table2"].items():
+        cM, kM, cTT, kTT, cTM, kTM, hT, hM = (w[k] for k in ("cM", "kM", "cTT", "kTT", "cTM", "kTM", "hT", "hM"))
         got = (t0 * kM / (L * L * cM), t0 * kTT / (L * L * cTT), t0 * kTM / (L * L * cTM), cTM * Pvi / (cTT * Ti),
                hM * L / kM, hT * L / kTT, Lv * hM * L * Pvi / (kTT * Ti),
                hM_in * L / kM, hT_in * L / kTT, Lv * hM_in * L * Pvi / (kTT * Ti))
-        for g, p in zip(got, printed[name]):
-            assert abs(g - p) <= 0.012 * abs(p), (name, g, p)
+        printed = g["appendix_b"][name]
+        for c, v in zip(cols, got):
+            p = printed[c]
+            assert abs(v - p) <= 0.012 * abs(p), (name, c, v, p)
     # cTM / cM = cw * 20 (the coupling storage with T in Celsius), for every wall of Table 2
-    for cM, _, _, _, cTM, *_ in walls.values():
-        assert abs(cTM / cM / (4180.0 * 20.0) - 1.0) < 0.01
+    for w in g["table2"].values():
+        assert abs(w["cTM"] / w["cM"] / (4180.0 * 20.0) - 1.0) < 0.01
 
 
 def test_dimensionless_similarity(oracle_mod):
