@@ -127,3 +127,28 @@ def test_2d_desc_layout_and_rejections_before_touching_the_device(lib):
     assert lib.hygro2d_run(None, 1) == H.HYGRO_E_INVALID
     assert lib.hygro2d_sync(None) == H.HYGRO_E_INVALID
     lib.hygro2d_destroy(None)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the built CUDA library the binding raises; there is no other code path to fall back on."""
+    monkeypatch.setattr(H, "_lib", None)
+    monkeypatch.setattr(H, "library_path", lambda: str(tmp_path / "absent" / "libhygro.so"))
+    with pytest.raises(ImportError, match="not built"):
+        H.lib()
+
+
+def test_no_device_is_an_error_not_a_fallback(lib):
+    """A valid description on a machine without a CUDA device gives HYGRO_E_CUDA from hygro_create: the
+    library computes on the GPU only."""
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    import numpy as np
+    n = np.array([10, 12], np.int32)
+    L = np.array([0.1, 0.2])
+    d = H.hygro_desc(n_walls=2, n_nodes=n.ctypes.data, thickness=L.ctypes.data, dt=60.0, Psat=2337.0,
+                     Lv=2.5e6)
+    with pytest.raises(H.HygroError) as e:
+        H.hygro_create(d)
+    assert e.value.status == H.HYGRO_E_CUDA
