@@ -14,6 +14,7 @@
 #include "hygro_internal.cuh"
 #include "host_layout.h"
 #include "host_noise.h"
+#include "host_fault.h"
 #include "host_forcing.h"
 #include "adjoint_reg.cuh"
 
@@ -251,6 +252,19 @@ hygro_status fail(hygro_ctx *c, hygro_status st, const char *fmt, ...)
     do {                                                                                                 \
         cudaError_t e_ = (call);                                                                         \
         if (e_ != cudaSuccess) return fail(ctx, HYGRO_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+// Host-side fault injection (host_fault.h): HYGRO_FAULT=<entry point>:<n> fails the n-th call of that entry
+// point with HYGRO_E_CUDA before it changes anything.
+bool fault_hit(const char *call)
+{
+    static FaultInjector inj(parse_fault(getenv("HYGRO_FAULT")));
+    return inj.hit(call);
+}
+
+#define FAULT_POINT(ctx, name)                                                                     \
+    do {                                                                                           \
+        if (fault_hit(name)) return fail(ctx, HYGRO_E_CUDA, "%s: injected fault (HYGRO_FAULT)", name); \
     } while (0)
 
 void free_all(hygro_ctx *c)
@@ -644,6 +658,7 @@ hygro_status hygro_create(const hygro_desc *desc, hygro_ctx **out)
 {
     if (out == nullptr) return fail(nullptr, HYGRO_E_INVALID, "out is NULL");
     *out = nullptr;
+    FAULT_POINT(nullptr, "hygro_create");
     if (desc == nullptr) return fail(nullptr, HYGRO_E_INVALID, "desc is NULL");
     if (desc->n_walls < 1) return fail(nullptr, HYGRO_E_INVALID, "n_walls must be >= 1");
     if (desc->n_nodes == nullptr || desc->thickness == nullptr)
@@ -769,6 +784,7 @@ hygro_status hygro_set_materials(hygro_ctx *c, const int32_t *n_layers, const in
                                  const hygro_layer *layers, const double *T_init, const double *P_init)
 {
     if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    FAULT_POINT(c, "hygro_set_materials");
     if (!n_layers || !layer_first || !layers || !T_init || !P_init)
         return fail(c, HYGRO_E_INVALID, "n_layers, layer_first, layers, T_init and P_init are required");
     const int W = c->W;
@@ -867,6 +883,7 @@ hygro_status hygro_set_materials(hygro_ctx *c, const int32_t *n_layers, const in
 hygro_status hygro_set_bc(hygro_ctx *c, int32_t face, const hygro_bc *bc)
 {
     if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    FAULT_POINT(c, "hygro_set_bc");
     if (face != 0 && face != 1) return fail(c, HYGRO_E_INVALID, "face must be 0 or 1");
     if (bc == nullptr) return fail(c, HYGRO_E_INVALID, "bc is NULL");
     for (int w = 0; w < c->W; ++w) {
@@ -896,6 +913,7 @@ hygro_status hygro_set_bc(hygro_ctx *c, int32_t face, const hygro_bc *bc)
 hygro_status hygro_set_rooms(hygro_ctx *c, int32_t n_rooms, const hygro_room *rooms, const double *wall_area)
 {
     if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    FAULT_POINT(c, "hygro_set_rooms");
     if (n_rooms < 0) return fail(c, HYGRO_E_INVALID, "n_rooms must be >= 0");
     if (n_rooms > 0 && (rooms == nullptr || wall_area == nullptr))
         return fail(c, HYGRO_E_INVALID, "rooms and wall_area are required");
@@ -945,6 +963,7 @@ hygro_status hygro_set_rooms(hygro_ctx *c, int32_t n_rooms, const hygro_room *ro
 hygro_status hygro_set_vapour_fraction(hygro_ctx *c, const double *nu)
 {
     if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    FAULT_POINT(c, "hygro_set_vapour_fraction");
     if (nu == nullptr) return fail(c, HYGRO_E_INVALID, "nu is NULL");
     for (int w = 0; w < c->W; ++w)
         if (!finite_nonneg(nu[w])) return fail(c, HYGRO_E_INVALID, "wall %d: nu must be finite and >= 0", w);
@@ -975,6 +994,7 @@ hygro_status hygro_set_vapour_fraction(hygro_ctx *c, const double *nu)
 hygro_status hygro_set_option(hygro_ctx *c, int32_t option, int64_t value)
 {
     if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    FAULT_POINT(c, "hygro_set_option");
     if (option == HYGRO_OPT_ROOM_SCHEME) {
         if (value != HYGRO_ROOM_DF && value != HYGRO_ROOM_EULER)
             return fail(c, HYGRO_E_INVALID, "room scheme must be HYGRO_ROOM_DF or HYGRO_ROOM_EULER");
@@ -989,6 +1009,7 @@ hygro_status hygro_set_option(hygro_ctx *c, int32_t option, int64_t value)
 hygro_status hygro_get_rooms(hygro_ctx *c, int32_t level, double *Ta, double *Pa)
 {
     if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    FAULT_POINT(c, "hygro_get_rooms");
     if (level != 0 && level != 1) return fail(c, HYGRO_E_INVALID, "level must be 0 (n) or 1 (n-1)");
     const int NR = (int)c->rooms.size();
     if (NR == 0) return HYGRO_OK;
@@ -1008,6 +1029,7 @@ hygro_status hygro_get_rooms(hygro_ctx *c, int32_t level, double *Ta, double *Pa
 hygro_status hygro_run(hygro_ctx *c, int64_t n_steps, int32_t sample_every, void *samples, size_t samples_bytes)
 {
     if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    FAULT_POINT(c, "hygro_run");
     if (n_steps < 0) return fail(c, HYGRO_E_INVALID, "n_steps must be >= 0");
     if (samples != nullptr && sample_every < 1) return fail(c, HYGRO_E_INVALID, "sample_every must be >= 1");
     if (!(c->have_materials && c->have_bc[0] && c->have_bc[1]))
@@ -1068,6 +1090,7 @@ hygro_status hygro_run(hygro_ctx *c, int64_t n_steps, int32_t sample_every, void
 hygro_status hygro_start_euler(hygro_ctx *c)
 {
     if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    FAULT_POINT(c, "hygro_start_euler");
     if (!(c->have_materials && c->have_bc[0] && c->have_bc[1]))
         return fail(c, HYGRO_E_STATE, "hygro_set_materials and hygro_set_bc (both faces) must come first");
     if (c->step != 0) return fail(c, HYGRO_E_STATE, "the Euler start applies at step 0 (the context is at %lld)",
@@ -1140,6 +1163,7 @@ hygro_status hygro_start_euler(hygro_ctx *c)
 hygro_status hygro_sync(hygro_ctx *c)
 {
     if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    FAULT_POINT(c, "hygro_sync");
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
     return check_nonfinite(c);
 }
@@ -1147,6 +1171,7 @@ hygro_status hygro_sync(hygro_ctx *c)
 hygro_status hygro_fluxes(hygro_ctx *c, double *flux, double *cumulative)
 {
     if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    FAULT_POINT(c, "hygro_fluxes");
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
     const size_t bytes = (size_t)c->W * 4 * sizeof(double);
     if (flux) CUDA_TRY(c, cudaMemcpyAsync(flux, c->d_flast, bytes, cudaMemcpyDefault, c->stream));
@@ -1157,6 +1182,7 @@ hygro_status hygro_fluxes(hygro_ctx *c, double *flux, double *cumulative)
 hygro_status hygro_balance(hygro_ctx *c, double *bal)
 {
     if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    FAULT_POINT(c, "hygro_balance");
     if (bal == nullptr) return fail(c, HYGRO_E_INVALID, "bal is NULL");
     if (!(c->have_materials && c->have_bc[0] && c->have_bc[1]))
         return fail(c, HYGRO_E_STATE, "hygro_set_materials and hygro_set_bc (both faces) must come first");
@@ -1229,6 +1255,7 @@ hygro_status hygro_balance(hygro_ctx *c, double *bal)
 hygro_status hygro_get_fields(hygro_ctx *c, int32_t level, double *T, double *P)
 {
     if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    FAULT_POINT(c, "hygro_get_fields");
     if (level != 0 && level != 1) return fail(c, HYGRO_E_INVALID, "level must be 0 (n) or 1 (n-1)");
     if (!c->have_materials) return fail(c, HYGRO_E_STATE, "hygro_set_materials must come first");
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
@@ -1251,6 +1278,7 @@ hygro_status hygro_get_fields(hygro_ctx *c, int32_t level, double *T, double *P)
 hygro_status hygro_set_fields(hygro_ctx *c, int32_t level, const double *T, const double *P)
 {
     if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    FAULT_POINT(c, "hygro_set_fields");
     if (level != 0 && level != 1) return fail(c, HYGRO_E_INVALID, "level must be 0 (n) or 1 (n-1)");
     if (!c->have_materials) return fail(c, HYGRO_E_STATE, "hygro_set_materials must come first");
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
@@ -1288,6 +1316,7 @@ hygro_status hygro_get_step(const hygro_ctx *c, int64_t *step)
 hygro_status hygro_get_state(hygro_ctx *c, void *buf, size_t *bytes)
 {
     if (c == nullptr || bytes == nullptr) return fail(c, HYGRO_E_INVALID, "ctx or bytes is NULL");
+    FAULT_POINT(c, "hygro_get_state");
     const size_t nf = (size_t)c->total_nodes * c->real_size;
     const size_t nroom = c->rooms.size() * 4 * sizeof(double);
     const size_t need = 5 * sizeof(int64_t) + 4 * nf + 2 * (size_t)c->W * 4 * sizeof(double) + nroom;
@@ -1319,6 +1348,7 @@ hygro_status hygro_get_state(hygro_ctx *c, void *buf, size_t *bytes)
 hygro_status hygro_set_state(hygro_ctx *c, const void *buf, size_t bytes)
 {
     if (c == nullptr || buf == nullptr) return fail(c, HYGRO_E_INVALID, "ctx or buf is NULL");
+    FAULT_POINT(c, "hygro_set_state");
     const size_t nf = (size_t)c->total_nodes * c->real_size;
     const size_t nroom = c->rooms.size() * 4 * sizeof(double);
     const size_t need = 5 * sizeof(int64_t) + 4 * nf + 2 * (size_t)c->W * 4 * sizeof(double) + nroom;
@@ -1370,6 +1400,7 @@ hygro_status hygro_run_noalloc(hygro_ctx *c, int64_t n_steps, int32_t sample_eve
                                size_t samples_bytes)
 {
     if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    FAULT_POINT(c, "hygro_run_noalloc");
     if (n_steps < 0) return fail(c, HYGRO_E_INVALID, "n_steps must be >= 0");
     if (samples != nullptr && sample_every < 1) return fail(c, HYGRO_E_INVALID, "sample_every must be >= 1");
     if (!(c->have_materials && c->have_bc[0] && c->have_bc[1]))
@@ -1426,6 +1457,7 @@ hygro_status hygro_loss_grad(hygro_ctx *c, int64_t n_steps, int32_t sample_every
                              double wP, int32_t checkpoint_every, double *loss, double *grad)
 {
     if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    FAULT_POINT(c, "hygro_loss_grad");
     if (n_steps < 1) return fail(c, HYGRO_E_INVALID, "n_steps must be >= 1");
     if (sample_every < 1) return fail(c, HYGRO_E_INVALID, "sample_every must be >= 1");
     if (loss == nullptr) return fail(c, HYGRO_E_INVALID, "loss is NULL");

@@ -1,7 +1,9 @@
 // Test shim: the library's CUDA-free host logic behind a C ABI, built with g++ by the CPU tests
 // (tests/test_host_layout.py, tests/test_host_noise.py, tests/test_host_forcing.py): the persistent
 // kernel's work partition (paper_1703_10119_gb300/csrc/host_layout.h), the noise-table gather
-// (csrc/host_noise.h) and the fixed-point forcing accumulators (csrc/host_forcing.h).
+// (csrc/host_noise.h), the fixed-point forcing accumulators (csrc/host_forcing.h) and the host-side fault
+// injection (csrc/host_fault.h, tests/test_host_fault.py).
+#include "host_fault.h"
 #include "host_forcing.h"
 #include "host_layout.h"
 #include "host_noise.h"
@@ -62,6 +64,23 @@ void shim_noise_fixed(double t0, double dt, double noise_dt, int64_t len, int64_
     out[0] = o.npos0;
     out[1] = o.nstep;
     out[2] = o.n_hi;
+}
+
+// Parses spec; returns 1 when active (then call_out holds the name, n_out the call to fail), else 0.
+int shim_parse_fault(const char *spec, char *call_out, int64_t *n_out)
+{
+    const hygro::FaultSpec f = hygro::parse_fault(spec);
+    if (!f.active) return 0;
+    memcpy(call_out, f.call, sizeof f.call);
+    *n_out = f.n;
+    return 1;
+}
+
+// hit_out[i] = 1 when the i-th of the k calls (names[i]) is the one to fail under spec.
+void shim_fault_sequence(const char *spec, const char *const *names, int k, int32_t *hit_out)
+{
+    hygro::FaultInjector inj(hygro::parse_fault(spec));
+    for (int i = 0; i < k; ++i) hit_out[i] = inj.hit(names[i]) ? 1 : 0;
 }
 
 }  // extern "C"
