@@ -71,6 +71,12 @@ typedef enum {
     HYGRO_E_UNSUPPORTED = -7   /* valid request the library does not handle (e.g. N too large) */
 } hygro_status;
 
+/* Fault injection for tests of the caller's error handling: with the environment variable
+ * HYGRO_FAULT=<entry point>:<n> (e.g. "hygro_run:3"), the n-th call of that entry point in the process,
+ * counted from 1, returns HYGRO_E_CUDA with an "injected fault" message before it changes anything or
+ * touches the device. The variable is read at the first call of any entry point; without it nothing
+ * is injected. hygro_get_step, hygro_last_error and hygro_destroy have no fault point. */
+
 enum { HYGRO_FP32 = 0, HYGRO_FP64 = 1 };
 
 /* How hygro_run advances the walls.
