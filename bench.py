@@ -93,11 +93,12 @@ def kernel_source_hash(sources=None) -> str:
 
 
 def measured_traffic(path=None, sources=None):
-    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel source."""
+    """DRAM bytes per launch from the committed ncu summary, if it matches the current kernel source and
+    was taken on a launch like the timed ones (starting at step 0)."""
     try:
         with open(path or TRAFFIC_FILE) as fh:
             t = json.load(fh)
-        if t.get("kernel_source_sha") == kernel_source_hash(sources):
+        if t.get("kernel_source_sha") == kernel_source_hash(sources) and t.get("launch_start_step", 0) == 0:
             return t.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         pass
@@ -423,6 +424,9 @@ def bench_ours(args):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
     g = H.Hygro(wl, precision="fp32", kernel="persistent", device=local, stream=stream.cuda_stream)
+    # every run (parity, warm-up, timed) is the same year from the initial state: a run continuing the
+    # previous one would start past the end of the hourly noise tables, which are then held constant
+    s0 = g.get_state()
 
     # parity of one full run from the initial state against the oracle on a sample of walls
     parity = None
@@ -448,6 +452,7 @@ def bench_ours(args):
                                   f"all {args.year_steps} steps, {el:.1f} s"}
 
     for _ in range(max(0, args.warmup - 1)):
+        g.set_state(s0)
         with torch.cuda.stream(stream):
             g.run(args.year_steps)
     torch.cuda.synchronize()
@@ -461,6 +466,7 @@ def bench_ours(args):
             pg.barrier()
         t_wall = time.perf_counter()
         for _ in range(args.steps):
+            g.set_state(s0)   # host call, outside the events; it waits for the context's stream first
             with torch.cuda.stream(stream):
                 flush.zero_()
                 e0 = torch.cuda.Event(enable_timing=True)
