@@ -36,6 +36,10 @@
  *     recognised with cudaPointerGetAttributes); with device outputs the
  *     call is stream-ordered on the context's stream and returns after
  *     enqueueing, with host outputs it returns when the data are there;
+ *   - what the set-up calls copied in is in place before the next run's
+ *     kernels start, on any stream: on a non-blocking context stream, a
+ *     call that launches work first waits for the copies (not while the
+ *     stream is being captured into a graph);
  *   - calls on one context are not thread-safe; separate contexts are;
  *   - hygro_last_error gives a readable message for the last failure.
  * Walls are concatenated: the nodes of wall w occupy

@@ -485,6 +485,7 @@ hygro_status hygro2d_run(hygro2d_ctx *c, int64_t n_steps)
         return fail(c, HYGRO_E_STATE, "hygro2d_set_materials and hygro2d_set_bc (all four faces) must come first");
     if (n_steps == 0) return HYGRO_OK;
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
+    CUDA_TRY2(c, after_host_copies(c->stream));
     for (int64_t done = 0; done < n_steps;) {
         const int sub = (int)std::min<int64_t>(c->k, n_steps - done);
         const cudaError_t e = c->precision == HYGRO_FP64

@@ -58,6 +58,25 @@ bool finite_nonneg(double x) { return std::isfinite(x) && x >= 0.0; }
 
 namespace hygro {
 
+cudaError_t after_host_copies(cudaStream_t stream)
+{
+    if (stream == nullptr) return cudaSuccess;
+    // first the capture status: the one query made while a graph may be being captured
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(stream, &cs) != cudaSuccess) {
+        (void)cudaGetLastError();   // leave no error behind for the launchers' cudaGetLastError
+        cs = cudaStreamCaptureStatusNone;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return cudaSuccess;
+    unsigned int flags = 0;
+    if (cudaStreamGetFlags(stream, &flags) != cudaSuccess) {
+        (void)cudaGetLastError();
+        flags = cudaStreamNonBlocking;
+    }
+    if (!(flags & cudaStreamNonBlocking)) return cudaSuccess;
+    return cudaStreamSynchronize(cudaStreamLegacy);
+}
+
 hygro_status check_bc(const hygro_bc &b, bool allow_room, double t0, double dt, std::string *why, bool scan_noise)
 {
     if (b.kind == HYGRO_BC_ROOM && !allow_room) {
@@ -266,6 +285,8 @@ bool fault_hit(const char *call)
     do {                                                                                           \
         if (fault_hit(name)) return fail(ctx, HYGRO_E_CUDA, "%s: injected fault (HYGRO_FAULT)", name); \
     } while (0)
+
+cudaError_t after_host_copies(const hygro_ctx *c) { return hygro::after_host_copies(c->stream); }
 
 void free_all(hygro_ctx *c)
 {
@@ -610,6 +631,7 @@ hygro_status rooms_ready(hygro_ctx *c)
 // Enqueues n_steps steps of every wall (and room) on the context's stream; samples go to dsamp.
 hygro_status launch_steps(hygro_ctx *c, int64_t n_steps, int se, void *dsamp)
 {
+    CUDA_TRY(c, after_host_copies(c));
     if (c->kernel == HYGRO_KERNEL_PERSISTENT) {
         // chunks of whole sampling periods below 2^30 steps
         int64_t chunk = int64_t(1) << 30;
@@ -1214,6 +1236,7 @@ hygro_status hygro_balance(hygro_ctx *c, double *bal)
     BAL_TRY(cudaMalloc(&sc, (size_t)c->W * 4 * sizeof(double)));
     BAL_TRY(cudaMalloc(&sf, (size_t)c->W * 4 * sizeof(double)));
     BAL_TRY(cudaMalloc(&db, (size_t)c->W * 8 * sizeof(double)));
+    BAL_TRY(after_host_copies(c));
     BAL_TRY(cudaMemsetAsync(db, 0, (size_t)c->W * 8 * sizeof(double), c->stream));
     BAL_TRY(cudaMemsetAsync(sc, 0, (size_t)c->W * 4 * sizeof(double), c->stream));
     // pass 1: the step n -> n+1 into scratch copies of level n-1 (the plain kernel writes in place)
@@ -1643,6 +1666,7 @@ hygro_status hygro_loss_grad(hygro_ctx *c, int64_t n_steps, int32_t sample_every
         d.Lv = c->Lv;
         d.Psat = c->Psat;
     };
+    ADJ_TRY(after_host_copies(c));
     cudaError_t le = cudaSuccess;
     if (f64) {
         AdjDev<double> d;

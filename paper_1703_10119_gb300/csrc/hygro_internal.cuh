@@ -120,6 +120,12 @@ struct DevCtx {
 };
 
 // Host helpers shared by the 1D and 2D entry points (hygro_api.cu).
+// The entry points' plain cudaMemcpy / cudaMemset calls go to the legacy default stream. A non-blocking
+// context stream (PyTorch's streams are) does not follow it, and a copy from pageable memory may return
+// before its last transfer lands, so an entry point that enqueues kernels on such a stream first waits for
+// the legacy stream. Returns at once for the legacy stream itself, for a blocking stream (which follows the
+// legacy one), and while the stream is being captured into a graph.
+cudaError_t after_host_copies(cudaStream_t stream);
 // Validates one face description (kind, coefficients, noise table against the time step, and the
 // table's values finite unless scan_noise is false, for a caller that checks them while copying);
 // room faces only where allow_room. Returns HYGRO_OK, or an error status with the reason in *why.
