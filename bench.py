@@ -57,6 +57,11 @@ TRAFFIC_FILE = os.path.join(ROOT, "profiles", "df1d_persistent_f32_traffic.json"
 # (T, Pv) pairs of levels n and n-1, write the pair of level n+1, 4-byte reals)
 BYTES_PER_CELL_UPDATE_2D = 24
 STEPS_PER_LAUNCH_2D = 4
+# 2D sections, algorithmic FP32 operations per cell-update of the five-point increment form for the
+# workload's materials (kTT, cTT independent of Pv, no cTM: constant thermal faces and T denominators),
+# each face counted once (shared by its two nodes): coefficients 2 (kM half-value, A), faces 2, Pv 12
+# (S 3, num 5, denominator, dPv, X, update), T 8 (num 5, latent, dT, update) = 24 (+ 1 reciprocal)
+OPS_2D = 24
 KERNEL_SOURCES_2D = ["paper_1703_10119_gb300/csrc/df2d.cuh", "paper_1703_10119_gb300/csrc/df1d_common.cuh"]
 TRAFFIC_FILE_2D = os.path.join(ROOT, "profiles", "df2d_f32_traffic.json")
 FALLBACK_HBM_GBS = 6800.0
@@ -103,6 +108,44 @@ def measured_traffic(path=None, sources=None):
     except (OSError, ValueError):
         pass
     return None
+
+
+def measure_peaks(H, device: int, stream) -> dict:
+    """Arithmetic peaks of this GPU by microbenchmark (hygro_peak_probe), in T lane-operations/s, with
+    the SM clock sampled while they run."""
+    out = {}
+    with ClockSampler(device) as cs:
+        for name, kind, ms in (("ffma", H.HYGRO_PEAK_FFMA, 200.0), ("ffma2", H.HYGRO_PEAK_FFMA2, 200.0),
+                               ("rcp", H.HYGRO_PEAK_RCP, 100.0), ("dfma", H.HYGRO_PEAK_DFMA, 100.0)):
+            ops, t = H.hygro_peak_probe(kind, device, stream, ms)
+            out[name + "_tops"] = ops / 1e12
+            out[name + "_ms"] = t
+    out["clocks"] = cs.summary()
+    # the FP32 roof: the faster of the scalar and the packed fused multiply-add, one operation per lane
+    # and FMA (the unit of the algorithmic counts)
+    out["fp32_tops"] = max(out["ffma_tops"], out["ffma2_tops"])
+    out["source"] = ("measured in this run: 8 independent FMA (scalar and f32x2), rcp.approx or FP64 FMA "
+                     "chains per thread, SMs x 4 blocks x 256 threads, CUDA events")
+    return out
+
+
+def fp32_peak(peaks, sms: int):
+    """The FP32 roof in T operations/s: measured in this run when the probes ran, else nominal."""
+    if peaks and peaks.get("fp32_tops"):
+        return peaks["fp32_tops"], "measured (hygro_peak_probe, this run)"
+    return sms * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12, f"nominal: {sms} SMs x {FP32_LANES_PER_SM} lanes x {SM_MAX_MHZ:.0f} MHz"
+
+
+def relinf(x, ref) -> float:
+    ref = np.asarray(ref, np.float64)
+    return float(np.max(np.abs(np.asarray(x, np.float64) - ref)) / np.max(np.abs(ref)))
+
+
+def rel_dev_linf(x, ref, init) -> float:
+    """Error relative to the reference's largest departure from the initial state (the stricter view of
+    the relative L-infinity error)."""
+    ref = np.asarray(ref, np.float64)
+    return float(np.max(np.abs(np.asarray(x, np.float64) - ref)) / np.max(np.abs(ref - init)))
 
 
 def measured_hbm_gbs():
@@ -238,7 +281,9 @@ def bench_reference(args):
     import oracle
 
     wl = wk.wall_batch(n_walls=args.walls, n_steps=args.year_steps)
-    pick, sub = cpu_sample(wl, max(8, args.cpu_walls // 8))
+    # the same sample as the cpu_baseline leg of the other arm (every 16th wall of 4096 by default): large
+    # enough that the host threads stay balanced
+    pick, sub = cpu_sample(wl, args.cpu_walls)
     units = sub.total_nodes * args.year_steps
     for _ in range(args.warmup):
         run_oracle_sample(sub, args.year_steps // 8)
@@ -261,7 +306,7 @@ def bench_reference(args):
     print(json.dumps(line))
 
 
-def bench_sections(args, H, wk, stream, local, rank):
+def bench_sections(args, H, wk, stream, local, rank, peaks=None):
     """The 2D thermal-bridge workload: throughput, its HBM roofline and parity on sampled sections."""
     import torch
 
@@ -286,17 +331,33 @@ def bench_sections(args, H, wk, stream, local, rank):
     workload = f"{sec.n_grids} sections {sec.nx}x{sec.ny}, {sec.n_steps} steps, FP32, {k} fused steps per launch"
     launches = -(-sec.n_steps // k)
     ms_launch = ms / launches
-    achieved = BYTES_PER_CELL_UPDATE_2D * sec.total_nodes * k / (ms_launch / 1e3) / 1e9
-    peak = measured_hbm_gbs()
+    # two roofs: HBM at the compulsory traffic of k fused steps per pass (24 / k B per cell-update) and
+    # the FP32 ALU at OPS_2D operations per cell-update; the lower one binds
+    bytes_cu = BYTES_PER_CELL_UPDATE_2D / k
+    hbm_peak = measured_hbm_gbs()
+    hbm_achieved = bytes_cu * value / 1e9
+    hbm_roof = hbm_peak * 1e9 / bytes_cu
+    alu_peak = peaks["fp32_tops"] if peaks else None
+    alu_achieved = OPS_2D * value / 1e12
+    alu_roof = alu_peak * 1e12 / OPS_2D if alu_peak else None
     traffic = measured_traffic(TRAFFIC_FILE_2D, KERNEL_SOURCES_2D)
+    binding = "hbm" if alu_roof is None or hbm_roof <= alu_roof else "alu"
+    if binding == "hbm":
+        roof = {"bound": "hbm", "achieved": hbm_achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": hbm_achieved / hbm_peak}
+    else:
+        roof = {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "Top/s",
+                "frac": alu_achieved / alu_peak}
+    roof.update({
+        "traffic": traffic,
+        "hbm_frac": hbm_achieved / hbm_peak, "hbm_bytes_per_cell_update": bytes_cu,
+        "alu_frac": alu_achieved / alu_peak if alu_peak else None, "alu_ops_per_cell_update": OPS_2D,
+        "note": (f"{k} fused steps per launch: {BYTES_PER_CELL_UPDATE_2D}/{k} B of compulsory HBM traffic per "
+                 "cell-update (read T, Pv at n and n-1, write T, Pv at n+1 once per launch, FP32) against the "
+                 f"measured copy bandwidth; {OPS_2D} algorithmic FP32 operations per cell-update against the "
+                 "measured FP32 FMA peak; the roof with the lower cell-update rate binds; kernel df2d_kernel<float>")})
     out = {"value": value, "unit": UNIT, "workload": workload, "ms_per_run": ms, "launches": launches,
-           "steps_per_launch": k,
-           "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                        "frac": achieved / peak if peak else None, "traffic": traffic,
-                        "note": (f"{BYTES_PER_CELL_UPDATE_2D} B of compulsory traffic per cell-update for one "
-                                 "step per pass (read T, Pv at n and n-1, write T, Pv at n+1, FP32) x cell-updates "
-                                 f"of one launch ({k} fused steps) / launch time; peak = measured copy bandwidth; "
-                                 "temporal blocking lets the fraction exceed 1; kernel df2d_kernel<float>")}}
+           "steps_per_launch": k, "roofline": roof}
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
 
@@ -309,13 +370,16 @@ def bench_sections(args, H, wk, stream, local, rank):
         g2.close()
         o = oracle.Oracle2D(sub)
         o.run(n)
+        Ti = np.asarray(sub.T_init, np.float64)[:, None, None]
+        Pi = np.asarray(sub.P_init, np.float64)[:, None, None]
         out["parity_vs_oracle"] = {"sections_checked": len(pick), "steps": n,
-                                   "rel_linf_T": float(np.abs(T - o.T_cur).max() / np.abs(o.T_cur).max()),
-                                   "rel_linf_P": float(np.abs(P - o.P_cur).max() / np.abs(o.P_cur).max())}
+                                   "rel_linf_T": relinf(T, o.T_cur), "rel_linf_P": relinf(P, o.P_cur),
+                                   "rel_dev_linf_T": rel_dev_linf(T, o.T_cur, Ti),
+                                   "rel_dev_linf_P": rel_dev_linf(P, o.P_cur, Pi)}
     return out
 
 
-def bench_adjoint(args, H, wk, stream, local, rank):
+def bench_adjoint(args, H, wk, stream, local, rank, peaks=None):
     """Gradient workload: misfit loss and its gradient over 30 days of 1024 two-layer walls (FP32 adjoint,
     sqrt(T) checkpoints), observations resident on the device; parity on sampled walls vs the oracle."""
     import torch
@@ -364,7 +428,7 @@ def bench_adjoint(args, H, wk, stream, local, rank):
     C = int(np.ceil(np.sqrt(wl.n_steps)))
     value = wl.total_nodes * wl.n_steps / (ms / 1e3)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = sms * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    peak, peak_source = fp32_peak(peaks, sms)
     achieved = OPS_ADJOINT * value / 1e12
     out = {"value": value, "unit": UNIT + " (forward steps differentiated)",
            "workload": f"{wl.n_walls} two-layer walls N=200, dt=60 s x {wl.n_steps} steps, sensors every "
@@ -373,7 +437,7 @@ def bench_adjoint(args, H, wk, stream, local, rank):
            "note": "forward + recompute + reverse sweep in one launch; cell-updates of the forward run per second; "
                    "the time is the whole hygro_loss_grad call (buffer allocation and copies included)",
            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s", "frac": achieved / peak,
-                        "traffic": None,
+                        "traffic": None, "peak_source": peak_source,
                         "note": f"FP32 FMA-pipe roof; {OPS_ADJOINT} algorithmic FP32 ops per differentiated "
                                 "cell-update (forward 24, recompute 24, reverse step 76) plus 6 reciprocals; "
                                 "kernel adjoint_reg_kernel<float>"}}
@@ -391,8 +455,14 @@ def bench_adjoint(args, H, wk, stream, local, rank):
         h2.close()
         rows = np.concatenate([np.arange(2 * w, 2 * w + 2) for w in pick])
         big = np.max(np.abs(g0 * sub.layer_par))
+        # per component: the relative error of each parameter's gradient, over the active parameters
+        # (kM0, a, cM0, b, kTT0, cTT0: the workload's aT = bT = chi = 0 leave the other three at zero)
+        active = [0, 1, 2, 3, 4, 6]
+        comp = np.abs(g[rows][:, active] - g0[:, active]) / np.maximum(np.abs(g0[:, active]), 1e-300)
         out["parity_vs_oracle"] = {"walls_checked": len(pick), "loss_rel": abs(L2 - L0) / abs(L0),
                                    "grad_scaled_max_rel": float(np.max(np.abs((g[rows] - g0) * sub.layer_par)) / big),
+                                   "grad_component_rel_max": float(np.max(comp)),
+                                   "grad_component_rel_median": float(np.median(comp)),
                                    "oracle_seconds": el0}
     return out
 
@@ -409,13 +479,14 @@ def bench_ours(args):
     H.lib(build_if_missing=True)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
+    peaks = measure_peaks(H, local, stream.cuda_stream)
     if args.only_2d:
-        out = bench_sections(args, H, wk, stream, local, rank)
+        out = bench_sections(args, H, wk, stream, local, rank, peaks)
         if rank == 0:
             print(json.dumps({"metric": METRIC, "unit": UNIT, "only": "2d sections", **out}))
         return
     if args.only_adjoint:
-        out = bench_adjoint(args, H, wk, stream, local, rank)
+        out = bench_adjoint(args, H, wk, stream, local, rank, peaks)
         if rank == 0:
             print(json.dumps({"metric": METRIC, "unit": UNIT, "only": "gradient workload", **out}))
         return
@@ -432,20 +503,43 @@ def bench_ours(args):
     parity = None
     cpu_baseline = None
     pick, sub = cpu_sample(wl, args.cpu_walls)
+    # the parity run also takes daily surface samples, so that every output of the run is compared
+    se = 144 if args.year_steps >= 144 else 1
+    smp = np.zeros((args.year_steps // se, wl.n_walls, 2, 2), np.float32)
     with torch.cuda.stream(stream):
-        g.run(args.year_steps)
+        g.run(args.year_steps, se, smp)
     g.sync()
     T, P = g.fields(0)
+    flux, cum = g.fluxes()
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
 
-        o, el = run_oracle_sample(sub, args.year_steps)
+        o = oracle.Oracle(sub)
+        t0 = time.perf_counter()
+        ro = o.run(args.year_steps, se)
+        el = time.perf_counter() - t0
         off = np.concatenate([[0], np.cumsum(wl.n_nodes)])
         Tg = np.concatenate([T[off[w]:off[w + 1]] for w in pick])
         Pg = np.concatenate([P[off[w]:off[w + 1]] for w in pick])
-        parity = {"walls_checked": int(len(pick)),
-                  "rel_linf_T": float(np.abs(Tg - o.T_cur).max() / np.abs(o.T_cur).max()),
-                  "rel_linf_P": float(np.abs(Pg - o.P_cur).max() / np.abs(o.P_cur).max())}
+        Ti = np.repeat(np.asarray(sub.T_init, np.float64), sub.n_nodes)
+        Pi = np.repeat(np.asarray(sub.P_init, np.float64), sub.n_nodes)
+        sg, so = smp[:, pick], ro["samples"]
+        sTi = np.asarray(sub.T_init, np.float64)[None, :, None]
+        sPi = np.asarray(sub.P_init, np.float64)[None, :, None]
+        # every output of the FP32 run against the FP64 oracle: the final fields, the daily surface samples,
+        # the last step's surface fluxes and their running sums (relative to the largest of the batch);
+        # rel_dev: relative to the largest departure from the initial state instead
+        parity = {"walls_checked": int(len(pick)), "samples": f"surface T, Pv every {se} steps",
+                  "rel_linf_T": relinf(Tg, o.T_cur), "rel_linf_P": relinf(Pg, o.P_cur),
+                  "rel_dev_linf_T": rel_dev_linf(Tg, o.T_cur, Ti), "rel_dev_linf_P": rel_dev_linf(Pg, o.P_cur, Pi),
+                  "samples_rel_linf_T": relinf(sg[..., 0], so[..., 0]),
+                  "samples_rel_linf_P": relinf(sg[..., 1], so[..., 1]),
+                  "samples_rel_dev_linf_T": rel_dev_linf(sg[..., 0], so[..., 0], sTi),
+                  "samples_rel_dev_linf_P": rel_dev_linf(sg[..., 1], so[..., 1], sPi),
+                  "flux_heat_rel_linf": relinf(flux[pick][..., 0], ro["flux"][..., 0]),
+                  "flux_moisture_rel_linf": relinf(flux[pick][..., 1], ro["flux"][..., 1]),
+                  "cumulative_heat_rel_linf": relinf(cum[pick][..., 0], o.cumul[..., 0]),
+                  "cumulative_moisture_rel_linf": relinf(cum[pick][..., 1], o.cumul[..., 1])}
         cpu_baseline = {"value": sub.total_nodes * args.year_steps / el, "unit": UNIT,
                         "cores": oracle.default_threads(), "kind": "oracle",
                         "sample": f"{len(pick)} of {wl.n_walls} walls (every {wl.n_walls // len(pick)}th), "
@@ -487,13 +581,16 @@ def bench_ours(args):
     value = units_total / (ms_max / 1e3)
 
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = sms * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    peak, peak_source = fp32_peak(peaks, sms)
     ops_per_step = algorithmic_ops_per_step(wl)
     achieved = ops_per_step * args.year_steps / (ms / 1e3) / 1e12
     traffic = measured_traffic()
+    nominal = sms * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s", "frac": achieved / peak,
-                "traffic": traffic,
-                "note": (f"FP32 FMA-pipe roof: {sms} SMs x {FP32_LANES_PER_SM} lanes x {SM_MAX_MHZ:.0f} MHz; "
+                "traffic": traffic, "peak_source": peak_source, "frac_of_nominal": achieved / nominal,
+                "target_frac": 0.6,
+                "note": (f"FP32 FMA roof (measured FMA microbenchmark; nominal {sms} SMs x {FP32_LANES_PER_SM} "
+                         f"lanes x {SM_MAX_MHZ:.0f} MHz = {nominal:.2f} T); "
                          f"{ops_per_step / wl.total_nodes:.1f} algorithmic FP32 ops per cell-update "
                          f"({OPS_SIMPLE_HEAT} on simple-heat walls, {OPS_GENERAL} otherwise) plus reciprocals on "
                          "the MUFU pipe; kernel df1d_persistent_kernel<float>, one launch per run")}
@@ -586,11 +683,11 @@ def bench_ours(args):
 
     # gradient workload (1024 walls x 30 days, reverse-time adjoint)
     if not args.no_adjoint:
-        other["adjoint_1024x200_30days"] = bench_adjoint(args, H, wk, stream, local, rank)
+        other["adjoint_1024x200_30days"] = bench_adjoint(args, H, wk, stream, local, rank, peaks)
 
     # 2D sections (64 x 512 x 512, 10000 steps, FP32, 4 fused steps per TMA-tiled launch)
     if not args.no_2d:
-        other["sections_64x512x512_10000steps"] = bench_sections(args, H, wk, stream, local, rank)
+        other["sections_64x512x512_10000steps"] = bench_sections(args, H, wk, stream, local, rank, peaks)
 
     # end to end through the C ABI with host buffers: inputs H2D, run, samples and fluxes D2H
     e2e = None
@@ -650,7 +747,8 @@ def bench_ours(args):
                            "l2": "flushed between timed runs (512 MB write)", "parallelism": f"replicas x{world}"},
                 "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,
                 "gpu_launches": args.steps, "clocks": cs.summary(), "parity_vs_oracle": parity,
-                "comparators": comparators, "other_workloads": other, "wall_seconds_timed": t_wall}
+                "comparators": comparators, "other_workloads": other, "wall_seconds_timed": t_wall,
+                "peaks": peaks}
         print(json.dumps(line))
     if pg is not None:
         pg.destroy_process_group()

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["hygro_api.cu", "df1d_plain.cu", "df1d_persistent_f32.cu", "df1d_persistent_f64.cu", "df1d_rooms_f32.cu",
            "df1d_rooms_f64.cu", "hygro2d_api.cu", "adjoint.cu",
-           "adjoint_reg_f32.cu", "adjoint_reg_f64.cu"]
+           "adjoint_reg_f32.cu", "adjoint_reg_f64.cu", "peak_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          "-I" + INCLUDE]
@@ -34,7 +34,8 @@ def nvcc() -> str:
 
 
 def _deps() -> list[str]:
-    out = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh"))]
+    # every source and header of the library: the kernels (.cu, .cuh) and the CUDA-free host headers (.h)
+    out = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h"))]
     out += [os.path.join(INCLUDE, h) for h in os.listdir(INCLUDE) if h.endswith(".h")]
     return out
 

@@ -44,6 +44,8 @@ ABI_FUNCTIONS = ("hygro_create", "hygro_set_materials", "hygro_set_bc", "hygro_r
 ABI_FUNCTIONS_2D = ("hygro2d_create", "hygro2d_set_materials", "hygro2d_set_bc", "hygro2d_run", "hygro2d_sync",
                     "hygro2d_get_fields", "hygro2d_set_fields", "hygro2d_get_step", "hygro2d_last_error",
                     "hygro2d_destroy")
+# Exported arithmetic-peak microbenchmark (include/hygro_peaks.h).
+ABI_FUNCTIONS_PEAKS = ("hygro_peak_probe",)
 HYGRO2D_MAX_REGIONS = 8
 
 
@@ -133,6 +135,7 @@ def lib(build_if_missing: bool = False) -> C.CDLL:
         "hygro2d_get_fields": [P, C.c_int32, P, P],
         "hygro2d_set_fields": [P, C.c_int32, P, P],
         "hygro2d_get_step": [P, C.POINTER(C.c_int64)],
+        "hygro_peak_probe": [C.c_int32, C.c_int32, P, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)],
     }
     for name, args in sig.items():
         f = getattr(L, name)
@@ -271,6 +274,19 @@ def hygro_loss_grad(ctx, n_steps: int, sample_every: int, obs, wT: float, wP: fl
     _check(lib().hygro_loss_grad(ctx, int(n_steps), int(sample_every), _ptr(obs), float(wT), float(wP),
                                  int(checkpoint_every), C.byref(loss), _ptr(grad)), ctx)
     return loss.value
+
+
+HYGRO_PEAK_FFMA, HYGRO_PEAK_FFMA2, HYGRO_PEAK_RCP, HYGRO_PEAK_DFMA = 0, 1, 2, 3
+
+
+def hygro_peak_probe(kind: int, device: int = -1, stream=None, target_ms: float = 100.0):
+    """One arithmetic-peak microbenchmark (include/hygro_peaks.h): (lane operations per second, ms)."""
+    ops = C.c_double()
+    ms = C.c_double()
+    st = lib().hygro_peak_probe(int(kind), int(device), stream, float(target_ms), C.byref(ops), C.byref(ms))
+    if st != HYGRO_OK:
+        raise HygroError(st, f"hygro_peak_probe(kind={kind}) failed")
+    return ops.value, ms.value
 
 
 def hygro_last_error(ctx) -> str:

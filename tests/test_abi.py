@@ -14,7 +14,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 def _declared(header=None):
     names = set()
-    for h in ([header] if header else ("hygro.h", "hygro2d.h")):
+    for h in ([header] if header else ("hygro.h", "hygro2d.h", "hygro_peaks.h")):
         src = open(os.path.join(ROOT, "include", h)).read()
         names |= set(re.findall(r"HYGRO_API\s+[\w\s\*]*?\b(hygro2?d?_\w+)\s*\(", src))
     return sorted(names)
@@ -33,6 +33,7 @@ def test_header_declares_the_boundary():
     assert set(names) == set(H.ABI_FUNCTIONS)
     names2d = _declared("hygro2d.h")
     assert set(names2d) == set(H.ABI_FUNCTIONS_2D)
+    assert set(_declared("hygro_peaks.h")) == set(H.ABI_FUNCTIONS_PEAKS)
 
 
 def test_library_exports_every_declared_symbol(lib):

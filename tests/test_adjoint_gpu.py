@@ -7,6 +7,8 @@ largest one is a difference of larger terms:
   * FP32 path: loss 1e-4 relative, scaled gradient 2e-3 (the FP32 trajectory and adjoint carry the
     single-precision rounding of every step; the bound is the measured error with a margin).
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -52,6 +54,8 @@ def test_matches_oracle_adjoint(H, oracle_mod, precision, tol_loss, tol_grad):
     L, g = gpu_loss_grad(H, wl, 120, obs.astype(np.float32), 10, 1.0, 1e-4, precision)
     # the GPU reads the observations in FP32: compare against the oracle on the same rounded values
     L0, g0 = oracle_mod.loss_and_gradient(wl, 120, obs.astype(np.float32).astype(np.float64), 10, 1.0, 1e-4)
+    print(f"measured-error adjoint-small {precision} loss={abs(L - L0) / L0:.3e} "
+          f"grad={scaled_err(g, g0, wl.layer_par):.3e}")
     assert abs(L - L0) <= tol_loss * L0, (L, L0)
     assert scaled_err(g, g0, wl.layer_par) <= tol_grad
 
@@ -82,6 +86,8 @@ def test_ragged_walls_and_lane_layouts(H, oracle_mod, precision, tol_loss, tol_g
                    -1).astype(np.float32)
     L0, g0 = oracle_mod.loss_and_gradient(wl, n, obs.astype(np.float64), every, 1.0, 1e-4)
     L, g = gpu_loss_grad(H, wl, n, obs, every, 1.0, 1e-4, precision, ck=9)
+    print(f"measured-error adjoint-ragged {precision} loss={abs(L - L0) / L0:.3e} "
+          f"grad={scaled_err(g, g0, wl.layer_par):.3e}")
     assert abs(L - L0) <= tol_loss * L0
     assert scaled_err(g, g0, wl.layer_par) <= tol_grad
 
@@ -111,6 +117,26 @@ def test_autograd_function(H):
             vals.append((lp - lm) / (2 * eps))
         fd = (4 * vals[1] - vals[0]) / 3
         assert abs(fd - np.sum(ref * d)) <= 1e-6 * np.sum(np.abs(ref * d))
+
+
+def test_autograd_function_keeps_the_run_state(H):
+    """MisfitLoss sets the context's materials to theta; the run state (levels, step, flux sums) that was
+    there before is restored, so a run under way goes on from where it was."""
+    import torch
+
+    from paper_1703_10119_gb300.autograd import MisfitLoss
+
+    wl, obs = small_batch()
+    obs = obs.astype(np.float32)
+    with H.Hygro(wl, precision="fp64") as g:
+        g.run(7)
+        before = [g.fields(0), g.fields(1), g.fluxes()]
+        theta = torch.tensor(wl.layer_par, dtype=torch.float64, requires_grad=True)
+        MisfitLoss.apply(theta, g, 120, 10, obs, 1.0, 1e-4).backward()
+        after = [g.fields(0), g.fields(1), g.fluxes()]
+        assert g.step == 7
+        for b, a in zip(before, after):
+            assert np.array_equal(b[0], a[0]) and np.array_equal(b[1], a[1])
 
 
 def test_invalid_calls(H):
@@ -148,4 +174,33 @@ def test_gradient_workload_full_size_sampled_walls(H, oracle_mod):
     L0, g0 = oracle_mod.loss_and_gradient(sub, wl.n_steps, s.obs[:, pick].astype(np.float64), s.sample_every,
                                           s.wT, s.wP)
     rows = np.concatenate([np.arange(2 * w, 2 * w + 2) for w in pick])
+    print(f"measured-error adjoint-full fp32 loss-part grad={scaled_err(grad[rows], g0, sub.layer_par):.3e}")
     assert scaled_err(grad[rows], g0, sub.layer_par) <= 2e-3
+
+
+def test_fp32_gradient_against_central_differences(H, oracle_mod):
+    """The FP32 GPU gradient (FP32 trajectory and adjoint, FP64 loss and parameter sums) against central
+    differences of the FP64 oracle's loss, each parameter of each layer moved by 1e-4 of its value
+    (the differences' own truncation error is O(1e-8) relative). Compared in the scaled form g_k theta_k
+    relative to the largest scaled component."""
+    wl, obs = small_batch()
+    obs = obs.astype(np.float32)
+    L, g = gpu_loss_grad(H, wl, 120, obs, 10, 1.0, 1e-4, "fp32")
+    obs64 = obs.astype(np.float64)
+    par = wl.layer_par
+    fd = np.zeros_like(par)
+    h = 1e-4
+    for r in range(par.shape[0]):
+        for k in range(par.shape[1]):
+            if par[r, k] == 0.0:
+                continue
+            vals = []
+            for sgn in (1.0, -1.0):
+                p2 = par.copy()
+                p2[r, k] *= 1.0 + sgn * h
+                w2 = dataclasses.replace(wl, layer_par=p2)
+                vals.append(oracle_mod.loss_and_gradient(w2, 120, obs64, 10, 1.0, 1e-4, gradient=False)[0])
+            fd[r, k] = (vals[0] - vals[1]) / (2 * h * par[r, k])
+    err = scaled_err(g, fd, par)
+    print(f"measured-error adjoint-fd fp32 grad-vs-central-differences={err:.3e}")
+    assert err <= 1e-4

@@ -94,11 +94,13 @@ def _compare(H, oracle_mod, wl, precision, kernel, n_steps, sample_every, splits
     tol = TOL[precision]
     errs = dict(T=relinf(T0, o.T_cur), P=relinf(P0, o.P_cur), Tm1=relinf(T1, o.T_prev), Pm1=relinf(P1, o.P_prev),
                 sT=relinf(samples[..., 0], ref_samples[..., 0]), sP=relinf(samples[..., 1], ref_samples[..., 1]))
-    for k, e in errs.items():
-        assert e <= tol, (precision, kernel, k, e, errs)
+    errs.update(flux=relinf(flux, rs[-1]["flux"]), cum=relinf(cum, o.cumul))
+    print(f"measured-error {wl.name} {precision} {kernel} " + " ".join(f"{k}={v:.3e}" for k, v in errs.items()))
+    for k in ("T", "P", "Tm1", "Pm1", "sT", "sP"):
+        assert errs[k] <= tol, (precision, kernel, k, errs[k], errs)
     ftol = 1e-9 if precision == "fp64" else 2e-3
-    assert relinf(flux, rs[-1]["flux"]) <= ftol, relinf(flux, rs[-1]["flux"])
-    assert relinf(cum, o.cumul) <= ftol, relinf(cum, o.cumul)
+    assert errs["flux"] <= ftol, errs["flux"]
+    assert errs["cum"] <= ftol, errs["cum"]
     return errs
 
 

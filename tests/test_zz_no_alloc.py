@@ -4,16 +4,16 @@ Some callers cannot call cudaMalloc when they run a step: their process hands al
 its own pool allocator (as PyTorch's caching allocator does), or they sit in a loop that must not
 allocate. hygro_run allocates a staging buffer for samples bound for host memory; hygro_run_noalloc
 stages them in a fixed device array that the library carries instead. These checks call it through
-the C ABI and compare it with hygro_run on two calls in a row, check that repeated calls leave the
-device's free memory unchanged, and that an oversized request is refused without changing anything.
+the C ABI and compare it with hygro_run on two calls in a row, bit for bit (both calls run the same
+kernels on the same inputs; only the staging of the samples differs), with samples bound for host memory
+and with samples in device memory (which neither call stages). They also check that repeated calls leave
+the device's free memory unchanged, and that an oversized request is refused without changing anything.
 This file is collected last so that a stop at the first failure has run every other test.
 """
 import numpy as np
 import pytest
 
 pytestmark = pytest.mark.gpu
-
-FP32_TOL = 1e-4   # the tolerance of the FP32 parity tests
 
 
 @pytest.fixture(scope="module")
@@ -28,13 +28,39 @@ def H():
     return hygro
 
 
-def _relinf(x, ref):
-    ref = np.asarray(ref, np.float64)
-    return float(np.max(np.abs(np.asarray(x, np.float64) - ref)) / np.max(np.abs(ref)))
+def _same_run(H, a, b, wl, n, every, device_samples):
+    """One hygro_run on a and one hygro_run_noalloc on b; samples, both stored levels and the fluxes must
+    agree bit for bit."""
+    import torch
+
+    shape = (n // every, wl.n_walls, 2, 2)
+    if device_samples:
+        sa = torch.zeros(shape, dtype=torch.float32, device="cuda")
+        sb = torch.zeros_like(sa)
+    else:
+        sa = np.zeros(shape, np.float32)
+        sb = np.zeros_like(sa)
+    H.hygro_run(a.ctx, n, every, sa)
+    H.hygro_run_noalloc(b.ctx, n, every, sb)
+    a.sync()
+    b.sync()
+    if device_samples:
+        sa, sb = sa.cpu().numpy(), sb.cpu().numpy()
+    assert np.any(sa != 0.0)
+    assert np.array_equal(sa, sb)
+    for level in (0, 1):
+        Ta, Pa = a.fields(level)
+        Tb, Pb = b.fields(level)
+        assert np.array_equal(Ta, Tb) and np.array_equal(Pa, Pb), level
+    fa, ca = a.fluxes()
+    fb, cb = b.fluxes()
+    assert np.array_equal(fa, fb) and np.array_equal(ca, cb)
+    assert a.step == b.step
 
 
+@pytest.mark.parametrize("device_samples", [False, True])
 @pytest.mark.parametrize("kernel", ["persistent", "plain"])
-def test_noalloc_matches_run_two_calls(H, kernel):
+def test_noalloc_matches_run_two_calls(H, kernel, device_samples):
     import torch
 
     from paper_1703_10119_gb300 import workloads as wk
@@ -43,16 +69,7 @@ def test_noalloc_matches_run_two_calls(H, kernel):
     a = H.Hygro(wl, precision="fp32", kernel=kernel)
     b = H.Hygro(wl, precision="fp32", kernel=kernel)
     for call in range(2):
-        n, every = 150 + 7 * call, 10
-        sa = np.zeros((n // every, wl.n_walls, 2, 2), np.float32)
-        sb = np.zeros_like(sa)
-        H.hygro_run(a.ctx, n, every, sa)
-        H.hygro_run_noalloc(b.ctx, n, every, sb)
-        assert _relinf(sb, sa) <= FP32_TOL, call
-        Ta, Pa = a.fields(0)
-        Tb, Pb = b.fields(0)
-        assert _relinf(Tb, Ta) <= FP32_TOL and _relinf(Pb, Pa) <= FP32_TOL, call
-        assert a.step == b.step
+        _same_run(H, a, b, wl, 150 + 7 * call, 10, device_samples)
     # once the first call on this device has looked up the array, further calls allocate nothing
     torch.cuda.synchronize()
     free0, _ = torch.cuda.mem_get_info()
