@@ -13,7 +13,9 @@
  * stream after a warm-up launch. Operations counted, per thread lane:
  *   HYGRO_PEAK_FFMA   fma.rn.f32          one operation per instruction
  *   HYGRO_PEAK_FFMA2  fma.rn.f32x2        two operations per instruction (a packed pair)
- *   HYGRO_PEAK_RCP    rcp.approx.ftz.f32  one operation per instruction
+ *   HYGRO_PEAK_RCP    rcp.approx.ftz.f32  one operation per instruction (each chain step adds a
+ *                                         constant first, which keeps consecutive reciprocals from
+ *                                         cancelling; the adds are not counted)
  *   HYGRO_PEAK_DFMA   fma.rn.f64          one operation per instruction
  * Results: *ops_per_s (lane operations per second over the whole GPU) and
  * *ms (the timed launch). The clock the GPU ran at is not controlled here:

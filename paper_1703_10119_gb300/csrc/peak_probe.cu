@@ -60,6 +60,8 @@ __global__ void __launch_bounds__(kBlock) ffma2_probe(int64_t iters, float a, fl
     if (s == never) g_probe_sink = s;
 }
 
+// x <- rcp(x + b): the added term keeps two reciprocals in a row from cancelling (a reciprocal of a
+// reciprocal could be folded away); the adds run on the FMA pipe, far from its limit at this rate.
 __global__ void __launch_bounds__(kBlock) rcp_probe(int64_t iters, float a, float b, float never)
 {
     float x[kChains];
@@ -69,7 +71,10 @@ __global__ void __launch_bounds__(kBlock) rcp_probe(int64_t iters, float a, floa
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u)
 #pragma unroll
-            for (int c = 0; c < kChains; ++c) asm volatile("rcp.approx.ftz.f32 %0, %0;" : "+f"(x[c]));
+            for (int c = 0; c < kChains; ++c) {
+                const float y = x[c] + b;
+                asm volatile("rcp.approx.ftz.f32 %0, %1;" : "=f"(x[c]) : "f"(y));
+            }
     }
     float s = 0.0f;
 #pragma unroll
@@ -100,7 +105,7 @@ cudaError_t launch(int32_t kind, int grid, cudaStream_t st, int64_t iters)
     switch (kind) {
         case HYGRO_PEAK_FFMA: ffma_probe<<<grid, kBlock, 0, st>>>(iters, 0.9999f, 1e-4f, -1.0f); break;
         case HYGRO_PEAK_FFMA2: ffma2_probe<<<grid, kBlock, 0, st>>>(iters, 0.9999f, 1e-4f, -1.0f); break;
-        case HYGRO_PEAK_RCP: rcp_probe<<<grid, kBlock, 0, st>>>(iters, 0.5f, 1.0f, -1.0f); break;
+        case HYGRO_PEAK_RCP: rcp_probe<<<grid, kBlock, 0, st>>>(iters, 0.5f, 0.75f, -1.0f); break;
         default: dfma_probe<<<grid, kBlock, 0, st>>>(iters, 0.9999, 1e-4, -1.0); break;
     }
     return cudaGetLastError();

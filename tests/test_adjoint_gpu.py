@@ -4,8 +4,10 @@ Gradients are compared in the scaled form g_k theta_k (the loss change per relat
 parameter), relative to the largest scaled component of the batch, because a component far below the
 largest one is a difference of larger terms:
   * FP64 path: loss 1e-12 relative, scaled gradient 1e-10;
-  * FP32 path: loss 1e-4 relative, scaled gradient 2e-3 (the FP32 trajectory and adjoint carry the
-    single-precision rounding of every step; the bound is the measured error with a margin).
+  * FP32 path: loss 1e-5 relative, scaled gradient 2e-5 (the FP32 trajectory and adjoint carry the
+    single-precision rounding of every step; measured at most 8.7e-7 (loss) and 4.2e-6 (gradient, the
+    full 30-day workload); the bounds keep a margin of about 5);
+  * FP32 gradient against central differences of the FP64 oracle's loss: 1e-5 (measured 9.3e-7).
 """
 import dataclasses
 
@@ -48,7 +50,7 @@ def gpu_loss_grad(H, wl, n_steps, obs, every, wT, wP, precision="fp64", ck=0):
     return L, grad
 
 
-@pytest.mark.parametrize("precision,tol_loss,tol_grad", [("fp64", 1e-12, 1e-10), ("fp32", 1e-4, 2e-3)])
+@pytest.mark.parametrize("precision,tol_loss,tol_grad", [("fp64", 1e-12, 1e-10), ("fp32", 1e-5, 2e-5)])
 def test_matches_oracle_adjoint(H, oracle_mod, precision, tol_loss, tol_grad):
     wl, obs = small_batch()
     L, g = gpu_loss_grad(H, wl, 120, obs.astype(np.float32), 10, 1.0, 1e-4, precision)
@@ -70,7 +72,7 @@ def test_checkpoint_stride_does_not_change_the_result(H):
         assert scaled_err(g, ref[1], wl.layer_par) <= 1e-13
 
 
-@pytest.mark.parametrize("precision,tol_loss,tol_grad", [("fp64", 1e-12, 1e-10), ("fp32", 1e-4, 2e-3)])
+@pytest.mark.parametrize("precision,tol_loss,tol_grad", [("fp64", 1e-12, 1e-10), ("fp32", 1e-5, 2e-5)])
 def test_ragged_walls_and_lane_layouts(H, oracle_mod, precision, tol_loss, tol_grad):
     """Walls of 3 to 512 nodes with 1 to 3 layers (some a few nodes thick), adiabatic faces, a run whose
     length is not a multiple of the sampling or the checkpoint stride. The lane runs span 1 to 17 nodes:
@@ -175,7 +177,7 @@ def test_gradient_workload_full_size_sampled_walls(H, oracle_mod):
                                           s.wT, s.wP)
     rows = np.concatenate([np.arange(2 * w, 2 * w + 2) for w in pick])
     print(f"measured-error adjoint-full fp32 loss-part grad={scaled_err(grad[rows], g0, sub.layer_par):.3e}")
-    assert scaled_err(grad[rows], g0, sub.layer_par) <= 2e-3
+    assert scaled_err(grad[rows], g0, sub.layer_par) <= 2e-5
 
 
 def test_fp32_gradient_against_central_differences(H, oracle_mod):
@@ -203,4 +205,4 @@ def test_fp32_gradient_against_central_differences(H, oracle_mod):
             fd[r, k] = (vals[0] - vals[1]) / (2 * h * par[r, k])
     err = scaled_err(g, fd, par)
     print(f"measured-error adjoint-fd fp32 grad-vs-central-differences={err:.3e}")
-    assert err <= 1e-4
+    assert err <= 1e-5

@@ -4,7 +4,9 @@ Tolerances (relative L-infinity per field, max |x - x_ref| / max |x_ref| over
 all nodes of all walls, and over all samples):
   * FP64 kernels: 1e-12;
   * FP32 kernel: 1e-4 (fields and samples) after the whole horizon.
-Fluxes are compared relative to the largest flux of the batch.
+Fluxes are compared relative to the largest flux of the batch, their running sums relative to the
+largest sum: FP64 1e-9; FP32 5e-5 (last step's fluxes, largest measured 8.7e-6) and 1e-3 (running sums,
+largest measured 2.1e-4, on the single wall whose day-long net sums are small against the gross flux).
 """
 import dataclasses
 
@@ -98,9 +100,9 @@ def _compare(H, oracle_mod, wl, precision, kernel, n_steps, sample_every, splits
     print(f"measured-error {wl.name} {precision} {kernel} " + " ".join(f"{k}={v:.3e}" for k, v in errs.items()))
     for k in ("T", "P", "Tm1", "Pm1", "sT", "sP"):
         assert errs[k] <= tol, (precision, kernel, k, errs[k], errs)
-    ftol = 1e-9 if precision == "fp64" else 2e-3
+    ftol, ctol = (1e-9, 1e-9) if precision == "fp64" else (5e-5, 1e-3)
     assert errs["flux"] <= ftol, errs["flux"]
-    assert errs["cum"] <= ftol, errs["cum"]
+    assert errs["cum"] <= ctol, errs["cum"]
     return errs
 
 
