@@ -312,20 +312,28 @@ def bench_sections(args, H, wk, stream, local, rank, peaks=None):
 
     sec = wk.sections_2d(seed=4 + rank, n_grids=args.sections, n_steps=args.section_steps)
     h = H.Hygro2D(sec, precision="fp32", device=local, stream=stream.cuda_stream)
-    k = STEPS_PER_LAUNCH_2D
     with torch.cuda.stream(stream):
         h.run(100)
     torch.cuda.synchronize()
-    with torch.cuda.stream(stream):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        h.run(sec.n_steps)
-        e1.record(stream)
-    torch.cuda.synchronize()
+    # the library's autotuner picks the temporal blocking depth on a short prefix of this workload
+    k, tune_ms = h.autotune(16)
+    graph_launches = h.option(H.HYGRO2D_OPT_GRAPH_LAUNCHES)
+
+    def timed_run():
+        with torch.cuda.stream(stream):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.run(sec.n_steps)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    ms = timed_run()   # whole intervals of launches replayed from CUDA graphs
+    h.set_option(H.HYGRO2D_OPT_GRAPH_LAUNCHES, 0)
+    ms_plain = timed_run()   # the same run from one launch at a time
     h.sync()
     h.close()
-    ms = e0.elapsed_time(e1)
     units = sec.total_nodes * sec.n_steps
     value = units / (ms / 1e3)
     workload = f"{sec.n_grids} sections {sec.nx}x{sec.ny}, {sec.n_steps} steps, FP32, {k} fused steps per launch"
@@ -357,7 +365,11 @@ def bench_sections(args, H, wk, stream, local, rank, peaks=None):
                  f"measured copy bandwidth; {OPS_2D} algorithmic FP32 operations per cell-update against the "
                  "measured FP32 FMA peak; the roof with the lower cell-update rate binds; kernel df2d_kernel<float>")})
     out = {"value": value, "unit": UNIT, "workload": workload, "ms_per_run": ms, "launches": launches,
-           "steps_per_launch": k, "roofline": roof}
+           "steps_per_launch": k, "roofline": roof,
+           "autotune": {"chosen_steps_per_launch": k, "ms_per_step_by_depth": [float(x) for x in tune_ms],
+                        "probe": "16 steps from the state after 100 steps, each depth from the same state"},
+           "graph": {"launches_per_graph": graph_launches, "ms_per_run_graph": ms, "ms_per_run_plain_launches": ms_plain,
+                     "value_plain_launches": units / (ms_plain / 1e3)}}
     if rank == 0 and not args.no_cpu_baseline:
         import oracle
 
@@ -498,6 +510,12 @@ def bench_ours(args):
     # every run (parity, warm-up, timed) is the same year from the initial state: a run continuing the
     # previous one would start past the end of the hourly noise tables, which are then held constant
     s0 = g.get_state()
+    # the library's autotuner refits the wall schedule's step-time model on a probe of this workload and
+    # keeps the faster schedule (the state is restored afterwards)
+    ta, tb, tms = g.autotune(2000)
+    autotune = {"probe_steps": 2000, "model_a_ns": [float(x) for x in ta], "model_b_ns": [float(x) for x in tb],
+                "probe_ms_previous_schedule": float(tms[0]), "probe_ms_refitted_schedule": float(tms[1]),
+                "kept": "refitted" if tms[1] <= tms[0] else "previous"}
 
     # parity of one full run from the initial state against the oracle on a sample of walls
     parity = None
@@ -748,7 +766,7 @@ def bench_ours(args):
                 "roofline": roofline, "cpu_baseline": cpu_baseline, "e2e": e2e,
                 "gpu_launches": args.steps, "clocks": cs.summary(), "parity_vs_oracle": parity,
                 "comparators": comparators, "other_workloads": other, "wall_seconds_timed": t_wall,
-                "peaks": peaks}
+                "peaks": peaks, "autotune": autotune}
         print(json.dumps(line))
     if pg is not None:
         pg.destroy_process_group()

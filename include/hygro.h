@@ -273,6 +273,19 @@ HYGRO_API hygro_status hygro_get_step(const hygro_ctx *ctx, int64_t *step);
 HYGRO_API hygro_status hygro_get_state(hygro_ctx *ctx, void *buf, size_t *bytes);
 HYGRO_API hygro_status hygro_set_state(hygro_ctx *ctx, const void *buf, size_t bytes);
 
+/* Autotuner of the persistent kernel's wall schedule (the walls each block runs, dealt by the
+ * longest-processing-time rule with a step-time model a + b K per code variant). From the current
+ * state it runs probe_steps steps (16 .. 2^20) with every wall's start and end recorded on the GPU
+ * clock, fits the model to the walls' measured time per step (least squares per variant), then times
+ * the same probe with the current schedule and with the schedule of the refitted model (CUDA events)
+ * and keeps the faster one. The stored levels, step and flux sums are restored afterwards; results of
+ * later runs do not depend on the schedule. model[0..3] = a, model[4..7] = b of the fitted model
+ * (nanoseconds; may be NULL); ms[0], ms[1] = probe time with the previous and the refitted schedule (may
+ * be NULL). Walls facing rooms run in the room kernel and are not scheduled: HYGRO_E_UNSUPPORTED for a
+ * context with rooms or with the plain kernel. Synchronous. The paper has no counterpart: the schedule
+ * changes where the walls run, not what the scheme computes. */
+HYGRO_API hygro_status hygro_autotune(hygro_ctx *ctx, int32_t probe_steps, double *model, double *ms);
+
 /* Size of the fixed device array behind hygro_run_noalloc: 8 MiB. */
 #define HYGRO_NOALLOC_SCRATCH_BYTES (8u << 20)
 

@@ -67,8 +67,31 @@ HYGRO_API hygro_status hygro2d_set_materials(hygro2d_ctx *ctx, int32_t n_regions
 HYGRO_API hygro_status hygro2d_set_bc(hygro2d_ctx *ctx, int32_t face, const hygro_bc *bc);
 
 /* Advance n_steps DF steps (n_steps >= 0): ceil(n_steps / steps_per_launch) launches, stream-ordered on
- * the context's stream; returns after enqueueing. */
+ * the context's stream; returns after enqueueing. Whole intervals of HYGRO2D_OPT_GRAPH_LAUNCHES launches
+ * (64 by default) are replayed from a CUDA graph of that interval, built on first use and kept until the
+ * materials, a boundary or an option changes; the rest of the run is launched one by one. The launches
+ * and their results are the same either way (the graph's launches read their step index from a device
+ * counter that the graph advances). */
 HYGRO_API hygro_status hygro2d_run(hygro2d_ctx *ctx, int64_t n_steps);
+
+/* Options (hygro2d_set_option / hygro2d_get_option):
+ *   HYGRO2D_OPT_STEPS_PER_LAUNCH: DF steps fused per launch (temporal blocking depth), 1..4;
+ *   HYGRO2D_OPT_GRAPH_LAUNCHES:   launches per CUDA graph interval, an even count up to 4096, 0 for none.
+ * The paper has no counterpart: these shape the launches, not the scheme. Setting an option waits for
+ * the context's stream. HYGRO_E_INVALID for an unknown option or a value out of range. */
+#define HYGRO2D_OPT_STEPS_PER_LAUNCH 1
+#define HYGRO2D_OPT_GRAPH_LAUNCHES 2
+HYGRO_API hygro_status hygro2d_set_option(hygro2d_ctx *ctx, int32_t option, int64_t value);
+HYGRO_API hygro_status hygro2d_get_option(const hygro2d_ctx *ctx, int32_t option, int64_t *value);
+
+/* Autotuner of the temporal blocking depth: from the current state, times probe_steps steps (1..100000)
+ * at each depth 1..4 (a warm-up launch first, CUDA events on the context's stream), restores the state
+ * after each, and keeps the fastest depth as HYGRO2D_OPT_STEPS_PER_LAUNCH. *k_best (may be NULL)
+ * receives it and ms_per_step[0..3] (may be NULL) the time per step of each depth. The state, the step
+ * and the results of later runs are unchanged: every depth gives the same bits. Temporarily allocates
+ * two copies of the stored levels. Synchronous. The paper has no counterpart. */
+HYGRO_API hygro_status hygro2d_autotune(hygro2d_ctx *ctx, int32_t probe_steps, int32_t *k_best,
+                                        double *ms_per_step);
 
 /* Wait for the context's stream. HYGRO_E_NONFINITE if a node went non-finite, HYGRO_E_TIMEOUT if a
  * bounded device wait gave up, since the last check. */

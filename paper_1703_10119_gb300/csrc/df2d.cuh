@@ -47,6 +47,8 @@ struct Dev2D {
     void *out_new, *out_old;    // output set: (T, Pv) pairs of level n and n-1 after this launch
     int32_t *err;               // 1: a bounded wait gave up
     int32_t *nonfinite;         // 1: some node went non-finite
+    const int64_t *step_dev;    // if set, the launch's first step is *step_dev + n0 (launches replayed from a
+                                // CUDA graph read the step from the device)
     double dt, t0, Lv;
 };
 
@@ -127,6 +129,7 @@ __global__ void __launch_bounds__(Tile2D<real, TX, TY, H, SEG>::NT, MINB)
     df2d_kernel(const __grid_constant__ CUtensorMap mCur, const __grid_constant__ CUtensorMap mPrev,
                 const __grid_constant__ CUtensorMap mFlags, const Dev2D d, int64_t n0, int32_t n_sub)
 {
+    if (d.step_dev != nullptr) n0 += *d.step_dev;
     using L = Tile2D<real, TX, TY, H, SEG>;
     using pair = typename L::pair;
     constexpr int BX = L::BX, BY = L::BY, NT = L::NT;

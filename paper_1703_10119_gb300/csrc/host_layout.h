@@ -84,14 +84,53 @@ struct SchedWall {
     int32_t N;
 };
 
-// Time per step of a wall when an SM is shared by its full warp count, a + b K nanoseconds (measured on
-// GB300 with a per-wall trace at 16 warps per SM for variants 0 and 3; variants 1 and 2 scaled from an
-// earlier 12-warp trace).
-inline double sched_cost(const SchedWall &x)
+// Time per step of a wall when an SM is shared by its full warp count, a[kind] + b[kind] K nanoseconds.
+struct CostModel {
+    double a[4], b[4];
+};
+
+// The built-in model: measured on GB300 with a per-wall trace at 16 warps per SM for variants 0 and 3;
+// variants 1 and 2 scaled from an earlier 12-warp trace.
+inline CostModel default_cost_model()
 {
-    static const double a[4] = {107.0, 234.0, 156.0, 191.0};
-    static const double b[4] = {64.2, 76.0, 125.0, 77.2};
-    return a[x.kind] + b[x.kind] * x.K;
+    return CostModel{{107.0, 234.0, 156.0, 191.0}, {64.2, 76.0, 125.0, 77.2}};
+}
+
+inline double sched_cost(const SchedWall &x, const CostModel &m) { return m.a[x.kind] + m.b[x.kind] * x.K; }
+inline double sched_cost(const SchedWall &x) { return sched_cost(x, default_cost_model()); }
+
+// Least-squares fit of a + b K per variant to measured step times ns[i] of walls[i] (ns[i] <= 0: not
+// measured). A variant whose measured walls span two or more K values gets both coefficients (b kept
+// >= 0); one with a single K keeps base's b and fits a; one with no measured wall keeps base. Returns the
+// number of variants fitted.
+inline int fit_cost_model(const std::vector<SchedWall> &walls, const std::vector<double> &ns, const CostModel &base,
+                          CostModel &out)
+{
+    out = base;
+    int fitted = 0;
+    for (int v = 0; v < 4; ++v) {
+        double n = 0, sk = 0, st = 0, skk = 0, skt = 0;
+        int kmin = 1 << 30, kmax = -1;
+        for (size_t i = 0; i < walls.size() && i < ns.size(); ++i) {
+            if (walls[i].kind != v || !(ns[i] > 0.0)) continue;
+            const double k = walls[i].K, t = ns[i];
+            n += 1;
+            sk += k;
+            st += t;
+            skk += k * k;
+            skt += k * t;
+            kmin = std::min(kmin, walls[i].K);
+            kmax = std::max(kmax, walls[i].K);
+        }
+        if (n == 0) continue;
+        const double var = skk - sk * sk / n;
+        double b = base.b[v];
+        if (kmax > kmin && var > 0) b = std::max(0.0, (skt - sk * st / n) / var);
+        out.b[v] = b;
+        out.a[v] = (st - b * sk) / n;
+        ++fitted;
+    }
+    return fitted;
 }
 
 // Walls sorted by nodes per lane (descending), then variant, then N (descending), cut into rounds of R
@@ -100,7 +139,8 @@ inline double sched_cost(const SchedWall &x)
 // order: the rounds of block 0, then block 1, ..., R entries each (-1 for the empty entries of the last
 // round); boff[g] .. boff[g + 1]: block g's entries. load (optional): each block's estimated cost.
 inline void lpt_rounds(std::vector<SchedWall> walls, int G, int R, std::vector<int32_t> &order,
-                       std::vector<int32_t> &boff, std::vector<double> *load_out = nullptr)
+                       std::vector<int32_t> &boff, std::vector<double> *load_out = nullptr,
+                       const CostModel &model = default_cost_model())
 {
     std::stable_sort(walls.begin(), walls.end(), [](const SchedWall &x, const SchedWall &y) {
         if (x.K != y.K) return x.K > y.K;
@@ -110,7 +150,7 @@ inline void lpt_rounds(std::vector<SchedWall> walls, int G, int R, std::vector<i
     const int Wf = (int)walls.size();
     const int n_rounds = (Wf + R - 1) / R;
     std::vector<double> rcost(n_rounds, 0.0);
-    for (int i = 0; i < Wf; ++i) rcost[i / R] = std::max(rcost[i / R], sched_cost(walls[i]));
+    for (int i = 0; i < Wf; ++i) rcost[i / R] = std::max(rcost[i / R], sched_cost(walls[i], model));
     std::vector<int32_t> ridx(n_rounds);
     for (int r = 0; r < n_rounds; ++r) ridx[r] = r;
     std::stable_sort(ridx.begin(), ridx.end(), [&](int a, int b) { return rcost[a] > rcost[b]; });

@@ -78,6 +78,12 @@ struct hygro2d_ctx {
     float2 *d_noise = nullptr;
     size_t noise_cap = 0;
     int32_t *d_flags = nullptr;   // [0] wait gave up, [1] non-finite
+    // CUDA graphs of graph_launches launches (an even count: the buffer sets are back where they were),
+    // one per buffer set at the interval's start, replayed for the whole intervals of a run; the launches
+    // read their first step from d_step, which the graph's last node advances
+    int graph_launches = 64;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int64_t *d_step = nullptr;
     size_t cells() const { return (size_t)G * ny * pitch; }
 };
 
@@ -105,12 +111,22 @@ hygro_status fail(hygro2d_ctx *c, hygro_status st, const char *fmt, ...)
                         cudaGetErrorString(e_));                                                         \
     } while (0)
 
+void drop_graphs(hygro2d_ctx *c)
+{
+    for (int s = 0; s < 2; ++s)
+        if (c->gexec[s]) {
+            cudaGraphExecDestroy(c->gexec[s]);
+            c->gexec[s] = nullptr;
+        }
+}
+
 void free_all(hygro2d_ctx *c)
 {
+    drop_graphs(c);
     for (int s = 0; s < 2; ++s)
         for (int l = 0; l < 2; ++l)
             if (c->F[s][l]) cudaFree(c->F[s][l]);
-    void *p[] = {c->d_flags8, c->d_tab, c->d_faces, c->d_noise, c->d_flags};
+    void *p[] = {c->d_flags8, c->d_tab, c->d_faces, c->d_noise, c->d_flags, c->d_step};
     for (void *q : p)
         if (q) cudaFree(q);
 }
@@ -155,10 +171,12 @@ hygro_status encode_maps(hygro2d_ctx *c)
     return HYGRO_OK;
 }
 
-template <typename real, int TX, int TY, int H, int SEG, int MINB>
-cudaError_t launch2d(const hygro2d_ctx *c, int64_t n0, int n_sub)
+__global__ void step_set_kernel(int64_t *p, int64_t v) { *p = v; }
+__global__ void step_add_kernel(int64_t *p, int64_t v) { *p += v; }
+
+// Kernel arguments of a launch that reads buffer set `set` (levels n, n-1) and writes the other one.
+Dev2D dev_args(const hygro2d_ctx *c, int set, const int64_t *step_dev)
 {
-    using L = Tile2D<real, TX, TY, H, SEG>;
     Dev2D d;
     d.G = c->G;
     d.nx = c->nx;
@@ -168,18 +186,107 @@ cudaError_t launch2d(const hygro2d_ctx *c, int64_t n0, int n_sub)
     d.region_tab = c->d_tab;
     d.faces = c->d_faces;
     d.noise = c->d_noise;
-    d.out_new = c->F[1 - c->set][0];
-    d.out_old = c->F[1 - c->set][1];
+    d.out_new = c->F[1 - set][0];
+    d.out_old = c->F[1 - set][1];
     d.err = c->d_flags;
     d.nonfinite = c->d_flags + 1;
+    d.step_dev = step_dev;
     d.dt = c->dt;
     d.t0 = c->t0;
     d.Lv = c->Lv;
+    return d;
+}
+
+template <typename real, int TX, int TY, int H, int SEG, int MINB>
+cudaError_t launch2d(const hygro2d_ctx *c, int64_t n0, int n_sub)
+{
+    using L = Tile2D<real, TX, TY, H, SEG>;
+    const Dev2D d = dev_args(c, c->set, nullptr);
     const int tiles = ((c->nx + TX - 1) / TX) * ((c->ny + TY - 1) / TY);
     const CUtensorMap *m = c->maps[c->set];
     df2d_kernel<real, TX, TY, H, SEG, MINB><<<(unsigned)((int64_t)tiles * c->G), L::NT, L::BYTES, c->stream>>>(
         m[0], m[1], c->flag_map, d, n0, n_sub);
     return cudaGetLastError();
+}
+
+// The graph of one interval starting on buffer set `set0`: graph_launches launches of k steps each, launch i
+// on set set0 ^ (i & 1) with its first step *d_step + i k, then d_step advanced by the interval's steps.
+template <typename real, int TX, int TY, int H, int SEG, int MINB>
+cudaError_t build_graph(hygro2d_ctx *c, int set0, cudaGraphExec_t *out)
+{
+    using L = Tile2D<real, TX, TY, H, SEG>;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return e;
+    const int tiles = ((c->nx + TX - 1) / TX) * ((c->ny + TY - 1) / TY);
+    cudaGraphNode_t prev = nullptr;
+    for (int i = 0; i < c->graph_launches && e == cudaSuccess; ++i) {
+        const int set = set0 ^ (i & 1);
+        Dev2D d = dev_args(c, set, c->d_step);
+        CUtensorMap m0 = c->maps[set][0], m1 = c->maps[set][1], mf = c->flag_map;
+        int64_t n0 = (int64_t)i * c->k;
+        int32_t n_sub = c->k;
+        void *args[] = {&m0, &m1, &mf, &d, &n0, &n_sub};
+        cudaKernelNodeParams p = {};
+        p.func = (void *)df2d_kernel<real, TX, TY, H, SEG, MINB>;
+        p.gridDim = dim3((unsigned)((int64_t)tiles * c->G));
+        p.blockDim = dim3(L::NT);
+        p.sharedMemBytes = L::BYTES;
+        p.kernelParams = args;
+        cudaGraphNode_t node;
+        e = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &p);
+        prev = node;
+    }
+    if (e == cudaSuccess) {
+        int64_t *ptr = c->d_step;
+        int64_t inc = (int64_t)c->graph_launches * c->k;
+        void *args[] = {&ptr, &inc};
+        cudaKernelNodeParams p = {};
+        p.func = (void *)step_add_kernel;
+        p.gridDim = dim3(1);
+        p.blockDim = dim3(1);
+        p.kernelParams = args;
+        cudaGraphNode_t node;
+        e = cudaGraphAddKernelNode(&node, g, prev ? &prev : nullptr, prev ? 1 : 0, &p);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    return e;
+}
+
+// Launches of n_steps from the current state: whole graph intervals replayed from the interval's graph,
+// the rest as single launches.
+hygro_status run2d(hygro2d_ctx *c, int64_t n_steps, bool use_graph)
+{
+    const bool f64 = c->precision == HYGRO_FP64;
+    int64_t done = 0;
+    const int64_t unit = (int64_t)c->graph_launches * c->k;
+    if (use_graph && c->graph_launches > 0 && n_steps >= unit) {
+        const int64_t reps = n_steps / unit;
+        if (c->gexec[c->set] == nullptr) {
+            const cudaError_t e = f64 ? build_graph<double, kTX64, kTY64, kH64, kSeg64, kMinB64>(c, c->set, &c->gexec[c->set])
+                                      : build_graph<float, kTX32, kTY32, kH32, kSeg32, kMinB32>(c, c->set, &c->gexec[c->set]);
+            if (e != cudaSuccess) {
+                c->gexec[c->set] = nullptr;
+                return fail(c, HYGRO_E_CUDA, "building the 2D run's CUDA graph: %s", cudaGetErrorString(e));
+            }
+        }
+        step_set_kernel<<<1, 1, 0, c->stream>>>(c->d_step, c->step);
+        CUDA_TRY2(c, cudaGetLastError());
+        for (int64_t r = 0; r < reps; ++r) CUDA_TRY2(c, cudaGraphLaunch(c->gexec[c->set], c->stream));
+        c->step += reps * unit;   // an even launch count leaves the buffer sets where they were
+        done = reps * unit;
+    }
+    while (done < n_steps) {
+        const int sub = (int)std::min<int64_t>(c->k, n_steps - done);
+        const cudaError_t e = f64 ? launch2d<double, kTX64, kTY64, kH64, kSeg64, kMinB64>(c, c->step, sub)
+                                  : launch2d<float, kTX32, kTY32, kH32, kSeg32, kMinB32>(c, c->step, sub);
+        if (e != cudaSuccess) return fail(c, HYGRO_E_CUDA, "2D DF launch: %s", cudaGetErrorString(e));
+        c->set = 1 - c->set;
+        c->step += sub;
+        done += sub;
+    }
+    return HYGRO_OK;
 }
 
 // Opt the kernel of the context's precision into its dynamic shared memory (on the current device).
@@ -194,6 +301,7 @@ cudaError_t prepare_kernel(int precision)
 
 hygro_status upload_faces2d(hygro2d_ctx *c)
 {
+    drop_graphs(c);   // the graphs hold the face and noise-table addresses
     if (!(c->have_materials && c->have_bc[0] && c->have_bc[1] && c->have_bc[2] && c->have_bc[3])) return HYGRO_OK;
     std::vector<FaceInfo> fi((size_t)c->G * 4);
     size_t total = 0;
@@ -366,6 +474,7 @@ hygro_status hygro2d_create(const hygro2d_desc *desc, hygro2d_ctx **out)
     CREATE2D_TRY(cu(cudaMalloc(&c->d_faces, (size_t)c->G * 4 * sizeof(FaceInfo)), "cudaMalloc(faces)"));
     CREATE2D_TRY(cu(cudaMalloc(&c->d_flags, 2 * sizeof(int32_t)), "cudaMalloc(flags)"));
     CREATE2D_TRY(cu(cudaMemset(c->d_flags, 0, 2 * sizeof(int32_t)), "cudaMemset(flags)"));
+    CREATE2D_TRY(cu(cudaMalloc(&c->d_step, sizeof(int64_t)), "cudaMalloc(step counter)"));
     CREATE2D_TRY(encode_maps(c));
 #undef CREATE2D_TRY
     *out = c;
@@ -420,6 +529,7 @@ hygro_status hygro2d_set_materials(hygro2d_ctx *c, int32_t n_regions, const uint
             t[LT_CHI] = y.chi;
         }
     }
+    drop_graphs(c);   // the graphs hold the region table's address
     if (c->d_tab) cudaFree(c->d_tab);
     c->d_tab = nullptr;
     CUDA_TRY2(c, cudaMalloc(&c->d_tab, tab.size() * c->rs));
@@ -486,16 +596,107 @@ hygro_status hygro2d_run(hygro2d_ctx *c, int64_t n_steps)
     if (n_steps == 0) return HYGRO_OK;
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
     CUDA_TRY2(c, after_host_copies(c->stream));
-    for (int64_t done = 0; done < n_steps;) {
-        const int sub = (int)std::min<int64_t>(c->k, n_steps - done);
-        const cudaError_t e = c->precision == HYGRO_FP64
-                                  ? launch2d<double, kTX64, kTY64, kH64, kSeg64, kMinB64>(c, c->step, sub)
-                                  : launch2d<float, kTX32, kTY32, kH32, kSeg32, kMinB32>(c, c->step, sub);
-        if (e != cudaSuccess) return fail(c, HYGRO_E_CUDA, "2D DF launch: %s", cudaGetErrorString(e));
-        c->set = 1 - c->set;
-        c->step += sub;
-        done += sub;
+    return run2d(c, n_steps, true);
+}
+
+hygro_status hygro2d_set_option(hygro2d_ctx *c, int32_t option, int64_t value)
+{
+    if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    if (option == HYGRO2D_OPT_STEPS_PER_LAUNCH) {
+        if (value < 1 || value > c->halo) return fail(c, HYGRO_E_INVALID, "steps per launch must be in 1..%d", c->halo);
+        if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
+        CUDA_TRY2(c, cudaStreamSynchronize(c->stream));
+        drop_graphs(c);
+        c->k = (int)value;
+        return HYGRO_OK;
     }
+    if (option == HYGRO2D_OPT_GRAPH_LAUNCHES) {
+        if (value < 0 || value > 4096 || (value & 1))
+            return fail(c, HYGRO_E_INVALID, "launches per graph must be 0 or an even count up to 4096");
+        if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
+        CUDA_TRY2(c, cudaStreamSynchronize(c->stream));
+        drop_graphs(c);
+        c->graph_launches = (int)value;
+        return HYGRO_OK;
+    }
+    return fail(c, HYGRO_E_INVALID, "unknown option %d", option);
+}
+
+hygro_status hygro2d_get_option(const hygro2d_ctx *c, int32_t option, int64_t *value)
+{
+    if (c == nullptr || value == nullptr) return HYGRO_E_INVALID;
+    if (option == HYGRO2D_OPT_STEPS_PER_LAUNCH) {
+        *value = c->k;
+        return HYGRO_OK;
+    }
+    if (option == HYGRO2D_OPT_GRAPH_LAUNCHES) {
+        *value = c->graph_launches;
+        return HYGRO_OK;
+    }
+    return HYGRO_E_INVALID;
+}
+
+hygro_status hygro2d_autotune(hygro2d_ctx *c, int32_t probe_steps, int32_t *k_best, double *ms_per_step)
+{
+    if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    if (probe_steps < 1 || probe_steps > 100000) return fail(c, HYGRO_E_INVALID, "probe_steps must be in 1..100000");
+    if (!(c->have_materials && c->have_bc[0] && c->have_bc[1] && c->have_bc[2] && c->have_bc[3]))
+        return fail(c, HYGRO_E_STATE, "hygro2d_set_materials and hygro2d_set_bc (all four faces) must come first");
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
+    CUDA_TRY2(c, after_host_copies(c->stream));
+    CUDA_TRY2(c, cudaStreamSynchronize(c->stream));
+    const size_t bytes = c->cells() * 2 * c->rs;
+    void *save[2] = {nullptr, nullptr};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    const int set0 = c->set, k0 = c->k;
+    const int64_t step0 = c->step;
+    hygro_status st = HYGRO_OK;
+    auto cu = [&](cudaError_t e, const char *what) {
+        if (e != cudaSuccess && st == HYGRO_OK)
+            st = fail(c, e == cudaErrorMemoryAllocation ? HYGRO_E_NOMEM : HYGRO_E_CUDA, "autotune, %s: %s", what,
+                      cudaGetErrorString(e));
+        return st == HYGRO_OK;
+    };
+    auto restore = [&]() {
+        for (int l = 0; l < 2; ++l)
+            cu(cudaMemcpyAsync(c->F[set0][l], save[l], bytes, cudaMemcpyDeviceToDevice, c->stream), "restore");
+        c->set = set0;
+        c->step = step0;
+    };
+    bool ok = cu(cudaMalloc(&save[0], bytes), "cudaMalloc") && cu(cudaMalloc(&save[1], bytes), "cudaMalloc") &&
+              cu(cudaEventCreate(&e0), "event") && cu(cudaEventCreate(&e1), "event");
+    for (int l = 0; l < 2 && ok; ++l)
+        ok = cu(cudaMemcpyAsync(save[l], c->F[set0][l], bytes, cudaMemcpyDeviceToDevice, c->stream), "save");
+    double best_ms = 0.0;
+    int best = k0;
+    for (int k = 1; k <= c->halo && ok; ++k) {
+        c->k = k;
+        restore();   // a warm-up launch from the saved state, then the timed probe from it again
+        hygro_status rs = st == HYGRO_OK ? run2d(c, std::min<int64_t>(k, probe_steps), false) : st;
+        if (rs == HYGRO_OK) restore();
+        float ms = 0.0f;
+        if (rs == HYGRO_OK && st == HYGRO_OK && cu(cudaEventRecord(e0, c->stream), "event")) rs = run2d(c, probe_steps, false);
+        ok = rs == HYGRO_OK && st == HYGRO_OK && cu(cudaEventRecord(e1, c->stream), "event") &&
+             cu(cudaEventSynchronize(e1), "event") && cu(cudaEventElapsedTime(&ms, e0, e1), "event");
+        if (rs != HYGRO_OK && st == HYGRO_OK) st = rs;
+        if (!ok) break;
+        const double per = (double)ms / probe_steps;
+        if (ms_per_step) ms_per_step[k - 1] = per;
+        if (k == 1 || per < best_ms) {
+            best_ms = per;
+            best = k;
+        }
+    }
+    if (save[0] && save[1]) restore();
+    cudaStreamSynchronize(c->stream);
+    c->k = ok ? best : k0;
+    drop_graphs(c);
+    for (void *p : save)
+        if (p) cudaFree(p);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (!ok) return st != HYGRO_OK ? st : fail(c, HYGRO_E_CUDA, "autotune failed");
+    if (k_best) *k_best = best;
     return HYGRO_OK;
 }
 

@@ -206,6 +206,7 @@ struct hygro_ctx {
     int cur = 0;
     int grid_persistent = 1;
     int round_size = 1;
+    CostModel cost = default_cost_model();   // step-time model of the wall schedule (hygro_autotune refits it)
     size_t real_size = 4;
     std::string err = "no error";
 
@@ -611,7 +612,7 @@ hygro_status build_schedule(hygro_ctx *c)
         const int R = std::max(1, std::min(wpb, Wf / G));
         c->round_size = R;
         std::vector<int32_t> order, boff;
-        lpt_rounds(std::move(sw), G, R, order, boff);
+        lpt_rounds(std::move(sw), G, R, order, boff, nullptr, c->cost);
         if (!order.empty())
             CUDA_TRY(c, cudaMemcpy(c->d_order, order.data(), order.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
         CUDA_TRY(c, cudaMemcpy(c->d_block_off, boff.data(), boff.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
@@ -672,6 +673,10 @@ hygro_status launch_steps(hygro_ctx *c, int64_t n_steps, int se, void *dsamp)
     }
     return HYGRO_OK;
 }
+
+// State image of hygro_get_state / hygro_set_state (no fault point: internal callers use these too).
+hygro_status get_state_impl(hygro_ctx *c, void *buf, size_t *bytes);
+hygro_status set_state_impl(hygro_ctx *c, const void *buf, size_t bytes);
 }  // namespace
 
 extern "C" {
@@ -1340,6 +1345,22 @@ hygro_status hygro_get_state(hygro_ctx *c, void *buf, size_t *bytes)
 {
     if (c == nullptr || bytes == nullptr) return fail(c, HYGRO_E_INVALID, "ctx or bytes is NULL");
     FAULT_POINT(c, "hygro_get_state");
+    return get_state_impl(c, buf, bytes);
+}
+
+hygro_status hygro_set_state(hygro_ctx *c, const void *buf, size_t bytes)
+{
+    if (c == nullptr || buf == nullptr) return fail(c, HYGRO_E_INVALID, "ctx or buf is NULL");
+    FAULT_POINT(c, "hygro_set_state");
+    return set_state_impl(c, buf, bytes);
+}
+
+}  // extern "C"
+
+namespace {
+
+hygro_status get_state_impl(hygro_ctx *c, void *buf, size_t *bytes)
+{
     const size_t nf = (size_t)c->total_nodes * c->real_size;
     const size_t nroom = c->rooms.size() * 4 * sizeof(double);
     const size_t need = 5 * sizeof(int64_t) + 4 * nf + 2 * (size_t)c->W * 4 * sizeof(double) + nroom;
@@ -1368,10 +1389,8 @@ hygro_status hygro_get_state(hygro_ctx *c, void *buf, size_t *bytes)
     return HYGRO_OK;
 }
 
-hygro_status hygro_set_state(hygro_ctx *c, const void *buf, size_t bytes)
+hygro_status set_state_impl(hygro_ctx *c, const void *buf, size_t bytes)
 {
-    if (c == nullptr || buf == nullptr) return fail(c, HYGRO_E_INVALID, "ctx or buf is NULL");
-    FAULT_POINT(c, "hygro_set_state");
     const size_t nf = (size_t)c->total_nodes * c->real_size;
     const size_t nroom = c->rooms.size() * 4 * sizeof(double);
     const size_t need = 5 * sizeof(int64_t) + 4 * nf + 2 * (size_t)c->W * 4 * sizeof(double) + nroom;
@@ -1397,6 +1416,113 @@ hygro_status hygro_set_state(hygro_ctx *c, const void *buf, size_t bytes)
     if (nroom) CUDA_TRY(c, cudaMemcpy(c->d_room_state, p, nroom, cudaMemcpyHostToDevice));
     c->step = hdr[4];
     return HYGRO_OK;
+}
+
+// The persistent kernel's n_steps from the current state, timed with CUDA events on the context's stream.
+hygro_status timed_probe(hygro_ctx *c, int64_t n_steps, float *ms)
+{
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CUDA_TRY(c, cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(c, HYGRO_E_CUDA, "cudaEventCreate failed");
+    }
+    hygro_status st = HYGRO_OK;
+    if (cudaEventRecord(e0, c->stream) != cudaSuccess) st = fail(c, HYGRO_E_CUDA, "cudaEventRecord failed");
+    if (st == HYGRO_OK) st = launch_steps(c, n_steps, 0, nullptr);
+    if (st == HYGRO_OK && (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                           cudaEventElapsedTime(ms, e0, e1) != cudaSuccess))
+        st = fail(c, HYGRO_E_CUDA, "timing the probe failed");
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+hygro_status hygro_autotune(hygro_ctx *c, int32_t probe_steps, double *model, double *ms)
+{
+    if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    FAULT_POINT(c, "hygro_autotune");
+    if (probe_steps < 16 || probe_steps > (1 << 20)) return fail(c, HYGRO_E_INVALID, "probe_steps must be in 16..2^20");
+    if (!(c->have_materials && c->have_bc[0] && c->have_bc[1]))
+        return fail(c, HYGRO_E_STATE, "hygro_set_materials and hygro_set_bc (both faces) must come first");
+    if (c->kernel != HYGRO_KERNEL_PERSISTENT || c->any_room_walls || c->n_free == 0)
+        return fail(c, HYGRO_E_UNSUPPORTED, "the autotuner schedules walls of the persistent kernel without rooms");
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
+    size_t bytes = 0;
+    hygro_status st = get_state_impl(c, nullptr, &bytes);
+    if (st != HYGRO_OK) return st;
+    std::vector<char> saved(bytes);
+    st = get_state_impl(c, saved.data(), &bytes);
+    if (st != HYGRO_OK) return st;
+    const CostModel old_model = c->cost;
+    // 1. a traced probe: every wall's start and end time on the GPU clock
+    unsigned long long *own_trace = nullptr;
+    if (c->d_trace == nullptr) {
+        CUDA_TRY(c, cudaMalloc(&own_trace, (size_t)c->W * 4 * sizeof(unsigned long long)));
+        c->d_trace = own_trace;
+    }
+    auto finish = [&](hygro_status s) {
+        if (own_trace) {
+            cudaFree(own_trace);
+            c->d_trace = nullptr;
+        }
+        const hygro_status r = set_state_impl(c, saved.data(), saved.size());
+        return s != HYGRO_OK ? s : r;
+    };
+    st = launch_steps(c, probe_steps, 0, nullptr);
+    std::vector<unsigned long long> tr((size_t)c->W * 4);
+    if (st == HYGRO_OK && (cudaMemcpyAsync(tr.data(), c->d_trace, tr.size() * sizeof(unsigned long long),
+                                           cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+                           cudaStreamSynchronize(c->stream) != cudaSuccess))
+        st = fail(c, HYGRO_E_CUDA, "reading the probe's wall trace failed");
+    if (own_trace) {
+        cudaFree(own_trace);
+        own_trace = nullptr;
+        c->d_trace = nullptr;
+    }
+    if (st != HYGRO_OK) return finish(st);
+    // 2. fit the per-variant step time a + b K to the walls' measured ns per step
+    std::vector<SchedWall> sw;
+    std::vector<double> ns;
+    for (int w = 0; w < c->W; ++w) {
+        const WallInfo &x = c->walls[w];
+        const bool simple = x.simple && c->precision == HYGRO_FP32;
+        sw.push_back({w, x.K, x.aligned ? (simple ? 0 : 1) : (simple ? 3 : 2), x.N});
+        const unsigned long long *t = &tr[(size_t)w * 4];
+        ns.push_back(t[2] > t[1] && t[3] > 0 ? (double)(t[2] - t[1]) / (double)t[3] : -1.0);
+    }
+    CostModel fitted;
+    fit_cost_model(sw, ns, old_model, fitted);
+    // 3. the probe again with the current schedule and with the refitted one; keep the faster
+    float ms_old = 0.0f, ms_new = 0.0f;
+    st = set_state_impl(c, saved.data(), saved.size());
+    if (st == HYGRO_OK) st = timed_probe(c, probe_steps, &ms_old);
+    if (st == HYGRO_OK) {
+        c->cost = fitted;
+        st = build_schedule(c);
+    }
+    if (st == HYGRO_OK) st = set_state_impl(c, saved.data(), saved.size());
+    if (st == HYGRO_OK) st = timed_probe(c, probe_steps, &ms_new);
+    if (st != HYGRO_OK || ms_new > ms_old) {
+        c->cost = old_model;
+        const hygro_status rs = build_schedule(c);
+        if (st == HYGRO_OK) st = rs;
+    }
+    if (model) {
+        for (int v = 0; v < 4; ++v) {
+            model[v] = fitted.a[v];
+            model[4 + v] = fitted.b[v];
+        }
+    }
+    if (ms) {
+        ms[0] = ms_old;
+        ms[1] = ms_new;
+    }
+    return finish(st);
 }
 
 }  // extern "C"

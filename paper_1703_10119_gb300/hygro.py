@@ -39,11 +39,13 @@ ABI_FUNCTIONS = ("hygro_create", "hygro_set_materials", "hygro_set_bc", "hygro_r
                  "hygro_fluxes", "hygro_get_fields", "hygro_set_fields", "hygro_get_step", "hygro_get_state",
                  "hygro_set_state", "hygro_last_error", "hygro_destroy", "hygro_run_noalloc", "hygro_set_rooms",
                  "hygro_get_rooms", "hygro_loss_grad", "hygro_balance", "hygro_set_option",
-                 "hygro_start_euler", "hygro_set_vapour_fraction")
+                 "hygro_start_euler", "hygro_set_vapour_fraction", "hygro_autotune")
 # Exported entry points of the 2D sections (names of include/hygro2d.h).
 ABI_FUNCTIONS_2D = ("hygro2d_create", "hygro2d_set_materials", "hygro2d_set_bc", "hygro2d_run", "hygro2d_sync",
                     "hygro2d_get_fields", "hygro2d_set_fields", "hygro2d_get_step", "hygro2d_last_error",
-                    "hygro2d_destroy")
+                    "hygro2d_destroy", "hygro2d_set_option", "hygro2d_get_option", "hygro2d_autotune")
+HYGRO2D_OPT_STEPS_PER_LAUNCH = 1
+HYGRO2D_OPT_GRAPH_LAUNCHES = 2
 # Exported arithmetic-peak microbenchmark (include/hygro_peaks.h).
 ABI_FUNCTIONS_PEAKS = ("hygro_peak_probe",)
 HYGRO2D_MAX_REGIONS = 8
@@ -126,6 +128,7 @@ def lib(build_if_missing: bool = False) -> C.CDLL:
         "hygro_set_state": [P, P, C.c_size_t],
         "hygro_set_rooms": [P, C.c_int32, P, P],
         "hygro_get_rooms": [P, C.c_int32, P, P],
+        "hygro_autotune": [P, C.c_int32, P, P],
         "hygro_loss_grad": [P, C.c_int64, C.c_int32, P, C.c_double, C.c_double, C.c_int32, C.POINTER(C.c_double), P],
         "hygro2d_create": [C.POINTER(hygro2d_desc), C.POINTER(P)],
         "hygro2d_set_materials": [P, C.c_int32, P, P, P, P],
@@ -135,6 +138,9 @@ def lib(build_if_missing: bool = False) -> C.CDLL:
         "hygro2d_get_fields": [P, C.c_int32, P, P],
         "hygro2d_set_fields": [P, C.c_int32, P, P],
         "hygro2d_get_step": [P, C.POINTER(C.c_int64)],
+        "hygro2d_set_option": [P, C.c_int32, C.c_int64],
+        "hygro2d_get_option": [P, C.c_int32, C.POINTER(C.c_int64)],
+        "hygro2d_autotune": [P, C.c_int32, C.POINTER(C.c_int32), P],
         "hygro_peak_probe": [C.c_int32, C.c_int32, P, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_double)],
     }
     for name, args in sig.items():
@@ -289,6 +295,10 @@ def hygro_peak_probe(kind: int, device: int = -1, stream=None, target_ms: float 
     return ops.value, ms.value
 
 
+def hygro_autotune(ctx, probe_steps: int, model=None, ms=None):
+    _check(lib().hygro_autotune(ctx, int(probe_steps), _ptr(model), _ptr(ms)), ctx)
+
+
 def hygro_last_error(ctx) -> str:
     return lib().hygro_last_error(ctx).decode()
 
@@ -334,6 +344,23 @@ def hygro2d_get_step(ctx) -> int:
     s = C.c_int64()
     _check2d(lib().hygro2d_get_step(ctx, C.byref(s)), ctx)
     return s.value
+
+
+def hygro2d_set_option(ctx, option: int, value: int):
+    _check2d(lib().hygro2d_set_option(ctx, int(option), int(value)), ctx)
+
+
+def hygro2d_get_option(ctx, option: int) -> int:
+    v = C.c_int64()
+    _check2d(lib().hygro2d_get_option(ctx, int(option), C.byref(v)), ctx)
+    return v.value
+
+
+def hygro2d_autotune(ctx, probe_steps: int, ms_per_step=None) -> int:
+    """Time each temporal blocking depth on probe_steps steps from the current state, keep the fastest."""
+    k = C.c_int32()
+    _check2d(lib().hygro2d_autotune(ctx, int(probe_steps), C.byref(k), _ptr(ms_per_step)), ctx)
+    return k.value
 
 
 def hygro2d_last_error(ctx) -> str:
@@ -479,6 +506,14 @@ class Hygro:
     def step(self) -> int:
         return hygro_get_step(self.ctx)
 
+    def autotune(self, probe_steps: int = 2000):
+        """Refit the wall schedule's step-time model on a probe of this workload (hygro_autotune); returns
+        (model a[4], b[4] in ns, probe ms with the previous and the refitted schedule)."""
+        model = np.zeros(8)
+        ms = np.zeros(2)
+        hygro_autotune(self.ctx, probe_steps, model, ms)
+        return model[:4], model[4:], ms
+
     def get_state(self) -> bytes:
         return hygro_get_state(self.ctx)
 
@@ -538,6 +573,19 @@ class Hygro2D:
 
     def run(self, n_steps: int):
         hygro2d_run(self.ctx, n_steps)
+
+    def set_option(self, option: int, value: int):
+        hygro2d_set_option(self.ctx, option, value)
+
+    def option(self, option: int) -> int:
+        return hygro2d_get_option(self.ctx, option)
+
+    def autotune(self, probe_steps: int = 16):
+        """Pick the temporal blocking depth by timing each one (hygro2d_autotune); returns (depth, ms per
+        step of depths 1..4)."""
+        ms = np.zeros(4)
+        k = hygro2d_autotune(self.ctx, probe_steps, ms)
+        return k, ms
 
     def sync(self):
         hygro2d_sync(self.ctx)

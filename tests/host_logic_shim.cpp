@@ -25,6 +25,25 @@ double shim_sched_cost(int K, int kind)
     return hygro::sched_cost({0, K, kind, 0});
 }
 
+// Fits the cost model to n walls (K, kind) with measured step times ns; base and out: a[4] then b[4].
+int shim_fit_cost_model(int n, const int32_t *K, const int32_t *kind, const double *ns, const double *base, double *out)
+{
+    std::vector<hygro::SchedWall> w(n);
+    std::vector<double> t(ns, ns + n);
+    for (int i = 0; i < n; ++i) w[i] = {i, K[i], kind[i], 0};
+    hygro::CostModel b, o;
+    for (int v = 0; v < 4; ++v) {
+        b.a[v] = base[v];
+        b.b[v] = base[4 + v];
+    }
+    const int f = hygro::fit_cost_model(w, t, b, o);
+    for (int v = 0; v < 4; ++v) {
+        out[v] = o.a[v];
+        out[4 + v] = o.b[v];
+    }
+    return f;
+}
+
 // Returns the number of order entries written (at most cap), or -1 when cap is too small.
 int shim_lpt_rounds(int n, const int32_t *wall, const int32_t *K, const int32_t *kind, const int32_t *N, int G,
                     int R, int32_t *order, int cap, int32_t *boff, double *load)

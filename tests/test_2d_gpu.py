@@ -114,6 +114,74 @@ def test_blocking_depth_does_not_change_the_bits(H, precision):
             assert np.array_equal(got[lev][f], base[lev][f])
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_graph_intervals_give_the_same_bits(H, precision):
+    """Runs whose whole intervals are replayed from CUDA graphs (2 and 6 launches per interval) against
+    single launches: the same bits and the same step, over calls that start on either buffer set (an odd
+    call in between flips the sets), with the step index of each replay read from the device."""
+    sec = mixed_sections(2, 97, 70, 80, seed=13)
+    pieces = [17, 3, 26, 34]   # 4-step launches: intervals of 8 and 24 steps, remainders, an odd launch count
+    ref = run_gpu(H, sec, precision, 80, k=4, pieces=pieces)
+    with H.Hygro2D(sec, precision=precision, steps_per_launch=4) as g0:
+        g0.set_option(H.HYGRO2D_OPT_GRAPH_LAUNCHES, 0)
+        for n in pieces:
+            g0.run(n)
+        g0.sync()
+        plain = g0.fields(0), g0.fields(1)
+    for launches in (2, 6):
+        with H.Hygro2D(sec, precision=precision, steps_per_launch=4) as g:
+            g.set_option(H.HYGRO2D_OPT_GRAPH_LAUNCHES, launches)
+            assert g.option(H.HYGRO2D_OPT_GRAPH_LAUNCHES) == launches
+            for n in pieces:
+                g.run(n)
+            g.sync()
+            assert g.step == 80
+            got = g.fields(0), g.fields(1)
+        for lev in range(2):
+            for f in range(2):
+                assert np.array_equal(got[lev][f], plain[lev][f]), (launches, lev, f)
+                assert np.array_equal(got[lev][f], ref[lev][f]), (launches, lev, f)
+
+
+def test_graph_option_validation(H):
+    sec = mixed_sections(1, 40, 30, 4, seed=3)
+    with H.Hygro2D(sec, precision="fp32") as g:
+        for opt, bad in ((H.HYGRO2D_OPT_GRAPH_LAUNCHES, 3), (H.HYGRO2D_OPT_GRAPH_LAUNCHES, -2),
+                         (H.HYGRO2D_OPT_GRAPH_LAUNCHES, 4098), (H.HYGRO2D_OPT_STEPS_PER_LAUNCH, 0),
+                         (H.HYGRO2D_OPT_STEPS_PER_LAUNCH, 5), (99, 1)):
+            with pytest.raises(H.HygroError) as e:
+                g.set_option(opt, bad)
+            assert e.value.status == H.HYGRO_E_INVALID
+        assert g.option(H.HYGRO2D_OPT_GRAPH_LAUNCHES) == 64
+        assert g.option(H.HYGRO2D_OPT_STEPS_PER_LAUNCH) == 4
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_autotune_keeps_state_and_bits(H, precision):
+    """The depth autotuner times every depth from the current state and restores it: afterwards the stored
+    levels and the step are as before, and the run that follows gives the bits of a run at any depth."""
+    sec = mixed_sections(2, 150, 130, 40, seed=17)
+    ref = run_gpu(H, sec, precision, 40, k=1, pieces=[9, 31])
+    with H.Hygro2D(sec, precision=precision, steps_per_launch=1) as g:
+        g.run(9)
+        g.sync()
+        before = g.fields(0), g.fields(1)
+        k, ms = g.autotune(6)
+        assert 1 <= k <= 4 and g.option(H.HYGRO2D_OPT_STEPS_PER_LAUNCH) == k
+        assert np.all(ms > 0) and ms[k - 1] == ms.min()
+        assert g.step == 9
+        after = g.fields(0), g.fields(1)
+        for lev in range(2):
+            for f in range(2):
+                assert np.array_equal(after[lev][f], before[lev][f])
+        g.run(31)
+        g.sync()
+        got = g.fields(0), g.fields(1)
+    for lev in range(2):
+        for f in range(2):
+            assert np.array_equal(got[lev][f], ref[lev][f])
+
+
 @pytest.mark.parametrize("shape", [(2, 2), (3, 2), (64, 64), (65, 63), (8, 200), (200, 5)])
 def test_edge_shapes(H, oracle_mod, shape):
     nx, ny = shape

@@ -144,3 +144,54 @@ def test_lpt_rounds(shim, n, G, R):
         assert load.max() - load.min() <= rcost.max() + 1e-9
     else:
         assert np.count_nonzero(load > 0) == n_rounds   # one round per block while rounds are fewer
+
+
+def _fit(shim, K, kind, ns, base):
+    K = np.ascontiguousarray(K, np.int32)
+    kind = np.ascontiguousarray(kind, np.int32)
+    ns = np.ascontiguousarray(ns, np.float64)
+    base = np.ascontiguousarray(base, np.float64)
+    out = np.zeros(8)
+    p = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
+    n = shim.shim_fit_cost_model(len(K), p(K), p(kind), p(ns), p(base), p(out))
+    return n, out[:4], out[4:]
+
+
+def test_cost_model_fit_recovers_exact_lines(shim):
+    """The autotuner's fit of the per-variant step time a + b K: exact data give back a and b; a variant
+    measured at a single K keeps the base slope and fits the intercept; a variant with no measured wall (or
+    only unmeasured ones) keeps the base model."""
+    rng = np.random.default_rng(3)
+    base = [100.0, 200.0, 150.0, 190.0, 60.0, 70.0, 120.0, 80.0]
+    a_true, b_true = [90.0, 250.0, 0, 0], [55.0, 81.0, 0, 0]
+    K, kind, ns = [], [], []
+    for v in (0, 1):
+        for k in rng.integers(2, 14, 40):
+            K.append(k)
+            kind.append(v)
+            ns.append(a_true[v] + b_true[v] * k)
+    for _ in range(5):            # variant 2 at one K only: 7 -> 1000 ns
+        K.append(7)
+        kind.append(2)
+        ns.append(1000.0)
+    K.append(5)
+    kind.append(3)
+    ns.append(-1.0)               # not measured
+    n, a, b = _fit(shim, K, kind, ns, base)
+    assert n == 3
+    np.testing.assert_allclose(a[:2], a_true[:2], rtol=1e-12)
+    np.testing.assert_allclose(b[:2], b_true[:2], rtol=1e-12)
+    assert b[2] == base[6] and abs(a[2] - (1000.0 - base[6] * 7)) < 1e-9
+    assert a[3] == base[3] and b[3] == base[7]
+
+
+def test_cost_model_fit_least_squares_and_nonnegative_slope(shim):
+    """Noisy data give the least-squares line (numpy's polyfit); a falling trend is clipped to a flat one."""
+    rng = np.random.default_rng(4)
+    K = rng.integers(2, 14, 200)
+    ns = 120.0 + 66.0 * K + rng.normal(0, 15.0, K.size)
+    n, a, b = _fit(shim, K, np.zeros(K.size), ns, [0.0] * 8)
+    slope, icpt = np.polyfit(K.astype(float), ns, 1)
+    assert n == 1 and abs(b[0] - slope) < 1e-9 * slope and abs(a[0] - icpt) < 1e-6 * abs(icpt)
+    n, a, b = _fit(shim, K, np.zeros(K.size), 900.0 - 10.0 * K, [0.0] * 8)
+    assert b[0] == 0.0 and abs(a[0] - np.mean(900.0 - 10.0 * K)) < 1e-9
