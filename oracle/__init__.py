@@ -61,7 +61,7 @@ class _Problem(C.Structure):
         ("noise", C.c_void_p * 2), ("noise_len", C.c_int32 * 2),
         ("dt", C.c_double), ("t0", C.c_double), ("Lv", C.c_double), ("Psat", C.c_double),
         ("n_rooms", C.c_int32), ("room_par", C.c_void_p), ("wall_area", C.c_void_p),
-        ("vapour_frac", C.c_void_p),
+        ("vapour_frac", C.c_void_p), ("layer_law", C.c_void_p),
     ]
 
 
@@ -117,7 +117,11 @@ def _load():
         lib.orc_euler_start.restype = C.c_int
         lib.orc_euler_start.argtypes = [C.POINTER(_Problem), C.POINTER(_State), C.c_double, C.c_int32]
         lib.orc_coefficients.restype = None
-        lib.orc_coefficients.argtypes = [C.POINTER(_Problem), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]
+        lib.orc_coefficients.argtypes = [C.POINTER(_Problem), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                         C.c_void_p]
+        lib.orc_table1.restype = None
+        lib.orc_table1.argtypes = [C.c_int32, C.c_double, C.c_double, C.c_double, C.c_void_p,
+                                   C.POINTER(C.c_double), C.POINTER(C.c_double)]
         _lib = lib
     return _lib
 
@@ -185,6 +189,8 @@ class Oracle:
             p.wall_area = _ptr(keep(np.zeros(max(W, 1)), np.float64))
         vf = getattr(wl, "vapour_frac", None)
         p.vapour_frac = None if vf is None else _ptr(keep(vf, np.float64))
+        law = getattr(wl, "layer_law", None)
+        p.layer_law = None if law is None else _ptr(keep(law, np.int32))
         self._p = p
 
         self.T_prev = np.repeat(np.asarray(wl.T_init, np.float64), wl.n_nodes)
@@ -251,14 +257,29 @@ class Oracle:
         _load().orc_ambient(C.byref(self._p), w, face, float(t), C.byref(T), C.byref(P))
         return T.value, P.value
 
-    def coefficients(self, w: int, P: np.ndarray):
-        """Node (kM, cM, kTT, cTT, kTM, cTM) and face (kM_f, kTT_f, kTM_f) values."""
+    def coefficients(self, w: int, P: np.ndarray, T: np.ndarray | None = None):
+        """Node (kM, cM, kTT, cTT, kTM, cTM) and face (kM_f, kTT_f, kTM_f) values at level values P (and T,
+        which only the Table-1 laws use)."""
         P = np.ascontiguousarray(P, np.float64)
+        T = None if T is None else np.ascontiguousarray(T, np.float64)
         N = P.shape[0]
         node = np.zeros((N, 6))
         face = np.zeros((N - 1, 3))
-        _load().orc_coefficients(C.byref(self._p), int(w), _ptr(P), _ptr(node), _ptr(face))
+        _load().orc_coefficients(C.byref(self._p), int(w), _ptr(T), _ptr(P), _ptr(node), _ptr(face))
         return node, face
+
+
+LAW_AFFINE, LAW_TABLE1, LAW_TABLE1_A, LAW_TABLE1_C = 0, 1, 2, 3
+
+
+def table1(law: int, T: float, Pv: float, Lv: float):
+    """Coefficients (kM, cM, kTT, cTT, kTM, cTM) of the Table-1 material at (T, Pv), with Ps(T) and the
+    sorption isotherm f: returns (coefficients[6], Ps, f)."""
+    out = np.zeros(6)
+    ps = C.c_double()
+    fw = C.c_double()
+    _load().orc_table1(int(law), float(T), float(Pv), float(Lv), _ptr(out), C.byref(ps), C.byref(fw))
+    return out, ps.value, fw.value
 
 
 def _misfit(wl, obs, sample_every, wT, wP, keep):

@@ -301,6 +301,12 @@ int orc_loss_adjoint(const orc_problem *p, int64_t n_steps, const orc_misfit *m,
 {
     if (p == NULL || m == NULL || loss_out == NULL || n_steps < 0 || m->sample_every < 1) return -1;
     if (p->n_rooms > 0) return -1;
+    if (p->layer_law != NULL) {   /* the adjoint differentiates the affine laws only */
+        int64_t nl = 0;
+        for (int32_t w = 0; w < p->n_walls; ++w) nl += p->n_layers[w];
+        for (int64_t l = 0; l < nl; ++l)
+            if (p->layer_law[l] != ORC_LAW_AFFINE) return -1;
+    }
     if (p->vapour_frac != NULL)
         for (int32_t w = 0; w < p->n_walls; ++w)
             if (p->vapour_frac[w] != 1.0) return -1;   /* the adjoint takes kTM = Lv kM */
@@ -421,6 +427,12 @@ int orc_loss_tangent(const orc_problem *p, int64_t n_steps, const orc_misfit *m,
                      double *dloss_out)
 {
     if (p == NULL || m == NULL || dir == NULL || n_steps < 0 || m->sample_every < 1 || p->n_rooms > 0) return -1;
+    if (p->layer_law != NULL) {   /* affine laws only, as the reverse sweep */
+        int64_t nl = 0;
+        for (int32_t w = 0; w < p->n_walls; ++w) nl += p->n_layers[w];
+        for (int64_t l = 0; l < nl; ++l)
+            if (p->layer_law[l] != ORC_LAW_AFFINE) return -1;
+    }
     if (p->vapour_frac != NULL)
         for (int32_t w = 0; w < p->n_walls; ++w)
             if (p->vapour_frac[w] != 1.0) return -1;

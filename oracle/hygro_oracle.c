@@ -57,6 +57,7 @@ typedef struct {
     int32_t nl;
     const int32_t *first;
     const double *par;
+    const int32_t *law;    /* coefficient law of each layer (NULL: all affine) */
     double nu;             /* kTM = nu Lv kM */
 } wall_view;
 
@@ -68,6 +69,7 @@ static wall_view view_of(const orc_problem *p, const int64_t *layer_off, int32_t
     v.nl = p->n_layers[w];
     v.first = p->layer_first + layer_off[w];
     v.par = p->layer_par + (size_t)layer_off[w] * ORC_NLAYER_PAR;
+    v.law = p->layer_law != NULL ? p->layer_law + layer_off[w] : NULL;
     v.nu = p->vapour_frac != NULL ? p->vapour_frac[w] : 1.0;
     return v;
 }
@@ -79,17 +81,73 @@ static int32_t layer_of(const wall_view *v, int32_t j)
     return l;
 }
 
+/* The load bearing material of Sec. 4, Table 1 (see hygro_oracle.h for the formulas and the readings of
+ * the parts the paper leaves open). The storage coefficient is the derivative of the sorption isotherm
+ * with respect to Pv, cM = f'(phi) / Ps = (df / dPc) (dPc / dPv) with dPc / dPv = rho_l Rv T / Pv. */
+void orc_table1(int32_t law, double T, double Pv, double Lv, double *out, double *ps, double *fw)
+{
+    const double rho_l = 1000.0, Rv = 461.5, c1 = 1.25e-5, c2 = 1.8e-5;
+    const double rho0 = 790.0, c0 = 870.0, cw = 4180.0;
+    const double theta = T - 273.15;
+    const double Ps = 610.94 * exp(17.625 * theta / (theta + 243.04));
+    /* above saturation the isotherm has no values: the capillary pressure is held at 0 (saturated) */
+    const double Pc = fmin(0.0, rho_l * Rv * T * log(Pv / Ps));
+    const double x1 = -c1 * Pc, x2 = -c2 * Pc;
+    const double f = 47.1 * pow(1.0 + pow(x1, 1.65), -0.39) + 109.9 * pow(1.0 + pow(x2, 6.0), -0.83);
+    /* df/dPc: each term a (1 + (-c Pc)^m)^-e gives a e m c (-c Pc)^(m-1) (1 + (-c Pc)^m)^(-e-1) */
+    const double dfdPc = 47.1 * 0.39 * 1.65 * c1 * pow(x1, 0.65) * pow(1.0 + pow(x1, 1.65), -1.39) +
+                         109.9 * 0.83 * 6.0 * c2 * pow(x2, 5.0) * pow(1.0 + pow(x2, 6.0), -1.83);
+    const double cM = dfdPc * rho_l * Rv * T / Pv;
+    const double s = 1.0 - f / 157.0;
+    const double dv = 1.88e-6 / T * s / (0.503 * s * s + 0.497);
+    const double x = 2.0 * Pv / Ps;
+    double liquid;
+    if (law == ORC_LAW_TABLE1_A) {
+        const double y = -8.0 * x - 2.0;
+        liquid = exp(y * y);
+    } else if (law == ORC_LAW_TABLE1_C) {
+        liquid = exp(-8.0 * (x - 2.0) * (x - 2.0));
+    } else {
+        const double e = exp(-8.0 * x - 2.0);
+        liquid = e * e;
+    }
+    const double kM = 1.97e-10 * exp(-0.07 * log10(x) + 1.44) + 1.77e-7 * liquid;
+    out[0] = kM;
+    out[1] = cM;
+    out[2] = 0.2 + 0.0045 * f;
+    out[3] = rho0 * c0 + f * cw;
+    out[4] = Lv * dv;
+    out[5] = cw * theta * cM;
+    if (ps) *ps = Ps;
+    if (fw) *fw = f;
+}
+
 /* Material coefficients of Sec. 2 evaluated at level n (explicitly, as the
  * paper prescribes for the DF scheme in Sec. 3.1), then their face values:
  * arithmetic mean of the two nodes inside a layer (for coefficients affine
  * in Pv this equals the coefficient at the face-mean Pv, Sec. 3.1) and the
- * harmonic mean across an interface between two layers. kTM_f = nu Lv kM_f. */
-static void coefficients(const orc_problem *p, const wall_view *v, const double *P,
+ * harmonic mean across an interface between two layers. Affine layers:
+ * kTM_f = nu Lv kM_f. Layers of a Table-1 law: their kTM = Lv dv takes the
+ * face rule of the other conductances. */
+static void coefficients(const orc_problem *p, const wall_view *v, const double *T, const double *P,
                          double *kM, double *cM, double *kTT, double *cTT, double *kTM, double *cTM,
                          double *kMf, double *kTTf, double *kTMf)
 {
     for (int32_t j = 0; j < v->N; ++j) {
-        const double *q = v->par + (size_t)layer_of(v, j) * ORC_NLAYER_PAR;
+        const int32_t l = layer_of(v, j);
+        const int32_t law = v->law != NULL ? v->law[l] : ORC_LAW_AFFINE;
+        if (law != ORC_LAW_AFFINE) {
+            double c[6];
+            orc_table1(law, T[j], P[j], p->Lv, c, NULL, NULL);
+            kM[j] = c[0];
+            cM[j] = c[1];
+            kTT[j] = c[2];
+            cTT[j] = c[3];
+            kTM[j] = c[4];
+            cTM[j] = c[5];
+            continue;
+        }
+        const double *q = v->par + (size_t)l * ORC_NLAYER_PAR;
         double r = P[j] / p->Psat;
         kM[j] = q[L_KM0] * (1.0 + q[L_A] * r);
         cM[j] = q[L_CM0] * (1.0 + q[L_B] * r);
@@ -99,25 +157,29 @@ static void coefficients(const orc_problem *p, const wall_view *v, const double 
         cTM[j] = q[L_CHI] * cM[j];
     }
     for (int32_t j = 0; j + 1 < v->N; ++j) {
-        if (layer_of(v, j) == layer_of(v, j + 1)) {
+        const int32_t l0 = layer_of(v, j), l1 = layer_of(v, j + 1);
+        const int affine = v->law == NULL || (v->law[l0] == ORC_LAW_AFFINE && v->law[l1] == ORC_LAW_AFFINE);
+        if (l0 == l1) {
             kMf[j] = 0.5 * (kM[j] + kM[j + 1]);
             kTTf[j] = 0.5 * (kTT[j] + kTT[j + 1]);
+            kTMf[j] = affine ? v->nu * p->Lv * kMf[j] : 0.5 * (kTM[j] + kTM[j + 1]);
         } else {
             kMf[j] = 2.0 * kM[j] * kM[j + 1] / (kM[j] + kM[j + 1]);
             kTTf[j] = 2.0 * kTT[j] * kTT[j + 1] / (kTT[j] + kTT[j + 1]);
+            kTMf[j] = affine ? v->nu * p->Lv * kMf[j] : 2.0 * kTM[j] * kTM[j + 1] / (kTM[j] + kTM[j + 1]);
         }
-        kTMf[j] = v->nu * p->Lv * kMf[j];
     }
 }
 
-void orc_coefficients(const orc_problem *p, int32_t w, const double *P, double *node6, double *face3)
+void orc_coefficients(const orc_problem *p, int32_t w, const double *T, const double *P, double *node6,
+                      double *face3)
 {
     int64_t *off = (int64_t *)calloc((size_t)p->n_walls + 1, sizeof(int64_t));
     for (int32_t i = 0; i < p->n_walls; ++i) off[i + 1] = off[i] + p->n_layers[i];
     wall_view v = view_of(p, off, w);
     int32_t N = v.N;
     double *buf = (double *)malloc(sizeof(double) * (size_t)(9 * N));
-    coefficients(p, &v, P, buf, buf + N, buf + 2 * N, buf + 3 * N, buf + 4 * N, buf + 5 * N,
+    coefficients(p, &v, T != NULL ? T : P, P, buf, buf + N, buf + 2 * N, buf + 3 * N, buf + 4 * N, buf + 5 * N,
                  buf + 6 * N, buf + 7 * N, buf + 8 * N);
     for (int32_t j = 0; j < N; ++j)
         for (int k = 0; k < 6; ++k) node6[j * 6 + k] = buf[k * N + j];
@@ -177,7 +239,7 @@ static void wall_step(const orc_problem *p, const wall_view *v, const face_bc bc
 {
     const int32_t N = v->N;
     const double dx = v->dx, dt = p->dt, Lv = p->Lv;
-    coefficients(p, v, Pc, sc->kM, sc->cM, sc->kTT, sc->cTT, sc->kTM, sc->cTM, sc->kMf, sc->kTTf,
+    coefficients(p, v, Tc, Pc, sc->kM, sc->cM, sc->kTT, sc->cTT, sc->kTM, sc->cTM, sc->kMf, sc->kTTf,
                  sc->kTMf);
 
     /* vapour pressure first */
@@ -391,7 +453,7 @@ int orc_euler_start(const orc_problem *p, orc_state *s, double refine, int32_t n
             P[j] = s->P_cur[o + j];
         }
         /* the stability bound at level 0 */
-        coefficients(p, &v, P, sc.kM, sc.cM, sc.kTT, sc.cTT, sc.kTM, sc.cTM, sc.kMf, sc.kTTf, sc.kTMf);
+        coefficients(p, &v, T, P, sc.kM, sc.cM, sc.kTT, sc.cTT, sc.kTM, sc.cTM, sc.kMf, sc.kTTf, sc.kTMf);
         face_bc b0[2] = {face_of(p, w, 0, p->t0, NULL), face_of(p, w, 1, p->t0, NULL)};
         double tmax = dt;
         for (int32_t j = 0; j < N; ++j) {
@@ -422,7 +484,7 @@ int orc_euler_start(const orc_problem *p, orc_state *s, double refine, int32_t n
         for (int64_t i = 0; i < m; ++i) {
             const double t = p->t0 + (double)i * tau;
             face_bc bc[2] = {face_of(p, w, 0, t, NULL), face_of(p, w, 1, t, NULL)};
-            coefficients(p, &v, P, sc.kM, sc.cM, sc.kTT, sc.cTT, sc.kTM, sc.cTM, sc.kMf, sc.kTTf, sc.kTMf);
+            coefficients(p, &v, T, P, sc.kM, sc.cM, sc.kTT, sc.cTT, sc.kTM, sc.cTM, sc.kMf, sc.kTTf, sc.kTMf);
             /* surface fluxes with the values at the substep's start */
             for (int f = 0; f < 2; ++f) {
                 const int32_t j = f == 0 ? 0 : N - 1;

@@ -54,6 +54,25 @@ extern "C" {
 
 enum { ORC_BC_AMBIENT = 0, ORC_BC_ADIABATIC = 1, ORC_BC_ROOM = 2 };
 
+/* Coefficient law of a layer. ORC_LAW_AFFINE: the affine laws above (layer_par). The others: the load
+ * bearing material of Sec. 4 (Table 1), whose coefficients depend on T and Pv, layer_par unused:
+ *   Ps(T) = 610.94 exp(17.625 theta / (theta + 243.04)) Pa, theta = T - 273.15 (the paper gives no
+ *           saturation pressure; this is the Magnus form of Alduchov & Eskridge, 1996);
+ *   Pc = rho_l Rv T ln(Pv / Ps) (Kelvin relation, Sec. 2), rho_l = 1000 kg/m3, Rv = 461.5 J/(kg K),
+ *        held at 0 (saturation) for Pv > Ps, where the isotherm has no values;
+ *   f = 47.1 [1 + (-c1 Pc)^1.65]^-0.39 + 109.9 [1 + (-c2 Pc)^6]^-0.83 kg/m3, c1 = 1.25e-5, c2 = 1.8e-5;
+ *   cM = df/dPv (through the Kelvin relation with ln), dv = 1.88e-6 / T (1 - f/157) / (0.503 (1 -
+ *   f/157)^2 + 0.497), kTT = 0.2 + 0.0045 f, cTT = rho0 c0 + f cw (rho0 = 790, c0 = 870, cw = 4180),
+ *   kTM = Lv dv, cTM = cw theta cM (theta in degrees Celsius);
+ *   kM = 1.97e-10 exp(-0.07 log10(x) + 1.44) + 1.77e-7 L(x), x = 2 Pv / Ps, with the liquid term L read
+ *   from Table 1's garbled bracket as (exp(-8 x - 2))^2 (ORC_LAW_TABLE1), exp((-8 x - 2)^2)
+ *   (ORC_LAW_TABLE1_A) or exp(-8 (x - 2)^2) (ORC_LAW_TABLE1_C). */
+enum { ORC_LAW_AFFINE = 0, ORC_LAW_TABLE1 = 1, ORC_LAW_TABLE1_A = 2, ORC_LAW_TABLE1_C = 3 };
+
+/* The six coefficients (kM, cM, kTT, cTT, kTM, cTM) of a Table-1 law at (T [K], Pv [Pa]), out[6];
+ * also the saturation pressure and the sorption isotherm f (kg/m3) through ps / fw when not NULL. */
+void orc_table1(int32_t law, double T, double Pv, double Lv, double *out, double *ps, double *fw);
+
 typedef struct {
     int32_t n_walls;
     const int32_t *n_nodes;      /* [n_walls], each >= 3 */
@@ -71,6 +90,7 @@ typedef struct {
     const double *room_par;      /* [n_rooms][ORC_NROOM_PAR] */
     const double *wall_area;     /* [n_walls], m^2, used by room faces */
     const double *vapour_frac;   /* [n_walls] nu of kTM = nu Lv kM inside the wall, or NULL (all 1) */
+    const int32_t *layer_law;    /* [sum n_layers] ORC_LAW_* of each layer, or NULL (all affine) */
 } orc_problem;
 
 typedef struct {
@@ -101,10 +121,11 @@ int orc_euler_start(const orc_problem *p, orc_state *s, double refine, int32_t n
 /* Ambient air state (T_inf, Pv_inf) seen by an ambient face at time t. */
 void orc_ambient(const orc_problem *p, int32_t wall, int32_t face, double t, double *T_inf, double *P_inf);
 
-/* Per-node coefficients (kM, cM, kTT, cTT, kTM, cTM) of wall w at vapour pressures P[0..N-1],
- * and face values (kM_f, kTT_f, kTM_f) for the N-1 interior faces. */
-void orc_coefficients(const orc_problem *p, int32_t wall, const double *P, double *node6 /* [N][6] */,
-                      double *face3 /* [N-1][3] */);
+/* Per-node coefficients (kM, cM, kTT, cTT, kTM, cTM) of wall w at temperatures T[0..N-1] (used by the
+ * Table-1 laws only; may be NULL for affine walls) and vapour pressures P[0..N-1], and face values
+ * (kM_f, kTT_f, kTM_f) for the N-1 interior faces. */
+void orc_coefficients(const orc_problem *p, int32_t wall, const double *T, const double *P,
+                      double *node6 /* [N][6] */, double *face3 /* [N-1][3] */);
 
 /* 2D wall sections (hygro_oracle2d.c): G grids of nx x ny nodes, spacing h in x and y. */
 typedef struct {

@@ -102,6 +102,7 @@ class Workload:
     Psat: float = PSAT_REF
     rooms: dict | None = None    # room description (whole-building workloads)
     vapour_frac: np.ndarray | None = None   # float64 [n_walls]: kTM = nu Lv kM inside the wall (None: 1)
+    layer_law: np.ndarray | None = None     # int32 [sum n_layers]: coefficient law of each layer (None: affine)
 
     @property
     def n_walls(self) -> int:
@@ -130,7 +131,8 @@ class Workload:
             P_init=self.P_init[walls].copy(), bc_kind=self.bc_kind[walls].copy(),
             bc_par=self.bc_par[walls].copy(), bc_room=self.bc_room[walls].copy(),
             noise=noise, rooms=None,
-            vapour_frac=None if self.vapour_frac is None else self.vapour_frac[walls].copy())
+            vapour_frac=None if self.vapour_frac is None else self.vapour_frac[walls].copy(),
+            layer_law=None if self.layer_law is None else self.layer_law[rows].copy())
 
 
 def _bc_row(hT, hM, T_mean, T_amp, P_mean, P_amp, period=86400.0, phase_T=0.0,
@@ -199,7 +201,9 @@ def concat(workloads: list[Workload], name="batch") -> Workload:
         bc_room=np.concatenate([w.bc_room for w in workloads]),
         noise=noise, rooms=None,
         vapour_frac=None if all(w.vapour_frac is None for w in workloads) else np.concatenate(
-            [np.ones(w.n_walls) if w.vapour_frac is None else w.vapour_frac for w in workloads]))
+            [np.ones(w.n_walls) if w.vapour_frac is None else w.vapour_frac for w in workloads]),
+        layer_law=None if all(w.layer_law is None for w in workloads) else np.concatenate(
+            [np.zeros(len(w.layer_par), np.int32) if w.layer_law is None else w.layer_law for w in workloads]))
 
 
 def single_wall(seed: int = 1) -> Workload:
@@ -552,3 +556,37 @@ def one_zone(N: int = 101, dt: float = 3.6, hours: float = 80.0) -> Workload:
     return dataclasses.replace(wl, bc_room=bc_room, vapour_frac=np.array(nu),
                                rooms=dict(par=par, wall_area=np.array(areas), Ta0=np.array([Ti]),
                                           Pa0=np.array([Pvi])))
+
+
+# Coefficient laws of a layer (hygro_set_layer_law): the affine laws of the layer parameters, or the load
+# bearing material of Sec. 4 (Table 1) with one of three readings of its liquid-transport bracket.
+LAW_AFFINE, LAW_TABLE1, LAW_TABLE1_A, LAW_TABLE1_C = 0, 1, 2, 3
+
+
+def table1_walls(seed: int = 6, n_walls: int = 256, N: int = 101, L: float = 0.1, dt: float = 3.6,
+                 hours: float = 120.0, law: int = LAW_TABLE1) -> Workload:
+    """Walls of the load bearing material of Sec. 4 (Table 1): 10 cm slabs, N = 101 (dx = 1 mm), dt = 3.6 s
+    (the paper's dx* = 1e-2, dt* = 1e-3 with a reference time of 1 h), 120 h.
+
+    * one layer of the Table-1 law ``law`` per wall (its affine parameters are placeholders, unused);
+    * initial state 20 C and 1166.7 Pa (50 % relative humidity with the library's saturation pressure);
+    * face 0: hT = 25 W/m2/K, hM = 2e-7 s/m; face 1: hT = 8, hM = 3e-8 (Sec. 4);
+    * the paper's boundary series exist only as figures, which are missing: each face instead sees a daily
+      sinusoid with seeded phases, T = 293.15 + a_T sin(.), a_T ~ U[4, 8] K (face 1: U[1, 2]), and
+      Pv = 1166.7 (1 + a_P sin(.)), a_P ~ U[0.05, 0.15] (face 1: U[0.02, 0.05]), which keeps the air below
+      saturation.
+    """
+    Ti, Pvi = 293.15, 1166.7
+    n_steps = int(round(hours * 3600.0 / dt))
+    key = stream_key(seed, np.arange(n_walls))
+    u = uniform(key[:, None], np.arange(8)[None, :])
+    walls = []
+    placeholder = dict(kM0=8.3e-10, cM0=4.0e-4, kTT0=0.2, cTT0=6.9e5)
+    for w in range(n_walls):
+        bc0 = dict(hT=25.0, hM=2e-7, T_mean=Ti, T_amp=4.0 + 4.0 * u[w, 0], P_mean=Pvi,
+                   P_amp=Pvi * (0.05 + 0.10 * u[w, 1]), phase_T=2 * math.pi * u[w, 2], phase_P=2 * math.pi * u[w, 3])
+        bc1 = dict(hT=8.0, hM=3e-8, T_mean=Ti, T_amp=1.0 + u[w, 4], P_mean=Pvi,
+                   P_amp=Pvi * (0.02 + 0.03 * u[w, 5]), phase_T=2 * math.pi * u[w, 6], phase_P=2 * math.pi * u[w, 7])
+        walls.append(uniform_wall(N, L, placeholder, T0=Ti, P0=Pvi, bc0=bc0, bc1=bc1, dt=dt, n_steps=n_steps))
+    wl = concat(walls, name=f"Table-1 material: {n_walls} walls N={N}, dt={dt:g} s x {n_steps}")
+    return dataclasses.replace(wl, layer_law=np.full(n_walls, law, np.int32))
