@@ -391,6 +391,90 @@ def bench_sections(args, H, wk, stream, local, rank, peaks=None):
     return out
 
 
+def bench_table1(args, H, wk, stream, local, rank):
+    """256 walls of the Table-1 material (Sec. 4: 10 cm, N = 101, dt = 3.6 s), 2 h of it (2000 steps) on
+    the plain kernel in FP32 and FP64; parity of two walls' surface samples and final fields against the
+    oracle over the same 2 h."""
+    import torch
+
+    wl = wk.table1_walls(seed=6 + rank, n_walls=256, hours=2.0)
+    n = wl.n_steps
+    out = {"workload": f"{wl.n_walls} walls of the Table-1 material, N=101, dt=3.6 s x {n} steps, plain kernel",
+           "unit": UNIT}
+    res = {}
+    for prec in ("fp32", "fp64"):
+        h = H.Hygro(wl, precision=prec, kernel="plain", device=local, stream=stream.cuda_stream)
+        s0 = h.get_state()
+        with torch.cuda.stream(stream):
+            h.run(200)
+        torch.cuda.synchronize()
+        h.set_state(s0)
+        with torch.cuda.stream(stream):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.run(n)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        T, P = h.fields(0)
+        h.close()
+        res[prec] = (T, P)
+        out[f"value_{prec}"] = wl.total_nodes * n / (ms / 1e3)
+        out[f"ms_per_run_{prec}"] = ms
+    out["value"] = out["value_fp32"]
+    out["note"] = ("one launch per step (launch-bound at 25 856 nodes per launch); each node evaluates the "
+                   "Table-1 laws (isotherm, its derivative, permeabilities, saturation pressure) for itself and "
+                   "its two neighbours")
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+
+        pick = [0, wl.n_walls - 1]
+        sub = wl.subset(pick)
+        o = oracle.Oracle(sub)
+        o.run(n)
+        off = np.concatenate([[0], np.cumsum(wl.n_nodes)])
+        par = {}
+        for prec, (T, P) in res.items():
+            Tg = np.concatenate([T[off[w]:off[w + 1]] for w in pick])
+            Pg = np.concatenate([P[off[w]:off[w + 1]] for w in pick])
+            par[prec] = {"rel_linf_T": relinf(Tg, o.T_cur), "rel_linf_P": relinf(Pg, o.P_cur)}
+        out["parity_vs_oracle"] = par
+    return out
+
+
+def bench_cpu_schemes(wk):
+    """The paper's CPU time comparison (Table tab:CPU_time) on this host's cores: DF (the oracle), Euler
+    implicit with the fixed-point sub-iterations of Alg. 1 (tolerance 0.01 dt*, dt* = dt / 1 h, Euclidean
+    norm) and Euler explicit within its stability bound, on the one-zone case (Sec. 5.2, 8 h of the 80 h) and
+    one Table-1 wall (Sec. 4, 2 h). The paper (Matlab, Intel i7): one zone DF 8.5 s vs implicit 95 s (9 %);
+    Table-1 wall DF 150 s, explicit 164 s, implicit 530 s (28 %, 31 %)."""
+    import oracle
+
+    out = {}
+    for name, wl, n in (("one_zone_8h", wk.one_zone(), 8000), ("table1_wall_2h", wk.table1_walls(n_walls=1, hours=2.0), 2000)):
+        eta = 0.01 * wl.dt / 3600.0
+        rec = {}
+        for scheme in ("df", "implicit", "explicit"):
+            o = oracle.Oracle(wl)
+            t = time.perf_counter()
+            if scheme == "df":
+                o.run(n)
+            elif scheme == "implicit":
+                rec["implicit_subiterations_per_step"] = o.run_implicit(n, eta=eta, norm="l2") / n
+            else:
+                rec["explicit_substeps_per_step"] = o.run_explicit(n, 1.0) / n
+            rec[f"{scheme}_seconds"] = time.perf_counter() - t
+        rec["df_over_implicit"] = rec["df_seconds"] / rec["implicit_seconds"]
+        rec["explicit_over_implicit"] = rec["explicit_seconds"] / rec["implicit_seconds"]
+        rec["steps"] = n
+        out[name] = rec
+    out["cores"] = oracle.default_threads()
+    out["paper"] = {"one_zone_df_over_implicit": 8.5 / 95.0, "table1_df_over_implicit": 150.0 / 530.0,
+                    "table1_explicit_over_implicit": 164.0 / 530.0, "hardware": "Matlab on an Intel i7 (paper)"}
+    return out
+
+
 def bench_adjoint(args, H, wk, stream, local, rank, peaks=None):
     """Gradient workload: misfit loss and its gradient over 30 days of 1024 two-layer walls (FP32 adjoint,
     sqrt(T) checkpoints), observations resident on the device; parity on sampled walls vs the oracle."""
@@ -698,6 +782,15 @@ def bench_ours(args):
                        for i, f in enumerate(("rel_linf_T", "rel_linf_P"))} for prec in ("fp32", "fp64")}
             out5["oracle_seconds"] = el5
         other["one_zone_80h"] = out5
+
+    # the Table-1 material of Sec. 4 (nonlinear coefficients of T and Pv) on the plain kernel: throughput and
+    # parity of a sampled wall against the oracle
+    if not args.no_fp64:
+        other["table1_material_256walls"] = bench_table1(args, H, wk, stream, local, rank)
+
+    # the paper's comparison schemes on the host cores (CPU time ratios of Sec. 4 and Sec. 5.2)
+    if rank == 0 and not args.no_cpu_baseline:
+        other["cpu_schemes"] = bench_cpu_schemes(wk)
 
     # gradient workload (1024 walls x 30 days, reverse-time adjoint)
     if not args.no_adjoint:

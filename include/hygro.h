@@ -211,6 +211,28 @@ HYGRO_API hygro_status hygro_set_option(hygro_ctx *ctx, int32_t option, int64_t 
  * time and applies from the next step. The adjoint (hygro_loss_grad) supports nu = 1 only. */
 HYGRO_API hygro_status hygro_set_vapour_fraction(hygro_ctx *ctx, const double *nu);
 
+/* Coefficient law of each layer (paper Sec. 4, Table 1: the load bearing material whose coefficients
+ * depend on T and Pv). law[l] for every layer l of hygro_set_materials' order (host memory, copied):
+ *   HYGRO_LAW_AFFINE    the affine laws of the layer's hygro_layer parameters (the default);
+ *   HYGRO_LAW_TABLE1    Table 1: the sorption isotherm f through the Kelvin relation (natural logarithm),
+ *                       cM = df/dPv, lambda, the vapour permeability dv, kTM = Lv dv, cTT = rho0 c0 + cw f,
+ *                       cTM = cw (T - 273.15) cM, the saturation pressure of the Magnus form (Alduchov &
+ *                       Eskridge 1996; the paper gives none), the capillary pressure held at 0 above
+ *                       saturation; kM's liquid term read as (exp(-8x-2))^2, x = 2 Pv / Ps;
+ *   HYGRO_LAW_TABLE1_A  the same with the liquid term read as exp((-8x-2)^2) (overflows in FP32);
+ *   HYGRO_LAW_TABLE1_C  the same with the liquid term read as exp(-8 (x-2)^2).
+ * The coefficients of a Table-1 layer come from each node's absolute T and Pv of level n (explicit, as
+ * Sec. 3.1 prescribes); faces take the arithmetic mean inside a layer and the harmonic mean across layers,
+ * kTM included. The hygro_layer parameters of a Table-1 layer are not used. hygro_set_materials resets
+ * every layer to HYGRO_LAW_AFFINE. Walls with a Table-1 layer run on the plain kernel only: hygro_run of a
+ * context of the persistent kernel, a wall facing a room and hygro_loss_grad refuse them with
+ * HYGRO_E_UNSUPPORTED. HYGRO_E_INVALID for an unknown law; HYGRO_E_STATE before hygro_set_materials. */
+#define HYGRO_LAW_AFFINE 0
+#define HYGRO_LAW_TABLE1 1
+#define HYGRO_LAW_TABLE1_A 2
+#define HYGRO_LAW_TABLE1_C 3
+HYGRO_API hygro_status hygro_set_layer_law(hygro_ctx *ctx, const int32_t *law);
+
 /* Room air state of level 0 (n) or 1 (n-1): Ta[n_rooms], Pa[n_rooms] (host or device memory). */
 HYGRO_API hygro_status hygro_get_rooms(hygro_ctx *ctx, int32_t level, double *Ta, double *Pa);
 

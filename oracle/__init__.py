@@ -25,7 +25,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "hygro_oracle.c")
 _SRC2 = os.path.join(_HERE, "hygro_oracle2d.c")
 _SRC3 = os.path.join(_HERE, "hygro_adjoint.c")
+_SRC4 = os.path.join(_HERE, "hygro_comparators.c")
 _HDR = os.path.join(_HERE, "hygro_oracle.h")
+_HDR2 = os.path.join(_HERE, "oracle_internal.h")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 
@@ -37,13 +39,13 @@ NROOM_PAR = 21
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (OpenMP if available); return the .so path."""
     os.makedirs(_BUILD, exist_ok=True)
-    newest = max(os.path.getmtime(f) for f in (_SRC, _SRC2, _SRC3, _HDR))
+    newest = max(os.path.getmtime(f) for f in (_SRC, _SRC2, _SRC3, _SRC4, _HDR, _HDR2))
     if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= newest:
         return _LIB
     cc = shutil.which("gcc") or shutil.which("cc")
     if cc is None:
         raise RuntimeError("no C compiler found to build the oracle")
-    base = [cc, "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", _LIB + ".tmp", _SRC, _SRC2, _SRC3, "-lm"]
+    base = [cc, "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", _LIB + ".tmp", _SRC, _SRC2, _SRC3, _SRC4, "-lm"]
     try:
         subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
     except subprocess.CalledProcessError:
@@ -119,6 +121,13 @@ def _load():
         lib.orc_coefficients.restype = None
         lib.orc_coefficients.argtypes = [C.POINTER(_Problem), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                          C.c_void_p]
+        for name in ("orc_euler_implicit_run", "orc_euler_explicit_run"):
+            f = getattr(lib, name)
+            f.restype = C.c_int
+        lib.orc_euler_implicit_run.argtypes = [C.POINTER(_Problem), C.POINTER(_State), C.c_int64, C.c_double,
+                                               C.c_int32, C.c_int32, C.POINTER(C.c_int64), C.c_int32]
+        lib.orc_euler_explicit_run.argtypes = [C.POINTER(_Problem), C.POINTER(_State), C.c_int64, C.c_double,
+                                               C.POINTER(C.c_int64), C.c_int32]
         lib.orc_table1.restype = None
         lib.orc_table1.argtypes = [C.c_int32, C.c_double, C.c_double, C.c_double, C.c_void_p,
                                    C.POINTER(C.c_double), C.POINTER(C.c_double)]
@@ -236,6 +245,33 @@ class Oracle:
         self.step = int(st.step)
         return dict(samples=samples, room_samples=room_samples, flux=flux if n_steps > 0 else None,
                     balance=bal)
+
+    def _state(self):
+        return _State(self.step, _ptr(self.T_prev), _ptr(self.T_cur), _ptr(self.P_prev), _ptr(self.P_cur),
+                      _ptr(self.cumul), _ptr(self.room))
+
+    def run_implicit(self, n_steps: int, eta: float, max_iter: int = 100, norm: str = "max") -> int:
+        """The paper's Euler implicit scheme with fixed-point sub-iterations (Alg. 1); returns the
+        sub-iterations done. norm: "max" (largest relative change) or "l2" (Euclidean norm of all)."""
+        st = self._state()
+        it = C.c_int64(0)
+        rc = _load().orc_euler_implicit_run(C.byref(self._p), C.byref(st), int(n_steps), float(eta), int(max_iter),
+                                            {"max": 0, "l2": 1}[norm], C.byref(it), int(self.n_threads))
+        if rc != 0:
+            raise RuntimeError(f"implicit Euler run failed with code {rc}")
+        self.step = int(st.step)
+        return it.value
+
+    def run_explicit(self, n_steps: int, refine: float = 1.0) -> int:
+        """The Euler explicit scheme within its stability bound; returns the substeps done."""
+        st = self._state()
+        ns = C.c_int64(0)
+        rc = _load().orc_euler_explicit_run(C.byref(self._p), C.byref(st), int(n_steps), float(refine),
+                                            C.byref(ns), int(self.n_threads))
+        if rc != 0:
+            raise RuntimeError(f"explicit Euler run failed with code {rc}")
+        self.step = int(st.step)
+        return ns.value
 
     def euler_start(self, refine: float = 1.0):
         """The first step by explicit Euler substeps (state at step 0): levels become (0, 1), step 1."""

@@ -4,6 +4,7 @@
  * for what each part follows. Scalar loops, no blocking, no reordering.
  */
 #include "hygro_oracle.h"
+#include "oracle_internal.h"
 
 #include <math.h>
 #include <stdlib.h>
@@ -12,12 +13,6 @@
 #include <omp.h>
 #endif
 
-enum { L_KM0, L_A, L_CM0, L_B, L_KTT0, L_AT, L_CTT0, L_BT, L_CHI };
-enum { B_HT, B_HM, B_QINF, B_GINF, B_TMEAN, B_TAMP, B_PMEAN, B_PAMP, B_PERIOD, B_PHT, B_PHP, B_NDT, B_PERIODP };
-enum { R_VOL, R_ACH, R_QGAIN, R_GVAP, R_TMEAN, R_TAMP, R_PMEAN, R_PAMP, R_PERIOD, R_PHT, R_PHP,
-       R_RHOA, R_CPA, R_CPV, R_PVREF, R_SCHEME, R_PERIODP, R_GPULSE, R_PON, R_POFF, R_PPER };
-
-static const double TWO_PI = 6.283185307179586476925286766559;
 
 /* Linear interpolation of an evenly spaced (T, Pv) noise table at time t,
  * held constant beyond its ends. */
@@ -51,17 +46,8 @@ void orc_ambient(const orc_problem *p, int32_t w, int32_t face, double t, double
     *P_inf = P;
 }
 
-typedef struct {
-    int32_t N;
-    double dx;
-    int32_t nl;
-    const int32_t *first;
-    const double *par;
-    const int32_t *law;    /* coefficient law of each layer (NULL: all affine) */
-    double nu;             /* kTM = nu Lv kM */
-} wall_view;
 
-static wall_view view_of(const orc_problem *p, const int64_t *layer_off, int32_t w)
+wall_view view_of(const orc_problem *p, const int64_t *layer_off, int32_t w)
 {
     wall_view v;
     v.N = p->n_nodes[w];
@@ -129,7 +115,7 @@ void orc_table1(int32_t law, double T, double Pv, double Lv, double *out, double
  * harmonic mean across an interface between two layers. Affine layers:
  * kTM_f = nu Lv kM_f. Layers of a Table-1 law: their kTM = Lv dv takes the
  * face rule of the other conductances. */
-static void coefficients(const orc_problem *p, const wall_view *v, const double *T, const double *P,
+void coefficients(const orc_problem *p, const wall_view *v, const double *T, const double *P,
                          double *kM, double *cM, double *kTT, double *cTT, double *kTM, double *cTM,
                          double *kMf, double *kTTf, double *kTMf)
 {
@@ -189,13 +175,8 @@ void orc_coefficients(const orc_problem *p, int32_t w, const double *T, const do
     free(off);
 }
 
-/* Surface exchange data of one face for this step: the air state and the
- * coefficients of [eq:HAM_BC]. An adiabatic face exchanges nothing. */
-typedef struct {
-    double hT, hM, q_inf, g_inf, T_inf, P_inf;
-} face_bc;
 
-static face_bc face_of(const orc_problem *p, int32_t w, int32_t f, double t, const double *room_state)
+face_bc face_of(const orc_problem *p, int32_t w, int32_t f, double t, const double *room_state)
 {
     face_bc s;
     memset(&s, 0, sizeof s);
@@ -342,6 +323,25 @@ static void wall_step(const orc_problem *p, const wall_view *v, const face_bc bc
     }
 }
 
+/* Outdoor air of a room's ventilation and the occupants' vapour production (Sec. 5.1: base load plus
+ * the daily pulse) at time t. */
+void room_sources(const orc_problem *p, int32_t r, double t, double *T_out, double *P_out, double *g_vap)
+{
+    const double *q = p->room_par + (size_t)r * ORC_NROOM_PAR;
+    double T = q[R_TMEAN], P = q[R_PMEAN];
+    const double period_P = q[R_PERIODP] > 0.0 ? q[R_PERIODP] : q[R_PERIOD];
+    if (q[R_PERIOD] > 0.0) T += q[R_TAMP] * sin(TWO_PI * t / q[R_PERIOD] + q[R_PHT]);
+    if (period_P > 0.0) P += q[R_PAMP] * sin(TWO_PI * t / period_P + q[R_PHP]);
+    double g = q[R_GVAP];
+    if (q[R_PPER] > 0.0) {
+        const double ph = fmod(t, q[R_PPER]);
+        if (ph >= q[R_PON] && ph < q[R_POFF]) g += q[R_GPULSE];
+    }
+    *T_out = T;
+    *P_out = P;
+    *g_vap = g;
+}
+
 /* Room air node of Sec. 5.1 ([eq:LAV_equation] with the sources of the
  * occupants and of ventilation, the wall exchanges [eq:LAV_couplage]),
  * humidity ratio w = Pva / Pv_ref. The wall surface values enter at level n
@@ -356,16 +356,8 @@ static void room_step(const orc_problem *p, int32_t r, double t, double *rs,
     double Ta_p = rs[0], Ta_c = rs[1], Pa_p = rs[2], Pa_c = rs[3];
     double rhoV = q[R_RHOA] * q[R_VOL];
     double gv = rhoV * q[R_ACH] / 3600.0;                        /* kg/s of exchanged air */
-    double T_out = q[R_TMEAN], P_out = q[R_PMEAN];
-    const double period_P = q[R_PERIODP] > 0.0 ? q[R_PERIODP] : q[R_PERIOD];
-    if (q[R_PERIOD] > 0.0) T_out += q[R_TAMP] * sin(TWO_PI * t / q[R_PERIOD] + q[R_PHT]);
-    if (period_P > 0.0) P_out += q[R_PAMP] * sin(TWO_PI * t / period_P + q[R_PHP]);
-    /* vapour production of the occupants (Sec. 5.1): base load plus the daily pulse */
-    double g_vap = q[R_GVAP];
-    if (q[R_PPER] > 0.0) {
-        const double ph = fmod(t, q[R_PPER]);
-        if (ph >= q[R_PON] && ph < q[R_POFF]) g_vap += q[R_GPULSE];
-    }
+    double T_out, P_out, g_vap;
+    room_sources(p, r, t, &T_out, &P_out, &g_vap);
     double Pref = q[R_PVREF];
     double w_out = P_out / Pref;
     if (q[R_SCHEME] == 1.0) {

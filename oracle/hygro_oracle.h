@@ -118,6 +118,24 @@ int orc_run(const orc_problem *p, orc_state *s, int64_t n_steps, int32_t sample_
  * tau_max the explicit stability bound at level 0. Afterwards the step is 1. 0 on success. */
 int orc_euler_start(const orc_problem *p, orc_state *s, double refine, int32_t n_threads);
 
+/* The paper's comparison schemes (hygro_comparators.c; Sec. 4, Sec. 5.2), on the DF oracle's spatial
+ * operator. Both advance n_steps steps of dt from the state's level n; afterwards T_prev / P_prev hold the
+ * level before the last and T_cur / P_cur the last, the room air likewise, and the flux sums grow.
+ *
+ * Euler implicit with the fixed-point sub-iterations of Alg. 1: each step iterates walls (backward Euler,
+ * coefficients at the iterate, room air of the iterate) and rooms (backward Euler with the walls' new surface
+ * values) until the largest relative change of any value is below eta; *iterations (if not NULL) grows by the
+ * sub-iterations done. The change is the largest relative change of any value (norm 0) or the Euclidean
+ * norm of the relative changes of all values (norm 1; the paper does not name its norm). Returns 0, -1
+ * (invalid), -2 (allocation), -3 (a step did not converge in max_iter).
+ *
+ * Euler explicit: each step in m substeps, m = ceil(refine dt / tau) with tau the explicit stability bound of
+ * every node and room at the step's start; *substeps (if not NULL) grows by the substeps done. */
+int orc_euler_implicit_run(const orc_problem *p, orc_state *s, int64_t n_steps, double eta, int32_t max_iter,
+                           int32_t norm, int64_t *iterations, int32_t n_threads);
+int orc_euler_explicit_run(const orc_problem *p, orc_state *s, int64_t n_steps, double refine, int64_t *substeps,
+                           int32_t n_threads);
+
 /* Ambient air state (T_inf, Pv_inf) seen by an ambient face at time t. */
 void orc_ambient(const orc_problem *p, int32_t wall, int32_t face, double t, double *T_inf, double *P_inf);
 

@@ -3,8 +3,91 @@
 // level n, face means, Pv then T, half-cell Robin surfaces; paper Sec. 3.1
 // [eq:DF_NL] and Appendix A), in its most direct GPU form.
 #include "df1d_common.cuh"
+#include "material_table1.cuh"
 
 namespace hygro {
+
+// Coefficients of one node of a wall with Table-1 layers: half-values kh = k / (2 dx) of kM, kTT and kTM,
+// and the storage terms dx c / (2 dt) of cM, cTT and cTM (before the surface half weight). Affine layers
+// give the values of their affine laws (kTM = nu Lv kM).
+template <typename real>
+struct NodeCoef {
+    real khM, khT, khX, A, B, C;
+    bool law;
+};
+
+template <typename real>
+__device__ __forceinline__ NodeCoef<real> node_coef(const DevCtx<real> &d, const WallInfo &wi, int w, const real *tab,
+                                                    int l, real Tdev, real Pdev)
+{
+    NodeCoef<real> k;
+    const int law = d.layer_law[wi.layer_off + l];
+    k.law = law != HYGRO_LAW_AFFINE;
+    if (!k.law) {
+        const LayerC<real> c = load_layer(tab, l);
+        k.khM = fma(c.kMb, Pdev, c.kMa);
+        k.khT = fma(c.kTb, Pdev, c.kTa);
+        k.khX = (real)(d.Lv * wi.nu) * k.khM;
+        k.A = fma(c.Ab, Pdev, c.Aa);
+        k.B = fma(c.Bb, Pdev, c.Ba);
+        k.C = c.chi * k.A;
+        return k;
+    }
+    const LawCoef<real> m = table1_law<real>(law, d.Tref[w] + Tdev, d.Pref[w] + Pdev, (real)d.Lv);
+    const real inv2dx = (real)(0.5 / wi.dx), s = (real)(wi.dx / (2.0 * d.dt));
+    k.khM = m.kM * inv2dx;
+    k.khT = m.kTT * inv2dx;
+    k.khX = m.kTM * inv2dx;
+    k.A = m.cM * s;
+    k.B = m.cTT * s;
+    k.C = m.cTM * s;
+    return k;
+}
+
+// One node of a wall with Table-1 layers: the balance of [eq:DF_NL] with every coefficient of level n from
+// node_coef; faces arithmetic inside a layer and harmonic across layers (the kTM face of two affine layers
+// is nu Lv times their kM face, as in the affine walls).
+template <typename real>
+__device__ __forceinline__ void law_node(const DevCtx<real> &d, const WallInfo &wi, int w, int g, int j, int l,
+                                         const real *tab, const real *Tc, const real *Pc, real &pp, real &tp,
+                                         real hM, real hT, real qi, real gi, real fT, real fP, real &dP, real &dT)
+{
+    const real half = real(0.5);
+    const int N = wi.N;
+    const NodeCoef<real> k = node_coef(d, wi, w, tab, l, Tc[g], Pc[g]);
+    real FMl = 0, FTl = 0, FXl = 0, FMr = 0, FTr = 0, FXr = 0, Tl = 0, Pl = 0, Tr = 0, Pr = 0;
+    auto face = [&](const NodeCoef<real> &o, bool same, real &FM, real &FT, real &FX) {
+        FM = same ? k.khM + o.khM : face_harmonic(k.khM, o.khM);
+        FT = same ? k.khT + o.khT : face_harmonic(k.khT, o.khT);
+        if (!k.law && !o.law)
+            FX = (real)(d.Lv * wi.nu) * FM;
+        else
+            FX = same ? k.khX + o.khX : face_harmonic(k.khX, o.khX);
+    };
+    if (j > 0) {
+        const int ll = d.node_layer[g - 1];
+        Tl = Tc[g - 1];
+        Pl = Pc[g - 1];
+        face(node_coef(d, wi, w, tab, ll, Tl, Pl), ll == l, FMl, FTl, FXl);
+    }
+    if (j < N - 1) {
+        const int lr = d.node_layer[g + 1];
+        Tr = Tc[g + 1];
+        Pr = Pc[g + 1];
+        face(node_coef(d, wi, w, tab, lr, Tr, Pr), lr == l, FMr, FTr, FXr);
+    }
+    const real wgt = (j == 0 || j == N - 1) ? half : real(1);
+    const real A = k.A * wgt, B = k.B * wgt, C = k.C * wgt;
+    const real numP = fma(hM, fP - pp, fma(FMl, Pl - pp, FMr * (Pr - pp)) + gi);
+    dP = fast_div(numP, fma(half, FMl + FMr + hM, A));
+    const real Pbar = fma(half, dP, pp);
+    const real Lv = (real)d.Lv;
+    real numT = fma(FTl, Tl - tp, FTr * (Tr - tp));
+    numT = fma(FXl, Pl - Pbar, fma(FXr, Pr - Pbar, numT));
+    numT = fma(-C, dP, numT);
+    numT = fma(hT, fT - tp, fma(Lv, hM * (fP - Pbar), numT + qi));
+    dT = fast_div(numT, fma(half, FTl + FTr + hT, B));
+}
 
 template <typename real>
 __global__ void __launch_bounds__(256)
@@ -24,6 +107,45 @@ __global__ void __launch_bounds__(256)
     const int l = d.node_layer[g];
     const LayerC<real> c = load_layer(tab, l);
     const real half = real(0.5);
+    if (wi.has_law) {
+        const int face = j == 0 ? 0 : (j == N - 1 ? 1 : -1);
+        real hM = 0, hT = 0, qi = 0, gi = 0, fT = 0, fP = 0;
+        if (face >= 0) {
+            const FaceInfo &fi = d.faces[(size_t)w * 2 + face];
+            if (fi.kind == HYGRO_BC_AMBIENT) {
+                hM = (real)fi.hM;
+                hT = (real)fi.hT;
+                qi = (real)fi.q_inf;
+                gi = (real)fi.g_inf;
+                ambient_at(fi, d.noise, n, d.t0, d.dt, fT, fP);
+            }
+        }
+        real pp = Pn[g], tp = Tn[g], dP, dT;
+        law_node(d, wi, w, g, j, l, tab, Tc, Pc, pp, tp, hM, hT, qi, gi, fT, fP, dP, dT);
+        const real Pnew = pp + dP, Tnew = tp + dT;
+        Pn[g] = Pnew;
+        Tn[g] = Tnew;
+        if (!(isfinite(Pnew) && isfinite(Tnew))) atomicExch(d.nonfinite, 1);
+        if (face >= 0) {
+            const real Lv = (real)d.Lv;
+            const real Pbar = fma(half, dP, pp), Tbar = fma(half, dT, tp);
+            const real hm = hM * (fP - Pbar);
+            const real q = fma(hT, fT - Tbar, fma(Lv, hm, qi));
+            const real gflux = hm + gi;
+            double *cu = d.cumul + (size_t)w * 4 + face * 2;
+            double *fl = d.flast + (size_t)w * 4 + face * 2;
+            cu[0] += d.dt * (double)q;
+            cu[1] += d.dt * (double)gflux;
+            fl[0] = (double)q;
+            fl[1] = (double)gflux;
+            if (samples != nullptr && sample_idx >= 0) {
+                real *o = samples + ((size_t)sample_idx * d.W + w) * 4 + face * 2;
+                o[0] = d.Tref[w] + Tnew;
+                o[1] = d.Pref[w] + Pnew;
+            }
+        }
+        return;
+    }
 
     const real Pk = Pc[g];
     const real khM = fma(c.kMb, Pk, c.kMa), khT = fma(c.kTb, Pk, c.kTa);

@@ -248,6 +248,9 @@ struct hygro_ctx {
     std::string trace_path;
     int32_t *d_node_wall = nullptr;
     int8_t *d_node_layer = nullptr;
+    std::vector<int32_t> law;      // coefficient law of each layer (HYGRO_LAW_*)
+    bool any_law = false;          // some layer takes a Table-1 law
+    int8_t *d_layer_law = nullptr; // [sum layers]
     void *d_samples = nullptr;
     size_t samples_cap = 0;
 };
@@ -293,7 +296,7 @@ void free_all(hygro_ctx *c)
 {
     void *ptrs[] = {c->dT[0], c->dT[1], c->dP[0], c->dP[1], c->d_walls, c->d_faces, c->d_layer_tab,
                     c->d_layer_first, c->d_noise, c->d_Tref, c->d_Pref, c->d_cumul, c->d_flast,
-                    c->d_nonfinite, c->d_order, c->d_block_off, c->d_trace, c->d_rooms, c->d_room_state, c->d_node_wall, c->d_node_layer, c->d_samples};
+                    c->d_nonfinite, c->d_order, c->d_block_off, c->d_trace, c->d_rooms, c->d_room_state, c->d_node_wall, c->d_node_layer, c->d_samples, c->d_layer_law};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->d_stage) cudaFree(c->d_stage);
@@ -337,6 +340,7 @@ DevCtx<real> make_dev(const hygro_ctx *c)
     d.n_rooms = (int32_t)c->rooms.size();
     d.node_wall = c->d_node_wall;
     d.node_layer = c->d_node_layer;
+    d.layer_law = c->d_layer_law;
     d.total_nodes = (int32_t)c->total_nodes;
     d.dt = c->dt;
     d.t0 = c->t0;
@@ -620,9 +624,12 @@ hygro_status build_schedule(hygro_ctx *c)
     return HYGRO_OK;
 }
 
-// Checks that the rooms of a context can run (hygro_run, hygro_run_noalloc).
+// Checks that the rooms of a context can run (hygro_run, hygro_run_noalloc), and that walls with a Table-1
+// coefficient law run on the plain kernel (the only one that evaluates those laws).
 hygro_status rooms_ready(hygro_ctx *c)
 {
+    if (c->any_law && c->kernel != HYGRO_KERNEL_PLAIN)
+        return fail(c, HYGRO_E_UNSUPPORTED, "walls with a Table-1 coefficient law run on the plain kernel only");
     if (!c->room_issue.empty()) return fail(c, HYGRO_E_STATE, "%s", c->room_issue.c_str());
     if (c->any_room_walls && c->kernel != HYGRO_KERNEL_PERSISTENT)
         return fail(c, HYGRO_E_UNSUPPORTED, "rooms need the persistent kernel");
@@ -859,6 +866,8 @@ hygro_status hygro_set_materials(hygro_ctx *c, const int32_t *n_layers, const in
             if (y.aT != 0.0 || y.bT != 0.0 || y.chi != 0.0) wi.simple = 0;
         }
         const double dx = c->L[w] / (double)(c->N[w] - 1);
+        wi.dx = dx;
+        wi.has_law = 0;
         const double Ps = c->Psat, Pr = c->Pref[w], dt = c->dt;
         for (int l = 0; l < wi.n_layers; ++l) {
             const hygro_layer &y = layers[lo + l];
@@ -887,6 +896,13 @@ hygro_status hygro_set_materials(hygro_ctx *c, const int32_t *n_layers, const in
     hygro_status st = upload_reals(c, c->d_layer_tab, tab);
     if (st != HYGRO_OK) return st;
     CUDA_TRY(c, cudaMemcpy(c->d_layer_first, layer_first, total_layers * sizeof(int32_t), cudaMemcpyHostToDevice));
+    // every layer back to its affine laws
+    c->law.assign(total_layers, HYGRO_LAW_AFFINE);
+    c->any_law = false;
+    if (c->d_layer_law) cudaFree(c->d_layer_law);
+    c->d_layer_law = nullptr;
+    CUDA_TRY(c, cudaMalloc(&c->d_layer_law, std::max<size_t>(1, total_layers)));
+    CUDA_TRY(c, cudaMemset(c->d_layer_law, 0, std::max<size_t>(1, total_layers)));
     CUDA_TRY(c, cudaMemcpy(c->d_node_layer, node_layer.data(), node_layer.size(), cudaMemcpyHostToDevice));
     CUDA_TRY(c, cudaMemcpy(c->d_walls, c->walls.data(), c->walls.size() * sizeof(WallInfo), cudaMemcpyHostToDevice));
 
@@ -1018,6 +1034,37 @@ hygro_status hygro_set_vapour_fraction(hygro_ctx *c, const double *nu)
     return HYGRO_OK;
 }
 
+hygro_status hygro_set_layer_law(hygro_ctx *c, const int32_t *law)
+{
+    if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    FAULT_POINT(c, "hygro_set_layer_law");
+    if (law == nullptr) return fail(c, HYGRO_E_INVALID, "law is NULL");
+    if (!c->have_materials) return fail(c, HYGRO_E_STATE, "hygro_set_materials must come first");
+    const size_t nl = c->law.size();
+    for (size_t l = 0; l < nl; ++l)
+        if (law[l] < HYGRO_LAW_AFFINE || law[l] > HYGRO_LAW_TABLE1_C)
+            return fail(c, HYGRO_E_INVALID, "layer %zu: unknown coefficient law %d", l, law[l]);
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    std::vector<int8_t> l8(std::max<size_t>(1, nl), 0);
+    bool any = false;
+    for (int w = 0; w < c->W; ++w) {
+        WallInfo &wi = c->walls[w];
+        wi.has_law = 0;
+        for (int l = 0; l < wi.n_layers; ++l) {
+            const int32_t v = law[wi.layer_off + l];
+            l8[wi.layer_off + l] = (int8_t)v;
+            if (v != HYGRO_LAW_AFFINE) wi.has_law = 1;
+        }
+        any = any || wi.has_law;
+    }
+    CUDA_TRY(c, cudaMemcpy(c->d_layer_law, l8.data(), l8.size(), cudaMemcpyHostToDevice));
+    CUDA_TRY(c, cudaMemcpy(c->d_walls, c->walls.data(), c->walls.size() * sizeof(WallInfo), cudaMemcpyHostToDevice));
+    c->law.assign(law, law + nl);
+    c->any_law = any;
+    return HYGRO_OK;
+}
+
 hygro_status hygro_set_option(hygro_ctx *c, int32_t option, int64_t value)
 {
     if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
@@ -1122,6 +1169,7 @@ hygro_status hygro_start_euler(hygro_ctx *c)
         return fail(c, HYGRO_E_STATE, "hygro_set_materials and hygro_set_bc (both faces) must come first");
     if (c->step != 0) return fail(c, HYGRO_E_STATE, "the Euler start applies at step 0 (the context is at %lld)",
                                   (long long)c->step);
+    if (c->any_law) return fail(c, HYGRO_E_UNSUPPORTED, "the Euler start covers the affine coefficient laws only");
     for (int w = 0; w < c->W; ++w)
         for (int f = 0; f < 2; ++f)
             if (c->bc[f][w].bc.kind == HYGRO_BC_ROOM)
@@ -1217,6 +1265,7 @@ hygro_status hygro_balance(hygro_ctx *c, double *bal)
         for (int f = 0; f < 2; ++f)
             if (c->bc[f][w].bc.kind == HYGRO_BC_ROOM)
                 return fail(c, HYGRO_E_UNSUPPORTED, "wall %d has a room face: the balance covers walls without rooms", w);
+    if (c->any_law) return fail(c, HYGRO_E_UNSUPPORTED, "the balance covers the affine coefficient laws only");
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
     const size_t nb = (size_t)c->total_nodes * c->real_size;
     void *sT = nullptr, *sP = nullptr, *sc = nullptr, *sf = nullptr, *db = nullptr;
@@ -1449,7 +1498,7 @@ hygro_status hygro_autotune(hygro_ctx *c, int32_t probe_steps, double *model, do
     if (probe_steps < 16 || probe_steps > (1 << 20)) return fail(c, HYGRO_E_INVALID, "probe_steps must be in 16..2^20");
     if (!(c->have_materials && c->have_bc[0] && c->have_bc[1]))
         return fail(c, HYGRO_E_STATE, "hygro_set_materials and hygro_set_bc (both faces) must come first");
-    if (c->kernel != HYGRO_KERNEL_PERSISTENT || c->any_room_walls || c->n_free == 0)
+    if (c->kernel != HYGRO_KERNEL_PERSISTENT || c->any_room_walls || c->n_free == 0 || c->any_law)
         return fail(c, HYGRO_E_UNSUPPORTED, "the autotuner schedules walls of the persistent kernel without rooms");
     if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
     size_t bytes = 0;
@@ -1620,6 +1669,7 @@ hygro_status hygro_loss_grad(hygro_ctx *c, int64_t n_steps, int32_t sample_every
         for (int f = 0; f < 2; ++f)
             if (c->bc[f][w].bc.kind == HYGRO_BC_ROOM)
                 return fail(c, HYGRO_E_UNSUPPORTED, "wall %d has a room face: the adjoint runs walls without rooms", w);
+        if (c->any_law) return fail(c, HYGRO_E_UNSUPPORTED, "the adjoint differentiates the affine coefficient laws only");
         if (c->walls[w].nu != 1.0)
             return fail(c, HYGRO_E_UNSUPPORTED, "wall %d: the adjoint takes kTM = Lv kM (vapour fraction 1)", w);
     }

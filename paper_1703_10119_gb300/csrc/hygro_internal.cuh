@@ -56,6 +56,9 @@ struct WallInfo {
     int16_t aligned;      // 1 when every layer interface falls on a lane boundary
     int16_t simple;       // 1 when kTT, cTT do not depend on Pv and cTM = 0 in every layer, and nu = 1
     double nu;            // latent share of kM: kTM = nu Lv kM at the faces inside the wall
+    double dx;            // node spacing (m)
+    int32_t has_law;      // 1 when some layer takes a Table-1 coefficient law (plain kernel only)
+    int32_t pad_;
 };
 
 struct FaceInfo {
@@ -115,6 +118,7 @@ struct DevCtx {
     int32_t n_rooms;
     const int32_t *node_wall;    // [total nodes] (plain kernel)
     const int8_t *node_layer;    // [total nodes] (plain kernel)
+    const int8_t *layer_law;     // [sum layers] HYGRO_LAW_* of each layer (plain kernel; walls with has_law)
     int32_t total_nodes;
     double dt, t0, Lv;
 };

@@ -39,7 +39,8 @@ ABI_FUNCTIONS = ("hygro_create", "hygro_set_materials", "hygro_set_bc", "hygro_r
                  "hygro_fluxes", "hygro_get_fields", "hygro_set_fields", "hygro_get_step", "hygro_get_state",
                  "hygro_set_state", "hygro_last_error", "hygro_destroy", "hygro_run_noalloc", "hygro_set_rooms",
                  "hygro_get_rooms", "hygro_loss_grad", "hygro_balance", "hygro_set_option",
-                 "hygro_start_euler", "hygro_set_vapour_fraction", "hygro_autotune")
+                 "hygro_start_euler", "hygro_set_vapour_fraction", "hygro_autotune", "hygro_set_layer_law")
+HYGRO_LAW_AFFINE, HYGRO_LAW_TABLE1, HYGRO_LAW_TABLE1_A, HYGRO_LAW_TABLE1_C = 0, 1, 2, 3
 # Exported entry points of the 2D sections (names of include/hygro2d.h).
 ABI_FUNCTIONS_2D = ("hygro2d_create", "hygro2d_set_materials", "hygro2d_set_bc", "hygro2d_run", "hygro2d_sync",
                     "hygro2d_get_fields", "hygro2d_set_fields", "hygro2d_get_step", "hygro2d_last_error",
@@ -129,6 +130,7 @@ def lib(build_if_missing: bool = False) -> C.CDLL:
         "hygro_set_rooms": [P, C.c_int32, P, P],
         "hygro_get_rooms": [P, C.c_int32, P, P],
         "hygro_autotune": [P, C.c_int32, P, P],
+        "hygro_set_layer_law": [P, P],
         "hygro_loss_grad": [P, C.c_int64, C.c_int32, P, C.c_double, C.c_double, C.c_int32, C.POINTER(C.c_double), P],
         "hygro2d_create": [C.POINTER(hygro2d_desc), C.POINTER(P)],
         "hygro2d_set_materials": [P, C.c_int32, P, P, P, P],
@@ -295,6 +297,11 @@ def hygro_peak_probe(kind: int, device: int = -1, stream=None, target_ms: float 
     return ops.value, ms.value
 
 
+def hygro_set_layer_law(ctx, law):
+    law = np.ascontiguousarray(law, np.int32)
+    _check(lib().hygro_set_layer_law(ctx, _ptr(law)), ctx)
+
+
 def hygro_autotune(ctx, probe_steps: int, model=None, ms=None):
     _check(lib().hygro_autotune(ctx, int(probe_steps), _ptr(model), _ptr(ms)), ctx)
 
@@ -427,6 +434,8 @@ class Hygro:
         hygro_set_materials(self.ctx, np.ascontiguousarray(wl.n_layers, np.int32),
                             np.ascontiguousarray(wl.layer_first, np.int32), lay,
                             np.ascontiguousarray(wl.T_init, np.float64), np.ascontiguousarray(wl.P_init, np.float64))
+        if getattr(wl, "layer_law", None) is not None:
+            hygro_set_layer_law(self.ctx, wl.layer_law)
 
     def set_bc(self):
         wl = self.wl
