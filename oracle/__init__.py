@@ -64,6 +64,8 @@ class _Problem(C.Structure):
         ("dt", C.c_double), ("t0", C.c_double), ("Lv", C.c_double), ("Psat", C.c_double),
         ("n_rooms", C.c_int32), ("room_par", C.c_void_p), ("wall_area", C.c_void_p),
         ("vapour_frac", C.c_void_p), ("layer_law", C.c_void_p),
+        ("face_emis", C.c_void_p), ("room_view", C.c_void_p), ("n_links", C.c_int32), ("link_zone", C.c_void_p),
+        ("link_flow", C.c_void_p),
     ]
 
 
@@ -192,6 +194,15 @@ class Oracle:
             assert par.shape[1] == NROOM_PAR, "room rows hold ROOM_FIELDS"
             p.room_par = _ptr(keep(par, np.float64))
             p.wall_area = _ptr(keep(rooms["wall_area"], np.float64))
+            # long-wave exchange among a room's surfaces, interzone airflow (both optional)
+            if rooms.get("emissivity") is not None:
+                p.face_emis = _ptr(keep(np.asarray(rooms["emissivity"], np.float64).reshape(W, 2), np.float64))
+                p.room_view = _ptr(keep(rooms["view"], np.float64))
+            links = rooms.get("links") or []
+            p.n_links = len(links)
+            if links:
+                p.link_zone = _ptr(keep(np.array([[a, b] for a, b, _ in links], np.int32), np.int32))
+                p.link_flow = _ptr(keep(np.array([g for _, _, g in links], np.float64), np.float64))
         else:
             p.n_rooms = 0
             p.room_par = None

@@ -101,8 +101,8 @@ static void implicit_wall(const orc_problem *p, const wall_view *v, const face_b
         if (j < N - 1) rhs += w->kTMf[j] / dx * (Pout[j + 1] - Pout[j]);
         for (int f = 0; f < 2; ++f)
             if ((f == 0 && j == 0) || (f == 1 && j == N - 1)) {
-                w->b[j] += bc[f].hT;
-                rhs += bc[f].hT * bc[f].T_inf + Lv * bc[f].hM * (bc[f].P_inf - Pout[j]) + bc[f].q_inf;
+                w->b[j] += bc[f].hT + bc[f].hR;
+                rhs += bc[f].hT * bc[f].T_inf + Lv * bc[f].hM * (bc[f].P_inf - Pout[j]) + bc[f].q_inf + bc[f].qR;
             }
         w->d[j] = rhs;
     }
@@ -116,8 +116,21 @@ static void surface_flux(const orc_problem *p, const face_bc bc[2], const double
     for (int f = 0; f < 2; ++f) {
         const int32_t j = f == 0 ? 0 : N - 1;
         const double g = bc[f].hM * (bc[f].P_inf - P[j]) + bc[f].g_inf;
-        fl[f][0] = bc[f].hT * (bc[f].T_inf - T[j]) + p->Lv * bc[f].hM * (bc[f].P_inf - P[j]) + bc[f].q_inf;
+        fl[f][0] = bc[f].hT * (bc[f].T_inf - T[j]) + p->Lv * bc[f].hM * (bc[f].P_inf - P[j]) + bc[f].q_inf +
+                   bc[f].qR - bc[f].hR * T[j];
         fl[f][1] = g;
+    }
+}
+
+/* Surface values [n_walls][2 faces][T, Pv] of the levels T, P. */
+static void surface_values(const orc_problem *p, const int64_t *node_off, const double *T, const double *P,
+                           double *surf)
+{
+    for (int32_t w = 0; w < p->n_walls; ++w) {
+        surf[w * 4 + 0] = T[node_off[w]];
+        surf[w * 4 + 1] = P[node_off[w]];
+        surf[w * 4 + 2] = T[node_off[w + 1] - 1];
+        surf[w * 4 + 3] = P[node_off[w + 1] - 1];
     }
 }
 
@@ -144,7 +157,7 @@ static void room_sums(const orc_problem *p, const int64_t *node_off, const doubl
 /* Backward-Euler room air of level n+1 (Ta, Pa of level n in Tn_a, Pn_a) at time t = t^{n+1}, with the
  * capacity at the iterate's vapour pressure Pk_a and the room sums of the walls' new surface values. */
 static void implicit_room(const orc_problem *p, int32_t r, double t, double Tn_a, double Pn_a, double Pk_a,
-                          const double *sum, double *Ta, double *Pa)
+                          const double *sum, const double *lk, double *Ta, double *Pa)
 {
     const double *q = p->room_par + (size_t)r * ORC_NROOM_PAR;
     const double dt = p->dt, Lv = p->Lv, Pref = q[R_PVREF];
@@ -153,11 +166,14 @@ static void implicit_room(const orc_problem *p, int32_t r, double t, double Tn_a
     room_sources(p, r, t, &T_out, &P_out, &g);
     const double w_out = P_out / Pref;
     const double CP = rhoV / Pref;
-    const double P1 = (CP / dt * Pn_a + g + gv * w_out + sum[r * 4 + 3]) / (CP / dt + gv / Pref + sum[r * 4 + 1]);
+    const double G = lk[r * 3 + 0], GT = lk[r * 3 + 1], Gw = lk[r * 3 + 2];   /* linked rooms of the iterate */
+    const double P1 = (CP / dt * Pn_a + g + gv * w_out + sum[r * 4 + 3] + Gw) /
+                      (CP / dt + gv / Pref + sum[r * 4 + 1] + G / Pref);
     const double CT = rhoV * (q[R_CPA] + q[R_CPV] * Pk_a / Pref);
     const double rhs = CT / dt * Tn_a + q[R_QGAIN] + Lv * g + gv * q[R_CPA] * T_out + Lv * gv * (w_out - P1 / Pref) +
-                       sum[r * 4 + 2] + Lv * (sum[r * 4 + 3] - sum[r * 4 + 1] * P1);
-    *Ta = rhs / (CT / dt + gv * q[R_CPA] + sum[r * 4 + 0]);
+                       sum[r * 4 + 2] + Lv * (sum[r * 4 + 3] - sum[r * 4 + 1] * P1) + q[R_CPA] * GT +
+                       Lv * (Gw - G * P1 / Pref);
+    *Ta = rhs / (CT / dt + gv * q[R_CPA] + sum[r * 4 + 0] + G * q[R_CPA]);
     *Pa = P1;
 }
 
@@ -198,11 +214,18 @@ int orc_euler_implicit_run(const orc_problem *p, orc_state *s, int64_t n_steps, 
     double *Pk = Tk + tot, *Tk1 = Tk + 2 * tot, *Pk1 = Tk + 3 * tot;
     double *rk = ra, *rsum = ra + 4 * R;   /* iterate's room air (Ta, Pa per room) and room sums */
     double *air = (double *)calloc((size_t)R * 4 + 1, sizeof(double));   /* rk in the room_state layout */
-    if (air == NULL) {
+    double *surf = (double *)calloc((size_t)W * 4 + 1, sizeof(double));
+    double *qrad = (double *)calloc((size_t)W * 4 + 1, sizeof(double));
+    double *lk = (double *)calloc((size_t)R * 3 + 1, sizeof(double));
+    if (air == NULL || surf == NULL || qrad == NULL || lk == NULL) {
         free(node_off);
         free(layer_off);
         free(Tk);
         free(ra);
+        free(air);
+        free(surf);
+        free(qrad);
+        free(lk);
         return -2;
     }
     if (n_threads <= 0) n_threads = 1;
@@ -218,10 +241,15 @@ int orc_euler_implicit_run(const orc_problem *p, orc_state *s, int64_t n_steps, 
         int32_t k = 0;
         double change = 0.0;
         do {
-            /* walls from level n with the coefficients of the iterate and the room air of the iterate */
+            /* walls from level n with the coefficients of the iterate, the room air of the iterate and the
+             * radiative exchange of the iterate's surface temperatures */
             for (int32_t r = 0; r < R; ++r) {
                 air[r * 4 + 1] = rk[r * 2 + 0];
                 air[r * 4 + 3] = rk[r * 2 + 1];
+            }
+            if (R > 0) {
+                surface_values(p, node_off, Tk, Pk, surf);
+                room_radiation(p, surf, qrad);
             }
             int err = 0;
 #ifdef _OPENMP
@@ -240,7 +268,11 @@ int orc_euler_implicit_run(const orc_problem *p, orc_state *s, int64_t n_steps, 
 #endif
                     for (int32_t w = 0; w < W; ++w) {
                         const wall_view v = view_of(p, layer_off, w);
-                        const face_bc bc[2] = {face_of(p, w, 0, t1, air), face_of(p, w, 1, t1, air)};
+                        face_bc bc[2] = {face_of(p, w, 0, t1, air), face_of(p, w, 1, t1, air)};
+                        for (int f = 0; f < 2 && R > 0; ++f) {
+                            bc[f].hR = qrad[(w * 2 + f) * 2 + 0];
+                            bc[f].qR = qrad[(w * 2 + f) * 2 + 1];
+                        }
                         const int64_t o = node_off[w];
                         memcpy(wk.Tk, Tk + o, sizeof(double) * (size_t)v.N);
                         memcpy(wk.Pk, Pk + o, sizeof(double) * (size_t)v.N);
@@ -259,9 +291,10 @@ int orc_euler_implicit_run(const orc_problem *p, orc_state *s, int64_t n_steps, 
             double sq = 0.0;
             if (R > 0) {
                 room_sums(p, node_off, Tk1, Pk1, rsum);
+                room_links(p, air, lk);   /* the linked rooms' air of the iterate (air holds rk) */
                 for (int32_t r = 0; r < R; ++r) {
                     double Ta, Pa;
-                    implicit_room(p, r, t1, s->room[r * 4 + 1], s->room[r * 4 + 3], rk[r * 2 + 1], rsum, &Ta, &Pa);
+                    implicit_room(p, r, t1, s->room[r * 4 + 1], s->room[r * 4 + 3], rk[r * 2 + 1], rsum, lk, &Ta, &Pa);
                     const double eT = fabs(Ta - rk[r * 2 + 0]) / fabs(Ta), eP = fabs(Pa - rk[r * 2 + 1]) / fabs(Pa);
                     change = fmax(change, fmax(eT, eP));
                     sq += eT * eT + eP * eP;
@@ -287,9 +320,17 @@ int orc_euler_implicit_run(const orc_problem *p, orc_state *s, int64_t n_steps, 
             air[r * 4 + 1] = rk[r * 2 + 0];
             air[r * 4 + 3] = rk[r * 2 + 1];
         }
+        if (R > 0) {
+            surface_values(p, node_off, Tk, Pk, surf);
+            room_radiation(p, surf, qrad);
+        }
         for (int32_t w = 0; w < W; ++w) {
             const int64_t o = node_off[w];
-            const face_bc bc[2] = {face_of(p, w, 0, t1, air), face_of(p, w, 1, t1, air)};
+            face_bc bc[2] = {face_of(p, w, 0, t1, air), face_of(p, w, 1, t1, air)};
+            for (int f = 0; f < 2 && R > 0; ++f) {
+                bc[f].hR = qrad[(w * 2 + f) * 2 + 0];
+                bc[f].qR = qrad[(w * 2 + f) * 2 + 1];
+            }
             double fl[2][2];
             surface_flux(p, bc, Tk + o, Pk + o, p->n_nodes[w], fl);
             for (int f = 0; f < 2; ++f)
@@ -312,6 +353,9 @@ int orc_euler_implicit_run(const orc_problem *p, orc_state *s, int64_t n_steps, 
     free(Tk);
     free(ra);
     free(air);
+    free(surf);
+    free(qrad);
+    free(lk);
     return rc;
 }
 
@@ -372,7 +416,8 @@ static void explicit_wall(const orc_problem *p, const wall_view *v, const face_b
         if (j < N - 1) q += (w->kTTf[j] * (T[j + 1] - T[j]) + w->kTMf[j] * (P[j + 1] - P[j])) / dx;
         for (int f = 0; f < 2; ++f)
             if ((f == 0 && j == 0) || (f == 1 && j == N - 1))
-                q += bc[f].hT * (bc[f].T_inf - T[j]) + Lv * bc[f].hM * (bc[f].P_inf - P[j]) + bc[f].q_inf;
+                q += bc[f].hT * (bc[f].T_inf - T[j]) + Lv * bc[f].hM * (bc[f].P_inf - P[j]) + bc[f].q_inf +
+                     bc[f].qR - bc[f].hR * T[j];
         q -= wj * dx * w->cTM[j] * (Pout[j] - P[j]) / tau;
         Tout[j] = T[j] + tau * q / (wj * dx * w->cTT[j]);
     }
@@ -407,12 +452,18 @@ int orc_euler_explicit_run(const orc_problem *p, orc_state *s, int64_t n_steps, 
     double *T = (double *)malloc(sizeof(double) * (size_t)tot * 4);
     double *ra = (double *)malloc(sizeof(double) * ((size_t)R * 10 + 4));
     double *tw = (double *)malloc(sizeof(double) * ((size_t)W + 1));
-    if (!T || !ra || !tw) {
+    double *surf = (double *)calloc((size_t)W * 4 + 1, sizeof(double));
+    double *qrad = (double *)calloc((size_t)W * 4 + 1, sizeof(double));
+    double *lk = (double *)calloc((size_t)R * 3 + 1, sizeof(double));
+    if (!T || !ra || !tw || !surf || !qrad || !lk) {
         free(node_off);
         free(layer_off);
         free(T);
         free(ra);
         free(tw);
+        free(surf);
+        free(qrad);
+        free(lk);
         return -2;
     }
     double *P = T + tot, *T1 = T + 2 * tot, *P1 = T + 3 * tot;
@@ -462,7 +513,11 @@ int orc_euler_explicit_run(const orc_problem *p, orc_state *s, int64_t n_steps, 
             for (int32_t r = 0; r < R; ++r) {
                 const double *q = p->room_par + (size_t)r * ORC_NROOM_PAR;
                 const double rhoV = q[R_RHOA] * q[R_VOL], gv = rhoV * q[R_ACH] / 3600.0, Pref = q[R_PVREF];
-                const double kP = gv / Pref + rsum[r * 4 + 1], kT = gv * q[R_CPA] + rsum[r * 4 + 0];
+                double G = 0.0;
+                for (int32_t l = 0; l < p->n_links; ++l)
+                    if (p->link_zone[2 * l] == r || p->link_zone[2 * l + 1] == r) G += p->link_flow[l];
+                const double kP = gv / Pref + rsum[r * 4 + 1] + G / Pref;
+                const double kT = gv * q[R_CPA] + rsum[r * 4 + 0] + G * q[R_CPA];
                 tmax = fmin(tmax, (rhoV / Pref) / kP);
                 tmax = fmin(tmax, rhoV * (q[R_CPA] + q[R_CPV] * air[r * 4 + 3] / Pref) / kT);
             }
@@ -472,6 +527,11 @@ int orc_euler_explicit_run(const orc_problem *p, orc_state *s, int64_t n_steps, 
         const double tau = p->dt / (double)m;
         for (int64_t i = 0; i < m && rc == 0; ++i) {
             const double t = t0 + (double)i * tau;
+            if (R > 0) {
+                surface_values(p, node_off, T, P, surf);
+                room_radiation(p, surf, qrad);
+                room_links(p, air, lk);
+            }
 #ifdef _OPENMP
 #pragma omp parallel num_threads(n_threads)
 #endif
@@ -488,7 +548,11 @@ int orc_euler_explicit_run(const orc_problem *p, orc_state *s, int64_t n_steps, 
 #endif
                     for (int32_t w = 0; w < W; ++w) {
                         const wall_view v = view_of(p, layer_off, w);
-                        const face_bc bc[2] = {face_of(p, w, 0, t, air), face_of(p, w, 1, t, air)};
+                        face_bc bc[2] = {face_of(p, w, 0, t, air), face_of(p, w, 1, t, air)};
+                        for (int f = 0; f < 2 && R > 0; ++f) {
+                            bc[f].hR = qrad[(w * 2 + f) * 2 + 0];
+                            bc[f].qR = qrad[(w * 2 + f) * 2 + 1];
+                        }
                         const int64_t o = node_off[w];
                         double fl[2][2];
                         explicit_wall(p, &v, bc, T + o, P + o, tau, &wk, T1 + o, P1 + o, fl);
@@ -512,11 +576,14 @@ int orc_euler_explicit_run(const orc_problem *p, orc_state *s, int64_t n_steps, 
                     double T_out, P_out, g;
                     room_sources(p, r, t, &T_out, &P_out, &g);
                     const double w_out = P_out / Pref, Ta = air[r * 4 + 1], Pa = air[r * 4 + 3];
-                    const double dP = (g + gv * (w_out - Pa / Pref) + rsum[r * 4 + 3] - rsum[r * 4 + 1] * Pa) /
+                    const double G = lk[r * 3 + 0], GT = lk[r * 3 + 1], Gw = lk[r * 3 + 2];
+                    const double dP = (g + gv * (w_out - Pa / Pref) + rsum[r * 4 + 3] - rsum[r * 4 + 1] * Pa +
+                                       Gw - G * Pa / Pref) /
                                       (rhoV / Pref);
                     const double CT = rhoV * (q[R_CPA] + q[R_CPV] * Pa / Pref);
                     const double dT = (q[R_QGAIN] + Lv * g + gv * q[R_CPA] * (T_out - Ta) + Lv * gv * (w_out - Pa / Pref) +
-                                       rsum[r * 4 + 2] - rsum[r * 4 + 0] * Ta + Lv * (rsum[r * 4 + 3] - rsum[r * 4 + 1] * Pa)) /
+                                       rsum[r * 4 + 2] - rsum[r * 4 + 0] * Ta + Lv * (rsum[r * 4 + 3] - rsum[r * 4 + 1] * Pa) +
+                                       q[R_CPA] * (GT - G * Ta) + Lv * (Gw - G * Pa / Pref)) /
                                       CT;
                     air[r * 4 + 1] = Ta + tau * dT;
                     air[r * 4 + 3] = Pa + tau * dP;
@@ -549,5 +616,8 @@ int orc_euler_explicit_run(const orc_problem *p, orc_state *s, int64_t n_steps, 
     free(layer_off);
     free(ra);
     free(tw);
+    free(surf);
+    free(qrad);
+    free(lk);
     return rc;
 }

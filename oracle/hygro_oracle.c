@@ -266,8 +266,8 @@ static void wall_step(const orc_problem *p, const wall_view *v, const face_bc bc
         }
         for (int f = 0; f < 2; ++f) {
             if ((f == 0 && j == 0) || (f == 1 && j == N - 1)) {
-                H += bc[f].hT;
-                src += bc[f].hT * bc[f].T_inf + Lv * bc[f].hM * (bc[f].P_inf - Pbar) + bc[f].q_inf;
+                H += bc[f].hT + bc[f].hR;
+                src += bc[f].hT * bc[f].T_inf + Lv * bc[f].hM * (bc[f].P_inf - Pbar) + bc[f].q_inf + bc[f].qR;
             }
         }
         sc->Tn[j] = ((B - 0.5 * S - 0.5 * H) * Tp[j] + nb + cross + src - C * (sc->Pn[j] - Pp[j])) /
@@ -280,7 +280,8 @@ static void wall_step(const orc_problem *p, const wall_view *v, const face_bc bc
         double Tbar = 0.5 * (sc->Tn[j] + Tp[j]);
         double Pbar = 0.5 * (sc->Pn[j] + Pp[j]);
         double g = bc[f].hM * (bc[f].P_inf - Pbar) + bc[f].g_inf;
-        double q = bc[f].hT * (bc[f].T_inf - Tbar) + Lv * bc[f].hM * (bc[f].P_inf - Pbar) + bc[f].q_inf;
+        double q = bc[f].hT * (bc[f].T_inf - Tbar) + Lv * bc[f].hM * (bc[f].P_inf - Pbar) + bc[f].q_inf +
+                   bc[f].qR - bc[f].hR * Tbar;
         flux[f][0] = q;
         flux[f][1] = g;
     }
@@ -347,9 +348,57 @@ void room_sources(const orc_problem *p, int32_t r, double t, double *T_out, doub
  * humidity ratio w = Pva / Pv_ref. The wall surface values enter at level n
  * as in [eq:wbse_tn_exp]; the room node itself is advanced with the DF
  * replacement (Ta^{n+1} + Ta^{n-1}) / 2 of its own value, vapour first. */
+/* q_rw = s eps sigma sum over the room's faces of (T'^4 - Ts^4) (Sec. 2). Each term factors exactly as
+ * h' (T' - Ts) with the radiative conductance h' = s eps sigma (T'^2 + Ts^2)(T' + Ts), symmetric in the two
+ * surfaces; written so, q_rw has the form of DF faces to the other surfaces: conductances and the other
+ * surfaces' temperatures of level n, the face's own value averaged over levels n+1 and n-1 (a level-n own
+ * value would be a leapfrog term, unstable in DF). rad = (hR, qR) = (sum h', sum h' T'), the face receiving
+ * qR - hR Ts. */
+void room_radiation(const orc_problem *p, const double *surf, double *rad)
+{
+    const int32_t W = p->n_walls;
+    for (int32_t i = 0; i < 4 * W; ++i) rad[i] = 0.0;
+    if (p->face_emis == NULL || p->room_view == NULL) return;
+    for (int32_t w = 0; w < W; ++w)
+        for (int f = 0; f < 2; ++f) {
+            if (p->bc_kind[w * 2 + f] != ORC_BC_ROOM) continue;
+            const int32_t r = p->bc_room[w * 2 + f];
+            const double Ts = surf[w * 4 + f * 2];
+            const double c = p->room_view[r] * p->face_emis[w * 2 + f] * ORC_SIGMA;
+            double hR = 0.0, qR = 0.0;
+            for (int32_t u = 0; u < W; ++u)
+                for (int g = 0; g < 2; ++g) {
+                    if (p->bc_kind[u * 2 + g] != ORC_BC_ROOM || p->bc_room[u * 2 + g] != r) continue;
+                    if (u == w && g == f) continue;
+                    const double To = surf[u * 4 + g * 2];
+                    const double h = c * (To * To + Ts * Ts) * (To + Ts);
+                    hR += h;
+                    qR += h * To;
+                }
+            rad[(w * 2 + f) * 2 + 0] = hR;
+            rad[(w * 2 + f) * 2 + 1] = qR;
+        }
+}
+
+void room_links(const orc_problem *p, const double *rs, double *lk)
+{
+    for (int32_t i = 0; i < 3 * p->n_rooms; ++i) lk[i] = 0.0;
+    for (int32_t l = 0; l < p->n_links; ++l) {
+        const double g = p->link_flow[l];
+        for (int e = 0; e < 2; ++e) {
+            const int32_t r = p->link_zone[2 * l + e], o = p->link_zone[2 * l + 1 - e];
+            const double *qo = p->room_par + (size_t)o * ORC_NROOM_PAR;
+            lk[r * 3 + 0] += g;
+            lk[r * 3 + 1] += g * rs[o * 4 + 1];
+            lk[r * 3 + 2] += g * rs[o * 4 + 3] / qo[R_PVREF];
+        }
+    }
+}
+
+/* lk: this room's interzone sums (room_links) at level n. */
 static void room_step(const orc_problem *p, int32_t r, double t, double *rs,
                       const double *sum_AhT, const double *sum_AhM, const double *sum_AhTTs,
-                      const double *sum_AhMPs)
+                      const double *sum_AhMPs, const double *lk)
 {
     const double *q = p->room_par + (size_t)r * ORC_NROOM_PAR;
     const double dt = p->dt, Lv = p->Lv;
@@ -360,12 +409,16 @@ static void room_step(const orc_problem *p, int32_t r, double t, double *rs,
     room_sources(p, r, t, &T_out, &P_out, &g_vap);
     double Pref = q[R_PVREF];
     double w_out = P_out / Pref;
+    /* interzone airflow: G_inz = sum g (w_o - w), Q_inz = sum g [cpa (T_o - Ta) + Lv (w_o - w)] */
+    const double G = lk[0], GT = lk[1], Gw = lk[2];
     if (q[R_SCHEME] == 1.0) {
         /* the explicit Euler update of Sec. 5.2: every term of both balances at level n */
-        double Pa_n = Pa_c + dt / (rhoV / Pref) * (g_vap + gv * (w_out - Pa_c / Pref) + sum_AhMPs[r] - sum_AhM[r] * Pa_c);
+        double Pa_n = Pa_c + dt / (rhoV / Pref) * (g_vap + gv * (w_out - Pa_c / Pref) + sum_AhMPs[r] - sum_AhM[r] * Pa_c +
+                                                   Gw - G * Pa_c / Pref);
         double CT0 = rhoV * (q[R_CPA] + q[R_CPV] * Pa_c / Pref);
         double rhs0 = q[R_QGAIN] + Lv * g_vap + gv * q[R_CPA] * (T_out - Ta_c) + Lv * gv * (w_out - Pa_c / Pref) +
-                      sum_AhTTs[r] - sum_AhT[r] * Ta_c + Lv * (sum_AhMPs[r] - sum_AhM[r] * Pa_c);
+                      sum_AhTTs[r] - sum_AhT[r] * Ta_c + Lv * (sum_AhMPs[r] - sum_AhM[r] * Pa_c) +
+                      q[R_CPA] * (GT - G * Ta_c) + Lv * (Gw - G * Pa_c / Pref);
         double Ta_n = Ta_c + dt / CT0 * rhs0;
         rs[0] = Ta_c;
         rs[1] = Ta_n;
@@ -376,16 +429,17 @@ static void room_step(const orc_problem *p, int32_t r, double t, double *rs,
     /* vapour: rhoV/Pref dPa/dt = g_vap + gv (w_out - Pa/Pref) + sum A hM (Ps - Pa) */
     double CP = rhoV / Pref;
     double a_p = CP / (2.0 * dt);
-    double k_p = gv / Pref + sum_AhM[r];
-    double Pa_n = ((a_p - 0.5 * k_p) * Pa_p + g_vap + gv * w_out + sum_AhMPs[r]) / (a_p + 0.5 * k_p);
+    double k_p = gv / Pref + sum_AhM[r] + G / Pref;
+    double Pa_n = ((a_p - 0.5 * k_p) * Pa_p + g_vap + gv * w_out + sum_AhMPs[r] + Gw) / (a_p + 0.5 * k_p);
     double Pa_bar = 0.5 * (Pa_n + Pa_p);
     /* heat: rhoV (cpa + cpv w) dTa/dt = Q + Lv g_vap + gv cpa (T_out - Ta) + Lv gv (w_out - w)
      *       + sum A [hT (Ts - Ta) + Lv hM (Ps - Pa)] */
     double CT = rhoV * (q[R_CPA] + q[R_CPV] * Pa_c / Pref);
     double a_t = CT / (2.0 * dt);
-    double k_t = gv * q[R_CPA] + sum_AhT[r];
+    double k_t = gv * q[R_CPA] + sum_AhT[r] + G * q[R_CPA];
     double rhs = q[R_QGAIN] + Lv * g_vap + gv * q[R_CPA] * T_out + Lv * gv * (w_out - Pa_bar / Pref) +
-                 sum_AhTTs[r] + Lv * (sum_AhMPs[r] - sum_AhM[r] * Pa_bar);
+                 sum_AhTTs[r] + Lv * (sum_AhMPs[r] - sum_AhM[r] * Pa_bar) + q[R_CPA] * GT +
+                 Lv * (Gw - G * Pa_bar / Pref);
     double Ta_n = ((a_t - 0.5 * k_t) * Ta_p + rhs) / (a_t + 0.5 * k_t);
     rs[0] = Ta_c;
     rs[1] = Ta_n;
@@ -552,8 +606,11 @@ int orc_run(const orc_problem *p, orc_state *s, int64_t n_steps, int32_t sample_
     double *surf = (double *)calloc((size_t)W * 4 + 1, sizeof(double)); /* Ts^n, Ps^n of face 0, face 1 */
     double *rsum = (double *)calloc((size_t)R * 4 + 1, sizeof(double));
     double *flux = (double *)calloc((size_t)W * 4 + 1, sizeof(double));
-    if (!surf || !rsum || !flux) {
-        free(node_off); free(layer_off); free(surf); free(rsum); free(flux);
+    double *qrad = (double *)calloc((size_t)W * 4 + 1, sizeof(double));   /* radiative hR, qR of each face */
+    double *lk = (double *)calloc((size_t)R * 3 + 1, sizeof(double));     /* interzone sums of each room */
+    double *rs0 = (double *)calloc((size_t)R * 4 + 1, sizeof(double));    /* room states of level n */
+    if (!surf || !rsum || !flux || !qrad || !lk || !rs0) {
+        free(node_off); free(layer_off); free(surf); free(rsum); free(flux); free(qrad); free(lk); free(rs0);
         return -2;
     }
     if (n_threads <= 0) n_threads = 1;
@@ -570,6 +627,8 @@ int orc_run(const orc_problem *p, orc_state *s, int64_t n_steps, int32_t sample_
             surf[w * 4 + 2] = s->T_cur[node_off[w] + p->n_nodes[w] - 1];
             surf[w * 4 + 3] = s->P_cur[node_off[w] + p->n_nodes[w] - 1];
         }
+        /* long-wave exchange among each room's surfaces at level n (explicit, a surface heat source) */
+        if (R > 0) room_radiation(p, surf, qrad);
 #ifdef _OPENMP
 #pragma omp parallel num_threads(n_threads)
 #endif
@@ -592,6 +651,10 @@ int orc_run(const orc_problem *p, orc_state *s, int64_t n_steps, int32_t sample_
                 for (int32_t w = 0; w < W; ++w) {
                     wall_view v = view_of(p, layer_off, w);
                     face_bc bc[2] = {face_of(p, w, 0, t, s->room), face_of(p, w, 1, t, s->room)};
+                    for (int f = 0; f < 2 && R > 0; ++f) {
+                        bc[f].hR = qrad[(w * 2 + f) * 2 + 0];
+                        bc[f].qR = qrad[(w * 2 + f) * 2 + 1];
+                    }
                     double fl[2][2], bl[2][4];
                     int64_t o = node_off[w];
                     wall_step(p, &v, bc, s->T_prev + o, s->T_cur + o, s->P_prev + o, s->P_cur + o, &sc,
@@ -634,7 +697,10 @@ int orc_run(const orc_problem *p, orc_state *s, int64_t n_steps, int32_t sample_
                     AhTTs[r] += A * b[B_HT] * surf[w * 4 + f * 2 + 0];
                     AhMPs[r] += A * b[B_HM] * surf[w * 4 + f * 2 + 1];
                 }
-            for (int32_t r = 0; r < R; ++r) room_step(p, r, t, s->room + r * 4, AhT, AhM, AhTTs, AhMPs);
+            /* interzone exchange with the linked rooms' air of level n */
+            for (int32_t i = 0; i < 4 * R; ++i) rs0[i] = s->room[i];
+            room_links(p, rs0, lk);
+            for (int32_t r = 0; r < R; ++r) room_step(p, r, t, s->room + r * 4, AhT, AhM, AhTTs, AhMPs, lk + r * 3);
         }
 
         s->step = n + 1;
@@ -661,5 +727,8 @@ int orc_run(const orc_problem *p, orc_state *s, int64_t n_steps, int32_t sample_
     free(surf);
     free(rsum);
     free(flux);
+    free(qrad);
+    free(lk);
+    free(rs0);
     return rc;
 }

@@ -91,7 +91,18 @@ typedef struct {
     const double *wall_area;     /* [n_walls], m^2, used by room faces */
     const double *vapour_frac;   /* [n_walls] nu of kTM = nu Lv kM inside the wall, or NULL (all 1) */
     const int32_t *layer_law;    /* [sum n_layers] ORC_LAW_* of each layer, or NULL (all affine) */
+    /* long-wave radiation among a room's wall surfaces (Sec. 2, q_rw): a room face of wall w receives
+     * s_r eps_wf sigma sum over the room's faces (Ts'^4 - Ts^4), surface temperatures of level n */
+    const double *face_emis;     /* [n_walls][2] emissivity eps of each face (room faces), or NULL (none) */
+    const double *room_view;     /* [n_rooms] view factor s of each room, or NULL (none) */
+    /* interzone airflow (Sec. 5.1, Q_inz and G_inz): link l carries link_flow[l] kg/s of air between rooms
+     * link_zone[2l] and link_zone[2l+1] in both directions */
+    int32_t n_links;
+    const int32_t *link_zone;    /* [n_links][2] */
+    const double *link_flow;     /* [n_links] */
 } orc_problem;
+
+#define ORC_SIGMA 5.670374419e-8   /* Stefan-Boltzmann constant, W/(m2 K4) */
 
 typedef struct {
     int64_t step;                /* n: T_cur / P_cur hold level n, T_prev / P_prev level n-1 */

@@ -35,9 +35,23 @@ void coefficients(const orc_problem *p, const wall_view *v, const double *T, con
  * coefficients of [eq:HAM_BC]. An adiabatic face exchanges nothing. */
 typedef struct {
     double hT, hM, q_inf, g_inf, T_inf, P_inf;
+    /* long-wave exchange with the other surfaces of a room (zero elsewhere): the face receives
+     * qR - hR Ts, the coefficient hR and the emission qR of level n */
+    double hR, qR;
 } face_bc;
 
 face_bc face_of(const orc_problem *p, int32_t w, int32_t f, double t, const double *room_state);
+
+/* Long-wave exchange q_rw (Sec. 2) of every room face at the surface temperatures surf ([n_walls][2 faces]
+ * [T, Pv]) of level n, in the form qR - hR Ts of faces to the room's other surfaces: rad[w][f][0] = hR = sum
+ * of the radiative conductances h' = s eps sigma (T'^2 + Ts^2)(T' + Ts) and rad[w][f][1] = qR = sum h' T';
+ * zero on other faces. */
+void room_radiation(const orc_problem *p, const double *surf, double *rad);
+
+/* Interzone exchange of every room with the air of the rooms it is linked to, at the room states rs
+ * ([n_rooms][Ta_prev, Ta, Pa_prev, Pa]): per room the total link flow G (kg/s) and the sums G T_o, G w_o of
+ * the linked rooms' level values (w = Pa / Pv_ref); lk[r][3]. */
+void room_links(const orc_problem *p, const double *rs, double *lk);
 
 /* Outdoor air and vapour production of room r at time t (Sec. 5.1). */
 void room_sources(const orc_problem *p, int32_t r, double t, double *T_out, double *P_out, double *g_vap);

@@ -17,7 +17,20 @@ Three checks, each against something the room update itself does not compute:
   point; the explicit Euler update has e^{n+1} = (1 - k dt / C) e^n;
 * with the vapour away from its steady state the latent ventilation drives the heat balance; the DF
   room node started from exact levels converges to the solution of the two ODEs at second order in dt.
+
+Interzone airflow (Sec. 5.1, Q_inz and G_inz) and long-wave radiation among a room's surfaces (Sec. 2,
+q_rw, taken in the DF step as faces to the room's other surfaces: T'^4 - Ts^4 = h' (T' - Ts), the
+conductance h' = s eps sigma (T'^2 + Ts^2)(T' + Ts) and T' of level n, Ts averaged over levels n+1 and n-1):
+two zones exchanging air
+converge at second order to the solution of their four ODEs (latent terms on); the radiative flux between
+two faces matches the linearised exchange 4 s eps sigma T^3 dT, is reciprocal for equal emissivities and
+areas, and takes each face's own emissivity; radiation alone equalises two walls' surfaces over a long run
+(a level-n own value would be a leapfrog term, and a level-n Ts^4 with only Ts^3 averaged leaves the
+explicit coupling four times the damping: both unstable in DF); and the
+closed-system balance of two linked rooms with radiating walls holds to 1e-12 with the interzone coupling
+defect and the radiation deposited in the walls.
 """
+import dataclasses
 import math
 
 import numpy as np
@@ -276,3 +289,184 @@ def test_lonely_room_transient_converges_at_second_order(oracle_mod):
             ratio = errs[i][fld] / errs[i + 1][fld]
             assert 3.6 < ratio < 4.4, (errs, i, fld)
     assert errs[-1][0] < 1e-3
+
+
+# --------------------------------------------------------------------------------------------------
+# interzone airflow and long-wave radiation among room surfaces (Sec. 5.1 Q_inz, G_inz; Sec. 2 q_rw)
+
+
+def _two_zones(V1, V2, g, dt, T0=(300.0, 290.0), P0=(1500.0, 900.0)):
+    """Two rooms without walls, no ventilation or gains, exchanging g kg/s of air (a dummy wall with two
+    ambient faces keeps the workload valid)."""
+    w = wk.uniform_wall(5, 0.05, dict(kM0=1e-11, cM0=5e-2, kTT0=0.5, cTT0=1e6), dt=dt,
+                        bc0=dict(hT=5.0, hM=1e-8), bc1=dict(hT=5.0, hM=1e-8))
+    par = np.stack([_room_row(V1, 0.0, 0.0, 0.0, 280.0, 900.0), _room_row(V2, 0.0, 0.0, 0.0, 280.0, 900.0)])
+    w.rooms = dict(par=par, wall_area=np.array([1.0]), Ta0=np.array(T0), Pa0=np.array(P0), links=[(0, 1, g)])
+    return w
+
+
+def test_interzone_transient_converges_at_second_order(oracle_mod):
+    """Two zones exchanging air: rho V_i dw_i/dt = g (w_j - w_i) and rho V_i (cpa + cpv w_i) dT_i/dt =
+    g cpa (T_j - T_i) + Lv g (w_j - w_i). From exact starting levels the DF zone nodes (each zone's own value
+    averaged over levels n+1 and n-1, the other zone's of level n) converge to the ODE solution at second
+    order, both fields."""
+    V1, V2, g, Lv = 40.0, 90.0, 0.02, wk.LV
+
+    def rhs(t, y):
+        T1, T2, w1, w2 = y
+        return [(g * CPA * (T2 - T1) + Lv * g * (w2 - w1)) / (RHO * V1 * (CPA + CPV * w1)),
+                (g * CPA * (T1 - T2) + Lv * g * (w1 - w2)) / (RHO * V2 * (CPA + CPV * w2)),
+                g * (w2 - w1) / (RHO * V1), g * (w1 - w2) / (RHO * V2)]
+
+    y0 = [300.0, 290.0, 1500.0 / PREF, 900.0 / PREF]
+    t_end = 4 * 3600.0
+    ex = solve_ivp(rhs, (0.0, t_end), y0, method="DOP853", rtol=1e-13, atol=1e-14).y[:, -1]
+    errs = []
+    for dt in (200.0, 100.0, 50.0, 25.0):
+        ym = solve_ivp(rhs, (0.0, -dt), y0, method="DOP853", rtol=1e-13, atol=1e-14).y[:, -1]
+        wl = _two_zones(V1, V2, g, dt)
+        o = oracle_mod.Oracle(wl, n_threads=1)
+        o.room[0] = [ym[0], y0[0], ym[2] * PREF, y0[2] * PREF]
+        o.room[1] = [ym[1], y0[1], ym[3] * PREF, y0[3] * PREF]
+        o.run(int(round(t_end / dt)))
+        errs.append((max(abs(o.room[0, 1] - ex[0]), abs(o.room[1, 1] - ex[1])),
+                     max(abs(o.room[0, 3] - ex[2] * PREF), abs(o.room[1, 3] - ex[3] * PREF))))
+    for i in range(3):
+        for f in range(2):
+            assert 3.6 < errs[i][f] / errs[i + 1][f] < 4.4, (errs, i, f)
+
+
+def _radiating_pair(eps, area, T0=(295.0, 285.0), hT_in=0.0):
+    """Two single-layer walls, outer faces adiabatic, inner faces on one room; the room faces exchange heat
+    with each other by long-wave radiation (view factor 0.2) and with the air through hT_in only."""
+    walls = []
+    for i in range(2):
+        w = wk.uniform_wall(11, 0.05, dict(kM0=1e-11, cM0=5e-2, kTT0=0.8, cTT0=1.2e6), T0=T0[i], P0=1000.0,
+                            dt=60.0, Lv=0.0, bc0=dict(hT=0.0, hM=0.0), bc1=dict(hT=hT_in, hM=0.0),
+                            kinds=(wk.BC_ADIABATIC, wk.BC_ROOM))
+        w.bc_room = np.array([[-1, 0]], np.int32)
+        walls.append(w)
+    wl = wk.concat(walls)
+    wl.Lv = 0.0
+    wl.rooms = dict(par=_room_row(30.0, 0.0, 0.0, 0.0, 290.0, 1000.0)[None], wall_area=np.array(area),
+                    Ta0=np.array([290.0]), Pa0=np.array([1000.0]),
+                    emissivity=np.array([[0.0, eps[0]], [0.0, eps[1]]]), view=np.array([0.2]))
+    return wl
+
+
+def test_radiation_linearised_conductance_and_reciprocity(oracle_mod):
+    """For a small temperature difference the radiative flux between two surfaces is the linearised
+    exchange 4 s eps sigma T^3 dT (the Stefan-Boltzmann law, sigma = 5.670374419e-8 W/m2/K4), flowing from the
+    warmer to the cooler face; with equal areas and emissivities the two faces' fluxes cancel (the radiation
+    moves energy between the walls and creates none)."""
+    T1, dT = 293.15, 1e-3
+    wl = dataclasses.replace(_radiating_pair((0.5, 0.5), (12.0, 12.0), T0=(T1, T1 + dT)), dt=1.0)
+    o = oracle_mod.Oracle(wl, n_threads=1)
+    r = o.run(1)
+    q0, q1 = r["flux"][0, 1, 0], r["flux"][1, 1, 0]   # heat into each wall at its room face over one 1 s step
+    h_r = 4 * 0.2 * 0.5 * 5.670374419e-8 * T1 ** 3
+    assert abs(q0 - h_r * dT) <= 1e-3 * h_r * dT and q0 > 0       # the cooler wall gains
+    assert abs(q0 + q1) <= 1e-3 * abs(q0)
+    # unequal emissivities: each face takes its own emissivity
+    wl = dataclasses.replace(_radiating_pair((0.5, 0.9), (12.0, 12.0), T0=(T1, T1 + dT)), dt=1.0)
+    r = oracle_mod.Oracle(wl, n_threads=1).run(1)
+    assert abs(r["flux"][1, 1, 0] / r["flux"][0, 1, 0] + 0.9 / 0.5) <= 1e-3
+
+
+def test_radiation_equalises_the_surfaces(oracle_mod):
+    """Two walls exchanging heat by radiation only (adiabatic outer faces, no air exchange): the surfaces
+    converge to one temperature, between the initial ones, and the radiative fluxes vanish. Without any
+    exchange to damp it, DF keeps its neutral odd-even mode ((-1)^j (-1)^n, amplification -1), so the check
+    is on the mean of the two newest levels, which cancels it; the mode itself stays bounded."""
+    wl = _radiating_pair((0.7, 0.7), (10.0, 10.0))
+    o = oracle_mod.Oracle(wl, n_threads=1)
+    for _ in range(100):
+        r = o.run(2000)
+    mean = [0.5 * (o.wall(w, "T", 0) + o.wall(w, "T", 1)) for w in range(2)]
+    assert np.ptp(np.concatenate(mean)) < 1e-6
+    assert 285.0 < mean[0][0] < 295.0
+    assert np.abs(np.concatenate([o.wall(0, "T"), o.wall(1, "T")]) - mean[0][0]).max() < 0.05
+    assert abs(r["flux"][0, 1, 0]) < 1e-2
+
+
+def test_closed_system_balance_two_linked_rooms_with_radiation(oracle_mod):
+    """Two rooms, each with its layered walls, linked by interzone airflow, their surfaces exchanging
+    long-wave radiation: over one step the stored heat and vapour of all walls and both airs equal the
+    outdoor fluxes + ventilation + gains + DF defects + the coupling defects of the room faces and of the
+    interzone link + the radiation deposited in the walls, to 1e-12 of the term magnitudes."""
+    wl = _building(Lv=2.5e6, scheme=0)
+    W = wl.n_walls
+    wl.bc_room = np.array([[-1, 0], [-1, 1], [-1, 1]], np.int32)
+    par0 = wl.rooms["par"][0]
+    par1 = _room_row(70.0, 0.8, 150.0, 1.2e-4, 279.0, 820.0, 0, T_amp=5.0, P_amp=200.0, phase_T=0.7, phase_P=2.1)
+    emis = np.array([[0.0, 0.9], [0.0, 0.5], [0.0, 0.6]])
+    g = 0.015
+    wl.rooms = dict(par=np.stack([par0, par1]), wall_area=wl.rooms["wall_area"], Ta0=np.array([292.0, 289.0]),
+                    Pa0=np.array([1400.0, 1100.0]), emissivity=emis, view=np.array([0.2, 0.3]),
+                    links=[(0, 1, g)])
+    o = oracle_mod.Oracle(wl, n_threads=1)
+    o.run(25)
+    n = o.step
+    room0 = o.room[:2].copy()
+    surf_prev = [(o.wall(w, "T", 1)[-1], o.wall(w, "P", 1)[-1]) for w in range(W)]
+    surf_n = [(o.wall(w, "T", 0)[-1], o.wall(w, "P", 0)[-1]) for w in range(W)]
+    r = o.run(1, want_balance=True)
+    room1 = o.room[:2].copy()
+    surf_next = [(o.wall(w, "T", 0)[-1], o.wall(w, "P", 0)[-1]) for w in range(W)]
+    Lv, dt = wl.Lv, wl.dt
+    t = wl.t0 + n * dt
+    A = wl.rooms["wall_area"]
+    sig = 5.670374419e-8
+    lhs = {"T": 0.0, "P": 0.0}
+    rhs = {"T": 0.0, "P": 0.0}
+    mag = {"T": 0.0, "P": 0.0}
+    bal, flux = r["balance"], r["flux"]
+    for k, fld in enumerate(("T", "P")):
+        lhs[fld] += float(np.sum(A * bal[:, k, 0]))
+        for term in (np.sum(A * flux[:, 0, k]), np.sum(A * bal[:, k, 2])):
+            rhs[fld] += float(term)
+            mag[fld] += abs(float(term))
+        mag[fld] += float(np.sum(A * bal[:, k, 3]))
+    zone_of = wl.bc_room[:, 1]
+    for z in range(2):
+        f = dict(zip(wk.ROOM_FIELDS, wl.rooms["par"][z]))
+        V, rho, Pref = f["volume"], f["rho_a"], f["Pv_ref"]
+        gv = rho * V * f["ach"] / 3600.0
+        T_out = f["T_out_mean"] + f["T_out_amp"] * np.sin(2 * np.pi * t / f["period"] + f["phase_T"])
+        P_out = f["P_out_mean"] + f["P_out_amp"] * np.sin(2 * np.pi * t / f["period"] + f["phase_P"])
+        Ta_m, Ta_n, Ta_p = room0[z, 0], room0[z, 1], room1[z, 1]
+        Pa_m, Pa_n, Pa_p = room0[z, 2], room0[z, 3], room1[z, 3]
+        Ta_s, Pa_s = 0.5 * (Ta_p + Ta_m), 0.5 * (Pa_p + Pa_m)
+        o_z = 1 - z
+        To_n, wo_n = room0[o_z, 1], room0[o_z, 3] / Pref
+        store = {"T": rho * V * (f["cp_a"] + f["cp_v"] * Pa_n / Pref) * (Ta_p - Ta_m) / (2 * dt),
+                 "P": rho * V / Pref * (Pa_p - Pa_m) / (2 * dt)}
+        src = {"T": [f["Q_gain"], Lv * f["g_vap"], gv * f["cp_a"] * (T_out - Ta_s), Lv * gv * (P_out / Pref - Pa_s / Pref),
+                     g * f["cp_a"] * (To_n - Ta_s), Lv * g * (wo_n - Pa_s / Pref)],
+               "P": [f["g_vap"], gv * (P_out / Pref - Pa_s / Pref), g * (wo_n - Pa_s / Pref)]}
+        for fld in ("T", "P"):
+            lhs[fld] += store[fld]
+            mag[fld] += abs(store[fld])
+            for x in src[fld]:
+                rhs[fld] += x
+                mag[fld] += abs(x)
+        # room-face coupling defects of this zone's walls
+        for w in np.where(zone_of == z)[0]:
+            hT, hM = wl.bc_par[w, 1, 0], wl.bc_par[w, 1, 1]
+            sT_bar = 0.5 * (surf_next[w][0] + surf_prev[w][0])
+            sP_bar = 0.5 * (surf_next[w][1] + surf_prev[w][1])
+            dPp = (Pa_n - sP_bar) + (surf_n[w][1] - Pa_s)
+            cT = A[w] * (hT * ((Ta_n - sT_bar) + (surf_n[w][0] - Ta_s)) + Lv * hM * dPp)
+            cP = A[w] * hM * dPp
+            # radiation deposited in the wall: T'^4 - Ts^4 = (T'^2 + Ts^2)(T' + Ts)(T' - Ts), conductance and
+            # the other faces' values of level n, the face's own value averaged over the step
+            others = [u for u in np.where(zone_of == z)[0] if u != w]
+            c = wl.rooms["view"][z] * emis[w, 1] * sig
+            Ts = surf_n[w][0]
+            qr = c * sum((surf_n[u][0] ** 2 + Ts ** 2) * (surf_n[u][0] + Ts) * (surf_n[u][0] - sT_bar) for u in others)
+            rhs["T"] += cT + A[w] * qr
+            rhs["P"] += cP
+            mag["T"] += abs(cT) + abs(A[w] * qr)
+            mag["P"] += abs(cP)
+    for fld in ("T", "P"):
+        assert abs(lhs[fld] - rhs[fld]) <= 1e-12 * mag[fld], (fld, lhs[fld], rhs[fld], mag[fld])
