@@ -201,6 +201,24 @@ HYGRO_API hygro_status hygro_set_bc(hygro_ctx *ctx, int32_t face, const hygro_bc
 HYGRO_API hygro_status hygro_set_rooms(hygro_ctx *ctx, int32_t n_rooms, const hygro_room *rooms,
                                        const double *wall_area);
 
+/* Long-wave radiation among the wall surfaces of each room (paper Sec. 2: q_rw, the heat a room face
+ * receives, = s eps sigma sum over the room's faces of (T'^4 - Ts^4), sigma the Stefan-Boltzmann constant).
+ * emissivity[w][f] (host, [n_walls][2], in [0, 1]) applies to room faces; view[r] (host, [n_rooms], in
+ * [0, 1]) is the view factor s of room r. Each term is taken as h' (T' - Ts) with the conductance
+ * h' = s eps sigma (T'^2 + Ts^2)(T' + Ts) (an exact factorisation): h' and the other faces' T' of level n,
+ * the face's own Ts averaged over levels n+1 and n-1 as for the convective exchange (the level-n form of
+ * the face's own term is unstable in DF). Radiating faces run the general code variant. hygro_set_rooms
+ * clears the radiation; HYGRO_E_STATE before it. */
+HYGRO_API hygro_status hygro_set_radiation(hygro_ctx *ctx, const double *emissivity, const double *view);
+
+/* Interzone airflow (paper Sec. 5.1: Q_inz = g (cpa (T_j - T_i)) + Lv g (w_j - w_i), G_inz = g (w_j - w_i) in
+ * both rooms of a link; the paper writes cw for the air's heat capacity, read as the room's cp_a).
+ * zones[l] (host, [n_links][2]) two different rooms, flow[l] >= 0 kg/s of air exchanged both ways. A room's
+ * own values enter as the mean of levels n+1 and n-1 (the room node's DF form), the linked room's as level
+ * n. Rooms linked together run in one block: a linked group holds at most 4 rooms, 3 links per room and 14
+ * walls in all (hygro_run reports HYGRO_E_STATE otherwise). hygro_set_rooms clears the links. */
+HYGRO_API hygro_status hygro_set_interzone(hygro_ctx *ctx, int32_t n_links, const int32_t *zones, const double *flow);
+
 /* Set an option (HYGRO_OPT_*) of the context; it applies from the next run. */
 HYGRO_API hygro_status hygro_set_option(hygro_ctx *ctx, int32_t option, int64_t value);
 

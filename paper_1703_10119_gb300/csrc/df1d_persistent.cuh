@@ -69,10 +69,13 @@ struct LaneCtx {
 // wall (see LaneCtx; only with one layer per lane).
 // With IFACE && SIMPLE, sft / srt hold this lane's per-slot right thermal face and reciprocal T
 // denominator (stride 32 between slots), set up once per wall.
-template <typename real, int K, bool IFACE, bool SIMPLE>
+// VARH (general variants of room walls): the surface thermal conductances of faces 0 and 1 are hT0v, hT1v
+// of this step instead of the constant hT0, hT1 (a room face exchanging long-wave radiation).
+template <typename real, int K, bool IFACE, bool SIMPLE, bool VARH = false>
 __device__ __forceinline__ void df_step(real (&Tp)[K], const real (&Tc)[K], real (&Pp)[K], const real (&Pc)[K],
                                         const LaneCtx<real> &L, const real *tab, const real fT, const real fP,
-                                        const real Lv, real &sT, real &sP, const real *sft, const real *srt)
+                                        const real Lv, real &sT, real &sP, const real *sft, const real *srt,
+                                        const real hT0v = real(0), const real hT1v = real(0))
 {
     constexpr unsigned FULL = 0xffffffffu;
     const real half = real(0.5);
@@ -103,7 +106,7 @@ __device__ __forceinline__ void df_step(real (&Tp)[K], const real (&Tc)[K], real
     }
     if (L.any_lb_iface && L.iface_right) FMb = face_harmonic(khM_last, rkM);
     FMb = L.has_right ? FMb : L.hM1;
-    if (!SIMPLE) FTb = L.has_right ? FTb : L.hT1;
+    if (!SIMPLE) FTb = L.has_right ? FTb : (VARH ? hT1v : L.hT1);
     // left boundary: the previous lane's last node and its right face, or before the face-0 surface
     // the ambient air through hM0 / hT0
     real lT = __shfl_up_sync(FULL, lastT, 1);
@@ -117,7 +120,7 @@ __device__ __forceinline__ void df_step(real (&Tp)[K], const real (&Tc)[K], real
     else
         FTl0 = __shfl_up_sync(FULL, FTb, 1);
     FMl0 = L.has_left ? FMl0 : L.hM0;
-    if (!SIMPLE) FTl0 = L.has_left ? FTl0 : L.hT0;
+    if (!SIMPLE) FTl0 = L.has_left ? FTl0 : (VARH ? hT0v : L.hT0);
 
     LayerC<real> c = L.c0;         // constants of the current slot's layer
     int lcur = L.l0;
@@ -288,7 +291,8 @@ struct RoomConst {
     double rhoV, gv, Pref;
     double a_p, k_p;          // vapour node: capacity rho V / Pv_ref / (2 dt), conductance gv / Pv_ref + sum A hM
     double at0, at1;          // heat capacity rho V (cp_a + cp_v Pv / Pv_ref) / (2 dt) = at0 + at1 Pv
-    double k_t;               // gv cp_a + sum A hT
+    double k_t;               // gv cp_a + sum A hT + G cp_a
+    double G;                 // interzone airflow of the room, kg/s (sum over its links)
 };
 
 static __device__ __forceinline__ RoomConst room_const(const RoomInfo &ri, const FaceInfo *faces, double dt)
@@ -308,10 +312,12 @@ static __device__ __forceinline__ RoomConst room_const(const RoomInfo &ri, const
     k.gv = k.rhoV * q[RP_ACH] / 3600.0;
     k.Pref = q[RP_PVREF];
     k.a_p = k.rhoV / k.Pref / (2.0 * dt);
-    k.k_p = k.gv / k.Pref + k.sAhM;
+    k.G = 0.0;
+    for (int l = 0; l < ri.n_links; ++l) k.G += ri.link_g[l];
+    k.k_p = k.gv / k.Pref + k.sAhM + k.G / k.Pref;
     k.at0 = k.rhoV * q[RP_CPA] / (2.0 * dt);
     k.at1 = k.rhoV * q[RP_CPV] / k.Pref / (2.0 * dt);
-    k.k_t = k.gv * q[RP_CPA] + k.sAhT;
+    k.k_t = k.gv * q[RP_CPA] + k.sAhT + k.G * q[RP_CPA];
     return k;
 }
 
@@ -343,8 +349,10 @@ static __device__ __forceinline__ void room_air_chunk(RoomShared &rs, const Room
 //   a_p (Pa+ - Pa-) = srcP + sum A hM Pvs - k_p Pabar,   k_p = gv / Pv_ref + sum A hM
 //   a_t (Ta+ - Ta-) = srcT + sum A hT Ts + Lv sum A hM Pvs - Lv k_p Pabar - k_t Tabar,  k_t = gv cp_a + sum A hT
 // i is the step's entry in the chunk, b the buffer of the level-n surface values.
+// Interzone airflow (Sec. 5.1, Q_inz and G_inz) enters with the linked rooms' air of level n (all_rs: the
+// block's rooms, slot b): the sources sum g cp_a T_o and sum g w_o, the room's own value in k_t and k_p.
 static __device__ void room_update(RoomShared &rs, const RoomConst &k, const RoomInfo &ri, int i, int b, double dt,
-                                   double Lv)
+                                   double Lv, const RoomShared *all_rs)
 {
     const double *q = ri.par;
     double AhTTs = 0.0, AhMPs = 0.0;
@@ -352,11 +360,19 @@ static __device__ void room_update(RoomShared &rs, const RoomConst &k, const Roo
         AhTTs = fma(k.AhT[w], rs.surfT[b][w], AhTTs);
         AhMPs = fma(k.AhM[w], rs.surfP[b][w], AhMPs);
     }
+    double GT = 0.0, Gw = 0.0;
+    for (int l = 0; l < ri.n_links; ++l) {
+        const RoomShared &o = all_rs[ri.link_slot[l]];
+        GT = fma(ri.link_g[l], o.airT[b], GT);
+        Gw = fma(ri.link_gw[l], o.airP[b], Gw);
+    }
+    const double srcP = rs.srcP[i] + Gw;
+    const double srcT = rs.srcT[i] + q[RP_CPA] * GT + Lv * Gw;
     if (q[RP_SCHEME] == (double)HYGRO_ROOM_EULER) {
         // explicit Euler of Sec. 5.2: every term at level n
-        const double Pa_n = rs.Pa_c + dt * k.Pref / k.rhoV * (rs.srcP[i] + AhMPs - k.k_p * rs.Pa_c);
+        const double Pa_n = rs.Pa_c + dt * k.Pref / k.rhoV * (srcP + AhMPs - k.k_p * rs.Pa_c);
         const double CT = 2.0 * dt * fma(k.at1, rs.Pa_c, k.at0);
-        const double rhs = rs.srcT[i] + AhTTs + Lv * AhMPs - Lv * k.k_p * rs.Pa_c - k.k_t * rs.Ta_c;
+        const double rhs = srcT + AhTTs + Lv * AhMPs - Lv * k.k_p * rs.Pa_c - k.k_t * rs.Ta_c;
         const double Ta_n = rs.Ta_c + dt / CT * rhs;
         rs.Ta_p = rs.Ta_c;
         rs.Ta_c = Ta_n;
@@ -364,10 +380,10 @@ static __device__ void room_update(RoomShared &rs, const RoomConst &k, const Roo
         rs.Pa_c = Pa_n;
         return;
     }
-    const double Pa_n = (fma(k.a_p - 0.5 * k.k_p, rs.Pa_p, rs.srcP[i]) + AhMPs) / (k.a_p + 0.5 * k.k_p);
+    const double Pa_n = (fma(k.a_p - 0.5 * k.k_p, rs.Pa_p, srcP) + AhMPs) / (k.a_p + 0.5 * k.k_p);
     const double Pa_bar = 0.5 * (Pa_n + rs.Pa_p);
     const double a_t = fma(k.at1, rs.Pa_c, k.at0);
-    const double rhs = rs.srcT[i] + AhTTs + Lv * (AhMPs - k.k_p * Pa_bar);
+    const double rhs = srcT + AhTTs + Lv * (AhMPs - k.k_p * Pa_bar);
     const double Ta_n = fma(a_t - 0.5 * k.k_t, rs.Ta_p, rhs) / (a_t + 0.5 * k.k_t);
     rs.Ta_p = rs.Ta_c;
     rs.Ta_c = Ta_n;
@@ -531,10 +547,17 @@ __device__ __forceinline__ void lane_setup(const DevCtx<real> &d, const WallInfo
     (void)Lv;
 }
 
+// Room walls (ROOM): rs is the room's shared state, room_face the wall's face on the room, room_slot its
+// position among the room's walls, ri the room (long-wave exchange: its view factor and the face's
+// emissivity). A radiating room face (general variants only) receives q_rw = sum over the room's other
+// faces of h' (T' - Ts), h' = s eps sigma (T'^2 + Ts^2)(T' + Ts), with h' and T' of level n and Ts averaged
+// over levels n+1 and n-1 like the convective exchange: the face's thermal conductance for the step is
+// hT + hR (hR = sum h') and its air value (hT Ta + qR) / (hT + hR) (qR = sum h' T').
 template <typename real, int K, bool IFACE, bool SIMPLE, bool ROOM = false>
 __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi, int w, const real *tab, int64_t n0,
                                       int32_t n_steps, int32_t sample_every, real *samples, real *sft, real *srt,
-                                      RoomShared *rs = nullptr, int room_face = -1)
+                                      RoomShared *rs = nullptr, int room_face = -1, int room_slot = 0,
+                                      const RoomInfo *ri = nullptr)
 {
     constexpr unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -601,9 +624,14 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
     // values (both double-buffered by level parity); one block barrier per step.
     const int room_lane = room_face == 0 ? 0 : Wl - 1;
     const double Tref_d = (double)Tref, Pref_d = (double)Pref;
-    const int wib = threadIdx.x >> 5;
+    // long-wave exchange of the room face (warp-uniform): s eps sigma of this face
+    const double rad_c = (ROOM && !SIMPLE && ri != nullptr) ? ri->view * ri->emis[room_slot] * 5.670374419e-8 : 0.0;
+    const bool radiating = rad_c > 0.0;
+    const real hT_room = room_face == 0 ? L.hT0 : L.hT1;   // the room face's convective conductance (room lane)
     // sums over the current batch of the lane's time-averaged surface values, and (room walls) of its air
-    real acc_sT = real(0), acc_sP = real(0), acc_fT = real(0), acc_fP = real(0);
+    // and of its radiative exchange
+    real acc_sT = real(0), acc_sP = real(0), acc_fT = real(0), acc_fP = real(0), acc_rad = real(0);
+    real last_rad = real(0);
     int64_t n_cur = n0;
     auto publish = [&](const real (&T_)[K], const real (&P_)[K], int b) {
         if (lane == room_lane) {
@@ -614,17 +642,37 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
                 ts = k == slot ? T_[k] : ts;
                 ps = k == slot ? P_[k] : ps;
             }
-            rs->surfT[b][wib] = Tref_d + (double)ts;
-            rs->surfP[b][wib] = Pref_d + (double)ps;
+            rs->surfT[b][room_slot] = Tref_d + (double)ts;
+            rs->surfP[b][room_slot] = Pref_d + (double)ps;
         }
     };
     auto one_step = [&](auto &Tp_, auto &Tc_, auto &Pp_, auto &Pc_, real bT, real bP, int src) {
         real fT = __shfl_sync(FULL, bT, src);
         real fP = __shfl_sync(FULL, bP, src);
+        real fT_step = fT, hT_step = hT_room, hR = real(0), qRd = real(0);
         if (ROOM) {
             if (lane == room_lane) {
                 fT = (real)(rs->airT[n_cur & 1] - Tref_d);
                 fP = (real)(rs->airP[n_cur & 1] - Pref_d);
+                fT_step = fT;
+                if (radiating) {
+                    // radiative conductances to the room's other faces at level n, in FP64
+                    const int b = (int)(n_cur & 1);
+                    const double Ts = rs->surfT[b][room_slot];
+                    double sh = 0.0, shT = 0.0;
+                    for (int u = 0; u < ri->n_walls; ++u) {
+                        if (u == room_slot) continue;
+                        const double To = rs->surfT[b][u];
+                        const double h = rad_c * (To * To + Ts * Ts) * (To + Ts);
+                        sh += h;
+                        shT = fma(h, To, shT);
+                    }
+                    hR = (real)sh;
+                    qRd = (real)(shT - sh * Tref_d);   // sum h' (T' - T_ref): the deviation form
+                    const double hT = (double)hT_room;
+                    fT_step = (real)((hT * (double)fT + (shT - sh * Tref_d)) / (hT + sh));
+                    hT_step = (real)(hT + sh);
+                }
             }
             acc_fT += fT;
             acc_fP += fP;
@@ -632,7 +680,18 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
             last_fP = fP;
         }
         real sT, sP;
-        df_step<real, K, IFACE, SIMPLE>(Tp_, Tc_, Pp_, Pc_, L, tab, fT, fP, Lv, sT, sP, sft, srt);
+        if constexpr (ROOM && !SIMPLE) {
+            const real hT0v = room_face == 0 ? hT_step : L.hT0, hT1v = room_face == 1 ? hT_step : L.hT1;
+            df_step<real, K, IFACE, SIMPLE, true>(Tp_, Tc_, Pp_, Pc_, L, tab, fT_step, fP, Lv, sT, sP, sft, srt, hT0v,
+                                                  hT1v);
+        } else {
+            df_step<real, K, IFACE, SIMPLE>(Tp_, Tc_, Pp_, Pc_, L, tab, fT, fP, Lv, sT, sP, sft, srt);
+        }
+        if (ROOM) {
+            // radiation received over the step: sum h' (T' - Tbar) = qRd - hR Tbar (zero where none)
+            last_rad = fma(-hR, sT, qRd);
+            acc_rad += last_rad;
+        }
         acc_sT += sT;
         acc_sP += sP;
         last_sT = sT;
@@ -660,7 +719,7 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
         bP = real(0);
         if (f_ambient) ambient_at(ff, d.noise, n0 + s + (lane % kForcingBatch), d.t0, d.dt, bT, bP);
         acc_sT = acc_sP = real(0);
-        if (ROOM) acc_fT = acc_fP = real(0);
+        if (ROOM) acc_fT = acc_fP = acc_rad = real(0);
         int i = 0;
         for (; i + 1 < cnt; i += 2) {
             one_step(Ta, Tb, Pa, Pb, bT, bP, src_base + i);
@@ -693,7 +752,7 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
             // g = hM (Pv_inf - Pvbar) + g_inf
             const real rc = (real)cnt;
             const real hm = L.hMs * (sfP - acc_sP);
-            const real acc_q = fma(L.hTs, sfT - acc_sT, fma(Lv, hm, rc * L.qs));
+            const real acc_q = fma(L.hTs, sfT - acc_sT, fma(Lv, hm, rc * L.qs)) + (ROOM ? acc_rad : real(0));
             const real acc_g = fma(rc, L.gs, hm);
             const real xq = acc_q * dt_r, xg = acc_g * dt_r;
             real t = kq + xq;
@@ -735,7 +794,7 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
         last_fP = __shfl_sync(FULL, bP, last_src);
     }
     const real last_hm = L.hMs * (last_fP - last_sP);
-    const real last_q = fma(L.hTs, last_fT - last_sT, fma(Lv, last_hm, L.qs));
+    const real last_q = fma(L.hTs, last_fT - last_sT, fma(Lv, last_hm, L.qs)) + (ROOM ? last_rad : real(0));
     const real last_g = last_hm + L.gs;
     if (my_face >= 0 && n_steps > 0) {
         d.cumul[(size_t)w * 4 + my_face * 2 + 0] = cum_q;

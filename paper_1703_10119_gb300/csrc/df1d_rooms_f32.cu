@@ -4,9 +4,13 @@
 namespace hygro {
 
 cudaError_t launch_rooms_f32(const DevCtx<float> &d, int64_t n0, int32_t n_steps, int32_t sample_every,
-                             float *samples, int n_rooms, int warps, cudaStream_t s)
+                             float *samples, int n_groups, int warps, cudaStream_t s)
 {
-    df1d_room_kernel<float><<<n_rooms, (warps + 1) * 32, 0, s>>>(d, n0, n_steps, sample_every, samples);
+    if (warps <= HYGRO_MAX_ROOM_WALLS + 1)
+        df1d_room_kernel<float, HYGRO_MAX_ROOM_WALLS + 1>
+            <<<n_groups, warps * 32, 0, s>>>(d, n0, n_steps, sample_every, samples);
+    else
+        df1d_room_kernel<float, kRoomBlockWarps><<<n_groups, warps * 32, 0, s>>>(d, n0, n_steps, sample_every, samples);
     return cudaGetLastError();
 }
 

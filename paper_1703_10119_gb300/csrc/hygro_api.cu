@@ -239,6 +239,12 @@ struct hygro_ctx {
     bool have_rooms = false;
     RoomInfo *d_rooms = nullptr;
     size_t rooms_cap = 0;
+    std::vector<double> face_emis;   // [W][2] emissivity of room faces (hygro_set_radiation; empty: none)
+    std::vector<double> room_view;   // [n_rooms] view factor s of each room
+    std::vector<int32_t> link_zone;  // [n_links][2] (hygro_set_interzone)
+    std::vector<double> link_flow;   // [n_links] kg/s
+    RoomGroup *d_groups = nullptr;   // room kernel blocks: rooms alone or linked by airflow
+    int n_groups = 0;
     double *d_room_state = nullptr;
     bool any_room_walls = false;   // some wall has a face on a room (those walls run in the room kernel)
     int room_warps = 1;            // warps of the room kernel's blocks (most walls of one room)
@@ -296,7 +302,7 @@ void free_all(hygro_ctx *c)
 {
     void *ptrs[] = {c->dT[0], c->dT[1], c->dP[0], c->dP[1], c->d_walls, c->d_faces, c->d_layer_tab,
                     c->d_layer_first, c->d_noise, c->d_Tref, c->d_Pref, c->d_cumul, c->d_flast,
-                    c->d_nonfinite, c->d_order, c->d_block_off, c->d_trace, c->d_rooms, c->d_room_state, c->d_node_wall, c->d_node_layer, c->d_samples, c->d_layer_law};
+                    c->d_nonfinite, c->d_order, c->d_block_off, c->d_trace, c->d_rooms, c->d_room_state, c->d_node_wall, c->d_node_layer, c->d_samples, c->d_layer_law, c->d_groups};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->d_stage) cudaFree(c->d_stage);
@@ -336,6 +342,7 @@ DevCtx<real> make_dev(const hygro_ctx *c)
     d.round_size = c->round_size;
     d.trace = c->d_trace;
     d.rooms = c->d_rooms;
+    d.groups = c->d_groups;
     d.room_state = c->d_room_state;
     d.n_rooms = (int32_t)c->rooms.size();
     d.node_wall = c->d_node_wall;
@@ -568,6 +575,50 @@ hygro_status build_schedule(hygro_ctx *c)
     for (int w = 0; w < W; ++w)
         if (in_room[w]) c->any_room_walls = true;
     if (NR > 0) {
+        // rooms linked by interzone airflow share a block: the groups are the link graph's components
+        std::vector<int> root(NR);
+        for (int r = 0; r < NR; ++r) root[r] = r;
+        auto find = [&](int r) {
+            while (root[r] != r) r = root[r] = root[root[r]];
+            return r;
+        };
+        const int NL = (int)c->link_flow.size();
+        for (int l = 0; l < NL; ++l) root[find(c->link_zone[2 * l])] = find(c->link_zone[2 * l + 1]);
+        std::vector<std::vector<int>> comp(NR);
+        for (int r = 0; r < NR; ++r) comp[find(r)].push_back(r);
+        std::vector<int> slot_of(NR, 0);
+        std::vector<RoomGroup> groups;
+        for (int r = 0; r < NR; ++r) {
+            if (comp[r].empty()) continue;
+            RoomGroup g;
+            memset(&g, 0, sizeof g);
+            const int nz = (int)comp[r].size();
+            int warps = 0;
+            for (int z = 0; z < nz && z < kMaxGroupZones; ++z) {
+                g.zone[z] = comp[r][z];
+                slot_of[comp[r][z]] = z;
+                g.wall_warp0[z] = warps;
+                warps += (int)members[comp[r][z]].size();
+            }
+            g.n_zones = std::min(nz, kMaxGroupZones);
+            g.air_warp0 = warps;
+            g.n_warps = warps + g.n_zones;
+            const int cap = nz > 1 ? kRoomBlockWarps : HYGRO_MAX_ROOM_WALLS + 1;
+            if ((nz > kMaxGroupZones || g.n_warps > cap) && c->room_issue.empty()) {
+                snprintf(msg, sizeof msg,
+                         "rooms linked by airflow with room %d: %d rooms and %d walls; a linked group holds at most %d "
+                         "rooms and %d walls plus one air warp per room",
+                         comp[r][0], nz, warps, kMaxGroupZones, kRoomBlockWarps);
+                c->room_issue = msg;
+            }
+            c->room_warps = std::max(c->room_warps, g.n_warps);
+            groups.push_back(g);
+        }
+        c->n_groups = (int)groups.size();
+        if (c->d_groups) cudaFree(c->d_groups);
+        c->d_groups = nullptr;
+        CUDA_TRY(c, dalloc(&c->d_groups, groups.size()));
+        CUDA_TRY(c, cudaMemcpy(c->d_groups, groups.data(), groups.size() * sizeof(RoomGroup), cudaMemcpyHostToDevice));
         std::vector<RoomInfo> ri(NR);
         for (int r = 0; r < NR; ++r) {
             RoomInfo &o = ri[r];
@@ -596,7 +647,28 @@ hygro_status build_schedule(hygro_ctx *c)
             o.par[RP_POFF] = q.pulse_off;
             o.par[RP_PPER] = q.pulse_period;
             o.par[RP_SCHEME] = (double)c->room_scheme;
-            c->room_warps = std::max(c->room_warps, (int)o.n_walls);
+            // long-wave exchange among the room's faces
+            o.view = c->room_view.empty() ? 0.0 : c->room_view[r];
+            for (int i = 0; i < o.n_walls; ++i)
+                o.emis[i] = c->face_emis.empty() ? 0.0 : c->face_emis[(size_t)o.wall[i] * 2 + o.face[i]];
+            // interzone links to rooms of the same group
+            o.n_links = 0;
+            for (int l = 0; l < NL; ++l)
+                for (int e = 0; e < 2; ++e) {
+                    if (c->link_zone[2 * l + e] != r) continue;
+                    const int other = c->link_zone[2 * l + 1 - e];
+                    if (o.n_links >= kMaxZoneLinks) {
+                        if (c->room_issue.empty()) {
+                            snprintf(msg, sizeof msg, "room %d has more than %d interzone links", r, kMaxZoneLinks);
+                            c->room_issue = msg;
+                        }
+                        continue;
+                    }
+                    o.link_slot[o.n_links] = slot_of[other];
+                    o.link_g[o.n_links] = c->link_flow[l];
+                    o.link_gw[o.n_links] = c->link_flow[l] / c->rooms[other].Pv_ref;
+                    ++o.n_links;
+                }
         }
         CUDA_TRY(c, cudaMemcpy(c->d_rooms, ri.data(), ri.size() * sizeof(RoomInfo), cudaMemcpyHostToDevice));
     }
@@ -655,16 +727,16 @@ hygro_status launch_steps(hygro_ctx *c, int64_t n_steps, int se, void *dsamp)
                     CUDA_TRY(c, launch_persistent_f64(make_dev<double>(c), c->step + done, (int32_t)len, se, sp,
                                                       c->grid_persistent, c->stream));
                 if (c->any_room_walls)
-                    CUDA_TRY(c, launch_rooms_f64(make_dev<double>(c), c->step + done, (int32_t)len, se, sp, NR,
-                                                 c->room_warps, c->stream));
+                    CUDA_TRY(c, launch_rooms_f64(make_dev<double>(c), c->step + done, (int32_t)len, se, sp,
+                                                 c->n_groups, c->room_warps, c->stream));
             } else {
                 float *sp = dsamp ? (float *)dsamp + soff : nullptr;
                 if (c->n_free > 0)
                     CUDA_TRY(c, launch_persistent_f32(make_dev<float>(c), c->step + done, (int32_t)len, se, sp,
                                                       c->grid_persistent, c->stream));
                 if (c->any_room_walls)
-                    CUDA_TRY(c, launch_rooms_f32(make_dev<float>(c), c->step + done, (int32_t)len, se, sp, NR,
-                                                 c->room_warps, c->stream));
+                    CUDA_TRY(c, launch_rooms_f32(make_dev<float>(c), c->step + done, (int32_t)len, se, sp,
+                                                 c->n_groups, c->room_warps, c->stream));
             }
             done += len;
         }
@@ -988,6 +1060,10 @@ hygro_status hygro_set_rooms(hygro_ctx *c, int32_t n_rooms, const hygro_room *ro
         c->rooms_cap = (size_t)n_rooms;
     }
     c->rooms.assign(rooms, rooms + n_rooms);
+    c->face_emis.clear();
+    c->room_view.clear();
+    c->link_zone.clear();
+    c->link_flow.clear();
     if (n_rooms > 0)
         c->wall_area.assign(wall_area, wall_area + c->W);
     else
@@ -1000,6 +1076,46 @@ hygro_status hygro_set_rooms(hygro_ctx *c, int32_t n_rooms, const hygro_room *ro
     if (n_rooms > 0)
         CUDA_TRY(c, cudaMemcpy(c->d_room_state, st.data(), st.size() * sizeof(double), cudaMemcpyHostToDevice));
     c->have_rooms = true;
+    return build_schedule(c);
+}
+
+hygro_status hygro_set_radiation(hygro_ctx *c, const double *emissivity, const double *view)
+{
+    if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    FAULT_POINT(c, "hygro_set_radiation");
+    if (!c->have_rooms || c->rooms.empty()) return fail(c, HYGRO_E_STATE, "hygro_set_rooms must come first");
+    if (emissivity == nullptr || view == nullptr) return fail(c, HYGRO_E_INVALID, "emissivity and view are required");
+    for (int i = 0; i < 2 * c->W; ++i)
+        if (!(emissivity[i] >= 0.0 && emissivity[i] <= 1.0))
+            return fail(c, HYGRO_E_INVALID, "wall %d face %d: emissivity must be in [0, 1]", i / 2, i % 2);
+    for (size_t r = 0; r < c->rooms.size(); ++r)
+        if (!(view[r] >= 0.0 && view[r] <= 1.0)) return fail(c, HYGRO_E_INVALID, "room %zu: view factor must be in [0, 1]", r);
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->face_emis.assign(emissivity, emissivity + 2 * c->W);
+    c->room_view.assign(view, view + c->rooms.size());
+    return build_schedule(c);
+}
+
+hygro_status hygro_set_interzone(hygro_ctx *c, int32_t n_links, const int32_t *zones, const double *flow)
+{
+    if (c == nullptr) return fail(nullptr, HYGRO_E_INVALID, "ctx is NULL");
+    FAULT_POINT(c, "hygro_set_interzone");
+    if (!c->have_rooms || c->rooms.empty()) return fail(c, HYGRO_E_STATE, "hygro_set_rooms must come first");
+    if (n_links < 0 || (n_links > 0 && (zones == nullptr || flow == nullptr)))
+        return fail(c, HYGRO_E_INVALID, "n_links must be >= 0, zones and flow given");
+    const int NR = (int)c->rooms.size();
+    for (int l = 0; l < n_links; ++l) {
+        const int a = zones[2 * l], b = zones[2 * l + 1];
+        if (a < 0 || a >= NR || b < 0 || b >= NR || a == b)
+            return fail(c, HYGRO_E_INVALID, "link %d: rooms must be two different rooms in 0..%d", l, NR - 1);
+        if (!(flow[l] >= 0.0) || !std::isfinite(flow[l]))
+            return fail(c, HYGRO_E_INVALID, "link %d: flow must be finite and >= 0", l);
+    }
+    if (cudaSetDevice(c->device) != cudaSuccess) return fail(c, HYGRO_E_CUDA, "cudaSetDevice failed");
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    c->link_zone.assign(zones, zones + 2 * n_links);
+    c->link_flow.assign(flow, flow + n_links);
     return build_schedule(c);
 }
 

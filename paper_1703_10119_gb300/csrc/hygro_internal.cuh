@@ -81,7 +81,11 @@ struct FaceInfo {
     int64_t n_hi;         // first step whose position reaches the last table entry (held from there on)
 };
 
-// A room and the walls facing it (room kernel: one block per room, one warp per wall).
+constexpr int kMaxZoneLinks = 3;     // interzone links of one room
+constexpr int kMaxGroupZones = 4;    // rooms of one block of the room kernel (rooms linked by airflow)
+constexpr int kRoomBlockWarps = 16;  // warps of the room kernel's block for rooms linked by airflow
+
+// A room and the walls facing it (room kernel: one warp per wall, one more for the room air).
 struct RoomInfo {
     int32_t n_walls;
     int32_t wall[HYGRO_MAX_ROOM_WALLS];   // ascending wall indices
@@ -89,6 +93,25 @@ struct RoomInfo {
     double area[HYGRO_MAX_ROOM_WALLS];    // m^2
     double par[21];                       // hygro_room fields volume .. Pv_ref, the room scheme, then
                                           // period_P, g_pulse, pulse_on, pulse_off, pulse_period
+    // long-wave exchange among the room's wall surfaces: view factor s (0: none) and each wall face's
+    // emissivity
+    double view;
+    double emis[HYGRO_MAX_ROOM_WALLS];
+    // interzone airflow: the linked rooms (their positions in the block's group) and the flows, kg/s
+    int32_t n_links;
+    int32_t link_slot[kMaxZoneLinks];
+    double link_g[kMaxZoneLinks];
+    double link_gw[kMaxZoneLinks];        // link_g / Pv_ref of the linked room (its humidity ratio w = Pv / Pv_ref)
+};
+
+// The rooms one block of the room kernel runs together (rooms linked by airflow share a block). Warps
+// wall_warp0[z] .. wall_warp0[z] + n_walls - 1 advance room z's walls, warp air_warp0 + z its air.
+struct RoomGroup {
+    int32_t n_zones;
+    int32_t zone[kMaxGroupZones];
+    int32_t wall_warp0[kMaxGroupZones];
+    int32_t air_warp0;
+    int32_t n_warps;
 };
 enum { RP_VOL = 0, RP_ACH, RP_QGAIN, RP_GVAP, RP_TMEAN, RP_TAMP, RP_PMEAN, RP_PAMP, RP_PERIOD, RP_PHT, RP_PHP,
        RP_RHOA, RP_CPA, RP_CPV, RP_PVREF, RP_SCHEME, RP_PERIODP, RP_GPULSE, RP_PON, RP_POFF, RP_PPER };
@@ -114,6 +137,7 @@ struct DevCtx {
     int32_t round_size;          // walls per round (warp i of a block takes entry i of each of its rounds)
     unsigned long long *trace;   // optional [W][4]: SM id << 32 | block << 8 | warp, start ns, end ns, steps
     const RoomInfo *rooms;       // [n_rooms] (room kernel)
+    const RoomGroup *groups;     // [n_groups] (room kernel: one block each)
     double *room_state;          // [n_rooms][4]: Ta(n-1), Ta(n), Pa(n-1), Pa(n)
     int32_t n_rooms;
     const int32_t *node_wall;    // [total nodes] (plain kernel)
@@ -148,10 +172,12 @@ cudaError_t launch_persistent_f64(const DevCtx<double> &d, int64_t n0, int32_t n
 cudaError_t occupancy_persistent_f32(int *blocks_per_sm);
 cudaError_t occupancy_persistent_f64(int *blocks_per_sm);
 
+// n_groups blocks of `warps` warps (<= HYGRO_MAX_ROOM_WALLS + 1: the single-room form; <= kRoomBlockWarps: the
+// form for rooms linked by airflow).
 cudaError_t launch_rooms_f32(const DevCtx<float> &d, int64_t n0, int32_t n_steps, int32_t sample_every,
-                             float *samples, int n_rooms, int warps, cudaStream_t s);
+                             float *samples, int n_groups, int warps, cudaStream_t s);
 cudaError_t launch_rooms_f64(const DevCtx<double> &d, int64_t n0, int32_t n_steps, int32_t sample_every,
-                             double *samples, int n_rooms, int warps, cudaStream_t s);
+                             double *samples, int n_groups, int warps, cudaStream_t s);
 
 template <typename real>
 struct AdjDev;

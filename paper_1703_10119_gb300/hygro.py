@@ -39,7 +39,8 @@ ABI_FUNCTIONS = ("hygro_create", "hygro_set_materials", "hygro_set_bc", "hygro_r
                  "hygro_fluxes", "hygro_get_fields", "hygro_set_fields", "hygro_get_step", "hygro_get_state",
                  "hygro_set_state", "hygro_last_error", "hygro_destroy", "hygro_run_noalloc", "hygro_set_rooms",
                  "hygro_get_rooms", "hygro_loss_grad", "hygro_balance", "hygro_set_option",
-                 "hygro_start_euler", "hygro_set_vapour_fraction", "hygro_autotune", "hygro_set_layer_law")
+                 "hygro_start_euler", "hygro_set_vapour_fraction", "hygro_autotune", "hygro_set_layer_law",
+                 "hygro_set_radiation", "hygro_set_interzone")
 HYGRO_LAW_AFFINE, HYGRO_LAW_TABLE1, HYGRO_LAW_TABLE1_A, HYGRO_LAW_TABLE1_C = 0, 1, 2, 3
 # Exported entry points of the 2D sections (names of include/hygro2d.h).
 ABI_FUNCTIONS_2D = ("hygro2d_create", "hygro2d_set_materials", "hygro2d_set_bc", "hygro2d_run", "hygro2d_sync",
@@ -131,6 +132,8 @@ def lib(build_if_missing: bool = False) -> C.CDLL:
         "hygro_get_rooms": [P, C.c_int32, P, P],
         "hygro_autotune": [P, C.c_int32, P, P],
         "hygro_set_layer_law": [P, P],
+        "hygro_set_radiation": [P, P, P],
+        "hygro_set_interzone": [P, C.c_int32, P, P],
         "hygro_loss_grad": [P, C.c_int64, C.c_int32, P, C.c_double, C.c_double, C.c_int32, C.POINTER(C.c_double), P],
         "hygro2d_create": [C.POINTER(hygro2d_desc), C.POINTER(P)],
         "hygro2d_set_materials": [P, C.c_int32, P, P, P, P],
@@ -297,6 +300,20 @@ def hygro_peak_probe(kind: int, device: int = -1, stream=None, target_ms: float 
     return ops.value, ms.value
 
 
+def hygro_set_radiation(ctx, emissivity, view):
+    e = np.ascontiguousarray(emissivity, np.float64)
+    v = np.ascontiguousarray(view, np.float64)
+    _check(lib().hygro_set_radiation(ctx, _ptr(e), _ptr(v)), ctx)
+
+
+def hygro_set_interzone(ctx, links):
+    """links: [(room_i, room_j, flow kg/s), ...]."""
+    z = np.ascontiguousarray([[a, b] for a, b, _ in links], np.int32).reshape(-1, 2)
+    f = np.ascontiguousarray([g for _, _, g in links], np.float64)
+    _check(lib().hygro_set_interzone(ctx, len(links), _ptr(z) if len(links) else None,
+                                     _ptr(f) if len(links) else None), ctx)
+
+
 def hygro_set_layer_law(ctx, law):
     law = np.ascontiguousarray(law, np.int32)
     _check(lib().hygro_set_layer_law(ctx, _ptr(law)), ctx)
@@ -454,6 +471,10 @@ class Hygro:
             arr[r] = hygro_room(*[float(x) for x in par[r, :15]], float(rm["Ta0"][r]), float(rm["Pa0"][r]),
                                 *[float(x) for x in par[r, 16:21]])
         hygro_set_rooms(self.ctx, len(par), arr, np.ascontiguousarray(rm["wall_area"], np.float64))
+        if rm.get("emissivity") is not None:
+            hygro_set_radiation(self.ctx, np.asarray(rm["emissivity"], np.float64).reshape(-1, 2), rm["view"])
+        if rm.get("links"):
+            hygro_set_interzone(self.ctx, rm["links"])
         if par.shape[1] > 15 and np.any(par[:, 15] == 1.0):
             # the room rows' scheme slot (the oracle's layout): explicit Euler rooms
             hygro_set_option(self.ctx, HYGRO_OPT_ROOM_SCHEME, HYGRO_ROOM_EULER)

@@ -131,3 +131,77 @@ def test_rooms_explicit_euler_option(H, oracle_mod, precision, tol):
     o2 = oracle_mod.Oracle(wl)
     o2.run(300, 10)
     assert relinf(o2.room[:, 1], o.room[:, 1]) > 1e-8
+
+
+def linked_radiating_building(seed=6, n_steps=600):
+    """Eight rooms of 2..7 walls: rooms 0-1 and 2-3-4 linked by interzone airflow (a pair and a chain of
+    three in one block each), rooms 5-7 alone; room faces of rooms 0, 2, 3 and 6 exchange long-wave
+    radiation (view factors 0.2-0.3, emissivities 0.5-0.9, one face black-less at 0)."""
+    counts = [4, 7, 3, 4, 5, 2, 6, 3]
+    base = wk.building(seed=seed, n_rooms=8, walls_per_room=8, n_steps=n_steps, n_min=3, n_max=260)
+    keep = []
+    for r, c in enumerate(counts):
+        keep += list(range(r * 8, r * 8 + c))
+    wl = base.subset(keep)
+    wl.bc_kind = base.bc_kind[keep].copy()
+    wl.bc_room = base.bc_room[keep].copy()
+    rooms = dict(base.rooms)
+    rooms["wall_area"] = base.rooms["wall_area"][keep]
+    rng = np.random.default_rng(seed)
+    emis = np.zeros((wl.n_walls, 2))
+    view = np.zeros(8)
+    for r in (0, 2, 3, 6):
+        view[r] = rng.uniform(0.2, 0.3)
+        for w in np.where(wl.bc_room[:, 1] == r)[0]:
+            emis[w, 1] = rng.uniform(0.5, 0.9)
+    emis[np.where(wl.bc_room[:, 1] == 2)[0][0], 1] = 0.0
+    rooms.update(emissivity=emis, view=view, links=[(0, 1, 0.012), (2, 3, 0.02), (3, 4, 0.008)])
+    wl.rooms = rooms
+    return wl
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 1e-4)])
+def test_rooms_linked_and_radiating(H, oracle_mod, precision, tol):
+    """Interzone airflow (Sec. 5.1) between rooms sharing a block and long-wave radiation among room
+    surfaces (Sec. 2 q_rw) against the oracle: wall fields, surface samples, room air, fluxes."""
+    wl = linked_radiating_building()
+    g = H.Hygro(wl, precision=precision)
+    s1 = g.run_sampled(301, 7)
+    s2 = g.run_sampled(299, 13)
+    T, P = g.fields(0)
+    Ta, Pa = g.rooms(0)
+    flux, cum = g.fluxes()
+    g.close()
+    o = oracle_mod.Oracle(wl)
+    r1 = o.run(301, 7)
+    r2 = o.run(299, 13)
+    errs = dict(T=relinf(T, o.T_cur), P=relinf(P, o.P_cur), s1=relinf(s1, r1["samples"]), s2=relinf(s2, r2["samples"]),
+                Ta=relinf(Ta, o.room[:, 1]), Pa=relinf(Pa, o.room[:, 3]), flux=relinf(flux, r2["flux"]),
+                cum=relinf(cum, o.cumul))
+    print(f"measured-error linked-radiating {precision} " + " ".join(f"{k}={v:.3e}" for k, v in errs.items()))
+    for k in ("T", "P", "s1", "s2", "Ta", "Pa"):
+        assert errs[k] <= tol, (k, errs)
+    ftol = 1e-9 if precision == "fp64" else 5e-4
+    assert errs["flux"] <= ftol and errs["cum"] <= ftol, errs
+    # the links matter: without them the rooms' air differs well beyond the tolerance
+    wl2 = linked_radiating_building()
+    wl2.rooms = dict(wl2.rooms, links=[])
+    o2 = oracle_mod.Oracle(wl2)
+    o2.run(600)
+    assert relinf(o2.room[:, 1], o.room[:, 1]) > 100 * tol
+
+
+def test_room_group_limits(H):
+    wl = linked_radiating_building(n_steps=10)
+    with H.Hygro(wl, precision="fp32") as g:
+        # room 1 (7 walls) with rooms 2-4 (12 walls) in one group: too many walls for a block
+        H.hygro_set_interzone(g.ctx, [(0, 1, 0.01), (1, 2, 0.01), (2, 3, 0.01), (3, 4, 0.01)])
+        with pytest.raises(H.HygroError) as e:
+            g.run(2)
+        assert e.value.status == H.HYGRO_E_STATE
+        with pytest.raises(H.HygroError) as e:
+            H.hygro_set_interzone(g.ctx, [(0, 0, 0.01)])
+        assert e.value.status == H.HYGRO_E_INVALID
+        with pytest.raises(H.HygroError) as e:
+            H.hygro_set_radiation(g.ctx, np.full((wl.n_walls, 2), 1.5), np.zeros(8))
+        assert e.value.status == H.HYGRO_E_INVALID
