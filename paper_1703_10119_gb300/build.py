@@ -19,7 +19,7 @@ LIB = os.path.join(BUILD, "libhygro.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 SOURCES = ["hygro_api.cu", "df1d_plain.cu", "df1d_persistent_f32.cu", "df1d_persistent_f64.cu", "df1d_rooms_f32.cu",
-           "df1d_rooms_f64.cu", "hygro2d_api.cu", "adjoint.cu",
+           "df1d_rooms_f64.cu", "df1d_rooms_wide_f32.cu", "df1d_rooms_wide_f64.cu", "hygro2d_api.cu", "adjoint.cu",
            "adjoint_reg_f32.cu", "adjoint_reg_f64.cu", "peak_probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

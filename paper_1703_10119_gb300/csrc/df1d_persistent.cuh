@@ -360,14 +360,17 @@ static __device__ void room_update(RoomShared &rs, const RoomConst &k, const Roo
         AhTTs = fma(k.AhT[w], rs.surfT[b][w], AhTTs);
         AhMPs = fma(k.AhM[w], rs.surfP[b][w], AhMPs);
     }
-    double GT = 0.0, Gw = 0.0;
-    for (int l = 0; l < ri.n_links; ++l) {
-        const RoomShared &o = all_rs[ri.link_slot[l]];
-        GT = fma(ri.link_g[l], o.airT[b], GT);
-        Gw = fma(ri.link_gw[l], o.airP[b], Gw);
+    double srcP = rs.srcP[i], srcT = rs.srcT[i];
+    if (ri.n_links > 0) {   // a room without links keeps the serial chain of its update short
+        double GT = 0.0, Gw = 0.0;
+        for (int l = 0; l < ri.n_links; ++l) {
+            const RoomShared &o = all_rs[ri.link_slot[l]];
+            GT = fma(ri.link_g[l], o.airT[b], GT);
+            Gw = fma(ri.link_gw[l], o.airP[b], Gw);
+        }
+        srcP += Gw;
+        srcT += q[RP_CPA] * GT + Lv * Gw;
     }
-    const double srcP = rs.srcP[i] + Gw;
-    const double srcT = rs.srcT[i] + q[RP_CPA] * GT + Lv * Gw;
     if (q[RP_SCHEME] == (double)HYGRO_ROOM_EULER) {
         // explicit Euler of Sec. 5.2: every term at level n
         const double Pa_n = rs.Pa_c + dt * k.Pref / k.rhoV * (srcP + AhMPs - k.k_p * rs.Pa_c);
@@ -549,11 +552,11 @@ __device__ __forceinline__ void lane_setup(const DevCtx<real> &d, const WallInfo
 
 // Room walls (ROOM): rs is the room's shared state, room_face the wall's face on the room, room_slot its
 // position among the room's walls, ri the room (long-wave exchange: its view factor and the face's
-// emissivity). A radiating room face (general variants only) receives q_rw = sum over the room's other
+// emissivity). A radiating room face (RAD, general variants only) receives q_rw = sum over the room's other
 // faces of h' (T' - Ts), h' = s eps sigma (T'^2 + Ts^2)(T' + Ts), with h' and T' of level n and Ts averaged
 // over levels n+1 and n-1 like the convective exchange: the face's thermal conductance for the step is
 // hT + hR (hR = sum h') and its air value (hT Ta + qR) / (hT + hR) (qR = sum h' T').
-template <typename real, int K, bool IFACE, bool SIMPLE, bool ROOM = false>
+template <typename real, int K, bool IFACE, bool SIMPLE, bool ROOM = false, bool RAD = false>
 __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi, int w, const real *tab, int64_t n0,
                                       int32_t n_steps, int32_t sample_every, real *samples, real *sft, real *srt,
                                       RoomShared *rs = nullptr, int room_face = -1, int room_slot = 0,
@@ -625,8 +628,8 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
     const int room_lane = room_face == 0 ? 0 : Wl - 1;
     const double Tref_d = (double)Tref, Pref_d = (double)Pref;
     // long-wave exchange of the room face (warp-uniform): s eps sigma of this face
-    const double rad_c = (ROOM && !SIMPLE && ri != nullptr) ? ri->view * ri->emis[room_slot] * 5.670374419e-8 : 0.0;
-    const bool radiating = rad_c > 0.0;
+    static_assert(!RAD || (ROOM && !SIMPLE), "radiating faces take the general room variants");
+    const double rad_c = RAD ? ri->view * ri->emis[room_slot] * 5.670374419e-8 : 0.0;
     const real hT_room = room_face == 0 ? L.hT0 : L.hT1;   // the room face's convective conductance (room lane)
     // sums over the current batch of the lane's time-averaged surface values, and (room walls) of its air
     // and of its radiative exchange
@@ -655,7 +658,7 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
                 fT = (real)(rs->airT[n_cur & 1] - Tref_d);
                 fP = (real)(rs->airP[n_cur & 1] - Pref_d);
                 fT_step = fT;
-                if (radiating) {
+                if (RAD) {
                     // radiative conductances to the room's other faces at level n, in FP64
                     const int b = (int)(n_cur & 1);
                     const double Ts = rs->surfT[b][room_slot];
@@ -680,15 +683,15 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
             last_fP = fP;
         }
         real sT, sP;
-        if constexpr (ROOM && !SIMPLE) {
+        if constexpr (RAD) {
             const real hT0v = room_face == 0 ? hT_step : L.hT0, hT1v = room_face == 1 ? hT_step : L.hT1;
             df_step<real, K, IFACE, SIMPLE, true>(Tp_, Tc_, Pp_, Pc_, L, tab, fT_step, fP, Lv, sT, sP, sft, srt, hT0v,
                                                   hT1v);
         } else {
             df_step<real, K, IFACE, SIMPLE>(Tp_, Tc_, Pp_, Pc_, L, tab, fT, fP, Lv, sT, sP, sft, srt);
         }
-        if (ROOM) {
-            // radiation received over the step: sum h' (T' - Tbar) = qRd - hR Tbar (zero where none)
+        if (RAD) {
+            // radiation received over the step: sum h' (T' - Tbar) = qRd - hR Tbar
             last_rad = fma(-hR, sT, qRd);
             acc_rad += last_rad;
         }
@@ -719,7 +722,8 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
         bP = real(0);
         if (f_ambient) ambient_at(ff, d.noise, n0 + s + (lane % kForcingBatch), d.t0, d.dt, bT, bP);
         acc_sT = acc_sP = real(0);
-        if (ROOM) acc_fT = acc_fP = acc_rad = real(0);
+        if (ROOM) acc_fT = acc_fP = real(0);
+        if (RAD) acc_rad = real(0);
         int i = 0;
         for (; i + 1 < cnt; i += 2) {
             one_step(Ta, Tb, Pa, Pb, bT, bP, src_base + i);
@@ -752,7 +756,7 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
             // g = hM (Pv_inf - Pvbar) + g_inf
             const real rc = (real)cnt;
             const real hm = L.hMs * (sfP - acc_sP);
-            const real acc_q = fma(L.hTs, sfT - acc_sT, fma(Lv, hm, rc * L.qs)) + (ROOM ? acc_rad : real(0));
+            const real acc_q = fma(L.hTs, sfT - acc_sT, fma(Lv, hm, rc * L.qs)) + (RAD ? acc_rad : real(0));
             const real acc_g = fma(rc, L.gs, hm);
             const real xq = acc_q * dt_r, xg = acc_g * dt_r;
             real t = kq + xq;
@@ -794,7 +798,7 @@ __device__ __noinline__ void run_wall(const DevCtx<real> &d, const WallInfo &wi,
         last_fP = __shfl_sync(FULL, bP, last_src);
     }
     const real last_hm = L.hMs * (last_fP - last_sP);
-    const real last_q = fma(L.hTs, last_fT - last_sT, fma(Lv, last_hm, L.qs)) + (ROOM ? last_rad : real(0));
+    const real last_q = fma(L.hTs, last_fT - last_sT, fma(Lv, last_hm, L.qs)) + (RAD ? last_rad : real(0));
     const real last_g = last_hm + L.gs;
     if (my_face >= 0 && n_steps > 0) {
         d.cumul[(size_t)w * 4 + my_face * 2 + 0] = cum_q;

@@ -86,8 +86,12 @@ __global__ void __launch_bounds__(NW * 32, 1)
         switch (wi.K * 2 + (simple ? 1 : 0)) {
 #define HYGRO_CASE(KK)                                                                                             \
     case 2 * KK:                                                                                                   \
-        run_wall<real, KK, true, false, true>(d, wi, w, tab, n0, n_steps, sample_every, samples, nullptr, nullptr,  \
-                                              &rs[zone], face, slot, &ri);                                         \
+        if (rad)                                                                                                   \
+            run_wall<real, KK, true, false, true, true>(d, wi, w, tab, n0, n_steps, sample_every, samples, nullptr, \
+                                                        nullptr, &rs[zone], face, slot, &ri);                      \
+        else                                                                                                       \
+            run_wall<real, KK, true, false, true>(d, wi, w, tab, n0, n_steps, sample_every, samples, nullptr,       \
+                                                  nullptr, &rs[zone], face, slot, &ri);                            \
         ran = true;                                                                                                \
         break;                                                                                                     \
     case 2 * KK + 1:                                                                                               \

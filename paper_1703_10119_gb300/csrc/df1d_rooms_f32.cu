@@ -1,16 +1,18 @@
-// float instantiation of the room kernel.
+// float instantiation of the room kernel, blocks of up to HYGRO_MAX_ROOM_WALLS + 1 warps (one room); the
+// blocks of linked room groups (up to kRoomBlockWarps warps) are in df1d_rooms_wide_f32.cu, compiled in
+// parallel.
 #include "df1d_rooms.cuh"
 
 namespace hygro {
 
+cudaError_t launch_rooms_wide_f32(const DevCtx<float> &d, int64_t n0, int32_t n_steps, int32_t sample_every,
+                                 float *samples, int n_groups, int warps, cudaStream_t s);
+
 cudaError_t launch_rooms_f32(const DevCtx<float> &d, int64_t n0, int32_t n_steps, int32_t sample_every,
                              float *samples, int n_groups, int warps, cudaStream_t s)
 {
-    if (warps <= HYGRO_MAX_ROOM_WALLS + 1)
-        df1d_room_kernel<float, HYGRO_MAX_ROOM_WALLS + 1>
-            <<<n_groups, warps * 32, 0, s>>>(d, n0, n_steps, sample_every, samples);
-    else
-        df1d_room_kernel<float, kRoomBlockWarps><<<n_groups, warps * 32, 0, s>>>(d, n0, n_steps, sample_every, samples);
+    if (warps > HYGRO_MAX_ROOM_WALLS + 1) return launch_rooms_wide_f32(d, n0, n_steps, sample_every, samples, n_groups, warps, s);
+    df1d_room_kernel<float, HYGRO_MAX_ROOM_WALLS + 1><<<n_groups, warps * 32, 0, s>>>(d, n0, n_steps, sample_every, samples);
     return cudaGetLastError();
 }
 

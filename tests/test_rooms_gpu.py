@@ -136,7 +136,8 @@ def test_rooms_explicit_euler_option(H, oracle_mod, precision, tol):
 def linked_radiating_building(seed=6, n_steps=600):
     """Eight rooms of 2..7 walls: rooms 0-1 and 2-3-4 linked by interzone airflow (a pair and a chain of
     three in one block each), rooms 5-7 alone; room faces of rooms 0, 2, 3 and 6 exchange long-wave
-    radiation (view factors 0.2-0.3, emissivities 0.5-0.9, one face black-less at 0)."""
+    radiation (view factors 0.2-0.3, emissivities 0.5-0.9, one face of room 2 at emissivity 0, which does
+    not radiate)."""
     counts = [4, 7, 3, 4, 5, 2, 6, 3]
     base = wk.building(seed=seed, n_rooms=8, walls_per_room=8, n_steps=n_steps, n_min=3, n_max=260)
     keep = []
@@ -183,12 +184,13 @@ def test_rooms_linked_and_radiating(H, oracle_mod, precision, tol):
         assert errs[k] <= tol, (k, errs)
     ftol = 1e-9 if precision == "fp64" else 5e-4
     assert errs["flux"] <= ftol and errs["cum"] <= ftol, errs
-    # the links matter: without them the rooms' air differs well beyond the tolerance
+    # the links matter: without them the linked rooms' air differs by more than 0.1 K (measured 0.35 K),
+    # some 500 times the FP32 error of the air temperature (6e-7 relative, 2e-4 K)
     wl2 = linked_radiating_building()
     wl2.rooms = dict(wl2.rooms, links=[])
     o2 = oracle_mod.Oracle(wl2)
     o2.run(600)
-    assert relinf(o2.room[:, 1], o.room[:, 1]) > 100 * tol
+    assert np.max(np.abs(o2.room[:, 1] - o.room[:, 1])) > 0.1
 
 
 def test_room_group_limits(H):
