@@ -135,7 +135,7 @@ typedef struct {
     double hT, hM;             /* W/m^2/K, s/m */
     double q_inf, g_inf;       /* extra heat (W/m^2) and moisture (kg/m^2/s) fluxes into the wall */
     double T_mean, T_amp, P_mean, P_amp, period, phase_T, phase_P;
-    const float *noise;        /* host memory, [noise_len][2], or NULL (copied) */
+    const float *noise;        /* host (pageable or page-locked) or device memory, [noise_len][2], or NULL (copied) */
     int32_t noise_len;
     double noise_dt;
     double period_P;           /* period of the Pv sinusoid, s (<= 0: period) */
@@ -192,7 +192,10 @@ HYGRO_API hygro_status hygro_set_materials(hygro_ctx *ctx, const int32_t *n_laye
  * a refused call leaves the face's previous description and tables in place. Setting one face does not
  * copy the other face's tables again, nor does hygro_set_materials. The copy uses up to 8 host threads
  * and two host staging chunks of up to 64 MB each (pinned when the allocation succeeds), which the
- * context keeps for its next uploads; the call returns when the tables are on the device. */
+ * context keeps for its next uploads; the call returns when the tables are on the device. When every run
+ * of tables adjacent in memory starts in page-locked host memory (cudaHostAlloc, cudaHostRegister) or in
+ * device memory, the tables skip the host threads: one DMA copy per run lands them in the device staging
+ * area, and a device kernel checks their values before they replace the face's tables. */
 HYGRO_API hygro_status hygro_set_bc(hygro_ctx *ctx, int32_t face, const hygro_bc *bc);
 
 /* Rooms of the whole-building model: rooms[r] for r in 0..n_rooms-1, wall_area[w] (m^2) the area

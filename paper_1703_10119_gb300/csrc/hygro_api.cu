@@ -226,6 +226,7 @@ struct hygro_ctx {
     size_t stage_pairs = 0;            // pairs per host chunk
     cudaEvent_t stage_ev[2] = {nullptr, nullptr};
     float2 *d_stage = nullptr;
+    unsigned long long *d_bad = nullptr;   // first non-finite pair of a directly copied noise upload
     size_t stage_cap = 0;              // pairs
     void *d_Tref = nullptr, *d_Pref = nullptr;
     double *d_cumul = nullptr, *d_flast = nullptr;
@@ -306,6 +307,7 @@ void free_all(hygro_ctx *c)
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->d_stage) cudaFree(c->d_stage);
+    if (c->d_bad) cudaFree(c->d_bad);
     for (int i = 0; i < 2; ++i) {
         if (c->h_stage[i]) {
             if (c->stage_pinned)
@@ -401,11 +403,34 @@ hygro_status upload_faces(hygro_ctx *c)
 
 constexpr size_t kStagePairs = size_t(1) << 23;   // (T, Pv) pairs per host chunk of the noise upload (64 MB)
 
+// First (T, Pv) pair of tab[0 .. n) with a non-finite value into *bad (which starts at ~0).
+__global__ void first_nonfinite_kernel(const float2 *tab, int64_t n, unsigned long long *bad)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float2 v = tab[i];
+        if (!isfinite(v.x) || !isfinite(v.y)) atomicMin(bad, (unsigned long long)i);
+    }
+}
+
+// True when p lies in page-locked host memory, device memory or managed memory: memory the DMA engines
+// read directly (pageable memory goes through the driver's own staging).
+bool dma_direct(const void *p)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
 // Uploads the noise tables of one face (hygro_bc array, validated except for the table values) and
 // records each wall's offset and length in v. Host threads gather the per-wall tables into two host
 // chunks (pinned when possible), checking each value as they copy, while the previous chunk's copy to
 // the device runs; the chunks land in a device staging area, which reaches the face's region of the
 // context's noise array only when every value was finite, so a refused call leaves the face as it was.
+// Tables in page-locked (or device) memory skip the host gather: each run of tables adjacent in memory
+// goes to the staging area in one copy, and a device kernel looks for non-finite values there.
 // The array grows when the region is too small (the other face's tables move with a device copy).
 hygro_status upload_noise(hygro_ctx *c, int face, const hygro_bc *bc, std::vector<RawBc> &v)
 {
@@ -433,7 +458,13 @@ hygro_status upload_noise(hygro_ctx *c, int face, const hygro_bc *bc, std::vecto
             CUDA_TRY(c, dalloc(&c->d_stage, (size_t)total));
             c->stage_cap = (size_t)total;
         }
-        const size_t want = std::min(kStagePairs, (size_t)total);
+        // runs of tables adjacent in memory; the direct path when each run starts in DMA-readable memory
+        std::vector<size_t> run0;
+        for (size_t k = 0; k < src.size(); ++k)
+            if (k == 0 || src[k] != src[k - 1] + 2 * len[k - 1]) run0.push_back(k);
+        bool direct = true;
+        for (size_t r = 0; r < run0.size() && direct; ++r) direct = dma_direct(src[run0[r]]);
+        const size_t want = direct ? 0 : std::min(kStagePairs, (size_t)total);
         if (want > c->stage_pairs) {   // host chunks sized to the need, up to kStagePairs
             for (int i = 0; i < 2; ++i) {
                 if (c->h_stage[i]) {
@@ -462,8 +493,24 @@ hygro_status upload_noise(hygro_ctx *c, int face, const hygro_bc *bc, std::vecto
                 CUDA_TRY(c, cudaEventCreateWithFlags(&c->stage_ev[i], cudaEventDisableTiming));
         const int threads = (int)std::min(8u, std::max(1u, std::thread::hardware_concurrency()));
         int64_t bad = -1;
+        if (direct) {
+            if (c->d_bad == nullptr) CUDA_TRY(c, dalloc(&c->d_bad, 1));
+            CUDA_TRY(c, cudaMemsetAsync(c->d_bad, 0xff, sizeof(unsigned long long), c->stream));
+            for (size_t r = 0; r < run0.size(); ++r) {
+                const size_t k0 = run0[r], k1 = r + 1 < run0.size() ? run0[r + 1] : src.size();
+                const int64_t pairs = start[k1 - 1] + len[k1 - 1] - start[k0];
+                CUDA_TRY(c, cudaMemcpyAsync(c->d_stage + start[k0], src[k0], (size_t)pairs * sizeof(float2),
+                                            cudaMemcpyDefault, c->stream));
+            }
+            first_nonfinite_kernel<<<4 * 152, 256, 0, c->stream>>>(c->d_stage, total, c->d_bad);
+            CUDA_TRY(c, cudaGetLastError());
+            unsigned long long first = 0;
+            CUDA_TRY(c, cudaMemcpyAsync(&first, c->d_bad, sizeof first, cudaMemcpyDeviceToHost, c->stream));
+            CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+            if (first != ~0ull) bad = (int64_t)first;
+        }
         int chunk = 0;
-        for (int64_t p0 = 0; p0 < total; p0 += (int64_t)c->stage_pairs, ++chunk) {
+        for (int64_t p0 = direct ? total : 0; p0 < total; p0 += (int64_t)c->stage_pairs, ++chunk) {
             const int64_t p1 = std::min(total, p0 + (int64_t)c->stage_pairs);
             const int slot = chunk & 1;
             if (chunk >= 2) CUDA_TRY(c, cudaEventSynchronize(c->stage_ev[slot]));

@@ -171,3 +171,57 @@ def test_nonfinite_value_in_a_later_chunk_is_refused(H):
         H.hygro_set_bc(g.ctx, 0, arr)
     assert "wall 62 face 0: non-finite noise" in str(e.value)
     g.close()
+
+
+def _pinned(a):
+    import torch
+
+    t = torch.empty(a.shape, dtype=torch.float32, pin_memory=True)
+    t.numpy()[...] = a
+    return t
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_pinned_tables_take_the_direct_copy(H, precision):
+    """Tables in page-locked host memory go to the device by DMA, one copy per run of adjacent tables,
+    and are checked on the device: one pinned array for all walls, and one pinned array per wall (runs of
+    one table) give the results of the pageable upload, bit for bit."""
+    wl = two_face_noise_batch()
+    ref = H.Hygro(wl, precision=precision)
+    ref.run(N_STEPS)
+    want = _state(ref)
+    ref.close()
+    keep = [_pinned(wl.noise[0]), _pinned(wl.noise[1])]
+    g = H.Hygro(wl, precision=precision)
+    for f in range(2):
+        H.hygro_set_bc(g.ctx, f, H._bc_array(wl.n_walls, wl.bc_kind[:, f], wl.bc_par[:, f], keep[f].numpy()))
+    g.run(N_STEPS)
+    assert np.array_equal(_state(g), want)
+    g.close()
+    per_wall = [_pinned(np.ascontiguousarray(wl.noise[1][w])) for w in reversed(range(wl.n_walls))][::-1]
+    g = H.Hygro(wl, precision=precision)
+    H.hygro_set_bc(g.ctx, 1, _bc_separate(H, wl, 1, [t.numpy() for t in per_wall]))
+    g.run(N_STEPS)
+    assert np.array_equal(_state(g), want)
+    g.close()
+
+
+@pytest.mark.parametrize("bad", [np.nan, np.inf])
+def test_pinned_nonfinite_table_is_refused_and_leaves_the_face(H, bad):
+    wl = two_face_noise_batch()
+    ref = H.Hygro(wl, precision="fp64")
+    ref.run(N_STEPS)
+    want = _state(ref)
+    ref.close()
+    z = np.array(wl.noise[0])
+    z[41, 7, 0] = bad
+    z[50, 3, 1] = bad   # a later one: the first is reported
+    t = _pinned(z)
+    g = H.Hygro(wl, precision="fp64")
+    with pytest.raises(H.HygroError) as e:
+        H.hygro_set_bc(g.ctx, 0, H._bc_array(wl.n_walls, wl.bc_kind[:, 0], wl.bc_par[:, 0], t.numpy()))
+    assert e.value.status == H.HYGRO_E_INVALID
+    assert "wall 41 face 0: non-finite noise" in str(e.value)
+    g.run(N_STEPS)
+    assert np.array_equal(_state(g), want)
+    g.close()
