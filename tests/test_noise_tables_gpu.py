@@ -225,3 +225,28 @@ def test_pinned_nonfinite_table_is_refused_and_leaves_the_face(H, bad):
     g.run(N_STEPS)
     assert np.array_equal(_state(g), want)
     g.close()
+
+
+def test_device_resident_tables(H):
+    """Tables already in device memory (a torch CUDA tensor) take the direct path too: a device-to-device
+    copy into the staging area. The results equal the host upload's, bit for bit."""
+    import torch
+
+    wl = two_face_noise_batch()
+    ref = H.Hygro(wl, precision="fp32")
+    ref.run(N_STEPS)
+    want = _state(ref)
+    ref.close()
+    dev = [torch.from_numpy(np.ascontiguousarray(z)).cuda() for z in wl.noise]
+    torch.cuda.synchronize()
+    g = H.Hygro(wl, precision="fp32")
+    for f in range(2):
+        arr = H._bc_array(wl.n_walls, wl.bc_kind[:, f], wl.bc_par[:, f], None)
+        L = dev[f].shape[1]
+        for w in range(wl.n_walls):
+            arr[w].noise = dev[f].data_ptr() + w * L * 2 * 4
+            arr[w].noise_len = L
+        H.hygro_set_bc(g.ctx, f, arr)
+    g.run(N_STEPS)
+    assert np.array_equal(_state(g), want)
+    g.close()
