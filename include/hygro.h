@@ -210,16 +210,20 @@ HYGRO_API hygro_status hygro_set_rooms(hygro_ctx *ctx, int32_t n_rooms, const hy
  * [0, 1]) is the view factor s of room r. Each term is taken as h' (T' - Ts) with the conductance
  * h' = s eps sigma (T'^2 + Ts^2)(T' + Ts) (an exact factorisation): h' and the other faces' T' of level n,
  * the face's own Ts averaged over levels n+1 and n-1 as for the convective exchange (the level-n form of
- * the face's own term is unstable in DF). Radiating faces run the general code variant. hygro_set_rooms
- * clears the radiation; HYGRO_E_STATE before it. */
+ * the face's own term is unstable in DF). Radiating faces run the general code variant. Both arrays are
+ * copied. HYGRO_E_INVALID for a NULL array or a value outside [0, 1] (NaN included); HYGRO_E_STATE before
+ * hygro_set_rooms, which clears the radiation. */
 HYGRO_API hygro_status hygro_set_radiation(hygro_ctx *ctx, const double *emissivity, const double *view);
 
 /* Interzone airflow (paper Sec. 5.1: Q_inz = g (cpa (T_j - T_i)) + Lv g (w_j - w_i), G_inz = g (w_j - w_i) in
  * both rooms of a link; the paper writes cw for the air's heat capacity, read as the room's cp_a).
  * zones[l] (host, [n_links][2]) two different rooms, flow[l] >= 0 kg/s of air exchanged both ways. A room's
  * own values enter as the mean of levels n+1 and n-1 (the room node's DF form), the linked room's as level
- * n. Rooms linked together run in one block: a linked group holds at most 4 rooms, 3 links per room and 14
- * walls in all (hygro_run reports HYGRO_E_STATE otherwise). hygro_set_rooms clears the links. */
+ * n. Both arrays are copied; n_links = 0 removes every link. Rooms linked together run in one block: a
+ * linked group holds at most 4 rooms and 3 links per room, and its walls plus one air warp per room fill
+ * at most 16 warps (hygro_run reports HYGRO_E_STATE otherwise). HYGRO_E_INVALID for n_links < 0, a NULL
+ * array with links, a link between a room and itself or to a room that does not exist, or a negative or
+ * non-finite flow; HYGRO_E_STATE before hygro_set_rooms, which clears the links. */
 HYGRO_API hygro_status hygro_set_interzone(hygro_ctx *ctx, int32_t n_links, const int32_t *zones, const double *flow);
 
 /* Set an option (HYGRO_OPT_*) of the context; it applies from the next run. */
