@@ -242,14 +242,19 @@ def reduce_sum(pg, x: float) -> float:
     return float(t.item())
 
 
-def algorithmic_ops_per_step(wl) -> float:
-    """FP32 FMA-pipe operations of one DF step over all walls (see OPS_GENERAL / OPS_SIMPLE_HEAT)."""
+def algorithmic_ops_per_step(wl, reciprocals: bool = False) -> float:
+    """FP32 FMA-pipe operations of one DF step over all walls (see OPS_GENERAL / OPS_SIMPLE_HEAT); with
+    reciprocals, the MUFU reciprocals instead (the Pv denominator, and the T one unless the wall's heat
+    coefficients are constant, when it is set up once)."""
     off = wl.layer_offset()
     ops = 0.0
     for w in range(wl.n_walls):
         lp = wl.layer_par[off[w]:off[w + 1]]
         simple = bool(np.all(lp[:, 5] == 0) and np.all(lp[:, 7] == 0) and np.all(lp[:, 8] == 0))
-        ops += wl.n_nodes[w] * (OPS_SIMPLE_HEAT if simple else OPS_GENERAL)
+        if reciprocals:
+            ops += wl.n_nodes[w] * (1 if simple else 2)
+        else:
+            ops += wl.n_nodes[w] * (OPS_SIMPLE_HEAT if simple else OPS_GENERAL)
     return ops
 
 
@@ -688,8 +693,19 @@ def bench_ours(args):
     achieved = ops_per_step * args.year_steps / (ms / 1e3) / 1e12
     traffic = measured_traffic()
     nominal = sms * FP32_LANES_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    # the second ALU roof: MUFU reciprocals against the measured rcp rate; the roof with the lower
+    # cell-update rate binds
+    rcp_per_step = algorithmic_ops_per_step(wl, reciprocals=True)
+    mufu = None
+    if peaks and peaks.get("rcp_tops"):
+        mufu_achieved = rcp_per_step * args.year_steps / (ms / 1e3) / 1e12
+        mufu = {"achieved": mufu_achieved, "peak": peaks["rcp_tops"], "unit": "T rcp/s",
+                "frac": mufu_achieved / peaks["rcp_tops"],
+                "rcp_per_cell_update": rcp_per_step / wl.total_nodes}
+    binding = "fma" if mufu is None or achieved / peak >= mufu["frac"] else "mufu"
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Top/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": peak_source, "frac_of_nominal": achieved / nominal,
+                "mufu": mufu, "binding_alu_roof": binding,
                 "target_frac": 0.6,
                 "note": (f"FP32 FMA roof (measured FMA microbenchmark; nominal {sms} SMs x {FP32_LANES_PER_SM} "
                          f"lanes x {SM_MAX_MHZ:.0f} MHz = {nominal:.2f} T); "
