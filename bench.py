@@ -624,7 +624,16 @@ def bench_ours(args):
         o = oracle.Oracle(sub)
         t0 = time.perf_counter()
         ro = o.run(args.year_steps, se)
-        el = time.perf_counter() - t0
+        times = [time.perf_counter() - t0]
+        # the baseline is the best of three runs of the same sample (the first one's output is the parity
+        # reference)
+        for _ in range(2):
+            o2 = oracle.Oracle(sub)
+            t0 = time.perf_counter()
+            o2.run(args.year_steps, se)
+            times.append(time.perf_counter() - t0)
+            del o2
+        el = min(times)
         off = np.concatenate([[0], np.cumsum(wl.n_nodes)])
         Tg = np.concatenate([T[off[w]:off[w + 1]] for w in pick])
         Pg = np.concatenate([P[off[w]:off[w + 1]] for w in pick])
@@ -650,7 +659,8 @@ def bench_ours(args):
         cpu_baseline = {"value": sub.total_nodes * args.year_steps / el, "unit": UNIT,
                         "cores": oracle.default_threads(), "kind": "oracle",
                         "sample": f"{len(pick)} of {wl.n_walls} walls (every {wl.n_walls // len(pick)}th), "
-                                  f"all {args.year_steps} steps, {el:.1f} s"}
+                                  f"all {args.year_steps} steps, best of 3 runs: {el:.1f} s "
+                                  f"({', '.join(f'{x:.1f}' for x in times)} s)"}
 
     for _ in range(max(0, args.warmup - 1)):
         g.set_state(s0)
